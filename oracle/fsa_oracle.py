@@ -1,0 +1,555 @@
+"""FP64 CPU oracle for the iterative full-scale approximation (FSA).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this module:
+only the tests, the smoke check of ``__graft_entry__`` and the CPU-baseline /
+reference legs of ``bench.py`` use it.  It shares no code with the CUDA path.
+
+Source: Gyger, Furrer & Sigrist, "Iterative Methods for Full-Scale Gaussian
+Process Approximations for Large Spatial Data" (arXiv 2405.14492).  Every
+function cites the section / equation / algorithm it follows.
+
+Two modes:
+  * ``DenseFSA``     — the plain definition, n <= a few thousand: the FSA
+                       covariance built densely (§2.1), dense Cholesky
+                       log-likelihood and exact gradient (Eq. NEGLLDNEGLLFSA),
+                       exact FSA predictive mean / variances (§2.3, Eq. MuPredFSA).
+  * ``IterativeFSA`` — the paper's iterative algorithm step by step: the FITC
+                       preconditioner (Eq. eqfitcp) with Woodbury / Sylvester
+                       (appendix "Runtime of the FITC preconditioner"), the
+                       preconditioned CG with Lanczos tridiagonals (Appendix A),
+                       preconditioned SLQ and STE (§3.3), and the simulation
+                       based predictive variances (Algorithm 1).
+
+Readings of points where the paper is silent (the same list is kept with the
+design notes of the repository):
+  * Matérn parameterisation: r(d) = exp(-d/rho) (nu = 1/2) and
+    (1 + sqrt(3) d/rho) exp(-sqrt(3) d/rho) (nu = 3/2), Sigma_ij = s1 * r(d_ij).
+  * Taper: Wendland phi_{3,1}, T(d) = (1-d/g)^4 (1+4d/g) for d < g, else 0.
+  * Support predicate: d^2 = dx*dx + dy*dy evaluated without fused
+    multiply-add, pair in the support iff d^2 < g*g (g*g rounded once).
+  * Residual diagonal s1 - |a_i|^2 is clamped at 0 (it is exactly 0 at
+    inducing points in exact arithmetic).
+  * The sampling factor "Sigma_m^{-1/2}" of the FITC sample is read as L^{-T}
+    with Sigma_m = L L^T, so that the sample has covariance P_hat.
+  * SLQ weight: the paper's n / l (exact weight z^T P^-1 z as an option).
+  * CG stop: absolute ||r||_2 < tol on the unpreconditioned residual, u0 = 0.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+LOG2PI = math.log(2.0 * math.pi)
+GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+STREAM_EPS2 = 4   # probe part on the n data points
+STREAM_EPS1 = 5   # probe part on the m inducing points
+STREAM_PRED = 6   # prediction-variance probes
+
+
+# ----------------------------------------------------------------------------
+# Covariance function and taper (§2, Assumption 3; §2.1 taper)
+# ----------------------------------------------------------------------------
+
+def corr(d, nu: float, rho: float):
+    """Matérn correlation r(d) for nu in {1/2, 3/2} (Assumption 3: r(0) = 1)."""
+    d = np.asarray(d, dtype=np.float64)
+    if nu == 0.5:
+        return np.exp(-d / rho)
+    if nu == 1.5:
+        x = math.sqrt(3.0) * d / rho
+        return (1.0 + x) * np.exp(-x)
+    raise ValueError("nu must be 0.5 or 1.5")
+
+
+def dcorr_drho(d, nu: float, rho: float):
+    """Derivative of r(d) with respect to the range rho."""
+    d = np.asarray(d, dtype=np.float64)
+    if nu == 0.5:
+        return (d / (rho * rho)) * np.exp(-d / rho)
+    if nu == 1.5:
+        x = math.sqrt(3.0) * d / rho
+        return (x * x / rho) * np.exp(-x)
+    raise ValueError("nu must be 0.5 or 1.5")
+
+
+def taper(d, gamma: float):
+    """Wendland taper phi_{3,1}: compactly supported on [0, gamma) (§2.1)."""
+    d = np.asarray(d, dtype=np.float64)
+    t = d / gamma
+    out = (1.0 - t) ** 4 * (1.0 + 4.0 * t)
+    return np.where(d < gamma, out, 0.0)
+
+
+def sqdist(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Pairwise squared distances dx*dx + dy*dy, each operation rounded
+    separately (numpy never fuses multiply and add)."""
+    dx = a[:, None, 0] - b[None, :, 0]
+    dy = a[:, None, 1] - b[None, :, 1]
+    return dx * dx + dy * dy
+
+
+def sqdist_pairs(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Row-wise squared distances between a[k] and b[k]."""
+    dx = a[:, 0] - b[:, 0]
+    dy = a[:, 1] - b[:, 1]
+    return dx * dx + dy * dy
+
+
+def cov_matrix(a: np.ndarray, b: np.ndarray, nu: float, sigma1_sq: float, rho: float):
+    """Sigma_ab = sigma1^2 r(|a_i - b_j|) (§2)."""
+    return sigma1_sq * corr(np.sqrt(sqdist(a, b)), nu, rho)
+
+
+def dcov_matrix(a, b, nu, sigma1_sq, rho, which: int):
+    """Derivative of sigma1^2 r(|a_i - b_j|) with respect to theta[which],
+    theta = (sigma1^2, rho, nugget)."""
+    d = np.sqrt(sqdist(a, b))
+    if which == 0:
+        return corr(d, nu, rho)
+    if which == 1:
+        return sigma1_sq * dcorr_drho(d, nu, rho)
+    return np.zeros_like(d)
+
+
+# ----------------------------------------------------------------------------
+# Taper support: the neighbour structure (§2.1)
+# ----------------------------------------------------------------------------
+
+def neighbour_csr(rows_pts: np.ndarray, cols_pts: np.ndarray, gamma: float,
+                  brute_force_limit: int = 4_000_000):
+    """CSR structure of {(i, j) : |r_i - c_j|^2 < gamma^2} with columns in
+    ascending order (self pairs included when rows_pts is cols_pts).
+
+    Small problems: brute force over all pairs.  Larger ones: candidate pairs
+    from a k-d tree with a slightly larger radius, then the exact predicate.
+    """
+    g2 = gamma * gamma
+    nr, nc = rows_pts.shape[0], cols_pts.shape[0]
+    rows_out, cols_out = [], []
+    if nr * nc <= brute_force_limit:
+        step = max(1, brute_force_limit // max(nc, 1))
+        for s in range(0, nr, step):
+            d2 = sqdist(rows_pts[s:s + step], cols_pts)
+            r, c = np.nonzero(d2 < g2)
+            rows_out.append(r + s)
+            cols_out.append(c)
+    else:
+        from scipy.spatial import cKDTree
+        tree = cKDTree(cols_pts)
+        cand = tree.query_ball_point(rows_pts, r=gamma * (1.0 + 1e-6))
+        lens = np.fromiter((len(x) for x in cand), dtype=np.int64, count=nr)
+        r = np.repeat(np.arange(nr, dtype=np.int64), lens)
+        c = np.fromiter((j for lst in cand for j in lst), dtype=np.int64, count=int(lens.sum()))
+        keep = sqdist_pairs(rows_pts[r], cols_pts[c]) < g2
+        rows_out.append(r[keep])
+        cols_out.append(c[keep])
+    r = np.concatenate(rows_out) if rows_out else np.zeros(0, np.int64)
+    c = np.concatenate(cols_out) if cols_out else np.zeros(0, np.int64)
+    order = np.lexsort((c, r))
+    r, c = r[order], c[order]
+    rowptr = np.zeros(nr + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, c.astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# Counter-based SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)
+# ----------------------------------------------------------------------------
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (mix64 variant with shifts 30, 27, 31)."""
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= np.uint64(0xBF58476D1CE4E5B9)
+        z ^= z >> np.uint64(27)
+        z *= np.uint64(0x94D049BB133111EB)
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def splitmix64(seed: int, stream: int, counters: np.ndarray) -> np.ndarray:
+    """Output number `counter` of a SplitMix64 generator whose state is
+    seeded with key = mix64(seed XOR stream*gamma): mix64(key + (counter+1)*gamma)."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([np.uint64(seed) ^ (np.uint64(stream) * GOLDEN_GAMMA)], dtype=np.uint64))[0]
+        c = counters.astype(np.uint64) + np.uint64(1)
+        state = key + c * GOLDEN_GAMMA
+    return _mix64(state)
+
+
+def rademacher(seed: int, stream: int, rows: np.ndarray, nrows: int, ncols: int) -> np.ndarray:
+    """(len(rows), ncols) matrix of +-1 with entry (r, k) drawn at counter
+    k * nrows + rows[r] (rows are ORIGINAL indices, so the draw does not
+    depend on any internal reordering)."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    cols = np.arange(ncols, dtype=np.uint64)
+    ctr = cols[None, :] * np.uint64(nrows) + rows[:, None]
+    h = splitmix64(seed, stream, ctr.ravel()).reshape(ctr.shape)
+    return 1.0 - 2.0 * (h >> np.uint64(63)).astype(np.float64)
+
+
+def gaussian(seed: int, stream: int, rows: np.ndarray, nrows: int, ncols: int) -> np.ndarray:
+    """Standard normals by Box-Muller from the counter pair (2c, 2c+1),
+    c = k * nrows + row, u = ((h >> 11) + 1) * 2^-53 in (0, 1]."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    cols = np.arange(ncols, dtype=np.uint64)
+    ctr = (cols[None, :] * np.uint64(nrows) + rows[:, None]).ravel()
+    h1 = splitmix64(seed, stream, ctr * np.uint64(2))
+    h2 = splitmix64(seed, stream, ctr * np.uint64(2) + np.uint64(1))
+    u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = ((h2 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    return z.reshape(len(rows), ncols)
+
+
+# ----------------------------------------------------------------------------
+# Dense-exact mode (plain definitions; n up to a few thousand)
+# ----------------------------------------------------------------------------
+
+class DenseFSA:
+    """The FSA covariance built densely from its definition (§2.1):
+    Sigma_l = Sigma_mn^T Sigma_m^-1 Sigma_mn,
+    Sigma_s = (Sigma - Sigma_l) o T(gamma),
+    Sigma_dag = Sigma_l + Sigma_s + nugget I."""
+
+    def __init__(self, locs, inducing, gamma, nu, theta):
+        self.locs = np.asarray(locs, np.float64)
+        self.inducing = np.asarray(inducing, np.float64)
+        self.gamma, self.nu = float(gamma), float(nu)
+        self.theta = tuple(float(t) for t in theta)
+        s1, rho, nug = self.theta
+        n = self.locs.shape[0]
+        d2 = sqdist(self.locs, self.locs)
+        self.support = d2 < gamma * gamma
+        d = np.sqrt(d2)
+        self.T = np.where(self.support, taper(d, gamma), 0.0)
+        self.Sigma = s1 * corr(d, nu, rho)
+        self.K = cov_matrix(self.inducing, self.locs, nu, s1, rho)          # m x n
+        self.Sm = cov_matrix(self.inducing, self.inducing, nu, s1, rho)     # m x m
+        self.Sl = self.K.T @ np.linalg.solve(self.Sm, self.K)
+        self.Sl = 0.5 * (self.Sl + self.Sl.T)
+        resid = self.Sigma - self.Sl
+        # residual diagonal clamped at 0 (a reading; exact 0 at inducing points)
+        np.fill_diagonal(resid, np.maximum(np.diag(resid), 0.0))
+        self.Ss = resid * self.T + nug * np.eye(n)
+        self.Sdag = self.Sl + self.Ss
+        self.D = np.diag(self.Ss).copy()
+        self.Phat = np.diag(self.D) + self.Sl           # Eq. (eqfitcp)
+
+    # -- log-likelihood and exact gradient (Eq. NEGLLDNEGLLFSA) --------------
+    def loglik(self, y):
+        """l(theta) = -[n/2 log 2pi + 1/2 logdet Sigma_dag + 1/2 y^T Sigma_dag^-1 y]."""
+        c, low = sla.cho_factor(self.Sdag, lower=True)
+        logdet = 2.0 * np.sum(np.log(np.diag(c)))
+        u = sla.cho_solve((c, low), y)
+        n = y.shape[0]
+        return -0.5 * (n * LOG2PI + logdet + float(y @ u)), logdet, float(y @ u)
+
+    def dSdag(self, which: int) -> np.ndarray:
+        """dSigma_dag/dtheta (§2.2): dSigma_l + (dSigma - dSigma_l) o T + dnugget I,
+        with dSigma_l = dK^T Sm^-1 K + K^T Sm^-1 dK - K^T Sm^-1 dSm Sm^-1 K."""
+        s1, rho, nug = self.theta
+        n = self.locs.shape[0]
+        if which == 2:
+            return np.eye(n)
+        dK = dcov_matrix(self.inducing, self.locs, self.nu, s1, rho, which)
+        dSm = dcov_matrix(self.inducing, self.inducing, self.nu, s1, rho, which)
+        dSig = dcov_matrix(self.locs, self.locs, self.nu, s1, rho, which)
+        SmK = np.linalg.solve(self.Sm, self.K)
+        dSl = dK.T @ SmK + SmK.T @ dK - SmK.T @ dSm @ SmK
+        return dSl + (dSig - dSl) * self.T
+
+    def grad(self, y):
+        """Exact d l / d theta = -1/2 [tr(Sdag^-1 dSdag) - u^T dSdag u] (Eq. NEGLLDNEGLLFSA)."""
+        Sinv = np.linalg.inv(self.Sdag)
+        u = Sinv @ y
+        g = np.zeros(3)
+        for k in range(3):
+            dS = self.dSdag(k)
+            g[k] = -0.5 * (np.sum(Sinv * dS.T) - u @ dS @ u)
+        return g
+
+    # -- exact FSA predictive distribution (§2.3, Eq. MuPredFSA) -------------
+    def cross(self, pred):
+        """Sigma^dag_{n,np} = Sigma^l_{n,np} + (Sigma_{n,np} - Sigma^l_{n,np}) o T_{n,np}."""
+        s1, rho, nug = self.theta
+        Kp = cov_matrix(self.inducing, pred, self.nu, s1, rho)
+        Snp = cov_matrix(self.locs, pred, self.nu, s1, rho)
+        Sl_np = self.K.T @ np.linalg.solve(self.Sm, Kp)
+        d2 = sqdist(self.locs, pred)
+        Tnp = np.where(d2 < self.gamma * self.gamma, taper(np.sqrt(d2), self.gamma), 0.0)
+        Ss_np = (Snp - Sl_np) * Tnp
+        return Sl_np + Ss_np, Sl_np, Ss_np, Kp
+
+    def predict(self, y, pred):
+        """mu^p = (Sigma^dag_{n,np})^T Sigma_dag^-1 y and
+        var^p = sigma1^2 + nugget - diag((Sigma^dag_{n,np})^T Sigma_dag^-1 Sigma^dag_{n,np})."""
+        s1, rho, nug = self.theta
+        C, _, _, _ = self.cross(pred)
+        c = sla.cho_factor(self.Sdag, lower=True)
+        mu = C.T @ sla.cho_solve(c, y)
+        var = s1 + nug - np.sum(C * sla.cho_solve(c, C), axis=0)
+        return mu, var
+
+
+# ----------------------------------------------------------------------------
+# Iterative mode (the paper's algorithms, step by step)
+# ----------------------------------------------------------------------------
+
+def pcg_lanczos(apply_A, apply_Pinv, B, tol, max_iter, fixed_iters=0):
+    """Preconditioned CG with Lanczos tridiagonals (Appendix A), for every
+    column of B independently (each column stops at its own first iteration
+    with ||r||_2 < tol; fixed_iters > 0 runs exactly that many iterations).
+
+    Returns U (solutions), Z0 = P^-1 B, and per column the diagonal and
+    off-diagonal of T_tilde, the number of iterations and ||r||."""
+    n, c = B.shape
+    U = np.zeros_like(B)
+    R = B.copy()
+    Z = apply_Pinv(R)
+    Z0 = Z.copy()
+    H = Z.copy()
+    rz = np.einsum("ij,ij->j", R, Z)
+    rz0 = rz.copy()
+    alpha_prev = np.ones(c)
+    beta_prev = np.zeros(c)
+    active = np.ones(c, dtype=bool)
+    diag = [[] for _ in range(c)]
+    off = [[] for _ in range(c)]
+    iters = np.zeros(c, dtype=np.int64)
+    rnorm = np.linalg.norm(R, axis=0)
+    n_iter = fixed_iters if fixed_iters > 0 else max_iter
+    for l in range(n_iter):
+        if not active.any():
+            break
+        cols = np.nonzero(active)[0]
+        V = apply_A(H[:, cols])
+        alpha = rz[cols] / np.einsum("ij,ij->j", H[:, cols], V)
+        U[:, cols] += alpha * H[:, cols]
+        R[:, cols] -= alpha * V
+        rn = np.linalg.norm(R[:, cols], axis=0)
+        stop = (rn < tol) if fixed_iters <= 0 else np.zeros(len(cols), dtype=bool)
+        Zc = apply_Pinv(R[:, cols])
+        rz_new = np.einsum("ij,ij->j", R[:, cols], Zc)
+        beta = rz_new / rz[cols]
+        H[:, cols] = Zc + beta * H[:, cols]
+        for t, k in enumerate(cols):
+            diag[k].append(1.0 / alpha[t] + beta_prev[k] / alpha_prev[k])
+            if l > 0:
+                off[k].append(math.sqrt(beta_prev[k]) / alpha_prev[k])
+            iters[k] = l + 1
+            rnorm[k] = rn[t]
+        alpha_prev[cols] = alpha
+        beta_prev[cols] = beta
+        rz[cols] = rz_new
+        active[cols[stop]] = False
+    return dict(U=U, Z0=Z0, diag=diag, off=off, iters=iters, rnorm=rnorm, rz0=rz0,
+                R=R, converged=not active.any() or fixed_iters > 0)
+
+
+def lanczos_quadrature(diag, off) -> float:
+    """e_1^T log(T) e_1 = sum_j q_1j^2 log(lambda_j) for the tridiagonal T
+    (stochastic Lanczos quadrature, §3.1)."""
+    d = np.asarray(diag, np.float64)
+    e = np.asarray(off, np.float64)
+    if d.size == 1:
+        return float(math.log(d[0]))
+    lam, Q = sla.eigh_tridiagonal(d, e)
+    return float(np.sum(Q[0, :] ** 2 * np.log(lam)))
+
+
+class IterativeFSA:
+    """The iterative FSA computations with sparse structures (§3)."""
+
+    def __init__(self, locs, inducing, gamma, nu, theta, csr=None):
+        self.locs = np.asarray(locs, np.float64)
+        self.inducing = np.asarray(inducing, np.float64)
+        self.gamma, self.nu = float(gamma), float(nu)
+        self.theta = tuple(float(t) for t in theta)
+        s1, rho, nug = self.theta
+        self.n, self.m = self.locs.shape[0], self.inducing.shape[0]
+        # low-rank part (§2.1): K = Sigma_mn, Sm = Sigma_m, A = K^T L^-T
+        self.K = cov_matrix(self.inducing, self.locs, nu, s1, rho)
+        self.Sm = cov_matrix(self.inducing, self.inducing, nu, s1, rho)
+        try:
+            self.Lm = np.linalg.cholesky(self.Sm)
+        except np.linalg.LinAlgError as exc:
+            raise ValueError("Sigma_m is not positive definite") from exc
+        self.A = sla.solve_triangular(self.Lm, self.K, lower=True).T      # n x m
+        # tapered residual (§2.1) on the taper support
+        if csr is None:
+            csr = neighbour_csr(self.locs, self.locs, gamma)
+        self.rowptr, self.col = csr
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        cols = self.col.astype(np.int64)
+        self.rows = rows
+        d = np.sqrt(sqdist_pairs(self.locs[rows], self.locs[cols]))
+        self.d = d
+        Tv = taper(d, gamma)
+        lowrank = self._rowdots(self.A, self.A, rows, cols)
+        resid = s1 * corr(d, nu, rho) - lowrank
+        diag_mask = rows == cols
+        resid[diag_mask] = np.maximum(resid[diag_mask], 0.0)
+        vals = resid * Tv
+        vals[diag_mask] += nug
+        self.vals = vals
+        self.Tv = Tv
+        self.Ss = sp.csr_matrix((vals, self.col, self.rowptr), shape=(self.n, self.n))
+        self.D = self.Ss.diagonal().copy()                    # D_s = diag(Sigma_s tilde)
+        # FITC preconditioner (Eq. eqfitcp) via Sylvester / Woodbury with the
+        # paper's core M_P = Sigma_m + Sigma_mn D^-1 Sigma_nm
+        self.Mp = self.Sm + (self.K / self.D) @ self.K.T
+        self.Lp = np.linalg.cholesky(self.Mp)
+        self.logdet_P = (2.0 * np.sum(np.log(np.diag(self.Lp)))
+                         - 2.0 * np.sum(np.log(np.diag(self.Lm)))
+                         + float(np.sum(np.log(self.D))))
+
+    @staticmethod
+    def _rowdots(X, Y, rows, cols, chunk=1 << 18):
+        out = np.empty(rows.shape[0])
+        for s in range(0, rows.shape[0], chunk):
+            out[s:s + chunk] = np.einsum("ij,ij->i", X[rows[s:s + chunk]], Y[cols[s:s + chunk]])
+        return out
+
+    # -- operators -----------------------------------------------------------
+    def apply_Sl(self, V):
+        """Sigma_mn^T Sigma_m^-1 Sigma_mn V (§3.1)."""
+        return self.K.T @ sla.cho_solve((self.Lm, True), self.K @ V)
+
+    def apply(self, V):
+        """Sigma_dag V = Sigma_s~ V + Sigma_mn^T Sigma_m^-1 Sigma_mn V (§3.1)."""
+        return self.Ss @ V + self.apply_Sl(V)
+
+    def apply_Pinv(self, V):
+        """P^-1 V = D^-1 V - D^-1 K^T M_P^-1 K D^-1 V (Woodbury, appendix
+        'Runtime of the FITC preconditioner')."""
+        V = np.asarray(V)
+        DV = V / self.D[:, None] if V.ndim == 2 else V / self.D
+        t = sla.cho_solve((self.Lp, True), self.K @ DV)
+        corr_ = self.K.T @ t
+        return DV - (corr_ / self.D[:, None] if V.ndim == 2 else corr_ / self.D)
+
+    def apply_Dinv(self, V):
+        return V / self.D[:, None] if V.ndim == 2 else V / self.D
+
+    # -- probes (§3.3, appendix 'Runtime of the FITC preconditioner') --------
+    def probes(self, num_probes, seed, kind="rademacher"):
+        """z = Sigma_mn^T L^-T eps1 + D^1/2 eps2 ~ (0, P_hat); eps1 (m x l) on
+        stream 5, eps2 (n x l) on stream 4."""
+        draw = rademacher if kind == "rademacher" else gaussian
+        e1 = draw(seed, STREAM_EPS1, np.arange(self.m), self.m, num_probes)
+        e2 = draw(seed, STREAM_EPS2, np.arange(self.n), self.n, num_probes)
+        return self.K.T @ sla.solve_triangular(self.Lm.T, e1, lower=False) + np.sqrt(self.D)[:, None] * e2
+
+    # -- log-likelihood and STE gradient -------------------------------------
+    def dS_apply(self, which, V):
+        """dSigma_dag/dtheta V (§2.2) with the sparse part evaluated per nonzero."""
+        s1, rho, nug = self.theta
+        if which == 2:
+            return V.copy()
+        dK = dcov_matrix(self.inducing, self.locs, self.nu, s1, rho, which)
+        dSm = dcov_matrix(self.inducing, self.inducing, self.nu, s1, rho, which)
+        cho = (self.Lm, True)
+        C = sla.cho_solve(cho, self.K)                     # Sm^-1 K  (m x n)
+        # low-rank part applied through m-space products
+        KV = self.K @ V
+        dSl_V = dK.T @ sla.cho_solve(cho, KV) + C.T @ (dK @ V) - C.T @ (dSm @ sla.cho_solve(cho, KV))
+        # sparse part: per nonzero (dSigma_ij - dSigma_l,ij) T_ij
+        rows, cols = self.rows, self.col.astype(np.int64)
+        if which == 0:
+            dsig = corr(self.d, self.nu, rho)
+        else:
+            dsig = s1 * dcorr_drho(self.d, self.nu, rho)
+        dl = (self._rowdots(dK.T, C.T, rows, cols) + self._rowdots(C.T, dK.T, rows, cols)
+              - self._rowdots(C.T, (dSm @ C).T, rows, cols))
+        dvals = (dsig - dl) * self.Tv
+        dSs = sp.csr_matrix((dvals, self.col, self.rowptr), shape=(self.n, self.n))
+        return dSs @ V + dSl_V
+
+    def loglik_grad(self, y, num_probes, seed, tol, max_iter=1000, fixed_iters=0,
+                    probe="rademacher", exact_weight=False, want_grad=True, Z=None):
+        """Log-likelihood by preconditioned SLQ (§3.3) and gradient by STE (§3.3).
+        ``Z`` replaces the random probes (used by deterministic checks)."""
+        n = self.n
+        if Z is None:
+            Z = self.probes(num_probes, seed, probe)
+        num_probes = Z.shape[1]
+        B = np.column_stack([y, Z])
+        res = pcg_lanczos(self.apply, self.apply_Pinv, B, tol, max_iter, fixed_iters)
+        quads = np.array([lanczos_quadrature(res["diag"][k], res["off"][k]) for k in range(1, num_probes + 1)])
+        weights = res["rz0"][1:] if exact_weight else np.full(num_probes, float(n))
+        terms = weights * quads
+        logdet = float(np.mean(terms)) + self.logdet_P
+        u = res["U"][:, 0]
+        yu = float(y @ u)
+        ll = -0.5 * (n * LOG2PI + logdet + yu)
+        out = dict(loglik=ll, logdet=logdet, quad=yu, logdet_P=self.logdet_P,
+                   logdet_se=float(np.std(terms, ddof=1) / math.sqrt(num_probes)) if num_probes > 1 else 0.0,
+                   iters=res["iters"], rnorm=res["rnorm"], Z=Z, res=res, quads=quads)
+        if want_grad:
+            U = res["U"][:, 1:]
+            W = res["Z0"][:, 1:]                # P^-1 z
+            g = np.zeros(3)
+            g_terms = np.zeros((3, num_probes))
+            for k in range(3):
+                dW = self.dS_apply(k, np.column_stack([W, u]))
+                per_probe = np.einsum("ij,ij->j", U, dW[:, :num_probes])
+                tr = float(np.mean(per_probe))
+                qf = float(u @ dW[:, num_probes])
+                g[k] = -0.5 * (tr - qf)
+                g_terms[k] = per_probe
+            out["grad"] = g
+            out["grad_terms"] = g_terms
+        return out
+
+    # -- predictive distribution (§2.3 and Algorithm 1) ----------------------
+    def cross_structures(self, pred):
+        """Sigma_{m,np}, and the sparse S = Sigma^s_{n,np} as an (n_p x n) CSR
+        (rows: prediction points) with values
+        (Sigma_{n,np} - Sigma^l_{n,np}) o T_{n,np}."""
+        s1, rho, nug = self.theta
+        Kp = cov_matrix(self.inducing, pred, self.nu, s1, rho)
+        Ap = sla.solve_triangular(self.Lm, Kp, lower=True).T            # n_p x m
+        rowptr, col = neighbour_csr(pred, self.locs, self.gamma)
+        rows = np.repeat(np.arange(pred.shape[0]), np.diff(rowptr))
+        cols = col.astype(np.int64)
+        d = np.sqrt(sqdist_pairs(pred[rows], self.locs[cols]))
+        lowrank = self._rowdots(Ap, self.A, rows, cols)
+        vals = (s1 * corr(d, self.nu, rho) - lowrank) * taper(d, self.gamma)
+        St = sp.csr_matrix((vals, col, rowptr), shape=(pred.shape[0], self.n))
+        return Kp, St, (rowptr, col)
+
+    def predict(self, y, pred, num_samples, seed, tol, max_iter=1000, probe="rademacher",
+                u=None, Zp=None):
+        """Predictive mean (§2.3) and simulation-based variances (Algorithm 1).
+        ``Zp`` replaces the random probes (used by deterministic checks)."""
+        s1, rho, nug = self.theta
+        n_p = pred.shape[0]
+        Kp, St, _ = self.cross_structures(pred)
+        cho_m = (self.Lm, True)
+        if u is None:
+            u = pcg_lanczos(self.apply, self.apply_Pinv, y[:, None], tol, max_iter)["U"][:, 0]
+        mean = Kp.T @ sla.cho_solve(cho_m, self.K @ u) + St @ u
+        # deterministic diagonals D1, D2, D3 with PCG solves (Algorithm 1)
+        W1 = pcg_lanczos(self.apply, self.apply_Pinv, self.K.T.copy(), tol, max_iter)["U"]
+        W2 = pcg_lanczos(lambda V: self.Ss @ V, self.apply_Dinv, self.K.T.copy(), tol, max_iter)["U"]
+        M = self.Sm + self.K @ W2
+        G = sla.cho_solve(cho_m, Kp)                                  # Sm^-1 Sigma_{m,np}
+        D1 = np.einsum("ij,ij->j", G, (self.K @ W1) @ G)
+        D2 = np.einsum("ij,ji->i", St @ W1, G)
+        V = St @ W2
+        D3 = np.einsum("ij,ji->i", V, np.linalg.solve(M, V.T))
+        # stochastic diagonal D_l (lines 4-8 of Algorithm 1)
+        if Zp is None:
+            draw = rademacher if probe == "rademacher" else gaussian
+            Zp = draw(seed, STREAM_PRED, np.arange(n_p), n_p, num_samples)
+        X = pcg_lanczos(lambda V_: self.Ss @ V_, self.apply_Dinv, St.T @ Zp, tol, max_iter)["U"]
+        Dl = np.mean(Zp * (St @ X), axis=1)
+        var = s1 + nug - D1 - 2.0 * D2 + D3 - Dl
+        return dict(mean=mean, var=var, D1=D1, D2=D2, D3=D3, Dl=Dl, u=u, Zp=Zp)
+

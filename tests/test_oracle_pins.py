@@ -1,0 +1,348 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a textbook
+routine, a closed form, an exact identity, a number printed in the paper, or a
+brute force.  A plausible mistake in the oracle (a dropped term, a wrong sign,
+a transposed operand, a shifted Lanczos index) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.optimize as so
+import scipy.stats as st
+
+import fsa_inputs as fi
+from oracle import fsa_oracle as O
+from tests.conftest import golden, read_golden_kv
+
+
+def _problem(n=150, m=20, nu=0.5, theta=(1.3, 0.15, 0.2), gamma=0.12, seed=7):
+    locs = fi.uniform_locations(n, seed)
+    idx = fi.inducing_subset(n, m, seed)
+    return locs, locs[idx].copy(), gamma, nu, theta
+
+
+# --------------------------------------------------------------------------
+# covariance function, taper, random numbers
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    want = [int(l, 16) for l in open(golden("splitmix64_seed0.txt")) if l.startswith("0x")]
+    st_ = np.arange(1, 6, dtype=np.uint64) * O.GOLDEN_GAMMA
+    got = [int(x) for x in O._mix64(st_)]
+    assert got == want
+
+
+def test_rademacher_balance_and_independence():
+    z = O.rademacher(3, O.STREAM_EPS2, np.arange(4000), 4000, 8)
+    assert set(np.unique(z)) == {-1.0, 1.0}
+    assert abs(z.mean()) < 0.03
+    c = np.corrcoef(z.T)
+    assert np.max(np.abs(c - np.eye(8))) < 0.06
+    g = O.gaussian(3, O.STREAM_PRED, np.arange(20000), 20000, 2)
+    assert abs(g.mean()) < 0.03 and abs(g.var() - 1) < 0.04
+    assert st.kstest(g[:, 0], "norm").pvalue > 1e-3
+
+
+def test_matern15_effective_range_factor_matches_paper():
+    """§4: effective range ~ 2.7 * rho for nu = 3/2 (with the sqrt(3) scaling;
+    without it the factor would be 4.74)."""
+    kv = read_golden_kv("paper_constants.txt")
+    x = so.brentq(lambda t: O.corr(t, 1.5, 1.0) - 0.05, 0.1, 20.0)
+    assert round(x, 1) == kv["effective_range_factor_matern15"][0]
+    for eff, rho in zip(kv["effective_ranges"], kv["range_parameters"]):
+        assert abs(eff / kv["effective_range_factor_matern15"][0] - rho) < 6e-5
+        # the printed rho gives correlation close to 0.05 at the effective range
+        assert abs(float(O.corr(eff, 1.5, rho)) - 0.05) < 0.004
+
+
+def test_matern_closed_forms_and_derivative():
+    d = np.linspace(0, 0.6, 31)
+    assert np.allclose(O.corr(d, 0.5, 0.2), np.exp(-d / 0.2))
+    assert O.corr(0.0, 1.5, 0.2) == 1.0
+    for nu in (0.5, 1.5):
+        h = 1e-6
+        fd = (O.corr(d, nu, 0.2 + h) - O.corr(d, nu, 0.2 - h)) / (2 * h)
+        assert np.allclose(O.dcorr_drho(d, nu, 0.2), fd, rtol=1e-6, atol=1e-9)
+
+
+def test_wendland_taper_properties():
+    g = 0.1
+    assert O.taper(0.0, g) == 1.0
+    assert O.taper(g, g) == 0.0 and O.taper(2 * g, g) == 0.0
+    d = np.linspace(0, g, 101)[:-1]
+    assert np.all(np.diff(O.taper(d, g)) <= 0)
+    # positive definite in R^2: the taper matrix of random points is PSD
+    pts = fi.uniform_locations(300, 11)
+    T = O.taper(np.sqrt(O.sqdist(pts, pts)), 0.3)
+    assert np.linalg.eigvalsh(T).min() > -1e-10
+
+
+# --------------------------------------------------------------------------
+# neighbour structure
+# --------------------------------------------------------------------------
+
+def test_neighbour_csr_brute_force_vs_tree_bit_exact():
+    pts = fi.uniform_locations(3000, 5)
+    g = 0.03
+    a = O.neighbour_csr(pts, pts, g, brute_force_limit=10 ** 8)
+    b = O.neighbour_csr(pts, pts, g, brute_force_limit=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    rowptr, col = a
+    rows = np.repeat(np.arange(3000), np.diff(rowptr))
+    # self pair present, columns ascending, support exact, symmetric pattern
+    assert np.all(np.isin(np.arange(3000), col[rows == col]))
+    for i in range(0, 3000, 97):
+        c = col[rowptr[i]:rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+    d2 = O.sqdist_pairs(pts[rows], pts[col])
+    assert np.all(d2 < g * g)
+    S = set(zip(rows.tolist(), col.tolist()))
+    assert all((j, i) in S for (i, j) in S)
+    # nothing missed: count pairs inside the radius by brute force
+    assert len(S) == int(np.sum(O.sqdist(pts, pts) < g * g))
+
+
+def test_neighbour_count_matches_paper_taper_choice():
+    """Appendix 'Choice of FSA parameters': gamma = 0.016 <-> n_gamma = 80 at n = 1e5."""
+    kv = read_golden_kv("paper_constants.txt")
+    n = int(kv["n"][0])
+    pts = fi.uniform_locations(n, 1)
+    rowptr, _ = O.neighbour_csr(pts, pts, kv["taper_range"][0])
+    mean = rowptr[-1] / n
+    assert abs(mean - kv["nnz_per_row"][0]) < 1.0
+    assert abs(fi.expected_neighbours(kv["taper_range"][0], n) - kv["nnz_per_row"][0]) < 0.5
+
+
+# --------------------------------------------------------------------------
+# FSA covariance assembly
+# --------------------------------------------------------------------------
+
+def test_m_equals_n_reduces_to_exact_gp():
+    """Inducing points = all points: Sigma_l = Sigma, residual 0, so the FSA is
+    the exact GP and the log-likelihood is the textbook Gaussian log density."""
+    n = 60
+    locs = fi.uniform_locations(n, 2)
+    theta = (1.1, 0.08, 0.3)
+    y = np.random.default_rng(0).standard_normal(n)
+    F = O.DenseFSA(locs, locs, 0.05, 0.5, theta)
+    Sig = theta[0] * np.exp(-np.sqrt(O.sqdist(locs, locs)) / theta[1]) + theta[2] * np.eye(n)
+    assert np.allclose(F.Sdag, Sig, atol=1e-9)
+    ll, _, _ = F.loglik(y)
+    want = st.multivariate_normal(mean=np.zeros(n), cov=Sig).logpdf(y)
+    assert abs(ll - want) < 1e-7 * abs(want)
+
+
+def test_fsa_spectral_bounds_and_symmetry():
+    locs, ind, g, nu, th = _problem()
+    F = O.DenseFSA(locs, ind, g, nu, th)
+    assert np.allclose(F.Sdag, F.Sdag.T, atol=1e-12)
+    # lambda_min >= nugget for Sigma_s~ and Sigma_dag (proof of Lemma 1)
+    assert np.linalg.eigvalsh(F.Ss).min() >= th[2] - 1e-10
+    assert np.linalg.eigvalsh(F.Sdag).min() >= th[2] - 1e-10
+    # taper support respected
+    assert np.all(F.Ss[~F.support] == 0.0)
+
+
+def test_iterative_structures_match_dense_definition():
+    locs, ind, g, nu, th = _problem(nu=1.5)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    V = np.random.default_rng(1).standard_normal((locs.shape[0], 3))
+    assert np.allclose(It.Ss.toarray(), D.Ss, atol=1e-12)
+    assert np.allclose(It.apply(V), D.Sdag @ V, rtol=1e-11, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# FITC preconditioner: Woodbury, Sylvester, condition bound
+# --------------------------------------------------------------------------
+
+def test_fitc_woodbury_sylvester_and_condition_bound():
+    locs, ind, g, nu, th = _problem()
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    V = np.random.default_rng(2).standard_normal((locs.shape[0], 4))
+    assert np.allclose(It.apply_Pinv(V), np.linalg.solve(D.Phat, V), rtol=1e-10, atol=1e-10)
+    sign, ld = np.linalg.slogdet(D.Phat)
+    assert sign > 0 and abs(It.logdet_P - ld) < 1e-9 * abs(ld)
+    # Lemma 2 proof: kappa(P^-1 Sdag) <= (1 + ||Ss - diag(Ss)||_2 / nugget)^2
+    ev = sla.eigh(D.Sdag, D.Phat, eigvals_only=True)
+    E = D.Ss - np.diag(np.diag(D.Ss))
+    bound = (1 + np.linalg.norm(E, 2) / th[2]) ** 2
+    assert ev.max() / ev.min() <= bound + 1e-9
+
+
+def test_fitc_sample_covariance_is_phat():
+    locs, ind, g, nu, th = _problem(n=40, m=6)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    Z = It.probes(20000, 9)
+    C = Z @ Z.T / Z.shape[1]
+    assert np.max(np.abs(C - D.Phat)) < 0.08 * np.max(np.abs(D.Phat))
+
+
+# --------------------------------------------------------------------------
+# PCG with Lanczos tridiagonals, SLQ, STE
+# --------------------------------------------------------------------------
+
+def test_tiny_taper_makes_fsa_equal_fitc_one_step():
+    """gamma below every pair distance: Sigma_dag = P_hat, so PCG converges in
+    one iteration with alpha_1 = 1 and T = [1] (Theorem 2 remark, gamma -> 0)."""
+    locs, ind, _, nu, th = _problem(n=80, m=10)
+    It = O.IterativeFSA(locs, ind, 1e-6, nu, th)
+    assert It.rowptr[-1] == 80
+    b = np.random.default_rng(3).standard_normal((80, 2))
+    res = O.pcg_lanczos(It.apply, It.apply_Pinv, b, 1e-10, 50)
+    assert np.all(res["iters"] == 1)
+    for k in range(2):
+        assert abs(res["diag"][k][0] - 1.0) < 1e-10
+    out = It.loglik_grad(b[:, 0], 5, 1, 1e-10, want_grad=False)
+    assert abs(out["logdet"] - It.logdet_P) < 1e-9 * abs(It.logdet_P)
+
+
+def test_pcg_solution_and_ritz_values_within_spectrum():
+    locs, ind, g, nu, th = _problem()
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    b = np.random.default_rng(4).standard_normal((150, 3))
+    res = O.pcg_lanczos(It.apply, It.apply_Pinv, b, 1e-11, 500)
+    assert np.allclose(res["U"], np.linalg.solve(D.Sdag, b), rtol=1e-8, atol=1e-9)
+    ev = sla.eigh(D.Sdag, D.Phat, eigvals_only=True)
+    for k in range(3):
+        T = np.diag(res["diag"][k]) + np.diag(res["off"][k], 1) + np.diag(res["off"][k], -1)
+        ritz = np.linalg.eigvalsh(T)
+        assert ritz.min() >= ev.min() * (1 - 1e-8) and ritz.max() <= ev.max() * (1 + 1e-8)
+
+
+def test_fixed_iteration_pcg_tridiagonal_equals_lanczos():
+    """The CG-derived T (Appendix A) equals the tridiagonal of k explicit Lanczos
+    steps on L^-1 Sdag L^-T started from L^-1 b/|L^-1 b| (P_hat = L L^T)."""
+    locs, ind, g, nu, th = _problem(n=90, m=12)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    b = np.random.default_rng(5).standard_normal((90, 1))
+    k = 6
+    res = O.pcg_lanczos(It.apply, It.apply_Pinv, b, 0.0, 100, fixed_iters=k)
+    L = np.linalg.cholesky(D.Phat)
+    Aop = sla.solve_triangular(L, sla.solve_triangular(L, D.Sdag, lower=True).T, lower=True).T
+    q = sla.solve_triangular(L, b[:, 0], lower=True)
+    q /= np.linalg.norm(q)
+    Q = [q]
+    al, be = [], []
+    qprev, bprev = np.zeros_like(q), 0.0
+    for j in range(k):
+        w = Aop @ Q[-1] - bprev * qprev
+        a = Q[-1] @ w
+        w -= a * Q[-1]
+        for qq in Q:                     # full reorthogonalisation
+            w -= (qq @ w) * qq
+        al.append(a)
+        bb = np.linalg.norm(w)
+        be.append(bb)
+        qprev, bprev = Q[-1], bb
+        Q.append(w / bb)
+    assert np.allclose(res["diag"][0], al, rtol=1e-8)
+    assert np.allclose(res["off"][0], be[:k - 1], rtol=1e-7)
+
+
+def test_slq_and_ste_with_full_basis_probes_are_exact():
+    """With probes z_i = sqrt(n) L e_i (P_hat = L L^T, i = 1..n) and full
+    convergence, the SLQ sum is exactly logdet(P^-1/2 Sdag P^-1/2) (start
+    vectors e_i) and the STE is exactly tr(Sdag^-1 dSdag) (sum z z^T = n P_hat),
+    so the iterative log-likelihood and gradient equal the dense ones."""
+    locs, ind, g, nu, th = _problem(n=70, m=9, nu=1.5, theta=(0.9, 0.2, 0.15), gamma=0.15)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    y = np.random.default_rng(6).standard_normal(70)
+    Z = math.sqrt(70) * np.linalg.cholesky(D.Phat)
+    out = It.loglik_grad(y, 70, 0, 1e-13, max_iter=400, Z=Z)
+    ll, logdet, _ = D.loglik(y)
+    assert abs(out["logdet"] - logdet) < 1e-8 * abs(logdet)
+    assert abs(out["loglik"] - ll) < 1e-8 * abs(ll)
+    assert np.allclose(out["grad"], D.grad(y), rtol=1e-7, atol=1e-8)
+
+
+def test_dense_gradient_matches_central_differences():
+    locs, ind, g, nu, th = _problem(n=80, m=10, nu=0.5)
+    y = np.random.default_rng(7).standard_normal(80)
+    gd = O.DenseFSA(locs, ind, g, nu, th).grad(y)
+    for k in range(3):
+        h = 1e-5 * th[k]
+        tp = list(th); tp[k] += h
+        tm = list(th); tm[k] -= h
+        fd = (O.DenseFSA(locs, ind, g, nu, tp).loglik(y)[0] - O.DenseFSA(locs, ind, g, nu, tm).loglik(y)[0]) / (2 * h)
+        assert abs(fd - gd[k]) < 1e-6 * max(1.0, abs(gd[k]))
+
+
+def test_euler_homogeneity_of_gradient():
+    """Sdag(t s1, rho, t nug) = t Sdag: s1 dl/ds1 + nug dl/dnug = -(n - y^T Sdag^-1 y)/2."""
+    locs, ind, g, nu, th = _problem(n=90, m=11, nu=1.5)
+    y = np.random.default_rng(8).standard_normal(90)
+    F = O.DenseFSA(locs, ind, g, nu, th)
+    gr = F.grad(y)
+    q = float(y @ np.linalg.solve(F.Sdag, y))
+    assert abs(th[0] * gr[0] + th[2] * gr[2] + 0.5 * (90 - q)) < 1e-8 * 90
+
+
+def test_random_probe_estimates_within_standard_error():
+    locs, ind, g, nu, th = _problem(n=400, m=25, gamma=0.08)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    y = np.linalg.cholesky(D.Sdag) @ np.random.default_rng(9).standard_normal(400)
+    out = It.loglik_grad(y, 200, 123, 1e-10)
+    ll, logdet, quad = D.loglik(y)
+    assert abs(out["quad"] - quad) < 1e-7 * quad
+    assert abs(out["logdet"] - logdet) < 4 * out["logdet_se"] + 1e-9
+    gd = D.grad(y)
+    se = np.std(out["grad_terms"], axis=1, ddof=1) / math.sqrt(200) * 0.5
+    assert np.all(np.abs(out["grad"] - gd) < 4 * se + 1e-9)
+
+
+# --------------------------------------------------------------------------
+# predictive distribution
+# --------------------------------------------------------------------------
+
+def test_dense_prediction_m_equals_n_is_kriging():
+    n = 50
+    locs = fi.uniform_locations(n, 12)
+    pred = fi.uniform_locations(20, 12, stream=7)
+    th = (1.0, 0.1, 0.2)
+    y = np.random.default_rng(10).standard_normal(n)
+    F = O.DenseFSA(locs, locs, 0.05, 0.5, th)
+    mu, var = F.predict(y, pred)
+    S = th[0] * np.exp(-np.sqrt(O.sqdist(locs, locs)) / th[1]) + th[2] * np.eye(n)
+    Snp = th[0] * np.exp(-np.sqrt(O.sqdist(locs, pred)) / th[1])
+    assert np.allclose(mu, Snp.T @ np.linalg.solve(S, y), atol=1e-8)
+    assert np.allclose(var, th[0] + th[2] - np.sum(Snp * np.linalg.solve(S, Snp), 0), atol=1e-8)
+
+
+def test_algorithm1_with_full_basis_probes_is_exact():
+    """Algorithm 1 with 'probes' sqrt(s) e_j (s = n_p) gives the exact diagonal,
+    so its variances equal the dense exact FSA variances (Proposition 1)."""
+    locs, ind, g, nu, th = _problem(n=120, m=15)
+    pred = fi.uniform_locations(30, 3, stream=7)
+    y = np.random.default_rng(11).standard_normal(120)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    mu, var = D.predict(y, pred)
+    out = It.predict(y, pred, 30, 0, 1e-12, Zp=math.sqrt(30) * np.eye(30))
+    assert np.allclose(out["mean"], mu, atol=1e-8)
+    assert np.allclose(out["var"], var, atol=1e-8)
+
+
+def test_algorithm1_random_probes_unbiased_within_tolerance():
+    locs, ind, g, nu, th = _problem(n=200, m=20)
+    pred = fi.uniform_locations(60, 4, stream=7)
+    y = np.random.default_rng(12).standard_normal(200)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    _, var = D.predict(y, pred)
+    s = 400
+    out = It.predict(y, pred, s, 77, 1e-12)
+    # Rademacher diagonal estimator: Var[D_l,j] = (1/s) sum_{k != j} A_jk^2
+    C, _, Ssnp, _ = D.cross(pred)
+    Amat = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
+    sd = np.sqrt((np.sum(Amat ** 2, 1) - np.diag(Amat) ** 2) / s)
+    assert np.all(np.abs(out["var"] - var) <= 5 * sd + 1e-9)
