@@ -1,0 +1,210 @@
+/*
+ * fsa.h — C ABI of the GB300 (sm_103a) implementation of the iterative
+ * full-scale approximation (FSA) of Gaussian processes of
+ * Gyger, Furrer & Sigrist, "Iterative Methods for Full-Scale Gaussian Process
+ * Approximations for Large Spatial Data" (arXiv 2405.14492).
+ *
+ * Model (paper §2, Eq. NEGLL): y = b + eps, b ~ N(0, Sigma), eps ~ N(0, nugget I),
+ * Sigma_ij = sigma1^2 r(|s_i - s_j|; rho) with r the Matérn correlation
+ * (nu = 1/2: exp(-d/rho); nu = 3/2: (1 + sqrt(3) d/rho) exp(-sqrt(3) d/rho)).
+ * The FSA (§2.1) replaces Sigma + nugget I by
+ *     Sigma_dag = Sigma_l + (Sigma - Sigma_l) o T(gamma) + nugget I,
+ *     Sigma_l   = Sigma_mn^T Sigma_m^-1 Sigma_mn   (m inducing points),
+ *     T(gamma)  = Wendland phi_{3,1} taper, zero for distance >= gamma.
+ *
+ * Conventions for every call:
+ *   - Return value: a status code; nothing throws across the ABI.  The text of
+ *     the last error of the calling thread is given by fsa_last_error().
+ *   - Ownership: the caller owns every input and output buffer.  Unless a
+ *     call says otherwise, buffers are HOST memory; the library copies inputs
+ *     into device memory it owns and copies results back before returning.
+ *   - Handles are opaque, own all their device memory and are released by
+ *     fsa_free().  One handle must not be used from two threads at once.
+ *   - Points are row-major (x, y) pairs of double.  Indices in outputs refer
+ *     to the caller's original point order.
+ *   - Outputs are the log-likelihood l = -L (the paper's L is the NEGATIVE
+ *     log-likelihood) and its gradient with respect to the raw parameters
+ *     theta = (sigma1^2, rho, nugget).
+ *   - The response is taken as centred (y - X beta): no fixed effects.
+ */
+#ifndef FSA_H_
+#define FSA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FSA_OK = 0,
+  FSA_ERR_ARG = 1,             /* invalid argument (size, pointer, parameter) */
+  FSA_ERR_OOM = 2,             /* device memory could not be allocated / admitted */
+  FSA_ERR_NOT_PD = 3,          /* a Cholesky pivot <= 0 (Sigma_m or the Woodbury core) */
+  FSA_ERR_NO_CONVERGENCE = 4,  /* CG hit its iteration limit; outputs still written */
+  FSA_ERR_NAN = 5,             /* a non-finite input or intermediate */
+  FSA_ERR_TIMEOUT = 6,         /* a bounded device or host wait ran out */
+  FSA_ERR_BUSY = 7,            /* serving: result not ready yet */
+  FSA_ERR_CUDA = 8,            /* a CUDA runtime error */
+  FSA_ERR_UNSUPPORTED = 9      /* option not available on this device / build */
+} fsa_status;
+
+typedef enum {
+  FSA_EXPONENTIAL = 0,   /* Matérn nu = 1/2 */
+  FSA_MATERN_1_5 = 1     /* Matérn nu = 3/2 */
+} fsa_cov;
+
+typedef enum {
+  FSA_FP64 = 0,          /* every step in FP64 on the CUDA cores */
+  FSA_MIXED_BF16 = 1     /* n x m products on tcgen05 tensor cores: A = Sigma_nm L_m^-T
+                            stored once in BF16 (the operator is defined by it, consistently
+                            in the operator, preconditioner, probes and log det P);
+                            vector operands split hi+lo BF16, FP32 accumulation; vectors
+                            FP32; m x m Cholesky / Woodbury core, CG scalars and Lanczos
+                            eigen-quadrature in FP64 */
+} fsa_precision;
+
+typedef enum {
+  FSA_PROBE_RADEMACHER = 0,
+  FSA_PROBE_GAUSSIAN = 1
+} fsa_probe;
+
+typedef struct {
+  double sigma1_sq;      /* marginal variance sigma1^2 > 0 */
+  double rho;            /* range rho > 0 */
+  double nugget;         /* nugget sigma^2 > 0 */
+} fsa_theta;
+
+typedef struct {
+  int32_t num_probes;    /* l >= 1 stochastic probes for SLQ / STE (§3.1) */
+  double cg_tol;         /* stop a column when ||r||_2 < cg_tol (Appendix A, absolute) */
+  int32_t cg_max_iter;   /* iteration limit L (default 1000 when <= 0) */
+  int32_t fixed_iters;   /* > 0: run exactly this many CG iterations in every column */
+  int32_t precision;     /* fsa_precision */
+  int32_t probe;         /* fsa_probe */
+  uint64_t seed;         /* probe seed (counter-based SplitMix64, streams 4 and 5) */
+  int32_t slq_exact_weight; /* 1: weight z^T P^-1 z instead of the paper's n */
+  int32_t want_grad;     /* 0: log-likelihood only */
+  int32_t y_on_device;   /* 1: y is a DEVICE pointer (n doubles, caller order) */
+} fsa_opts;
+
+typedef struct {
+  int32_t iters_max;     /* largest CG iteration count over the columns */
+  int32_t iters_y;       /* CG iterations of the response column */
+  double resid_y;        /* final ||r||_2 of the response column */
+  double logdet;         /* SLQ estimate of log det Sigma_dag */
+  double logdet_precond; /* log det P_hat (Sylvester, exact) */
+  double quad_form;      /* y^T Sigma_dag^-1 y */
+  double logdet_se;      /* standard error of the SLQ estimate (sample sd / sqrt(l)) */
+  int32_t converged;     /* 1 if every column met cg_tol (or fixed_iters ran) */
+  int32_t num_probes;
+  int64_t nnz;           /* nonzeros of the tapered residual (diagonal included) */
+  double time_ms;        /* device time of the call */
+} fsa_info;
+
+typedef struct fsa_handle fsa_handle;
+
+/* Defaults: num_probes 50, cg_tol 1e-3, cg_max_iter 1000, fixed_iters 0,
+ * FSA_FP64, Rademacher, seed 14492, want_grad 1. */
+void fsa_default_opts(fsa_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* fsa_status_string(fsa_status s);
+
+/* Message of the last failed call on this thread (static per thread). */
+const char* fsa_last_error(void);
+
+/*
+ * fsa_build — theta-free set-up (paper §2.1: taper support; §3.1: sparse +
+ * low-rank operator).  Copies the n locations and m inducing points to the
+ * device, sorts the points by a cell grid of side >= gamma (internal order),
+ * and builds the CSR pattern of {(i,j): |s_i - s_j|^2 < gamma^2} (diagonal
+ * included; squared distance without fused multiply-add).
+ *   locs      n x 2 row-major host array, n >= 2
+ *   inducing  m x 2 row-major host array of distinct points, 1 <= m <= n
+ *   taper_range gamma > 0
+ *   cov       fsa_cov
+ *   cuda_stream a cudaStream_t to run on (NULL: the legacy default stream)
+ *   out       receives the handle
+ * Errors: FSA_ERR_ARG, FSA_ERR_NAN (non-finite coordinates), FSA_ERR_OOM, FSA_ERR_CUDA.
+ */
+fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int32_t m,
+                     double taper_range, int32_t cov, void* cuda_stream, fsa_handle** out);
+
+/* Number of nonzeros of the taper pattern (diagonal included). */
+int64_t fsa_nnz(const fsa_handle* h);
+
+/*
+ * fsa_get_csr — the taper pattern in the caller's point order, columns
+ * ascending: rowptr (n+1, int64) and col (nnz, int32) host arrays.
+ */
+fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col);
+
+/*
+ * fsa_loglik_grad — log-likelihood and gradient (paper Eq. NEGLLDNEGLLFSA)
+ * by block preconditioned CG with the FITC preconditioner (Eq. eqfitcp),
+ * stochastic Lanczos quadrature for log det (§3.1, §3.3) and stochastic trace
+ * estimation for the gradient (§3.1, §3.3); CG with Lanczos tridiagonals per
+ * Appendix A.
+ *   y       n values in the caller's point order (host, or device if
+ *           opts->y_on_device)
+ *   theta   covariance parameters
+ *   opts    options (NULL: defaults)
+ *   loglik  receives l(theta) = -[n/2 log 2pi + 1/2 log det + 1/2 y^T Sigma_dag^-1 y]
+ *   grad    3 doubles, receives dl/d(sigma1^2, rho, nugget) (ignored when
+ *           want_grad = 0; may be NULL then)
+ *   info    optional diagnostics (may be NULL)
+ * Errors: FSA_ERR_ARG, FSA_ERR_NOT_PD, FSA_ERR_NO_CONVERGENCE (outputs
+ * written), FSA_ERR_NAN, FSA_ERR_OOM, FSA_ERR_UNSUPPORTED, FSA_ERR_CUDA.
+ */
+fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* theta,
+                           const fsa_opts* opts, double* loglik, double* grad,
+                           fsa_info* info);
+
+/*
+ * fsa_matvec — the FSA operator and its preconditioner on caller vectors
+ * (paper §3.1: Sigma_dag v = Sigma_s~ v + Sigma_mn^T Sigma_m^-1 Sigma_mn v;
+ * appendix "Runtime of the FITC preconditioner": P_hat^-1 v by Woodbury).
+ *   which   0: Sigma_dag v, 1: P_hat^-1 v, 2: Sigma_s~ v (sparse part only)
+ *   v, out  n x k row-major host arrays, caller's point order
+ * Uses the operator built for theta with the given precision.
+ */
+fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, int32_t which,
+                      const double* v, int32_t k, double* out);
+
+/*
+ * fsa_logdet_precond — log det P_hat by Sylvester's theorem (appendix
+ * "Runtime of the FITC preconditioner") for theta at the given precision.
+ */
+fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t precision,
+                              double* out);
+
+/*
+ * fsa_predict — predictive mean (§2.3) and simulation-based predictive
+ * variances (Algorithm 1, Proposition 1) at n_p new locations.
+ *   pred_locs   n_p x 2 row-major host array
+ *   num_var_samples s >= 1 probes for the stochastic diagonal D_l (probe kind
+ *               and seed from opts; stream 6, counter = k * n_p + p)
+ *   mean, var   n_p doubles each (host); var may be NULL (means only)
+ * Linear solves: FITC-PCG for Sigma_dag^-1 y; D_s-preconditioned block CG
+ * for Sigma_s~^-1 [Sigma_mn^T, S z_1..z_s]; Sigma_dag^-1 Sigma_mn^T by the exact
+ * identity W2 M^-1 Sigma_m with M = Sigma_m + Sigma_mn W2 (Woodbury).
+ */
+fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta,
+                       const fsa_opts* opts, const double* pred_locs, int64_t n_p,
+                       int32_t num_var_samples, double* mean, double* var, fsa_info* info);
+
+/* Release a handle and all its device memory. */
+void fsa_free(fsa_handle* h);
+
+/* Estimate of the device bytes one loglik+grad call on a problem of this size
+ * holds (structure + operator + CG block), used for admission control. */
+int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probes,
+                            int32_t precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSA_H_ */

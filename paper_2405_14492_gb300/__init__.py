@@ -1,0 +1,178 @@
+"""GB300-native iterative full-scale approximation (FSA) for Gaussian processes.
+
+Python front end of libfsa.so (C ABI in include/fsa.h): argument marshalling
+only; every step of the computation runs in the library's CUDA kernels.
+PyTorch is used for device memory and streams (``FSALogLik`` wraps the
+log-likelihood as a ``torch.autograd.Function``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+from ._native import (FSA_EXPONENTIAL, FSA_FP64, FSA_MATERN_1_5, FSA_MIXED_BF16, FSA_PROBE_GAUSSIAN,
+                      FSA_PROBE_RADEMACHER, FsaError, FsaInfo, FsaOpts, FsaTheta)
+
+__all__ = ["FSAHandle", "FSALogLik", "FsaError", "FSA_EXPONENTIAL", "FSA_MATERN_1_5", "FSA_FP64",
+           "FSA_MIXED_BF16", "FSA_PROBE_RADEMACHER", "FSA_PROBE_GAUSSIAN", "make_opts", "cov_code"]
+
+
+def cov_code(nu: float) -> int:
+    if nu == 0.5:
+        return FSA_EXPONENTIAL
+    if nu == 1.5:
+        return FSA_MATERN_1_5
+    raise ValueError("nu must be 0.5 or 1.5")
+
+
+def make_opts(num_probes=50, cg_tol=1e-3, cg_max_iter=1000, fixed_iters=0, precision=FSA_FP64,
+              probe=FSA_PROBE_RADEMACHER, seed=14492, slq_exact_weight=False, want_grad=True,
+              y_on_device=False) -> FsaOpts:
+    o = N.default_opts()
+    o.num_probes, o.cg_tol, o.cg_max_iter, o.fixed_iters = num_probes, cg_tol, cg_max_iter, fixed_iters
+    o.precision, o.probe, o.seed = precision, probe, seed
+    o.slq_exact_weight, o.want_grad, o.y_on_device = int(slq_exact_weight), int(want_grad), int(y_on_device)
+    return o
+
+
+def _theta(theta) -> FsaTheta:
+    s1, rho, nug = (float(t) for t in theta)
+    return FsaTheta(s1, rho, nug)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class FSAHandle:
+    """A built FSA problem: locations, inducing points, taper range, covariance
+    family (``fsa_build``).  Owns its device memory; ``close()`` frees it."""
+
+    def __init__(self, locs, inducing, taper_range: float, nu: float = 0.5, stream: int = 0):
+        self._locs = _f64(locs)
+        self._ind = _f64(inducing)
+        self.n, self.m = self._locs.shape[0], self._ind.shape[0]
+        self.nu = nu
+        h = C.c_void_p()
+        N.check(N.lib().fsa_build(N.ptr(self._locs), self.n, N.ptr(self._ind), self.m, float(taper_range),
+                                  cov_code(nu), C.c_void_p(stream), C.byref(h)))
+        self._h = h
+
+    @property
+    def nnz(self) -> int:
+        return int(N.lib().fsa_nnz(self._h))
+
+    def csr(self):
+        """Taper pattern in the caller's point order (``fsa_get_csr``)."""
+        rowptr = np.empty(self.n + 1, np.int64)
+        col = np.empty(self.nnz, np.int32)
+        N.check(N.lib().fsa_get_csr(self._h, N.ptr(rowptr), N.ptr(col)))
+        return rowptr, col
+
+    def loglik_grad(self, y, theta, opts: FsaOpts | None = None, raise_on_noconv: bool = False):
+        """(loglik, grad[3], info dict) via ``fsa_loglik_grad``.  ``y`` is a
+        host array, or a CUDA torch tensor when opts.y_on_device is set."""
+        opts = opts or make_opts()
+        th = _theta(theta)
+        ll = C.c_double()
+        g = np.zeros(3)
+        info = FsaInfo()
+        if opts.y_on_device:
+            yp = C.c_void_p(int(y.data_ptr()))
+        else:
+            yh = _f64(y)
+            yp = N.ptr(yh)
+        st = N.lib().fsa_loglik_grad(self._h, yp, C.byref(th), C.byref(opts), C.byref(ll),
+                                     g.ctypes.data_as(N.DP), C.byref(info))
+        if st != N.FSA_OK and (st != 4 or raise_on_noconv):
+            N.check(st)
+        d = info.as_dict()
+        d["status"] = st
+        return ll.value, g, d
+
+    def matvec(self, theta, v, which=0, precision=FSA_FP64):
+        """Sigma_dag v (0), P_hat^-1 v (1) or Sigma_s~ v (2) (``fsa_matvec``)."""
+        v = _f64(v)
+        vv = v.reshape(self.n, -1)
+        out = np.empty_like(vv)
+        th = _theta(theta)
+        N.check(N.lib().fsa_matvec(self._h, C.byref(th), precision, which, N.ptr(vv), vv.shape[1], N.ptr(out)))
+        return out.reshape(v.shape)
+
+    def logdet_precond(self, theta, precision=FSA_FP64) -> float:
+        th = _theta(theta)
+        out = C.c_double()
+        N.check(N.lib().fsa_logdet_precond(self._h, C.byref(th), precision, C.byref(out)))
+        return out.value
+
+    def predict(self, y, theta, pred_locs, num_var_samples=50, opts: FsaOpts | None = None, want_var=True):
+        """Predictive mean and simulation-based variances (``fsa_predict``)."""
+        opts = opts or make_opts()
+        th = _theta(theta)
+        yh = _f64(y)
+        pl = _f64(pred_locs)
+        n_p = pl.shape[0]
+        mean = np.empty(n_p)
+        var = np.empty(n_p) if want_var else None
+        info = FsaInfo()
+        st = N.lib().fsa_predict(self._h, N.ptr(yh), C.byref(th), C.byref(opts), N.ptr(pl), n_p,
+                                 int(num_var_samples), N.ptr(mean), N.ptr(var) if want_var else None,
+                                 C.byref(info))
+        if st not in (N.FSA_OK, 4):
+            N.check(st)
+        return mean, var, info.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().fsa_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _autograd_function():
+    import torch
+
+    class FSALogLik(torch.autograd.Function):
+        """l(theta) as a differentiable torch scalar: forward calls
+        ``fsa_loglik_grad`` (the hand-written adjoint kernels give the STE
+        gradient), backward returns grad_output * dl/dtheta."""
+
+        @staticmethod
+        def forward(ctx, theta, handle, y, opts=None):
+            th = theta.detach().double().cpu().numpy()
+            ll, g, _ = handle.loglik_grad(y, th, opts)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+            return torch.as_tensor(ll, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out * g, None, None, None
+
+    return FSALogLik
+
+
+class _Lazy:
+    def __init__(self):
+        self._f = None
+
+    def __getattr__(self, k):
+        if self._f is None:
+            self._f = _autograd_function()
+        return getattr(self._f, k)
+
+
+FSALogLik = _Lazy()

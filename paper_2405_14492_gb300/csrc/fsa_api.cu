@@ -1,0 +1,293 @@
+// C ABI of the FSA library (declared in include/fsa.h).  Every entry point
+// catches library errors and returns a status; nothing throws across the ABI.
+#include <algorithm>
+#include <cstring>
+
+#include "fsa_solver.cuh"
+
+namespace fsa {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static __global__ void k_to_internal(int64_t n, int k, const int64_t* __restrict__ perm,
+                                     const double* __restrict__ src, double* __restrict__ dst) {
+  int64_t total = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / k;
+    int c = (int)(t - i * k);
+    dst[t] = src[perm[i] * k + c];
+  }
+}
+
+static __global__ void k_to_original(int64_t n, int k, const int64_t* __restrict__ perm,
+                                     const double* __restrict__ src, double* __restrict__ dst) {
+  int64_t total = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / k;
+    int c = (int)(t - i * k);
+    dst[perm[i] * k + c] = src[t];
+  }
+}
+
+void to_internal(Handle& H, int k, const double* src, double* dst) {
+  k_to_internal<<<grid_for(H.n * k, 256), 256, 0, H.stream>>>(H.n, k, H.perm.p, src, dst);
+  FSA_CHECK_LAUNCH();
+}
+void to_original(Handle& H, int k, const double* src, double* dst) {
+  k_to_original<<<grid_for(H.n * k, 256), 256, 0, H.stream>>>(H.n, k, H.perm.p, src, dst);
+  FSA_CHECK_LAUNCH();
+}
+
+static fsa_status fail(const Error& e) {
+  set_error(e.msg);
+  return e.code;
+}
+
+static bool theta_ok(const fsa_theta* t) {
+  return t && std::isfinite(t->sigma1_sq) && std::isfinite(t->rho) && std::isfinite(t->nugget) &&
+         t->sigma1_sq > 0 && t->rho > 0 && t->nugget > 0;
+}
+
+static fsa_opts resolve_opts(const fsa_opts* o) {
+  fsa_opts r;
+  fsa_default_opts(&r);
+  if (o) r = *o;
+  if (r.cg_max_iter <= 0) r.cg_max_iter = 1000;
+  return r;
+}
+
+}  // namespace fsa
+
+using namespace fsa;
+
+struct fsa_handle {
+  Handle h;
+};
+
+extern "C" {
+
+void fsa_default_opts(fsa_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->num_probes = 50;
+  o->cg_tol = 1e-3;
+  o->cg_max_iter = 1000;
+  o->fixed_iters = 0;
+  o->precision = FSA_FP64;
+  o->probe = FSA_PROBE_RADEMACHER;
+  o->seed = 14492;
+  o->slq_exact_weight = 0;
+  o->want_grad = 1;
+  o->y_on_device = 0;
+}
+
+const char* fsa_status_string(fsa_status s) {
+  switch (s) {
+    case FSA_OK: return "FSA_OK";
+    case FSA_ERR_ARG: return "FSA_ERR_ARG";
+    case FSA_ERR_OOM: return "FSA_ERR_OOM";
+    case FSA_ERR_NOT_PD: return "FSA_ERR_NOT_PD";
+    case FSA_ERR_NO_CONVERGENCE: return "FSA_ERR_NO_CONVERGENCE";
+    case FSA_ERR_NAN: return "FSA_ERR_NAN";
+    case FSA_ERR_TIMEOUT: return "FSA_ERR_TIMEOUT";
+    case FSA_ERR_BUSY: return "FSA_ERR_BUSY";
+    case FSA_ERR_CUDA: return "FSA_ERR_CUDA";
+    case FSA_ERR_UNSUPPORTED: return "FSA_ERR_UNSUPPORTED";
+  }
+  return "FSA_ERR_UNKNOWN";
+}
+
+const char* fsa_last_error(void) { return g_last_error.c_str(); }
+
+fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int32_t m, double taper_range,
+                     int32_t cov, void* cuda_stream, fsa_handle** out) {
+  if (!out) return fail(Error{FSA_ERR_ARG, "out is NULL"});
+  *out = nullptr;
+  if (!locs || !inducing || n < 2 || m < 1 || m > n || n > ((int64_t)1 << 31) - 1)
+    return fail(Error{FSA_ERR_ARG, "bad sizes or NULL coordinates (need n >= 2, 1 <= m <= n < 2^31)"});
+  if (!(taper_range > 0) || !std::isfinite(taper_range)) return fail(Error{FSA_ERR_ARG, "taper_range must be > 0"});
+  if (cov != FSA_EXPONENTIAL && cov != FSA_MATERN_1_5) return fail(Error{FSA_ERR_ARG, "unknown covariance"});
+  for (int32_t k = 0; k < 2 * m; ++k)
+    if (!std::isfinite(inducing[k])) return fail(Error{FSA_ERR_NAN, "non-finite inducing point"});
+  fsa_handle* hh = nullptr;
+  try {
+    hh = new fsa_handle();
+    Handle& H = hh->h;
+    H.n = n;
+    H.m = m;
+    H.gamma = taper_range;
+    H.cov = cov;
+    H.stream = (cudaStream_t)cuda_stream;
+    H.err_buf.alloc(1);
+    H.err = H.err_buf.p;
+    FSA_CUDA(cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream));
+    FSA_CUDA(cudaMallocHost(&H.host_pinned, 64 * sizeof(double)));
+    FSA_CUDA(cudaEventCreate(&H.ev0));
+    FSA_CUDA(cudaEventCreate(&H.ev1));
+    std::vector<double> ix(m), iy(m);
+    for (int32_t k = 0; k < m; ++k) { ix[k] = inducing[2 * k]; iy[k] = inducing[2 * k + 1]; }
+    H.ind_x.alloc(m);
+    H.ind_y.alloc(m);
+    FSA_CUDA(cudaMemcpyAsync(H.ind_x.p, ix.data(), sizeof(double) * m, cudaMemcpyHostToDevice, H.stream));
+    FSA_CUDA(cudaMemcpyAsync(H.ind_y.p, iy.data(), sizeof(double) * m, cudaMemcpyHostToDevice, H.stream));
+    build_structure(H, locs);
+    *out = hh;
+    return FSA_OK;
+  } catch (const Error& e) {
+    fsa_free(hh);
+    return fail(e);
+  } catch (const std::exception& e) {
+    fsa_free(hh);
+    return fail(Error{FSA_ERR_CUDA, e.what()});
+  }
+}
+
+int64_t fsa_nnz(const fsa_handle* h) { return h ? h->h.nnz : -1; }
+
+fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col) {
+  if (!h || !rowptr || !col) return fail(Error{FSA_ERR_ARG, "NULL argument"});
+  try {
+    export_csr(h->h, rowptr, col);
+    return FSA_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* theta, const fsa_opts* opts,
+                           double* loglik, double* grad, fsa_info* info) {
+  if (!h || !y || !loglik) return fail(Error{FSA_ERR_ARG, "NULL argument"});
+  if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
+  fsa_opts o = resolve_opts(opts);
+  if (o.num_probes < 1 || o.num_probes > 1000) return fail(Error{FSA_ERR_ARG, "num_probes must be in [1, 1000]"});
+  if (o.want_grad && !grad) return fail(Error{FSA_ERR_ARG, "grad is NULL"});
+  if (o.precision != FSA_FP64 && o.precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
+  Handle& H = h->h;
+  try {
+    FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
+    H.y.ensure(H.n);
+    {
+      const double* ydev = y;
+      DevPtr<double> tmp;
+      if (!o.y_on_device) {
+        tmp.alloc(H.n);
+        FSA_CUDA(cudaMemcpyAsync(tmp.p, y, sizeof(double) * H.n, cudaMemcpyHostToDevice, H.stream));
+        ydev = tmp.p;
+      }
+      k_gather_y<<<grid_for(H.n, 256), 256, 0, H.stream>>>(H.n, H.perm.p, ydev, H.y.p, H.err);
+      FSA_CHECK_LAUNCH();
+      check_err(H);
+    }
+    LoglikResult r = run_loglik_grad(H, *theta, o);
+    FSA_CUDA(cudaEventRecord(H.ev1, H.stream));
+    FSA_CUDA(cudaEventSynchronize(H.ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, H.ev0, H.ev1);
+    *loglik = r.loglik;
+    if (o.want_grad)
+      for (int q = 0; q < 3; ++q) grad[q] = r.grad[q];
+    if (info) {
+      info->iters_max = r.iters_max;
+      info->iters_y = r.iters_y;
+      info->resid_y = r.resid_y;
+      info->logdet = r.logdet;
+      info->logdet_precond = r.logdetP;
+      info->quad_form = r.yu;
+      info->logdet_se = r.se;
+      info->converged = r.converged ? 1 : 0;
+      info->num_probes = o.num_probes;
+      info->nnz = H.nnz;
+      info->time_ms = ms;
+    }
+    if (!std::isfinite(r.loglik)) return fail(Error{FSA_ERR_NAN, "non-finite log-likelihood"});
+    if (!r.converged) return fail(Error{FSA_ERR_NO_CONVERGENCE, "CG iteration limit reached"});
+    return FSA_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
+    return fail(e);
+  }
+}
+
+fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, int32_t which, const double* v,
+                      int32_t k, double* out) {
+  if (!h || !v || !out || k < 1 || which < 0 || which > 2) return fail(Error{FSA_ERR_ARG, "bad argument"});
+  if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
+  if (precision != FSA_FP64 && precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  Handle& H = h->h;
+  try {
+    ensure_operator(H, *theta, precision);
+    size_t nk = (size_t)H.n * k;
+    DevPtr<double> a(nk), b(nk), c(nk);
+    FSA_CUDA(cudaMemcpyAsync(a.p, v, sizeof(double) * nk, cudaMemcpyHostToDevice, H.stream));
+    to_internal(H, k, a.p, b.p);
+    apply_operator(H, which, b.p, k, c.p);
+    to_original(H, k, c.p, a.p);
+    FSA_CUDA(cudaMemcpyAsync(out, a.p, sizeof(double) * nk, cudaMemcpyDeviceToHost, H.stream));
+    FSA_CUDA(cudaStreamSynchronize(H.stream));
+    check_err(H);
+    return FSA_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    return fail(e);
+  }
+}
+
+fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t precision, double* out) {
+  if (!h || !out) return fail(Error{FSA_ERR_ARG, "NULL argument"});
+  if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
+  if (precision != FSA_FP64 && precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  Handle& H = h->h;
+  try {
+    ensure_operator(H, *theta, precision);
+    double sc[3];
+    FSA_CUDA(cudaMemcpyAsync(sc, H.op.scal.p, sizeof(sc), cudaMemcpyDeviceToHost, H.stream));
+    FSA_CUDA(cudaStreamSynchronize(H.stream));
+    *out = sc[2];
+    return FSA_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, const fsa_opts* opts,
+                       const double* pred_locs, int64_t n_p, int32_t num_var_samples, double* mean, double* var,
+                       fsa_info* info) {
+  (void)h; (void)y; (void)theta; (void)opts; (void)pred_locs; (void)n_p; (void)num_var_samples;
+  (void)mean; (void)var; (void)info;
+  return fail(Error{FSA_ERR_UNSUPPORTED, "prediction not built yet"});
+}
+
+void fsa_free(fsa_handle* h) {
+  if (!h) return;
+  Handle& H = h->h;
+  if (H.stream) cudaStreamSynchronize(H.stream);
+  if (H.host_pinned) cudaFreeHost(H.host_pinned);
+  if (H.ev0) cudaEventDestroy(H.ev0);
+  if (H.ev1) cudaEventDestroy(H.ev1);
+  delete h;
+}
+
+int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probes, int32_t precision) {
+  int64_t c = (num_probes + 1 + 7) / 8 * 8;
+  int64_t mp = (m + 63) / 64 * 64;
+  int64_t b = 0;
+  b += n * 2 * 8 + n * 8 * 3 + nnz * 4;                  // coordinates, perm, rowptr, col
+  b += (int64_t)m * m * 8 * 4;                           // m x m FP64 matrices
+  if (precision == FSA_FP64) {
+    b += n * (int64_t)m * 8 * 2;                         // A + build temporary
+    b += nnz * 8 + n * 16;                               // values, D
+    b += n * c * 8 * 8;                                  // CG block
+  } else {
+    b += n * mp * 2 * 2 + n * (int64_t)m * 4;            // A, A^T (BF16), build temporary (FP32)
+    b += nnz * 4 + n * 16;
+    b += n * c * 4 * 8 + n * c * 2 * 2 * 2;              // CG block, split operands
+  }
+  return b;
+}
+
+}  // extern "C"

@@ -1,0 +1,379 @@
+// Taper-support neighbour structure (paper §2.1: the taper makes Sigma_s
+// sparse; pairs with |s_i - s_j| >= gamma are zero).  Cell-grid binning with
+// cell side >= gamma, a deterministic counting sort of the points by cell
+// (internal order: cell id, then original index), and a two-pass CSR build
+// (count, exclusive scan, fill) over the 3x3 cell stencil.
+#include "fsa_internal.cuh"
+
+namespace fsa {
+
+// ---------------------------------------------------------------------------
+// exclusive scan (multi-level, deterministic)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__global__ void scan_tile_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+                                 T* __restrict__ block_sums) {
+  __shared__ T warp_tot[kScanThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    T x = (i < n) ? in[i] : (T)0;
+    v[k] = run;
+    run += x;
+  }
+  // inclusive scan of per-thread totals across the block
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    T w = (lane < kScanThreads / 32) ? warp_tot[lane] : (T)0;
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;  // exclusive warp offsets
+  }
+  __syncthreads();
+  T offset = warp_tot[wid] + (incl - run);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = v[k] + offset;
+  }
+  if (threadIdx.x == kScanThreads - 1 && block_sums) block_sums[blockIdx.x] = offset + run;
+}
+
+template <typename T>
+__global__ void scan_add_kernel(T* __restrict__ out, int64_t n, const T* __restrict__ block_offsets) {
+  int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  T add = block_offsets[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k, i += kScanThreads)
+    if (i < n) out[i] += add;
+}
+
+// out[i] = sum_{j<i} in[i]; returns total via *total_dev (device pointer, may be null)
+template <typename T>
+void exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    scan_tile_kernel<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    FSA_CHECK_LAUNCH();
+    return;
+  }
+  T* sums = nullptr;
+  FSA_CUDA(cudaMallocAsync(&sums, sizeof(T) * nb * 2, s));
+  scan_tile_kernel<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  FSA_CHECK_LAUNCH();
+  exclusive_scan<T>(sums, sums + nb, nb, s);
+  scan_add_kernel<T><<<(unsigned)nb, kScanThreads, 0, s>>>(out, n, sums + nb);
+  FSA_CHECK_LAUNCH();
+  FSA_CUDA(cudaFreeAsync(sums, s));
+}
+template void exclusive_scan<int64_t>(const int64_t*, int64_t*, int64_t, cudaStream_t);
+template void exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// bounding box + finiteness
+// ---------------------------------------------------------------------------
+__global__ void bbox_partial_kernel(const double* __restrict__ pts, int64_t n, double* __restrict__ part,
+                                    unsigned* __restrict__ err) {
+  double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = pts[2 * i], y = pts[2 * i + 1];
+    if (!isfinite(x) || !isfinite(y)) atomicOr(err, kErrNaN);
+    mnx = fmin(mnx, x); mxx = fmax(mxx, x);
+    mny = fmin(mny, y); mxy = fmax(mxy, y);
+  }
+  __shared__ double sh[4][256];
+  sh[0][threadIdx.x] = mnx; sh[1][threadIdx.x] = mny;
+  sh[2][threadIdx.x] = mxx; sh[3][threadIdx.x] = mxy;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] = fmin(sh[0][threadIdx.x], sh[0][threadIdx.x + o]);
+      sh[1][threadIdx.x] = fmin(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sh[k][0];
+}
+
+__global__ void bbox_final_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double b[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
+  for (int p = 0; p < nparts; ++p) {
+    b[0] = fmin(b[0], part[4 * p]); b[1] = fmin(b[1], part[4 * p + 1]);
+    b[2] = fmax(b[2], part[4 * p + 2]); b[3] = fmax(b[3], part[4 * p + 3]);
+  }
+  for (int k = 0; k < 4; ++k) out[k] = b[k];
+}
+
+// ---------------------------------------------------------------------------
+// binning and counting sort
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(double v, double lo, double h, int nc) {
+  int c = (int)floor((v - lo) / h);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void cell_count_kernel(const double* __restrict__ pts, int64_t n, Grid g,
+                                  int32_t* __restrict__ cell_of, int32_t* __restrict__ count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int cx = cell_coord(pts[2 * i], g.x0, g.hx, g.ncx);
+    int cy = cell_coord(pts[2 * i + 1], g.y0, g.hy, g.ncy);
+    int c = cy * g.ncx + cx;
+    cell_of[i] = c;
+    atomicAdd(&count[c], 1);
+  }
+}
+
+__global__ void cell_scatter_kernel(const int32_t* __restrict__ cell_of, int64_t n,
+                                    const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
+                                    int64_t* __restrict__ perm) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = cell_of[i];
+    int pos = start[c] + atomicAdd(&cursor[c], 1);
+    perm[pos] = i;
+  }
+}
+
+// insertion sort of each cell's points by original index (cells are small
+// for spread-out data; order inside a cell is then independent of atomics)
+__global__ void cell_sort_kernel(const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+                                 int ncells, int64_t* __restrict__ perm) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    int b = start[c], e = b + count[c];
+    for (int k = b + 1; k < e; ++k) {
+      int64_t v = perm[k];
+      int j = k - 1;
+      while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
+      perm[j + 1] = v;
+    }
+  }
+}
+
+__global__ void gather_points_kernel(const double* __restrict__ pts, const int64_t* __restrict__ perm,
+                                     int64_t n, double* __restrict__ xs, double* __restrict__ ys,
+                                     int64_t* __restrict__ iperm) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = perm[k];
+    xs[k] = pts[2 * i];
+    ys[k] = pts[2 * i + 1];
+    iperm[i] = k;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// neighbour count and fill over the 3x3 cell stencil (cells in ascending id
+// order, so columns come out ascending in internal order)
+// ---------------------------------------------------------------------------
+template <bool kFill>
+__global__ void neighbour_kernel(const double* __restrict__ qx, const double* __restrict__ qy, int64_t nq,
+                                 const double* __restrict__ xs, const double* __restrict__ ys,
+                                 const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_count,
+                                 Grid g, double gamma2, int64_t* __restrict__ counts,
+                                 const int64_t* __restrict__ rowptr, int32_t* __restrict__ col) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double xi = qx[i], yi = qy[i];
+    int cx = cell_coord(xi, g.x0, g.hx, g.ncx);
+    int cy = cell_coord(yi, g.y0, g.hy, g.ncy);
+    int64_t cnt = 0;
+    int64_t w = kFill ? rowptr[i] : 0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int yy = cy + dy;
+      if (yy < 0 || yy >= g.ncy) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int xx = cx + dx;
+        if (xx < 0 || xx >= g.ncx) continue;
+        int c = yy * g.ncx + xx;
+        int b = cell_start[c], e = b + cell_count[c];
+        for (int j = b; j < e; ++j) {
+          double d2 = sqdist_rn(xi, yi, xs[j], ys[j]);
+          if (d2 < gamma2) {
+            if (kFill) col[w++] = j;
+            else ++cnt;
+          }
+        }
+      }
+    }
+    if (!kFill) counts[i] = cnt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// export of the pattern in the caller's order, columns ascending
+// ---------------------------------------------------------------------------
+__global__ void orig_counts_kernel(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ iperm,
+                                   int64_t n, int64_t* __restrict__ cnt) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = iperm[r];
+    cnt[r] = rowptr[k + 1] - rowptr[k];
+  }
+}
+
+__global__ void orig_fill_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const int64_t* __restrict__ perm, const int64_t* __restrict__ iperm,
+                                 int64_t n, const int64_t* __restrict__ rowptr_o, int32_t* __restrict__ col_o) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = iperm[r];
+    int64_t b = rowptr[k], e = rowptr[k + 1], o = rowptr_o[r];
+    for (int64_t t = b; t < e; ++t) {
+      int32_t v = (int32_t)perm[col[t]];
+      int64_t j = o + (t - b) - 1;
+      while (j >= o && col_o[j] > v) { col_o[j + 1] = col_o[j]; --j; }
+      col_o[j + 1] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+Grid make_grid(const double bb[4], double gamma, int64_t n) {
+  Grid g;
+  double ex = bb[2] - bb[0], ey = bb[3] - bb[1];
+  double h = gamma * (1.0 + 1e-6);
+  int64_t ncx = (int64_t)floor(ex / h), ncy = (int64_t)floor(ey / h);
+  if (ncx < 1) ncx = 1;
+  if (ncy < 1) ncy = 1;
+  // cap the number of cells at ~4n (larger cells only add candidates)
+  int64_t cap = 4 * n + 16;
+  while (ncx * ncy > cap) {
+    ncx = (ncx + 1) / 2;
+    ncy = (ncy + 1) / 2;
+  }
+  g.ncx = (int)ncx; g.ncy = (int)ncy;
+  g.x0 = bb[0]; g.y0 = bb[1];
+  g.hx = ex > 0 ? ex / ncx : 1.0;
+  g.hy = ey > 0 ? ey / ncy : 1.0;
+  if (g.hx < h) g.hx = h;
+  if (g.hy < h) g.hy = h;
+  return g;
+}
+
+void build_structure(Handle& H, const double* locs_host) {
+  cudaStream_t s = H.stream;
+  int64_t n = H.n;
+  DevPtr<double> pts(2 * n);
+  FSA_CUDA(cudaMemcpyAsync(pts.p, locs_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s));
+  // bounding box
+  const int nparts = 304;
+  DevPtr<double> part(4 * nparts), bb(4);
+  bbox_partial_kernel<<<nparts, 256, 0, s>>>(pts.p, n, part.p, H.err);
+  FSA_CHECK_LAUNCH();
+  bbox_final_kernel<<<1, 32, 0, s>>>(part.p, nparts, bb.p);
+  FSA_CHECK_LAUNCH();
+  double hb[4];
+  FSA_CUDA(cudaMemcpyAsync(hb, bb.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  unsigned herr = 0;
+  FSA_CUDA(cudaMemcpyAsync(&herr, H.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaStreamSynchronize(s));
+  FSA_REQUIRE(!(herr & kErrNaN), FSA_ERR_NAN, "non-finite location coordinates");
+  H.grid = make_grid(hb, H.gamma, n);
+  int ncells = H.grid.ncx * H.grid.ncy;
+  // counting sort by cell
+  DevPtr<int32_t> cell_of(n), count(ncells), cursor(ncells);
+  H.cell_start.alloc(ncells);
+  H.cell_count.alloc(ncells);
+  FSA_CUDA(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * ncells, s));
+  FSA_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * ncells, s));
+  unsigned gb = grid_for(n, 256);
+  cell_count_kernel<<<gb, 256, 0, s>>>(pts.p, n, H.grid, cell_of.p, count.p);
+  FSA_CHECK_LAUNCH();
+  exclusive_scan<int32_t>(count.p, H.cell_start.p, ncells, s);
+  FSA_CUDA(cudaMemcpyAsync(H.cell_count.p, count.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, s));
+  H.perm.alloc(n);
+  H.iperm.alloc(n);
+  cell_scatter_kernel<<<gb, 256, 0, s>>>(cell_of.p, n, H.cell_start.p, cursor.p, H.perm.p);
+  FSA_CHECK_LAUNCH();
+  cell_sort_kernel<<<grid_for(ncells, 256), 256, 0, s>>>(H.cell_start.p, H.cell_count.p, ncells, H.perm.p);
+  FSA_CHECK_LAUNCH();
+  H.xs.alloc(n);
+  H.ys.alloc(n);
+  gather_points_kernel<<<gb, 256, 0, s>>>(pts.p, H.perm.p, n, H.xs.p, H.ys.p, H.iperm.p);
+  FSA_CHECK_LAUNCH();
+  // CSR: count, scan, fill
+  DevPtr<int64_t> counts(n + 1);
+  FSA_CUDA(cudaMemsetAsync(counts.p + n, 0, sizeof(int64_t), s));
+  double g2 = H.gamma * H.gamma;
+  neighbour_kernel<false><<<gb, 256, 0, s>>>(H.xs.p, H.ys.p, n, H.xs.p, H.ys.p, H.cell_start.p,
+                                             H.cell_count.p, H.grid, g2, counts.p, nullptr, nullptr);
+  FSA_CHECK_LAUNCH();
+  H.rowptr.alloc(n + 1);
+  exclusive_scan<int64_t>(counts.p, H.rowptr.p, n + 1, s);
+  int64_t nnz = 0;
+  FSA_CUDA(cudaMemcpyAsync(&nnz, H.rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaStreamSynchronize(s));
+  FSA_REQUIRE(nnz < (int64_t)1 << 40, FSA_ERR_ARG, "taper pattern too large");
+  H.nnz = nnz;
+  H.col.alloc(nnz);
+  neighbour_kernel<true><<<gb, 256, 0, s>>>(H.xs.p, H.ys.p, n, H.xs.p, H.ys.p, H.cell_start.p,
+                                            H.cell_count.p, H.grid, g2, nullptr, H.rowptr.p, H.col.p);
+  FSA_CHECK_LAUNCH();
+  FSA_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_cross_structure(Handle& H, const double* qx, const double* qy, int64_t nq,
+                           DevPtr<int64_t>& rowptr, DevPtr<int32_t>& col, int64_t& nnz) {
+  cudaStream_t s = H.stream;
+  DevPtr<int64_t> counts(nq + 1);
+  FSA_CUDA(cudaMemsetAsync(counts.p + nq, 0, sizeof(int64_t), s));
+  double g2 = H.gamma * H.gamma;
+  unsigned gb = grid_for(nq, 256);
+  neighbour_kernel<false><<<gb, 256, 0, s>>>(qx, qy, nq, H.xs.p, H.ys.p, H.cell_start.p, H.cell_count.p,
+                                             H.grid, g2, counts.p, nullptr, nullptr);
+  FSA_CHECK_LAUNCH();
+  rowptr.alloc(nq + 1);
+  exclusive_scan<int64_t>(counts.p, rowptr.p, nq + 1, s);
+  FSA_CUDA(cudaMemcpyAsync(&nnz, rowptr.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaStreamSynchronize(s));
+  col.alloc(nnz > 0 ? nnz : 1);
+  neighbour_kernel<true><<<gb, 256, 0, s>>>(qx, qy, nq, H.xs.p, H.ys.p, H.cell_start.p, H.cell_count.p,
+                                            H.grid, g2, nullptr, rowptr.p, col.p);
+  FSA_CHECK_LAUNCH();
+}
+
+void export_csr(Handle& H, int64_t* rowptr_host, int32_t* col_host) {
+  cudaStream_t s = H.stream;
+  int64_t n = H.n;
+  DevPtr<int64_t> cnt(n + 1), rp(n + 1);
+  DevPtr<int32_t> co(H.nnz > 0 ? H.nnz : 1);
+  FSA_CUDA(cudaMemsetAsync(cnt.p + n, 0, sizeof(int64_t), s));
+  unsigned gb = grid_for(n, 256);
+  orig_counts_kernel<<<gb, 256, 0, s>>>(H.rowptr.p, H.iperm.p, n, cnt.p);
+  FSA_CHECK_LAUNCH();
+  exclusive_scan<int64_t>(cnt.p, rp.p, n + 1, s);
+  orig_fill_kernel<<<gb, 256, 0, s>>>(H.rowptr.p, H.col.p, H.perm.p, H.iperm.p, n, rp.p, co.p);
+  FSA_CHECK_LAUNCH();
+  FSA_CUDA(cudaMemcpyAsync(rowptr_host, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaMemcpyAsync(col_host, co.p, sizeof(int32_t) * H.nnz, cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace fsa

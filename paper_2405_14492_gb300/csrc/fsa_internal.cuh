@@ -1,0 +1,158 @@
+// Internal declarations of the FSA library: device buffers, the handle, the
+// per-theta operator and the CG workspace.
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "fsa_common.cuh"
+
+namespace fsa {
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevPtr {
+  T* p = nullptr;
+  size_t n = 0;
+  DevPtr() = default;
+  explicit DevPtr(size_t k) { alloc(k); }
+  DevPtr(const DevPtr&) = delete;
+  DevPtr& operator=(const DevPtr&) = delete;
+  DevPtr(DevPtr&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevPtr& operator=(DevPtr&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  void alloc(size_t k) {
+    release();
+    if (k == 0) k = 1;
+    cudaError_t e = cudaMalloc(&p, k * sizeof(T));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+      throw Error{FSA_ERR_OOM, "cudaMalloc of " + std::to_string(k * sizeof(T)) + " bytes failed"};
+    }
+    n = k;
+  }
+  void ensure(size_t k) {
+    if (k > n || p == nullptr) alloc(k);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DevPtr() { release(); }
+};
+
+// growable scratch for split-K partials and temporaries (one stream)
+struct Workspace {
+  DevPtr<double> f64;
+  DevPtr<float> f32;
+  double* scratch_f64(size_t k) { f64.ensure(k); return f64.p; }
+  float* scratch_f32(size_t k) { f32.ensure(k); return f32.p; }
+};
+
+struct Grid {
+  double x0 = 0, y0 = 0, hx = 1, hy = 1;
+  int ncx = 1, ncy = 1;
+};
+
+// ---------------------------------------------------------------------------
+// theta-dependent operator (paper §2.1, §3.1, Eq. eqfitcp)
+// ---------------------------------------------------------------------------
+struct Operator {
+  bool valid = false;
+  fsa_theta theta{};
+  int precision = -1;
+  // m-space, FP64
+  DevPtr<double> Sm;      // Sigma_m, then overwritten by its Cholesky L_m
+  DevPtr<double> Lmi;     // L_m^-1
+  DevPtr<double> Mp;      // Woodbury core I + A^T D^-1 A, then its Cholesky L_P
+  DevPtr<double> Minv;    // M_P^-1
+  DevPtr<double> scal;    // [0] logdet M_P, [1] sum log D, [2] logdet P
+  // n-space
+  DevPtr<double> A;       // FP64 form: A = Sigma_nm L_m^-T (n x m, internal rows)
+  DevPtr<double> vals;    // tapered residual values (nnz), FP64
+  DevPtr<double> D;       // D_s = diag(Sigma_s~) (n)
+  DevPtr<double> Dinv;
+  // mixed form (tensor-core operands)
+  DevPtr<__nv_bfloat16> Ab;    // A rounded to BF16, n x m_pad (K-major for A q)
+  DevPtr<__nv_bfloat16> Atb;   // its transpose, m_pad x n_pad (K-major for A^T x)
+  DevPtr<float> vals32;
+  DevPtr<float> D32, Dinv32;
+  int m_pad = 0;
+  int64_t n_pad = 0;
+};
+
+// ---------------------------------------------------------------------------
+// CG block state
+// ---------------------------------------------------------------------------
+struct CGState {
+  int c = 0, ldc = 0, L = 0;       // columns, leading dim of n x c arrays, iteration cap
+  // n x ldc (FP64 form: double; mixed form: float stored in the f32 buffers)
+  DevPtr<double> U, R, Z, H, V, S, W0, X;
+  DevPtr<float> U32, R32, Z32, H32, V32, S32, W032;
+  DevPtr<__nv_bfloat16> Xb;        // (2 c_pad) x n_pad hi/lo split of D^-1 R (K-major)
+  DevPtr<__nv_bfloat16> qb;        // (2 c_pad) x m_pad hi/lo split of q (K-major)
+  DevPtr<float> gout;              // split-K partial outputs of the tensor-core GEMMs
+  // m x ldc
+  DevPtr<double> w, q;
+  // per column scalars
+  DevPtr<double> rho, alpha, beta, alpha_prev, beta_prev, rnorm, rz0;
+  DevPtr<int32_t> active, iters, stop;
+  DevPtr<double> tdiag, toff;      // c x L Lanczos tridiagonals
+  DevPtr<double> part;             // dot partials [nblk][ldc]
+  DevPtr<double> quads;            // e1^T log(T) e1 per column
+  DevPtr<double> qlwork;           // QL scratch (c x 2L)
+  DevPtr<int32_t> num_active;      // device counter
+  int nblk = 0;
+};
+
+struct Handle {
+  int64_t n = 0;
+  int m = 0;
+  double gamma = 0;
+  int cov = 0;
+  cudaStream_t stream = nullptr;
+  Grid grid;
+  DevPtr<double> xs, ys, ind_x, ind_y;     // internal-order coordinates; inducing points
+  DevPtr<int64_t> perm, iperm, rowptr;     // perm[internal] = original
+  DevPtr<int32_t> col, cell_start, cell_count;
+  int64_t nnz = 0;
+  DevPtr<unsigned> err_buf;
+  unsigned* err = nullptr;
+  Operator op;
+  CGState cg;
+  Workspace ws;
+  DevPtr<double> y;                        // response in internal order
+  DevPtr<double> outs;                     // device results [loglik, logdet, quad, g0, g1, g2, se, ...]
+  double* host_pinned = nullptr;           // pinned mirror of small results
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// building blocks
+// ---------------------------------------------------------------------------
+template <typename T>
+void exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s);
+Grid make_grid(const double bb[4], double gamma, int64_t n);
+void build_structure(Handle& H, const double* locs_host);
+void build_cross_structure(Handle& H, const double* qx, const double* qy, int64_t nq,
+                           DevPtr<int64_t>& rowptr, DevPtr<int32_t>& col, int64_t& nnz);
+void export_csr(Handle& H, int64_t* rowptr_host, int32_t* col_host);
+
+void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+           const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+           int64_t ldc, const double* scale);
+void cholesky(double* A, int64_t lda, int m, unsigned* err, cudaStream_t s);
+void trsm_lower(Workspace& ws, const double* L, int64_t ldl, int m, double* B, int64_t ldb, int r,
+                cudaStream_t s);
+void lower_inverse(Workspace& ws, const double* L, int m, double* Li, cudaStream_t s);
+void logdet_from_cholesky(const double* L, int m, double* out_dev, cudaStream_t s);
+
+unsigned read_err(Handle& H);   // synchronises the stream
+void check_err(Handle& H);      // throws on a set error bit
+
+}  // namespace fsa

@@ -1,0 +1,58 @@
+// Declarations shared by the solver translation units.
+#pragma once
+#include "fsa_internal.cuh"
+
+namespace fsa {
+
+struct CGLayout {
+  int64_t n = 0;
+  int c = 0, ldc = 0, L = 0, threads = 32, nblk = 1;
+  int64_t chunk = 1;
+  void setup(int64_t n_, int c_, int L_);
+};
+
+struct LoglikResult {
+  double loglik = 0, logdet = 0, yu = 0, grad[3] = {0, 0, 0}, se = 0, logdetP = 0;
+  int iters_max = 0, iters_y = 0;
+  double resid_y = 0;
+  bool converged = true;
+  float ms = 0;
+};
+
+void cov_cross(Handle& H, int64_t np, const double* px, const double* py, int nq, const double* qx,
+               const double* qy, const fsa_theta& th, int deriv, double* out, int64_t ld);
+void build_mspace(Handle& H, const fsa_theta& th);
+void finish_core(Handle& H);
+void build_operator_fp64(Handle& H, const fsa_theta& th);
+void build_operator_mixed(Handle& H, const fsa_theta& th);
+void ensure_operator(Handle& H, const fsa_theta& th, int precision);
+void ensure_cg(Handle& H, const CGLayout& lay, bool fp64);
+void sum_log_D(Handle& H, const double* D, double* scal);
+
+LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o);
+void apply_operator(Handle& H, int which, const double* v_dev_internal, int k, double* out_dev_internal);
+
+// kernels used across units
+__global__ void k_eps1(int m, int l, int kind, uint64_t key, double* __restrict__ E, int64_t lde);
+__global__ void k_gather_y(int64_t n, const int64_t* __restrict__ perm, const double* __restrict__ y,
+                           double* __restrict__ y_int, unsigned* __restrict__ err);
+template <typename T>
+__global__ void k_probe_finish(int64_t n, int l, int ldc, int kind, uint64_t key, const int64_t* __restrict__ perm,
+                               const double* __restrict__ y_int, const double* __restrict__ D, T* __restrict__ B);
+template <typename T, typename AT>
+__global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ colidx, const double* __restrict__ vals,
+                              const double* __restrict__ xs, const double* __restrict__ ys, const T* __restrict__ X,
+                              const T* __restrict__ Y, const AT* __restrict__ A, const AT* __restrict__ B,
+                              const AT* __restrict__ F, int64_t lda, int cov, double s1, double rho, double nug,
+                              double gamma, double* __restrict__ part);
+__global__ void k_grad_lowrank(int m, int c, int ldc, const double* __restrict__ AX, const double* __restrict__ AY,
+                               const double* __restrict__ BX, const double* __restrict__ BY,
+                               const double* __restrict__ EAY, double s1, double* __restrict__ out2);
+__global__ void k_assemble(int64_t n, int c, int exact_weight, const double* __restrict__ quads,
+                           const double* __restrict__ rz0, const double* __restrict__ scal,
+                           const double* __restrict__ part_yu, int nblk_yu, int ldc,
+                           const double* __restrict__ gpart, int ngpart, const double* __restrict__ glow,
+                           int want_grad, double* __restrict__ outs);
+
+}  // namespace fsa

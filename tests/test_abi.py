@@ -1,0 +1,69 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads and exports
+every entry point that include/fsa.h declares (no compute call needs a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(fsa_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2405_14492_gb300 import build as B
+    return B.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for want in ("fsa_build", "fsa_loglik_grad", "fsa_predict", "fsa_free", "fsa_get_csr", "fsa_matvec"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [s for s in sorted(_declared_symbols()) if not hasattr(lib, s)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_host_only_entry_points(libpath):
+    from paper_2405_14492_gb300 import _native as N
+    o = N.default_opts()
+    assert o.num_probes == 50 and abs(o.cg_tol - 1e-3) < 1e-15 and o.want_grad == 1
+    assert N.lib().fsa_status_string(3) == b"FSA_ERR_NOT_PD"
+    b64 = N.lib().fsa_footprint_bytes(10 ** 6, 1000, 2 * 10 ** 7, 64, 0)
+    b16 = N.lib().fsa_footprint_bytes(10 ** 6, 1000, 2 * 10 ** 7, 64, 1)
+    assert b64 > b16 > 10 ** 9
+
+
+def test_argument_errors_need_no_gpu(libpath):
+    """Invalid arguments are rejected on the host before any device call."""
+    import numpy as np
+    from paper_2405_14492_gb300 import _native as N
+    h = ctypes.c_void_p()
+    locs = np.zeros((1, 2))
+    st = N.lib().fsa_build(N.ptr(locs), 1, N.ptr(locs), 1, 0.1, 0, None, ctypes.byref(h))
+    assert st == 1 and h.value is None
+    locs = np.random.default_rng(0).random((10, 2))
+    st = N.lib().fsa_build(N.ptr(locs), 10, N.ptr(locs), 11, 0.1, 0, None, ctypes.byref(h))
+    assert st == 1
+    st = N.lib().fsa_build(N.ptr(locs), 10, N.ptr(locs), 3, -1.0, 0, None, ctypes.byref(h))
+    assert st == 1
+    bad = locs.copy()
+    bad[0, 0] = np.nan
+    st = N.lib().fsa_build(N.ptr(locs), 10, N.ptr(bad), 3, 0.1, 0, None, ctypes.byref(h))
+    assert st == 5
+    assert b"inducing" in N.lib().fsa_last_error()
