@@ -150,6 +150,24 @@ __global__ void k_coldot(int64_t n, int c, int ldc, int64_t chunk, const T* __re
   FSA_ROWLOOP_END
 }
 
+// part[blk * ldc] = sum over the block's rows of y_i U[i][0]
+template <typename T>
+__global__ void k_dot_col0(int64_t n, int ldc, int64_t chunk, const double* __restrict__ y,
+                           const T* __restrict__ U, double* __restrict__ part) {
+  if (threadIdx.x != 0) return;
+  int64_t r0 = (int64_t)blockIdx.x * chunk;
+  int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
+  double s = 0.0;
+  for (int64_t i = r0; i < r1; ++i) s += y[i] * (double)U[i * ldc];
+  part[(int64_t)blockIdx.x * ldc] = s;
+}
+
+template <typename T>
+__global__ void k_copy_col0(int64_t n, int ldc, const T* __restrict__ src, T* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i * ldc] = src[i * ldc];
+}
+
 #undef FSA_ROWLOOP_BEGIN
 #undef FSA_ROWLOOP_END
 #undef FSA_ACC
@@ -163,7 +181,7 @@ __device__ __forceinline__ double sum_part(const double* part, int nblk, int ldc
   return s;
 }
 
-__global__ void k_cg_init(int c, int ldc, int nblk, const double* __restrict__ part, double* __restrict__ rho,
+static __global__ void k_cg_init(int c, int ldc, int nblk, const double* __restrict__ part, double* __restrict__ rho,
                           double* __restrict__ rz0, double* __restrict__ alpha_prev, double* __restrict__ beta_prev,
                           double* __restrict__ beta, int32_t* __restrict__ active, int32_t* __restrict__ iters,
                           int32_t* __restrict__ stop, unsigned* __restrict__ err) {
@@ -181,7 +199,7 @@ __global__ void k_cg_init(int c, int ldc, int nblk, const double* __restrict__ p
   stop[col] = 0;
 }
 
-__global__ void k_cg_alpha(int c, int ldc, int nblk, const double* __restrict__ part, const double* __restrict__ rho,
+static __global__ void k_cg_alpha(int c, int ldc, int nblk, const double* __restrict__ part, const double* __restrict__ rho,
                            double* __restrict__ alpha, const int32_t* __restrict__ active, unsigned* __restrict__ err) {
   int col = threadIdx.x;
   if (col >= ldc) return;
@@ -194,7 +212,7 @@ __global__ void k_cg_alpha(int c, int ldc, int nblk, const double* __restrict__ 
   alpha[col] = a;
 }
 
-__global__ void k_cg_resid(int c, int ldc, int nblk, const double* __restrict__ part, double* __restrict__ rnorm,
+static __global__ void k_cg_resid(int c, int ldc, int nblk, const double* __restrict__ part, double* __restrict__ rnorm,
                            const int32_t* __restrict__ active, int32_t* __restrict__ stop, double tol, int fixed) {
   int col = threadIdx.x;
   if (col >= ldc || col >= c || !active[col]) return;
@@ -203,7 +221,7 @@ __global__ void k_cg_resid(int c, int ldc, int nblk, const double* __restrict__ 
   stop[col] = (!fixed && rn < tol) ? 1 : 0;
 }
 
-__global__ void k_cg_beta(int c, int ldc, int nblk, int l, int L, const double* __restrict__ part,
+static __global__ void k_cg_beta(int c, int ldc, int nblk, int l, int L, const double* __restrict__ part,
                           double* __restrict__ rho, const double* __restrict__ alpha, double* __restrict__ beta,
                           double* __restrict__ alpha_prev, double* __restrict__ beta_prev,
                           int32_t* __restrict__ active, int32_t* __restrict__ iters, const int32_t* __restrict__ stop,
@@ -249,7 +267,7 @@ __global__ void k_cg_beta(int c, int ldc, int nblk, int l, int L, const double* 
 // Wilkinson-type shifts (Bowdler, Martin, Reinsch & Wilkinson 1968; EISPACK
 // tql1/tql2), carrying only the first row of the eigenvector matrix.
 // ---------------------------------------------------------------------------
-__global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, const double* __restrict__ tdiag,
+static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, const double* __restrict__ tdiag,
                       const double* __restrict__ toff, double* __restrict__ work, double* __restrict__ quads,
                       unsigned* __restrict__ err) {
   int col = 1 + blockIdx.x * blockDim.x + threadIdx.x;   // probe columns 1..c-1

@@ -1,19 +1,673 @@
-// Mixed-precision form (placeholder until the tensor-core path lands).
+// Mixed-precision form of the FSA operator, preconditioner and block PCG.
+//
+//   A = Sigma_nm L_m^-T is formed on the tensor cores from hi/lo BF16 splits
+//   of Sigma_nm (FP32 kernel values) and of L_m^-1 (FP64), three products
+//   (hi.hi + hi.lo + lo.hi) with FP32 accumulation, then rounded once to BF16:
+//   that rounded A~ DEFINES the operator Sigma_dag = Sigma_s~ + A~ A~^T, and the
+//   same A~ is used in the residual values (a_i . a_j), in D_s, in the
+//   Woodbury core M = I + A~^T D^-1 A~, in log det P_hat and in the probes, so
+//   the preconditioner applied is the one whose log-determinant is added
+//   (paper §3.3: log det Sigma = log det(P^-1/2 Sigma P^-1/2) + log det P).
+//   Vector operands of the tensor-core products are split hi/lo BF16 (stacked
+//   along N, summed in the epilogue) so that each product is linear in the
+//   vector to ~2^-16 relative.  Vectors are FP32; CG scalars, dot-product
+//   accumulation, the m x m Cholesky factors / inverse and the Lanczos
+//   eigen-quadrature are FP64.
+#include "fsa_kernels.cuh"
 #include "fsa_solver.cuh"
+#include "fsa_tc.cuh"
 
 namespace fsa {
 
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Sigma_nm (or its rho-derivative) in FP32, split hi/lo BF16, n x m_pad (zero padded)
+__global__ void k_cov_nm_split(int64_t n, int m, int m_pad, const double* __restrict__ xs,
+                               const double* __restrict__ ys, const double* __restrict__ ix,
+                               const double* __restrict__ iy, int cov, float s1, float rho, int deriv,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  int64_t total = n * m_pad;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / m_pad;
+    int k = (int)(t - i * m_pad);
+    float v = 0.f;
+    if (k < m) {
+      float dx = (float)(xs[i] - ix[k]), dy = (float)(ys[i] - iy[k]);
+      float d = sqrtf(dx * dx + dy * dy);
+      if (cov == 0) {
+        float e = expf(-d / rho);
+        v = deriv ? s1 * (d / (rho * rho)) * e : s1 * e;
+      } else {
+        float x = 1.7320508f * d / rho;
+        float e = expf(-x);
+        v = deriv ? s1 * (x * x / rho) * e : s1 * (1.f + x) * e;
+      }
+    }
+    split_bf16(v, hi[t], lo[t]);
+  }
+}
+
+// FP64 rows x cols (ld) -> BF16 hi/lo rows_pad x cols_pad (zero padded)
+__global__ void k_split_f64(int rows, int cols, const double* __restrict__ src, int64_t lds, int rows_pad,
+                            int cols_pad, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  int64_t total = (int64_t)rows_pad * cols_pad;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / cols_pad), c = (int)(t % cols_pad);
+    double v = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.0;
+    __nv_bfloat16 h = __double2bfloat16(v);
+    hi[t] = h;
+    lo[t] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+__global__ void k_f32_to_bf16(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = __float2bfloat16_rn(src[t]);
+}
+
+// dst (cols x ld_dst) = src^T, src rows x cols (ld_src); 32 x 32 tiles through shared memory
+__global__ void k_transpose_bf16(int64_t rows, int cols, const __nv_bfloat16* __restrict__ src, int64_t ld_src,
+                                 __nv_bfloat16* __restrict__ dst, int64_t ld_dst) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  int64_t r0 = (int64_t)blockIdx.x * 32;
+  int c0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    int64_t r = r0 + k;
+    int c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[r * ld_src + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    int c = c0 + k;
+    int64_t r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[(int64_t)c * ld_dst + r] = tile[threadIdx.x][k];
+  }
+}
+
+// residual values from the BF16 A~ (FP32 products of BF16 values are exact;
+// FP32 accumulation), values kept in FP64 and FP32; D rounded to FP32 once so
+// that every consumer sees the same diagonal
+__global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ col, const double* __restrict__ xs,
+                                   const double* __restrict__ ys, const __nv_bfloat16* __restrict__ A, int cov,
+                                   double s1, double rho, double nug, double gamma, double* __restrict__ vals,
+                                   float* __restrict__ vals32, double* __restrict__ D, float* __restrict__ D32,
+                                   float* __restrict__ Dinv32) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int np2 = m_pad / 2;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const __nv_bfloat162* ai = reinterpret_cast<const __nv_bfloat162*>(A + i * m_pad);
+    double xi = xs[i], yi = ys[i];
+    for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+      int j = col[t];
+      const __nv_bfloat162* aj = reinterpret_cast<const __nv_bfloat162*>(A + (int64_t)j * m_pad);
+      float s = 0.f;
+      for (int k = lane; k < np2; k += 32) {
+        float2 a = __bfloat1622float2(ai[k]);
+        float2 b = __bfloat1622float2(aj[k]);
+        s = fmaf(a.x, b.x, s);
+        s = fmaf(a.y, b.y, s);
+      }
+      s = warp_sum(s);
+      if (lane == 0) {
+        double v;
+        if (j == i) {
+          float dv = (float)(fmax(s1 - (double)s, 0.0) + nug);
+          v = (double)dv;
+          D[i] = v;
+          D32[i] = dv;
+          Dinv32[i] = 1.0f / dv;
+        } else {
+          double d = sqrt(sqdist_rn(xi, yi, xs[j], ys[j]));
+          v = (s1 * matern_r(cov, d, rho) - (double)s) * wendland(d, gamma);
+        }
+        vals[t] = v;
+        vals32[t] = (float)v;
+      }
+    }
+  }
+}
+
+// Y^T = (D^-1 A~)^T split hi/lo, from A~^T (m_pad x n_pad)
+__global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __nv_bfloat16* __restrict__ At,
+                                   const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo) {
+  int64_t total = (int64_t)m_pad * n_pad;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t % n_pad;
+    float v = i < n ? __bfloat162float(At[t]) * Dinv[i] : 0.f;
+    split_bf16(v, hi[t], lo[t]);
+  }
+}
+
+// out[r][c] = sum_s part[s][r][c] (+1 on the diagonal), FP64
+__global__ void k_reduce_splits(int splits, int rows, int cols, const float* __restrict__ part, int64_t ldp,
+                                int64_t split_stride, double* __restrict__ out, int64_t ldo, int add_identity) {
+  int64_t total = (int64_t)rows * cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / cols), c = (int)(t % cols);
+    double s = (add_identity && r == c) ? 1.0 : 0.0;
+    for (int z = 0; z < splits; ++z) s += (double)part[(int64_t)z * split_stride + (int64_t)r * ldp + c];
+    out[(int64_t)r * ldo + c] = s;
+  }
+}
+
+// src (n x ldc FP32) optionally scaled by rowscale -> dst (2 ldc x n_pad BF16): rows
+// 0..ldc-1 hi, ldc..2ldc-1 lo; 64 points per block through shared memory
+constexpr int kSTRows = 64;
+__global__ void k_split_transpose(int64_t n, int c, int ldc, const float* __restrict__ src,
+                                  const float* __restrict__ rowscale, int64_t n_pad,
+                                  __nv_bfloat16* __restrict__ dst) {
+  extern __shared__ __nv_bfloat16 tl[];   // [2 ldc][kSTRows + 2]
+  const int W = kSTRows + 2;
+  int64_t r0 = (int64_t)blockIdx.x * kSTRows;
+  for (int t = threadIdx.x; t < kSTRows * ldc; t += blockDim.x) {
+    int rr = t / ldc, cc = t % ldc;
+    int64_t r = r0 + rr;
+    float v = 0.f;
+    if (r < n && cc < c) {
+      v = src[r * ldc + cc];
+      if (rowscale) v *= rowscale[r];
+    }
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    tl[cc * W + rr] = h;
+    tl[(ldc + cc) * W + rr] = l;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * ldc * kSTRows; t += blockDim.x) {
+    int cc = t / kSTRows, rr = t % kSTRows;
+    int64_t r = r0 + rr;
+    if (r < n_pad) dst[(int64_t)cc * n_pad + r] = (r < n) ? tl[cc * W + rr] : __float2bfloat16(0.f);
+  }
+}
+
+// q (m x ldc FP64) -> (2 ldc x m_pad) BF16 hi/lo, K-major (q transposed)
+__global__ void k_split_q(int m, int c, int ldc, int m_pad, const double* __restrict__ q,
+                          __nv_bfloat16* __restrict__ dst) {
+  int64_t total = (int64_t)ldc * m_pad;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int cc = (int)(t / m_pad), k = (int)(t % m_pad);
+    float v = (cc < c && k < m) ? (float)q[(int64_t)k * ldc + cc] : 0.f;
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    dst[(int64_t)cc * m_pad + k] = h;
+    dst[(int64_t)(ldc + cc) * m_pad + k] = l;
+  }
+}
+
+// eps1^T (l16 x m_pad) hi/lo BF16 (Rademacher values are exact in BF16)
+__global__ void k_eps1_split(int m, int l, int l16, int m_pad, int kind, uint64_t key, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo) {
+  int64_t total = (int64_t)l16 * m_pad;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(t / m_pad), k = (int)(t % m_pad);
+    float v = (p < l && k < m) ? (float)probe_at(kind, key, (uint64_t)p * m + k) : 0.f;
+    split_bf16(v, hi[t], lo[t]);
+  }
+}
+
+// R[:,0] = y; R[:,1+p] = (A~ eps1)[:,p] + sqrt(D_i) eps2
+__global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kind, uint64_t key,
+                                     const int64_t* __restrict__ perm, const double* __restrict__ y_int,
+                                     const float* __restrict__ D32, const float* __restrict__ Zp,
+                                     float* __restrict__ R) {
+  int64_t total = n * ldc;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / ldc;
+    int c = (int)(t - i * ldc);
+    float v = 0.f;
+    if (c == 0) v = (float)y_int[i];
+    else if (c <= l)
+      v = (float)((double)Zp[i * ldz + (c - 1)] +
+                  sqrt((double)D32[i]) * probe_at(kind, key, (uint64_t)(c - 1) * n + perm[i]));
+    R[t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operator build
+// ---------------------------------------------------------------------------
+static inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
 void build_operator_mixed(Handle& H, const fsa_theta& th) {
-  (void)H;
-  (void)th;
-  throw Error{FSA_ERR_UNSUPPORTED, "mixed precision not built"};
+  Operator& op = H.op;
+  cudaStream_t s = H.stream;
+  int64_t n = H.n;
+  int m = H.m;
+  int m_pad = round_up(m, 64);
+  int64_t n_pad = ((n + 63) / 64) * 64;
+  op.m_pad = m_pad;
+  op.n_pad = n_pad;
+  build_mspace(H, th);
+  size_t nm = (size_t)n * m_pad;
+  // A~ = bf16( Sigma_nm L^-T ) with the split products
+  {
+    DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
+    DevPtr<float> A32(nm);
+    k_cov_nm_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>(n, m, m_pad, H.xs.p, H.ys.p, H.ind_x.p, H.ind_y.p,
+                                                                H.cov, (float)th.sigma1_sq, (float)th.rho, 0,
+                                                                Khi.p, Klo.p);
+    FSA_CHECK_LAUNCH();
+    k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
+                                                                       Llo.p);
+    FSA_CHECK_LAUNCH();
+    TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+    TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128), mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
+    TcGemm g;
+    g.a[0] = &mKh; g.a[1] = &mKl; g.num_a = 2;
+    g.b[0] = &mLh; g.b[1] = &mLl; g.num_b = 2;
+    g.pairs = 1u | 2u | 4u;   // hi.hi + hi.lo + lo.hi
+    g.M = (int)n; g.N = m_pad; g.K = m_pad; g.bn = 128;
+    g.out = A32.p; g.ldo = m_pad;
+    tc_gemm(g, H.err, s);
+    op.Ab.ensure(nm);
+    k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  }
+  op.Atb.ensure((size_t)m_pad * n_pad);
+  FSA_CUDA(cudaMemsetAsync(op.Atb.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
+  k_transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (m_pad + 31) / 32), dim3(32, 8), 0, s>>>(n, m_pad, op.Ab.p, m_pad,
+                                                                                          op.Atb.p, n_pad);
+  FSA_CHECK_LAUNCH();
+  // residual values, D
+  op.vals.ensure(H.nnz);
+  op.vals32.ensure(H.nnz);
+  op.D.ensure(n);
+  op.D32.ensure(n);
+  op.Dinv32.ensure(n);
+  k_csr_values_mixed<<<grid_for(n * 32, 256, 152 * 64), 256, 0, s>>>(
+      n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, op.Ab.p, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma,
+      op.vals.p, op.vals32.p, op.D.p, op.D32.p, op.Dinv32.p);
+  FSA_CHECK_LAUNCH();
+  // Woodbury core M = I + A~^T D^-1 A~ on the tensor cores (split-K, FP64 reduction)
+  {
+    size_t mn = (size_t)m_pad * n_pad;
+    DevPtr<__nv_bfloat16> Yhi(mn), Ylo(mn);
+    k_scale_cols_split<<<grid_for((int64_t)mn, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, op.Dinv32.p, Yhi.p,
+                                                                    Ylo.p);
+    FSA_CHECK_LAUNCH();
+    TmaMap mAt = make_tma_bf16(op.Atb.p, m_pad, n, n_pad, 128);
+    TmaMap mYh = make_tma_bf16(Yhi.p, m_pad, n, n_pad, 128), mYl = make_tma_bf16(Ylo.p, m_pad, n, n_pad, 128);
+    TcGemm g;
+    g.a[0] = &mAt; g.num_a = 1;
+    g.b[0] = &mYh; g.b[1] = &mYl; g.num_b = 2;
+    g.pairs = 1u | 2u;
+    g.M = m_pad; g.N = m_pad; g.K = (int)n; g.bn = 128;
+    g.splits = tc_pick_splits(g.M, g.N, g.K, g.bn);
+    int kb = (g.K + 63) / 64, per = (kb + g.splits - 1) / g.splits, splits = (kb + per - 1) / per;
+    DevPtr<float> part((size_t)splits * m_pad * m_pad);
+    g.out = part.p; g.ldo = m_pad; g.split_stride = (int64_t)m_pad * m_pad;
+    tc_gemm(g, H.err, s);
+    op.Mp.ensure((size_t)m * m);
+    k_reduce_splits<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(splits, m, m, part.p, m_pad, g.split_stride,
+                                                                  op.Mp.p, m, 1);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  }
+  check_err(H);
+  finish_core(H);
+  op.theta = th;
+  op.precision = FSA_MIXED_BF16;
+  op.valid = true;
+}
+
+// ---------------------------------------------------------------------------
+// per-iteration products on the tensor cores
+// ---------------------------------------------------------------------------
+struct MixedCtx {
+  int ldc = 0, c = 0, m_pad = 0;
+  int64_t n = 0, n_pad = 0;
+  int splits_w = 1;
+  TmaMap mAt, mA, mX, mQ;
+  float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
+};
+
+// w (FP64, m x ldc) = A~^T X  where X = rows of `src` (scaled by rowscale), split hi/lo
+static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w) {
+  cudaStream_t s = H.stream;
+  CGState& g = H.cg;
+  int ldc = C.ldc;
+  size_t smem = (size_t)2 * ldc * (kSTRows + 2) * sizeof(__nv_bfloat16);
+  k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, src, rowscale,
+                                                                                    C.n_pad, g.Xb.p);
+  FSA_CHECK_LAUNCH();
+  TcGemm t;
+  t.a[0] = &C.mAt; t.num_a = 1;
+  t.b[0] = &C.mX; t.num_b = 1;
+  t.pairs = 1u;
+  t.M = C.m_pad; t.N = 2 * ldc; t.K = (int)C.n; t.bn = 2 * ldc;
+  t.halves = 1;
+  t.splits = C.splits_w;
+  int kb = (t.K + 63) / 64, per = (kb + t.splits - 1) / t.splits, splits = (kb + per - 1) / per;
+  t.out = C.wpart; t.ldo = ldc; t.split_stride = (int64_t)C.m_pad * ldc;
+  tc_gemm(t, H.err, s);
+  k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
+                                                                    t.split_stride, w, ldc, 0);
+  FSA_CHECK_LAUNCH();
+}
+
+// S (FP32 n x ldc) = A~ q, q FP64 m x ldc
+static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S) {
+  cudaStream_t s = H.stream;
+  CGState& g = H.cg;
+  int ldc = C.ldc;
+  k_split_q<<<grid_for((int64_t)ldc * C.m_pad, 256), 256, 0, s>>>(H.m, C.c, ldc, C.m_pad, q, g.qb.p);
+  FSA_CHECK_LAUNCH();
+  TcGemm t;
+  t.a[0] = &C.mA; t.num_a = 1;
+  t.b[0] = &C.mQ; t.num_b = 1;
+  t.pairs = 1u;
+  t.M = (int)C.n; t.N = 2 * ldc; t.K = C.m_pad; t.bn = 2 * ldc;
+  t.halves = 1;
+  t.out = S; t.ldo = ldc;
+  tc_gemm(t, H.err, s);
+}
+
+// S = A~ M^-1 A~^T (D^-1 R)
+static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
+  CGState& g = H.cg;
+  Operator& op = H.op;
+  mixed_AtX(H, C, R, op.Dinv32.p, g.w.p);
+  dgemm(H.ws, H.stream, false, false, H.m, C.c, H.m, 1.0, op.Minv.p, H.m, g.w.p, C.ldc, 0.0, g.q.p, C.ldc,
+        nullptr);
+  mixed_Aq(H, C, g.q.p, S);
 }
 
 LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
-  (void)H;
-  (void)th;
-  (void)o;
-  throw Error{FSA_ERR_UNSUPPORTED, "mixed precision not built"};
+  cudaStream_t s = H.stream;
+  Operator& op = H.op;
+  CGState& g = H.cg;
+  int64_t n = H.n;
+  int m = H.m;
+  int l = o.num_probes;
+  FSA_REQUIRE(l + 1 <= 128, FSA_ERR_UNSUPPORTED, "mixed precision supports at most 127 probes");
+  CGLayout lay;
+  int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
+  lay.setup(n, l + 1, L);
+  ensure_cg(H, lay, false);
+  int ldc = lay.ldc;
+  size_t nc = (size_t)n * ldc;
+  g.U32.ensure(nc); g.R32.ensure(nc); g.Z32.ensure(nc); g.H32.ensure(nc); g.V32.ensure(nc);
+  g.S32.ensure(nc); g.W032.ensure(nc);
+  MixedCtx C;
+  C.ldc = ldc; C.c = lay.c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
+  g.Xb.ensure((size_t)2 * ldc * C.n_pad);
+  g.qb.ensure((size_t)2 * ldc * C.m_pad);
+  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
+  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
+  C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
+  C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);
+  DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
+  C.wpart = wpart_buf.p;
+  dim3 cgrid(lay.nblk), cblk(lay.threads);
+  // probes: R = [y, A~ eps1 + D^1/2 eps2]
+  {
+    int l16 = round_up(l, 16);
+    DevPtr<__nv_bfloat16> Ehi((size_t)l16 * C.m_pad), Elo((size_t)l16 * C.m_pad);
+    DevPtr<float> Zp((size_t)n * l16);
+    k_eps1_split<<<grid_for((int64_t)l16 * C.m_pad, 256), 256, 0, s>>>(m, l, l16, C.m_pad, o.probe,
+                                                                       rng_key(o.seed, kStreamEps1), Ehi.p, Elo.p);
+    FSA_CHECK_LAUNCH();
+    TmaMap mEh = make_tma_bf16(Ehi.p, l16, C.m_pad, C.m_pad, l16), mEl = make_tma_bf16(Elo.p, l16, C.m_pad, C.m_pad, l16);
+    TcGemm t;
+    t.a[0] = &C.mA; t.num_a = 1;
+    t.b[0] = &mEh; t.b[1] = &mEl; t.num_b = 2;
+    t.pairs = 1u | 2u;
+    t.M = (int)n; t.N = l16; t.K = C.m_pad; t.bn = l16;
+    t.out = Zp.p; t.ldo = l16;
+    tc_gemm(t, H.err, s);
+    k_probe_finish_mixed<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, l16, o.probe,
+                                                                    rng_key(o.seed, kStreamEps2), H.perm.p, H.y.p,
+                                                                    op.D32.p, Zp.p, g.R32.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  }
+  FSA_CUDA(cudaMemsetAsync(g.U32.p, 0, nc * sizeof(float), s));
+  FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
+  FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
+  lowrank_mixed(H, C, g.R32.p, g.S32.p);
+  k_z_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+                                           g.part.p);
+  FSA_CHECK_LAUNCH();
+  k_cg_init<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.rz0.p, g.alpha_prev.p, g.beta_prev.p,
+                               g.beta.p, g.active.p, g.iters.p, g.stop.p, H.err);
+  FSA_CHECK_LAUNCH();
+  FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  k_spmm_fused<float, float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals32.p,
+                                                     g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
+  FSA_CHECK_LAUNCH();
+  int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
+  for (int it = 0; it < L; ++it) {
+    k_cg_alpha<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.alpha.p, g.active.p, H.err);
+    FSA_CHECK_LAUNCH();
+    k_ur_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
+                                              op.Dinv32.p, nullptr, g.alpha.p, g.active.p, g.part.p);
+    FSA_CHECK_LAUNCH();
+    k_cg_resid<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rnorm.p, g.active.p, g.stop.p, o.cg_tol,
+                                  o.fixed_iters > 0);
+    FSA_CHECK_LAUNCH();
+    lowrank_mixed(H, C, g.R32.p, g.S32.p);
+    k_z_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+                                             g.part.p);
+    FSA_CHECK_LAUNCH();
+    k_cg_beta<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, it, L, g.part.p, g.rho.p, g.alpha.p, g.beta.p,
+                                 g.alpha_prev.p, g.beta_prev.p, g.active.p, g.iters.p, g.stop.p, g.tdiag.p,
+                                 g.toff.p, g.num_active.p, H.err);
+    FSA_CHECK_LAUNCH();
+    k_spmm_fused<float, float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals32.p,
+                                                       g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
+    FSA_CHECK_LAUNCH();
+    if (o.fixed_iters <= 0) {
+      FSA_CUDA(cudaMemcpyAsync(pin_active, g.num_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      FSA_CUDA(cudaStreamSynchronize(s));
+      if (*pin_active == 0) break;
+    }
+  }
+  k_slq<<<(lay.c + 63) / 64, 64, 0, s>>>(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.qlwork.p, g.quads.p, H.err);
+  FSA_CHECK_LAUNCH();
+  DevPtr<double> ypart((size_t)lay.nblk * ldc);
+  k_dot_col0<float><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U32.p, ypart.p);
+  FSA_CHECK_LAUNCH();
+  H.outs.ensure(16);
+  DevPtr<double> gbuf;
+  if (o.want_grad) {
+    // X = U (u in column 0), Y = W with u in column 0
+    FSA_CUDA(cudaMemcpyAsync(g.Z32.p, g.W032.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_copy_col0<float><<<grid_for(n, 256), 256, 0, s>>>(n, ldc, g.U32.p, g.Z32.p);
+    FSA_CHECK_LAUNCH();
+    int c = lay.c;
+    int m_pad = C.m_pad;
+    size_t mc = (size_t)m * ldc;
+    size_t nm = (size_t)n * m_pad;
+    DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc), E((size_t)m * m), T1((size_t)m * m);
+    mixed_AtX(H, C, g.U32.p, nullptr, AX.p);
+    mixed_AtX(H, C, g.Z32.p, nullptr, AY.p);
+    DevPtr<__nv_bfloat16> Bb(nm), Fb(nm);
+    {
+      // B = dK L^-T (split products), and B^T for the m-space projections
+      DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
+      DevPtr<float> B32(nm);
+      k_cov_nm_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>(n, m, m_pad, H.xs.p, H.ys.p, H.ind_x.p, H.ind_y.p,
+                                                                  H.cov, (float)th.sigma1_sq, (float)th.rho, 1,
+                                                                  Khi.p, Klo.p);
+      FSA_CHECK_LAUNCH();
+      k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
+                                                                         Llo.p);
+      FSA_CHECK_LAUNCH();
+      TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+      TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128),
+             mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
+      TcGemm t;
+      t.a[0] = &mKh; t.a[1] = &mKl; t.num_a = 2;
+      t.b[0] = &mLh; t.b[1] = &mLl; t.num_b = 2;
+      t.pairs = 1u | 2u | 4u;
+      t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
+      t.out = B32.p; t.ldo = m_pad;
+      tc_gemm(t, H.err, s);
+      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Bb.p);
+      FSA_CHECK_LAUNCH();
+      // E = L^-1 dSigma_m L^-T (FP64), F = A~ E (split products)
+      DevPtr<double> dSm((size_t)m * m);
+      cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
+      dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
+      dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, E.p, m, nullptr);
+      k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, E.p, m, m_pad, m_pad, Lhi.p, Llo.p);
+      FSA_CHECK_LAUNCH();
+      TcGemm f;
+      f.a[0] = &C.mA; f.num_a = 1;
+      f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
+      f.pairs = 1u | 2u;
+      f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
+      f.out = B32.p; f.ldo = m_pad;
+      FSA_CUDA(cudaStreamSynchronize(s));
+      // B32 now free for F
+      tc_gemm(f, H.err, s);
+      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Fb.p);
+      FSA_CHECK_LAUNCH();
+      FSA_CUDA(cudaStreamSynchronize(s));
+    }
+    {
+      DevPtr<__nv_bfloat16> Bt((size_t)m_pad * C.n_pad);
+      FSA_CUDA(cudaMemsetAsync(Bt.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * C.n_pad, s));
+      k_transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (m_pad + 31) / 32), dim3(32, 8), 0, s>>>(n, m_pad, Bb.p,
+                                                                                              m_pad, Bt.p, C.n_pad);
+      FSA_CHECK_LAUNCH();
+      MixedCtx CB = C;
+      CB.mAt = make_tma_bf16(Bt.p, m_pad, n, C.n_pad, 128);
+      mixed_AtX(H, CB, g.U32.p, nullptr, BX.p);
+      mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p);
+      FSA_CUDA(cudaStreamSynchronize(s));
+    }
+    dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
+    int ngpart = 152 * 8;
+    gbuf.alloc((size_t)ngpart * 3 + 2);
+    launch_grad_sparse_bf16(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th, gbuf.p);
+    k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq,
+                                             gbuf.p + (size_t)ngpart * 3);
+    FSA_CHECK_LAUNCH();
+    k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
+                                gbuf.p, ngpart, gbuf.p + (size_t)ngpart * 3, 1, H.outs.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  } else {
+    k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
+                                nullptr, 0, nullptr, 0, H.outs.p);
+    FSA_CHECK_LAUNCH();
+  }
+  LoglikResult res;
+  double outs[8];
+  FSA_CUDA(cudaMemcpyAsync(outs, H.outs.p, sizeof(outs), cudaMemcpyDeviceToHost, s));
+  std::vector<int32_t> iters(lay.c);
+  std::vector<double> rn(lay.c);
+  FSA_CUDA(cudaMemcpyAsync(iters.data(), g.iters.p, sizeof(int32_t) * lay.c, cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaMemcpyAsync(rn.data(), g.rnorm.p, sizeof(double) * lay.c, cudaMemcpyDeviceToHost, s));
+  int32_t nact = 0;
+  FSA_CUDA(cudaMemcpyAsync(&nact, g.num_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FSA_CUDA(cudaStreamSynchronize(s));
+  check_err(H);
+  res.loglik = outs[0];
+  res.logdet = outs[1];
+  res.yu = outs[2];
+  for (int q = 0; q < 3; ++q) res.grad[q] = outs[3 + q];
+  res.se = outs[6];
+  res.logdetP = outs[7];
+  res.iters_y = iters[0];
+  res.resid_y = rn[0];
+  for (int k = 0; k < lay.c; ++k) res.iters_max = std::max(res.iters_max, (int)iters[k]);
+  res.converged = o.fixed_iters > 0 || nact == 0;
+  return res;
+}
+
+__global__ void k_f64_to_f32_pad(int64_t n, int k, int ldk, const double* __restrict__ src, float* __restrict__ dst) {
+  int64_t total = n * ldk;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / ldk;
+    int c = (int)(t - i * ldk);
+    dst[t] = c < k ? (float)src[i * k + c] : 0.f;
+  }
+}
+
+__global__ void k_f32_to_f64_unpad(int64_t n, int k, int ldk, const float* __restrict__ src, double* __restrict__ dst) {
+  int64_t total = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / k;
+    int c = (int)(t - i * k);
+    dst[t] = (double)src[i * ldk + c];
+  }
+}
+
+// mixed-precision operator on vectors in internal order (n x k FP64):
+// 0: Sigma_dag v = Sigma_s~ v + A~ (A~^T v); 1: P_hat^-1 v; 2: Sigma_s~ v
+void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* out) {
+  cudaStream_t s = H.stream;
+  Operator& op = H.op;
+  CGState& g = H.cg;
+  int64_t n = H.n;
+  int m = H.m;
+  FSA_REQUIRE(k <= 128, FSA_ERR_UNSUPPORTED, "mixed matvec supports at most 128 columns");
+  CGLayout lay;
+  lay.setup(n, k, 1);
+  int ldc = lay.ldc;
+  size_t nc = (size_t)n * ldc;
+  DevPtr<float> V32(nc), S32(nc), O32(nc);
+  k_f64_to_f32_pad<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, k, ldc, v, V32.p);
+  FSA_CHECK_LAUNCH();
+  MixedCtx C;
+  C.ldc = ldc; C.c = k; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
+  g.Xb.ensure((size_t)2 * ldc * C.n_pad);
+  g.qb.ensure((size_t)2 * ldc * C.m_pad);
+  g.w.ensure((size_t)m * ldc);
+  g.q.ensure((size_t)m * ldc);
+  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
+  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
+  C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
+  C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);
+  DevPtr<float> wpart((size_t)C.splits_w * C.m_pad * ldc);
+  C.wpart = wpart.p;
+  DevPtr<double> part((size_t)lay.nblk * ldc), beta(ldc);
+  FSA_CUDA(cudaMemsetAsync(beta.p, 0, sizeof(double) * ldc, s));
+  if (which == 1) {
+    lowrank_mixed(H, C, V32.p, S32.p);
+    k_z_update<float><<<lay.nblk, lay.threads, 0, s>>>(n, k, ldc, lay.chunk, V32.p, S32.p, op.Dinv32.p, O32.p,
+                                                       part.p);
+    FSA_CHECK_LAUNCH();
+  } else {
+    if (which == 0) {
+      mixed_AtX(H, C, V32.p, nullptr, g.w.p);
+      mixed_Aq(H, C, g.w.p, S32.p);
+    } else {
+      FSA_CUDA(cudaMemsetAsync(S32.p, 0, nc * sizeof(float), s));
+    }
+    DevPtr<float> Hd(nc);
+    FSA_CUDA(cudaMemsetAsync(Hd.p, 0, nc * sizeof(float), s));
+    FSA_CUDA(cudaMemsetAsync(O32.p, 0, nc * sizeof(float), s));
+    k_spmm_fused<float, float><<<lay.nblk, lay.threads, 0, s>>>(n, k, ldc, lay.chunk, H.rowptr.p, H.col.p,
+                                                                 op.vals32.p, V32.p, S32.p, O32.p, Hd.p, beta.p,
+                                                                 part.p);
+    FSA_CHECK_LAUNCH();
+  }
+  k_f32_to_f64_unpad<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, ldc, O32.p, out);
+  FSA_CHECK_LAUNCH();
+  FSA_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace fsa

@@ -290,6 +290,15 @@ __global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* _
   }
 }
 
+void launch_grad_sparse_bf16(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
+                             const float* X, const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B,
+                             const __nv_bfloat16* F, const fsa_theta& th, double* part) {
+  k_grad_sparse<float, __nv_bfloat16><<<nblocks, 256, 0, H.stream>>>(
+      H.n, m_pad, c, ldc, H.rowptr.p, H.col.p, vals, H.xs.p, H.ys.p, X, Y, A, B, F, m_pad, H.cov, th.sigma1_sq,
+      th.rho, th.nugget, H.gamma, part);
+  FSA_CHECK_LAUNCH();
+}
+
 // low-rank part: sum_k w_k [ (A^T X_k).(A^T Y_k) / s1 ,
 //   (B^T X_k).(A^T Y_k) + (A^T X_k).(B^T Y_k) - (A^T X_k).(E A^T Y_k) ]
 __global__ void k_grad_lowrank(int m, int c, int ldc, const double* __restrict__ AX, const double* __restrict__ AY,
@@ -399,32 +408,6 @@ void ensure_cg(Handle& H, const CGLayout& lay, bool fp64) {
 // drivers
 // ===========================================================================
 namespace fsa {
-
-__global__ void k_dot_col0(int64_t n, int ldc, int64_t chunk, const double* __restrict__ y,
-                           const double* __restrict__ U, double* __restrict__ part) {
-  if (threadIdx.x != 0) return;
-  int64_t r0 = (int64_t)blockIdx.x * chunk;
-  int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
-  double s = 0.0;
-  for (int64_t i = r0; i < r1; ++i) s += y[i] * U[i * ldc];
-  part[(int64_t)blockIdx.x * ldc] = s;
-}
-
-__global__ void k_dot_col0_f(int64_t n, int ldc, int64_t chunk, const double* __restrict__ y,
-                             const float* __restrict__ U, double* __restrict__ part) {
-  if (threadIdx.x != 0) return;
-  int64_t r0 = (int64_t)blockIdx.x * chunk;
-  int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
-  double s = 0.0;
-  for (int64_t i = r0; i < r1; ++i) s += y[i] * (double)U[i * ldc];
-  part[(int64_t)blockIdx.x * ldc] = s;
-}
-
-template <typename T>
-__global__ void k_copy_col0(int64_t n, int ldc, const T* __restrict__ src, T* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i * ldc] = src[i * ldc];
-}
 
 unsigned read_err(Handle& H) {
   unsigned e = 0;
@@ -542,7 +525,7 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   k_slq<<<(lay.c + 63) / 64, 64, 0, s>>>(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.qlwork.p, g.quads.p, H.err);
   FSA_CHECK_LAUNCH();
   // y^T u
-  k_dot_col0<<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U.p, g.part.p);
+  k_dot_col0<double><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U.p, g.part.p);
   FSA_CHECK_LAUNCH();
   double* gpart = nullptr;
   double* glow = nullptr;
@@ -630,7 +613,10 @@ LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o) 
 }
 
 // out = Sigma_dag v (0), P_hat^-1 v (1), Sigma_s~ v (2), FP64 operator
+void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* out);
+
 void apply_operator(Handle& H, int which, const double* v, int k, double* out) {
+  if (H.op.precision == FSA_MIXED_BF16) return apply_operator_mixed(H, which, v, k, out);
   Operator& op = H.op;
   cudaStream_t s = H.stream;
   int64_t n = H.n;

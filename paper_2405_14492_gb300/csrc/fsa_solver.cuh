@@ -39,6 +39,9 @@ __global__ void k_gather_y(int64_t n, const int64_t* __restrict__ perm, const do
 template <typename T>
 __global__ void k_probe_finish(int64_t n, int l, int ldc, int kind, uint64_t key, const int64_t* __restrict__ perm,
                                const double* __restrict__ y_int, const double* __restrict__ D, T* __restrict__ B);
+void launch_grad_sparse_bf16(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
+                             const float* X, const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B,
+                             const __nv_bfloat16* F, const fsa_theta& th, double* part);
 template <typename T, typename AT>
 __global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colidx, const double* __restrict__ vals,

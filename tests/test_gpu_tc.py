@@ -1,0 +1,86 @@
+"""Tensor-core path: the tcgen05/TMA BF16 GEMM against an FP64 reference of
+the same BF16 operands, and the mixed-precision FSA log-likelihood against
+the FP64 oracle under identical probes."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import fsa_inputs as fi
+from oracle import fsa_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import paper_2405_14492_gb300 as F
+    return F
+
+
+def _selftest(M, N, K, na, nb, pairs, halves, splits, seed=1):
+    from paper_2405_14492_gb300 import _native as N_
+    lib = N_.lib()
+    lib.fsa_selftest_tc_gemm.restype = ctypes.c_int
+    lib.fsa_selftest_tc_gemm.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint, ctypes.c_int, ctypes.c_int,
+                                                              ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                                              ctypes.POINTER(ctypes.c_int)]
+    err = ctypes.c_double(-1.0)
+    act = ctypes.c_int(0)
+    st = lib.fsa_selftest_tc_gemm(M, N, K, na, nb, pairs, halves, splits, seed, ctypes.byref(err),
+                                  ctypes.byref(act))
+    return st, err.value, act.value
+
+
+@pytest.mark.parametrize("M,N,K,na,nb,pairs,halves,splits", [
+    (128, 16, 64, 1, 1, 1, 0, 1),          # one tile, one K block
+    (256, 144, 320, 1, 1, 1, 1, 1),        # hi/lo halves epilogue (N = 2 x 72)
+    (300, 80, 1000, 1, 1, 1, 0, 1),        # ragged M and K (TMA zero fill)
+    (1000, 256, 512, 2, 2, 7, 0, 1),       # three split products hi.hi + hi.lo + lo.hi
+    (520, 128, 2048, 1, 2, 3, 0, 1),       # one A, two B
+    (1024, 144, 20000, 1, 1, 1, 1, 38),    # split-K with halves (the A^T X shape)
+    (70, 32, 2000, 1, 1, 1, 0, 5),         # split-K, ragged everything
+    (4096, 48, 1024, 1, 1, 1, 1, 1),       # many M tiles (the A q shape)
+])
+def test_tc_gemm_selftest(F, M, N, K, na, nb, pairs, halves, splits):
+    st, err, act = _selftest(M, N, K, na, nb, pairs, halves, splits)
+    assert st == 0, f"status {st}"
+    tol = 2e-6 * math.sqrt(K) + 1e-6
+    assert err < tol, f"max rel err {err} (tol {tol}), splits {act}"
+
+
+def test_mixed_operator_close_to_fp64(F):
+    n, m, nu, gamma = 20011, 200, 0.5, 0.015
+    locs = fi.uniform_locations(n, 71)
+    ind = locs[fi.inducing_subset(n, m, 71)]
+    th = (1.0, 0.05, 0.05)
+    V = np.random.default_rng(3).standard_normal((n, 5))
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        ref0 = h.matvec(th, V, 0, F.FSA_FP64)
+        ref1 = h.matvec(th, V, 1, F.FSA_FP64)
+        got0 = h.matvec(th, V, 0, F.FSA_MIXED_BF16)
+        got1 = h.matvec(th, V, 1, F.FSA_MIXED_BF16)
+        ld64 = h.logdet_precond(th, F.FSA_FP64)
+        ld16 = h.logdet_precond(th, F.FSA_MIXED_BF16)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    # the BF16-rounded A~ perturbs the operator at ~2^-8 per entry of A
+    assert rel(got0, ref0) < 1e-2
+    assert rel(got1, ref1) < 1e-2
+    assert abs(ld16 - ld64) < 1e-3 * abs(ld64)
+
+
+@pytest.mark.parametrize("n,m,nu,gamma,l,K", [(20011, 200, 0.5, 0.015, 16, 30), (30011, 300, 1.5, 0.012, 12, 25)])
+def test_mixed_loglik_within_1e4_of_oracle(F, n, m, nu, gamma, l, K):
+    locs = fi.uniform_locations(n, 81)
+    ind = locs[fi.inducing_subset(n, m, 81)]
+    th = (1.0, 0.05, 0.05) if nu == 0.5 else (1.0, 0.03, 0.05)
+    y = fi.random_field(locs, nu, *th, 81)
+    ref = O.IterativeFSA(locs, ind, gamma, nu, th).loglik_grad(y, l, 5, 0.0, fixed_iters=K)
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        ll, g, info = h.loglik_grad(y, th, F.make_opts(num_probes=l, fixed_iters=K, seed=5,
+                                                       precision=F.FSA_MIXED_BF16))
+        ll64, g64, _ = h.loglik_grad(y, th, F.make_opts(num_probes=l, fixed_iters=K, seed=5))
+    assert abs(ll64 - ref["loglik"]) < 1e-6 * abs(ref["loglik"])
+    assert abs(ll - ref["loglik"]) < 1e-4 * abs(ref["loglik"]), (ll, ref["loglik"])
+    assert np.linalg.norm(g - ref["grad"]) < 2e-2 * np.linalg.norm(ref["grad"]), (g, ref["grad"])
