@@ -1,0 +1,43 @@
+/*
+ * fsa_profile.h — measurement hooks of libfsa (no counterpart in the paper;
+ * they report how the hot path of §3.1 uses the GPU).
+ *
+ * Launch counting is always on.  Kernel timing, when enabled, brackets every
+ * tensor-core GEMM launch with CUDA events recorded on the stream the GEMM is
+ * launched on, and attributes the elapsed device time and the GEMM's
+ * algorithmic bytes (operands read once, outputs written once) to a tag:
+ *   "pcg_AtX"  per-CG-iteration  w = A~^T (D^-1 R)      (split-K)
+ *   "pcg_Aq"   per-CG-iteration  s = A~ q
+ *   "build"    operator build    A = Sigma_nm L^-T, M = I + A~^T D^-1 A~, probes
+ *   "grad"     gradient          B = dK L^-T, F = A~ E, projections
+ * Timing adds one event pair per GEMM launch; it is meant for measurement
+ * runs.  Not thread-safe across concurrent callers.
+ */
+#ifndef FSA_PROFILE_H_
+#define FSA_PROFILE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Total number of CUDA kernels launched by this library since load. */
+uint64_t fsa_launch_count(void);
+
+/* 1: start recording GEMM launch timings; 0: stop (recorded data kept). */
+void fsa_profile_enable(int on);
+
+/* Drop recorded timings (and release their events). */
+void fsa_profile_reset(void);
+
+/* Synchronise on the recorded events and sum the data of one tag:
+ * launches, total device milliseconds and total algorithmic bytes.
+ * Returns 0, or a negative value if the tag is unknown or nothing recorded. */
+int fsa_profile_collect(const char* tag, int64_t* launches, double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -32,7 +32,13 @@ struct Error {
     }                                                                             \
   } while (0)
 
-#define FSA_CHECK_LAUNCH() FSA_CUDA(cudaGetLastError())
+void count_launch();
+
+#define FSA_CHECK_LAUNCH()    \
+  do {                        \
+    ::fsa::count_launch();    \
+    FSA_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define FSA_REQUIRE(cond, code, text)                     \
   do {                                                    \

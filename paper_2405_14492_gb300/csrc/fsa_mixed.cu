@@ -273,6 +273,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th) {
     g.pairs = 1u | 2u | 4u;   // hi.hi + hi.lo + lo.hi
     g.M = (int)n; g.N = m_pad; g.K = m_pad; g.bn = 128;
     g.out = A32.p; g.ldo = m_pad;
+    g.tag = "build";
     tc_gemm(g, H.err, s);
     op.Ab.ensure(nm);
     k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p);
@@ -312,6 +313,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th) {
     int kb = (g.K + 63) / 64, per = (kb + g.splits - 1) / g.splits, splits = (kb + per - 1) / per;
     DevPtr<float> part((size_t)splits * m_pad * m_pad);
     g.out = part.p; g.ldo = m_pad; g.split_stride = (int64_t)m_pad * m_pad;
+    g.tag = "build";
     tc_gemm(g, H.err, s);
     op.Mp.ensure((size_t)m * m);
     k_reduce_splits<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(splits, m, m, part.p, m_pad, g.split_stride,
@@ -338,7 +340,8 @@ struct MixedCtx {
 };
 
 // w (FP64, m x ldc) = A~^T X  where X = rows of `src` (scaled by rowscale), split hi/lo
-static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w) {
+static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w,
+                      const char* tag) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
@@ -355,6 +358,8 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   t.splits = C.splits_w;
   int kb = (t.K + 63) / 64, per = (kb + t.splits - 1) / t.splits, splits = (kb + per - 1) / per;
   t.out = C.wpart; t.ldo = ldc; t.split_stride = (int64_t)C.m_pad * ldc;
+  t.tag = tag;
+  t.alg_bytes = (double)H.m * C.n * 2.0 + 2.0 * C.c * C.n * 2.0 + (double)splits * H.m * C.c * 4.0;
   tc_gemm(t, H.err, s);
   k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
                                                                     t.split_stride, w, ldc, 0);
@@ -362,7 +367,7 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
 }
 
 // S (FP32 n x ldc) = A~ q, q FP64 m x ldc
-static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S) {
+static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
@@ -375,6 +380,8 @@ static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S) {
   t.M = (int)C.n; t.N = 2 * ldc; t.K = C.m_pad; t.bn = 2 * ldc;
   t.halves = 1;
   t.out = S; t.ldo = ldc;
+  t.tag = tag;
+  t.alg_bytes = (double)C.n * H.m * 2.0 + 2.0 * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
   tc_gemm(t, H.err, s);
 }
 
@@ -382,10 +389,10 @@ static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S) {
 static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
   CGState& g = H.cg;
   Operator& op = H.op;
-  mixed_AtX(H, C, R, op.Dinv32.p, g.w.p);
+  mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
   dgemm(H.ws, H.stream, false, false, H.m, C.c, H.m, 1.0, op.Minv.p, H.m, g.w.p, C.ldc, 0.0, g.q.p, C.ldc,
         nullptr);
-  mixed_Aq(H, C, g.q.p, S);
+  mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
 }
 
 LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
@@ -431,6 +438,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     t.pairs = 1u | 2u;
     t.M = (int)n; t.N = l16; t.K = C.m_pad; t.bn = l16;
     t.out = Zp.p; t.ldo = l16;
+    t.tag = "build";
     tc_gemm(t, H.err, s);
     k_probe_finish_mixed<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, l16, o.probe,
                                                                     rng_key(o.seed, kStreamEps2), H.perm.p, H.y.p,
@@ -496,8 +504,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     size_t mc = (size_t)m * ldc;
     size_t nm = (size_t)n * m_pad;
     DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc), E((size_t)m * m), T1((size_t)m * m);
-    mixed_AtX(H, C, g.U32.p, nullptr, AX.p);
-    mixed_AtX(H, C, g.Z32.p, nullptr, AY.p);
+    mixed_AtX(H, C, g.U32.p, nullptr, AX.p, "grad");
+    mixed_AtX(H, C, g.Z32.p, nullptr, AY.p, "grad");
     DevPtr<__nv_bfloat16> Bb(nm), Fb(nm);
     {
       // B = dK L^-T (split products), and B^T for the m-space projections
@@ -519,6 +527,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       t.pairs = 1u | 2u | 4u;
       t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
       t.out = B32.p; t.ldo = m_pad;
+      t.tag = "grad";
       tc_gemm(t, H.err, s);
       k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Bb.p);
       FSA_CHECK_LAUNCH();
@@ -537,6 +546,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       f.out = B32.p; f.ldo = m_pad;
       FSA_CUDA(cudaStreamSynchronize(s));
       // B32 now free for F
+      f.tag = "grad";
       tc_gemm(f, H.err, s);
       k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Fb.p);
       FSA_CHECK_LAUNCH();
@@ -550,8 +560,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       FSA_CHECK_LAUNCH();
       MixedCtx CB = C;
       CB.mAt = make_tma_bf16(Bt.p, m_pad, n, C.n_pad, 128);
-      mixed_AtX(H, CB, g.U32.p, nullptr, BX.p);
-      mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p);
+      mixed_AtX(H, CB, g.U32.p, nullptr, BX.p, "grad");
+      mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p, "grad");
       FSA_CUDA(cudaStreamSynchronize(s));
     }
     dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
@@ -652,8 +662,8 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
     FSA_CHECK_LAUNCH();
   } else {
     if (which == 0) {
-      mixed_AtX(H, C, V32.p, nullptr, g.w.p);
-      mixed_Aq(H, C, g.w.p, S32.p);
+      mixed_AtX(H, C, V32.p, nullptr, g.w.p, nullptr);
+      mixed_Aq(H, C, g.w.p, S32.p, nullptr);
     } else {
       FSA_CUDA(cudaMemsetAsync(S32.p, 0, nc * sizeof(float), s));
     }

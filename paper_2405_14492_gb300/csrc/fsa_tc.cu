@@ -11,8 +11,11 @@
 // frees its TMEM before returning.
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "fsa_tc.cuh"
 
@@ -356,9 +359,102 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   });
   FSA_REQUIRE(smem <= 200 * 1024, FSA_ERR_ARG, "tc_gemm stage ring too large");
   dim3 grid((g.M + tc::BM - 1) / tc::BM, (g.N + bn - 1) / bn, splits);
+  const bool prof = g.tag && profile_on();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) {
+    e0 = profile_event();
+    e1 = profile_event();
+    FSA_CUDA(cudaEventRecord(e0, s));
+  }
   tc::gemm_kernel<<<grid, tc::kThreads, smem, s>>>(p);
   FSA_CHECK_LAUNCH();
+  if (prof) {
+    FSA_CUDA(cudaEventRecord(e1, s));
+    double bytes = g.alg_bytes;
+    if (bytes <= 0) {
+      double rows_a = 0, rows_b = 0;
+      for (int a = 0; a < g.num_a; ++a) rows_a += g.M;
+      for (int b = 0; b < g.num_b; ++b) rows_b += g.N;
+      bytes = (rows_a + rows_b) * g.K * 2.0 + (double)g.M * p.n_valid * 4.0 * splits;
+    }
+    profile_record(g.tag, e0, e1, bytes);
+  }
   return 1;
 }
+
+// ---------------------------------------------------------------------------
+// launch counter and GEMM timing registry
+// ---------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfRec {
+  std::string tag;
+  cudaEvent_t a, b;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+bool profile_on() { return g_prof_on; }
+
+cudaEvent_t profile_event() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  FSA_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void profile_record(const char* tag, cudaEvent_t a, cudaEvent_t b, double bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(ProfRec{tag, a, b, bytes});
+}
+
+}  // namespace fsa
+
+extern "C" {
+
+uint64_t fsa_launch_count(void) { return fsa::g_launches.load(); }
+
+void fsa_profile_enable(int on) { fsa::g_prof_on = on != 0; }
+
+void fsa_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(fsa::g_prof_mu);
+  for (auto& r : fsa::g_prof) {
+    fsa::g_prof_pool.push_back(r.a);
+    fsa::g_prof_pool.push_back(r.b);
+  }
+  fsa::g_prof.clear();
+}
+
+int fsa_profile_collect(const char* tag, int64_t* launches, double* ms, double* bytes) {
+  std::lock_guard<std::mutex> lk(fsa::g_prof_mu);
+  int64_t n = 0;
+  double t = 0, by = 0;
+  for (auto& r : fsa::g_prof) {
+    if (!tag || r.tag != tag) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return -2;
+    float e = 0;
+    if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return -2;
+    ++n;
+    t += e;
+    by += r.bytes;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (bytes) *bytes = by;
+  return n > 0 ? 0 : -1;
+}
+
+}  // extern "C"
+
+namespace fsa {
 
 }  // namespace fsa

@@ -39,7 +39,14 @@ struct TcGemm {
   int64_t ldo = 0;
   int64_t split_stride = 0;
   int n_valid = 0;          // columns of out written (<= N or N/2)
+  const char* tag = nullptr;  // profiling tag (fsa_profile.h)
+  double alg_bytes = 0;       // algorithmic bytes of this launch (0: from the shapes)
 };
+
+// profiling registry (fsa_profile.h)
+bool profile_on();
+void profile_record(const char* tag, cudaEvent_t a, cudaEvent_t b, double bytes);
+cudaEvent_t profile_event();
 
 // Launch; returns the number of kernel launches (1).
 int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s);

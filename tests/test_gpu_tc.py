@@ -23,7 +23,7 @@ def _selftest(M, N, K, na, nb, pairs, halves, splits, seed=1):
     from paper_2405_14492_gb300 import _native as N_
     lib = N_.lib()
     lib.fsa_selftest_tc_gemm.restype = ctypes.c_int
-    lib.fsa_selftest_tc_gemm.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint, ctypes.c_int, ctypes.c_int,
+    lib.fsa_selftest_tc_gemm.argtypes = [ctypes.c_int] * 5 + [ctypes.c_uint, ctypes.c_int, ctypes.c_int,
                                                               ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                                                               ctypes.POINTER(ctypes.c_int)]
     err = ctypes.c_double(-1.0)
