@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: FSA log-likelihood + gradient evaluations per second on GB300.
+
+One step = one call of ``fsa_loglik_grad`` (the whole theta-dependent hot
+path: covariance and A~ build, residual values, Woodbury core, probes, block
+PCG with Lanczos tridiagonals, SLQ log det, STE gradient) on the workload
+n = 1e6 uniform locations, m = 1000 inducing points, exponential covariance
+(sigma1^2 = 1, rho = 0.02, nugget = 0.01), taper for ~20 nonzeros per row,
+l = 64 Rademacher probes, CG tolerance 1e-3, mixed BF16 / FP32 / FP64 form.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import fsa_inputs as fi  # noqa: E402
+
+METRIC = "FSA loglik+grad evals/s at n=1e6,m=1000 (mixed vs FP64); serving p50/p99 ms"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(k)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _tc_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2405_14492_gb300", "csrc", "fsa_tc.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current tensor-core kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_tag)
+    if not e or e.get("source_sha") != _tc_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+def make_workload(name, with_response=True, features=256):
+    w = fi.WORKLOADS[name]
+    locs = fi.uniform_locations(w.n, w.seed)
+    idx = fi.inducing_subset(w.n, w.m, w.seed)
+    y = fi.random_field(locs, w.nu, w.sigma1_sq, w.rho, w.nugget, w.seed, features=features) if with_response else None
+    return w, locs, locs[idx].copy(), y
+
+
+def window_sample(locs, y, n_target):
+    """Points of the workload inside a lower-left square window holding about
+    n_target points (same density, same taper, same inducing points)."""
+    side = math.sqrt(n_target / locs.shape[0])
+    sel = np.nonzero((locs[:, 0] < side) & (locs[:, 1] < side))[0]
+    return locs[sel], y[sel], side
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle arm (reference arm of this benchmark and the cpu_baseline field)
+# ----------------------------------------------------------------------------
+def oracle_sample_eval(w, locs, ind, y, n_sample):
+    """Time one oracle log-likelihood + gradient on a window sample; return
+    (seconds, n_s, evals/s scaled to the full n by n_s / n)."""
+    from oracle import fsa_oracle as O
+    ls, ys, side = window_sample(locs, y, n_sample)
+    th = (w.sigma1_sq, w.rho, w.nugget)
+    t0 = time.perf_counter()
+    it = O.IterativeFSA(ls, ind, w.taper_range(), w.nu, th)
+    out = it.loglik_grad(ys, w.num_probes, w.seed, w.cg_tol, max_iter=1000)
+    dt = time.perf_counter() - t0
+    return dt, ls.shape[0], (1.0 / dt) * (ls.shape[0] / w.n), int(np.max(out["iters"]))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, locs, ind, y = make_workload(args.workload)
+    n_s = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample_eval(w, locs, ind, y, n_s)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        dt, ns, v, iters = oracle_sample_eval(w, locs, ind, y, n_s)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.median(vals))
+    cores = os.cpu_count()
+    sample = (f"window of {ns} of the {w.n} points (same density, taper, {w.m} inducing points, "
+              f"l={w.num_probes}, tol {w.cg_tol}); evals/s scaled by n_s/n (per-eval cost is O(n) at fixed m)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.median(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "m": w.m, "num_probes": w.num_probes},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args):
+    import ctypes
+
+    import torch
+
+    import paper_2405_14492_gb300 as F
+    from paper_2405_14492_gb300 import _native as N
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = N.lib()
+    lib.fsa_launch_count.restype = ctypes.c_uint64
+    lib.fsa_profile_collect.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    w, locs, ind, y = make_workload(args.workload)
+    if world > 1:   # replicas: each rank evaluates its own problem
+        y = y + 1e-3 * rank
+    th = (w.sigma1_sq, w.rho, w.nugget)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    h = F.FSAHandle(locs, ind, w.taper_range(), w.nu, stream=stream.cuda_stream)
+    build_s = time.perf_counter() - t0
+    y_dev = torch.tensor(y, device="cuda", dtype=torch.float64)
+    opts = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed,
+                       y_on_device=True)
+    infos = []
+    for _ in range(args.warmup):
+        ll, g, info = h.loglik_grad(y_dev, th, opts)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    lib.fsa_profile_reset()
+    lib.fsa_profile_enable(1)
+    l0 = lib.fsa_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ll, g, info = h.loglik_grad(y_dev, th, opts)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = int(lib.fsa_launch_count() - l0)
+    lib.fsa_profile_enable(0)
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1000.0)
+    # dominant kernel: the per-iteration tensor-core GEMMs
+    prof = {}
+    for tag in ("pcg_Aq", "pcg_AtX", "build", "grad"):
+        nl, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        if lib.fsa_profile_collect(tag.encode(), ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(by)) == 0:
+            prof[tag] = {"launches": nl.value, "ms": ms.value, "bytes": by.value}
+    peaks, peak_src = _peaks()
+    dom = max(("pcg_Aq", "pcg_AtX"), key=lambda k: prof.get(k, {}).get("ms", 0.0))
+    roof = None
+    if dom in prof:
+        d = prof[dom]
+        per_launch_ms = d["ms"] / d["launches"]
+        per_launch_bytes = d["bytes"] / d["launches"]
+        achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": f"tc_gemm[{dom}]", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": _traffic_for(dom), "alg_bytes_per_launch": per_launch_bytes,
+                "avg_launch_ms": per_launch_ms, "peak_source": f"{peak_src} (copy bandwidth)",
+                "launches": d["launches"], "share_of_step": round(d["ms"] / elapsed_ms, 4)}
+        other = "pcg_AtX" if dom == "pcg_Aq" else "pcg_Aq"
+        if other in prof:
+            o = prof[other]
+            roof["other_gemm"] = {"kernel": f"tc_gemm[{other}]",
+                                  "achieved": round(o["bytes"] / o["launches"] / (o["ms"] / o["launches"] / 1000) / 1e9, 1),
+                                  "share_of_step": round(o["ms"] / elapsed_ms, 4)}
+    result = {"metric": METRIC, "value": round(value, 4), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+              "config": {"workload": w.name, "n": w.n, "m": w.m, "nu": w.nu, "theta": list(th),
+                         "taper_range": w.taper_range(), "nnz_per_row": h.nnz / w.n, "num_probes": w.num_probes,
+                         "cg_tol": w.cg_tol, "precision": "mixed_bf16", "parallelism": f"replicas{world}",
+                         "l2": "inputs larger than L2 (A~ alone is 2 GB BF16)",
+                         "cg_iters_max": int(infos[-1]["iters_max"]), "cg_iters_y": int(infos[-1]["iters_y"]),
+                         "build_s_theta_free": round(build_s, 3)},
+              "gpu_launches": launches, "clocks": clk, "roofline": roof, "kernel_times": prof,
+              "loglik": ll, "grad": list(map(float, g)), "logdet_se": infos[-1]["logdet_se"]}
+    # end to end through the C ABI with a host (pinned) response
+    if not args.no_e2e:
+        y_pin = torch.empty(w.n, dtype=torch.float64, pin_memory=True)
+        y_pin.numpy()[:] = y
+        opts_h = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed)
+        h.loglik_grad(y_pin.numpy(), th, opts_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.loglik_grad(y_pin.numpy(), th, opts_h)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        result["e2e"] = {"value": round(world / e2e_s, 4), "unit": "evals/s", "h2d_bytes_per_step": 8 * w.n,
+                         "d2h_bytes_per_step": 8 * 4, "timing": "host wall clock around the C-ABI call"}
+    # the plain FP64 GPU form on the same workload and probes
+    if not args.no_fp64 and rank == 0:
+        opts64 = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_FP64, seed=w.seed,
+                             y_on_device=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ll64, g64, info64 = h.loglik_grad(y_dev, th, opts64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        result["fp64_form"] = {"evals_per_s": round(1.0 / t64, 5), "seconds_per_eval": round(t64, 3),
+                               "loglik": ll64, "grad": list(map(float, g64)), "cg_iters_max": int(info64["iters_max"]),
+                               "mixed_loglik_rel_err": abs(ll - ll64) / abs(ll64),
+                               "mixed_speedup": round(value / world * t64, 2)}
+    h.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, ns, v, iters = oracle_sample_eval(w, locs, ind, y, args.cpu_sample)
+        result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                                  "sample": f"one oracle loglik+grad on a window of {ns} of the {w.n} points "
+                                            f"(same density, taper, all {w.m} inducing points), {dt:.1f} s, "
+                                            f"scaled by n_s/n"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="exp-n1e6-m1000", choices=sorted(fi.WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--ref-sample", type=int, default=2500)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
