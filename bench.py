@@ -202,7 +202,8 @@ def run_gpu(args):
     h = F.FSAHandle(locs, ind, w.taper_range(), w.nu, stream=stream.cuda_stream)
     build_s = time.perf_counter() - t0
     y_dev = torch.tensor(y, device="cuda", dtype=torch.float64)
-    opts = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed,
+    prec = {"bf16x2": F.FSA_MIXED_BF16X2, "bf16": F.FSA_MIXED_BF16, "fp64": F.FSA_FP64}[args.precision]
+    opts = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=prec, seed=w.seed,
                        y_on_device=True)
     infos = []
     for _ in range(args.warmup):
@@ -264,7 +265,7 @@ def run_gpu(args):
               "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
               "config": {"workload": w.name, "n": w.n, "m": w.m, "nu": w.nu, "theta": list(th),
                          "taper_range": w.taper_range(), "nnz_per_row": h.nnz / w.n, "num_probes": w.num_probes,
-                         "cg_tol": w.cg_tol, "precision": "mixed_bf16", "parallelism": f"replicas{world}",
+                         "cg_tol": w.cg_tol, "precision": args.precision, "parallelism": f"replicas{world}",
                          "l2": "inputs larger than L2 (A~ alone is 2 GB BF16)",
                          "cg_iters_max": int(infos[-1]["iters_max"]), "cg_iters_y": int(infos[-1]["iters_y"]),
                          "build_s_theta_free": round(build_s, 3)},
@@ -274,7 +275,7 @@ def run_gpu(args):
     if not args.no_e2e:
         y_pin = torch.empty(w.n, dtype=torch.float64, pin_memory=True)
         y_pin.numpy()[:] = y
-        opts_h = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed)
+        opts_h = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=prec, seed=w.seed)
         h.loglik_grad(y_pin.numpy(), th, opts_h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -283,6 +284,17 @@ def run_gpu(args):
         e2e_s = (time.perf_counter() - t0) / args.steps
         result["e2e"] = {"value": round(world / e2e_s, 4), "unit": "evals/s", "h2d_bytes_per_step": 8 * w.n,
                          "d2h_bytes_per_step": 8 * 4, "timing": "host wall clock around the C-ABI call"}
+    # the faster single-BF16 operator form (lower accuracy) on the same workload and probes
+    if args.precision != "bf16" and not args.no_fp64 and rank == 0:
+        opts1 = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed,
+                            y_on_device=True)
+        h.loglik_grad(y_dev, th, opts1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ll1, g1, _ = h.loglik_grad(y_dev, th, opts1)
+        torch.cuda.synchronize()
+        result["bf16_single_form"] = {"evals_per_s": round(3.0 / (time.perf_counter() - t0), 4), "loglik": ll1}
     # the plain FP64 GPU form on the same workload and probes
     if not args.no_fp64 and rank == 0:
         opts64 = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_FP64, seed=w.seed,
@@ -296,6 +308,8 @@ def run_gpu(args):
                                "loglik": ll64, "grad": list(map(float, g64)), "cg_iters_max": int(info64["iters_max"]),
                                "mixed_loglik_rel_err": abs(ll - ll64) / abs(ll64),
                                "mixed_speedup": round(value / world * t64, 2)}
+        if "bf16_single_form" in result:
+            result["bf16_single_form"]["loglik_rel_err_vs_fp64"] = abs(result["bf16_single_form"]["loglik"] - ll64) / abs(ll64)
     h.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, ns, v, iters = oracle_sample_eval(w, locs, ind, y, args.cpu_sample)
@@ -316,6 +330,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="exp-n1e6-m1000", choices=sorted(fi.WORKLOADS))
+    ap.add_argument("--precision", default="bf16x2", choices=["bf16x2", "bf16", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

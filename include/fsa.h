@@ -57,12 +57,17 @@ typedef enum {
 
 typedef enum {
   FSA_FP64 = 0,          /* every step in FP64 on the CUDA cores */
-  FSA_MIXED_BF16 = 1     /* n x m products on tcgen05 tensor cores: A = Sigma_nm L_m^-T
+  FSA_MIXED_BF16 = 1,    /* n x m products on tcgen05 tensor cores: A = Sigma_nm L_m^-T
                             stored once in BF16 (the operator is defined by it, consistently
                             in the operator, preconditioner, probes and log det P);
                             vector operands split hi+lo BF16, FP32 accumulation; vectors
                             FP32; m x m Cholesky / Woodbury core, CG scalars and Lanczos
                             eigen-quadrature in FP64 */
+  FSA_MIXED_BF16X2 = 2   /* as FSA_MIXED_BF16, but A is stored as a hi + lo pair of BF16
+                            matrices (A = A_hi + A_lo, ~2^-17 relative) and every tensor-core
+                            product uses both halves; twice the A traffic, FP32-level operator
+                            accuracy (the form that meets 1e-4 relative log-likelihood error
+                            at n = 1e6) */
 } fsa_precision;
 
 typedef enum {

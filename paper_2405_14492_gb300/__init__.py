@@ -12,11 +12,12 @@ import ctypes as C
 import numpy as np
 
 from . import _native as N
-from ._native import (FSA_EXPONENTIAL, FSA_FP64, FSA_MATERN_1_5, FSA_MIXED_BF16, FSA_PROBE_GAUSSIAN,
-                      FSA_PROBE_RADEMACHER, FsaError, FsaInfo, FsaOpts, FsaTheta)
+from ._native import (FSA_EXPONENTIAL, FSA_FP64, FSA_MATERN_1_5, FSA_MIXED_BF16, FSA_MIXED_BF16X2,
+                      FSA_PROBE_GAUSSIAN, FSA_PROBE_RADEMACHER, FsaError, FsaInfo, FsaOpts, FsaTheta)
 
 __all__ = ["FSAHandle", "FSALogLik", "FsaError", "FSA_EXPONENTIAL", "FSA_MATERN_1_5", "FSA_FP64",
-           "FSA_MIXED_BF16", "FSA_PROBE_RADEMACHER", "FSA_PROBE_GAUSSIAN", "make_opts", "cov_code"]
+           "FSA_MIXED_BF16", "FSA_MIXED_BF16X2", "FSA_PROBE_RADEMACHER", "FSA_PROBE_GAUSSIAN", "make_opts",
+           "cov_code"]
 
 
 def cov_code(nu: float) -> int:

@@ -18,7 +18,7 @@ FSA_OK = 0
 STATUS = {0: "FSA_OK", 1: "FSA_ERR_ARG", 2: "FSA_ERR_OOM", 3: "FSA_ERR_NOT_PD", 4: "FSA_ERR_NO_CONVERGENCE",
           5: "FSA_ERR_NAN", 6: "FSA_ERR_TIMEOUT", 7: "FSA_ERR_BUSY", 8: "FSA_ERR_CUDA", 9: "FSA_ERR_UNSUPPORTED"}
 FSA_EXPONENTIAL, FSA_MATERN_1_5 = 0, 1
-FSA_FP64, FSA_MIXED_BF16 = 0, 1
+FSA_FP64, FSA_MIXED_BF16, FSA_MIXED_BF16X2 = 0, 1, 2
 FSA_PROBE_RADEMACHER, FSA_PROBE_GAUSSIAN = 0, 1
 
 

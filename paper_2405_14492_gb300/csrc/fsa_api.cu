@@ -164,7 +164,7 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   fsa_opts o = resolve_opts(opts);
   if (o.num_probes < 1 || o.num_probes > 1000) return fail(Error{FSA_ERR_ARG, "num_probes must be in [1, 1000]"});
   if (o.want_grad && !grad) return fail(Error{FSA_ERR_ARG, "grad is NULL"});
-  if (o.precision != FSA_FP64 && o.precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
   Handle& H = h->h;
   try {
@@ -217,7 +217,7 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
                       int32_t k, double* out) {
   if (!h || !v || !out || k < 1 || which < 0 || which > 2) return fail(Error{FSA_ERR_ARG, "bad argument"});
   if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
-  if (precision != FSA_FP64 && precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  if (precision < FSA_FP64 || precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   Handle& H = h->h;
   try {
     ensure_operator(H, *theta, precision);
@@ -240,7 +240,7 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
 fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t precision, double* out) {
   if (!h || !out) return fail(Error{FSA_ERR_ARG, "NULL argument"});
   if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
-  if (precision != FSA_FP64 && precision != FSA_MIXED_BF16) return fail(Error{FSA_ERR_ARG, "bad precision"});
+  if (precision < FSA_FP64 || precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   Handle& H = h->h;
   try {
     ensure_operator(H, *theta, precision);

@@ -80,6 +80,8 @@ struct Operator {
   // mixed form (tensor-core operands)
   DevPtr<__nv_bfloat16> Ab;    // A rounded to BF16, n x m_pad (K-major for A q)
   DevPtr<__nv_bfloat16> Atb;   // its transpose, m_pad x n_pad (K-major for A^T x)
+  DevPtr<__nv_bfloat16> Ab_lo, Atb_lo;   // low halves (FSA_MIXED_BF16X2): A = Ab + Ab_lo
+  bool has_lo = false;
   DevPtr<float> vals32;
   DevPtr<float> D32, Dinv32;
   int m_pad = 0;

@@ -16,6 +16,7 @@
 #include "fsa_kernels.cuh"
 #include "fsa_solver.cuh"
 #include "fsa_tc.cuh"
+#include "fsa_vec.cuh"
 
 namespace fsa {
 
@@ -71,6 +72,23 @@ __global__ void k_f32_to_bf16(int64_t total, const float* __restrict__ src, __nv
     dst[t] = __float2bfloat16_rn(src[t]);
 }
 
+__global__ void k_f32_split(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                            __nv_bfloat16* __restrict__ lo) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    split_bf16(src[t], hi[t], lo[t]);
+}
+
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat162* hi, const __nv_bfloat162* lo, int k) {
+  float2 a = __bfloat1622float2(hi[k]);
+  if (lo) {
+    float2 b = __bfloat1622float2(lo[k]);
+    a.x += b.x;
+    a.y += b.y;
+  }
+  return a;
+}
+
 // dst (cols x ld_dst) = src^T, src rows x cols (ld_src); 32 x 32 tiles through shared memory
 __global__ void k_transpose_bf16(int64_t rows, int cols, const __nv_bfloat16* __restrict__ src, int64_t ld_src,
                                  __nv_bfloat16* __restrict__ dst, int64_t ld_dst) {
@@ -95,7 +113,8 @@ __global__ void k_transpose_bf16(int64_t rows, int cols, const __nv_bfloat16* __
 // that every consumer sees the same diagonal
 __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ col, const double* __restrict__ xs,
-                                   const double* __restrict__ ys, const __nv_bfloat16* __restrict__ A, int cov,
+                                   const double* __restrict__ ys, const __nv_bfloat16* __restrict__ A,
+                                   const __nv_bfloat16* __restrict__ Alo, int cov,
                                    double s1, double rho, double nug, double gamma, double* __restrict__ vals,
                                    float* __restrict__ vals32, double* __restrict__ D, float* __restrict__ D32,
                                    float* __restrict__ Dinv32) {
@@ -105,14 +124,16 @@ __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restri
   const int np2 = m_pad / 2;
   for (int64_t i = warp; i < n; i += nwarps) {
     const __nv_bfloat162* ai = reinterpret_cast<const __nv_bfloat162*>(A + i * m_pad);
+    const __nv_bfloat162* ali = Alo ? reinterpret_cast<const __nv_bfloat162*>(Alo + i * m_pad) : nullptr;
     double xi = xs[i], yi = ys[i];
     for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
       int j = col[t];
       const __nv_bfloat162* aj = reinterpret_cast<const __nv_bfloat162*>(A + (int64_t)j * m_pad);
+      const __nv_bfloat162* alj = Alo ? reinterpret_cast<const __nv_bfloat162*>(Alo + (int64_t)j * m_pad) : nullptr;
       float s = 0.f;
       for (int k = lane; k < np2; k += 32) {
-        float2 a = __bfloat1622float2(ai[k]);
-        float2 b = __bfloat1622float2(aj[k]);
+        float2 a = ld_pair(ai, ali, k);
+        float2 b = ld_pair(aj, alj, k);
         s = fmaf(a.x, b.x, s);
         s = fmaf(a.y, b.y, s);
       }
@@ -138,13 +159,14 @@ __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restri
 
 // Y^T = (D^-1 A~)^T split hi/lo, from A~^T (m_pad x n_pad)
 __global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __nv_bfloat16* __restrict__ At,
-                                   const float* __restrict__ Dinv, __nv_bfloat16* __restrict__ hi,
-                                   __nv_bfloat16* __restrict__ lo) {
+                                   const __nv_bfloat16* __restrict__ At_lo, const float* __restrict__ Dinv,
+                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   int64_t total = (int64_t)m_pad * n_pad;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = t % n_pad;
-    float v = i < n ? __bfloat162float(At[t]) * Dinv[i] : 0.f;
+    float a = __bfloat162float(At[t]) + (At_lo ? __bfloat162float(At_lo[t]) : 0.f);
+    float v = i < n ? a * Dinv[i] : 0.f;
     split_bf16(v, hi[t], lo[t]);
   }
 }
@@ -243,18 +265,20 @@ __global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kin
 // ---------------------------------------------------------------------------
 static inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
-void build_operator_mixed(Handle& H, const fsa_theta& th) {
+void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   Operator& op = H.op;
   cudaStream_t s = H.stream;
   int64_t n = H.n;
   int m = H.m;
   int m_pad = round_up(m, 64);
   int64_t n_pad = ((n + 63) / 64) * 64;
+  const bool lo = precision == FSA_MIXED_BF16X2;
   op.m_pad = m_pad;
   op.n_pad = n_pad;
+  op.has_lo = lo;
   build_mspace(H, th);
   size_t nm = (size_t)n * m_pad;
-  // A~ = bf16( Sigma_nm L^-T ) with the split products
+  // A = Sigma_nm L^-T with the split products, rounded once to BF16 (or a BF16 hi + lo pair)
   {
     DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
     DevPtr<float> A32(nm);
@@ -276,15 +300,28 @@ void build_operator_mixed(Handle& H, const fsa_theta& th) {
     g.tag = "build";
     tc_gemm(g, H.err, s);
     op.Ab.ensure(nm);
-    k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p);
+    if (lo) {
+      op.Ab_lo.ensure(nm);
+      k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, op.Ab_lo.p);
+    } else {
+      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p);
+    }
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
   }
+  dim3 tgrid((unsigned)((n + 31) / 32), (m_pad + 31) / 32), tblk(32, 8);
   op.Atb.ensure((size_t)m_pad * n_pad);
   FSA_CUDA(cudaMemsetAsync(op.Atb.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
-  k_transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (m_pad + 31) / 32), dim3(32, 8), 0, s>>>(n, m_pad, op.Ab.p, m_pad,
-                                                                                          op.Atb.p, n_pad);
+  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab.p, m_pad, op.Atb.p, n_pad);
   FSA_CHECK_LAUNCH();
+  if (lo) {
+    op.Atb_lo.ensure((size_t)m_pad * n_pad);
+    FSA_CUDA(cudaMemsetAsync(op.Atb_lo.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
+    k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab_lo.p, m_pad, op.Atb_lo.p, n_pad);
+    FSA_CHECK_LAUNCH();
+  }
+  const __nv_bfloat16* Alo = lo ? op.Ab_lo.p : nullptr;
+  const __nv_bfloat16* Atlo = lo ? op.Atb_lo.p : nullptr;
   // residual values, D
   op.vals.ensure(H.nnz);
   op.vals32.ensure(H.nnz);
@@ -292,22 +329,23 @@ void build_operator_mixed(Handle& H, const fsa_theta& th) {
   op.D32.ensure(n);
   op.Dinv32.ensure(n);
   k_csr_values_mixed<<<grid_for(n * 32, 256, 152 * 64), 256, 0, s>>>(
-      n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, op.Ab.p, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma,
+      n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, op.Ab.p, Alo, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma,
       op.vals.p, op.vals32.p, op.D.p, op.D32.p, op.Dinv32.p);
   FSA_CHECK_LAUNCH();
-  // Woodbury core M = I + A~^T D^-1 A~ on the tensor cores (split-K, FP64 reduction)
+  // Woodbury core M = I + A^T D^-1 A on the tensor cores (split-K, FP64 reduction)
   {
     size_t mn = (size_t)m_pad * n_pad;
     DevPtr<__nv_bfloat16> Yhi(mn), Ylo(mn);
-    k_scale_cols_split<<<grid_for((int64_t)mn, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, op.Dinv32.p, Yhi.p,
-                                                                    Ylo.p);
+    k_scale_cols_split<<<grid_for((int64_t)mn, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, Atlo, op.Dinv32.p,
+                                                                    Yhi.p, Ylo.p);
     FSA_CHECK_LAUNCH();
     TmaMap mAt = make_tma_bf16(op.Atb.p, m_pad, n, n_pad, 128);
+    TmaMap mAtl = lo ? make_tma_bf16(op.Atb_lo.p, m_pad, n, n_pad, 128) : mAt;
     TmaMap mYh = make_tma_bf16(Yhi.p, m_pad, n, n_pad, 128), mYl = make_tma_bf16(Ylo.p, m_pad, n, n_pad, 128);
     TcGemm g;
-    g.a[0] = &mAt; g.num_a = 1;
+    g.a[0] = &mAt; g.a[1] = &mAtl; g.num_a = lo ? 2 : 1;
     g.b[0] = &mYh; g.b[1] = &mYl; g.num_b = 2;
-    g.pairs = 1u | 2u;
+    g.pairs = lo ? (1u | 2u | 4u) : (1u | 2u);
     g.M = m_pad; g.N = m_pad; g.K = (int)n; g.bn = 128;
     g.splits = tc_pick_splits(g.M, g.N, g.K, g.bn);
     int kb = (g.K + 63) / 64, per = (kb + g.splits - 1) / g.splits, splits = (kb + per - 1) / per;
@@ -324,7 +362,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th) {
   check_err(H);
   finish_core(H);
   op.theta = th;
-  op.precision = FSA_MIXED_BF16;
+  op.precision = precision;
   op.valid = true;
 }
 
@@ -336,8 +374,20 @@ struct MixedCtx {
   int64_t n = 0, n_pad = 0;
   int splits_w = 1;
   TmaMap mAt, mA, mX, mQ;
+  TmaMap mAt_lo, mA_lo;     // low halves of A (FSA_MIXED_BF16X2)
+  bool lo = false;
   float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
 };
+
+static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C) {
+  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
+  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  C.lo = op.has_lo;
+  if (C.lo) {
+    C.mAt_lo = make_tma_bf16(op.Atb_lo.p, C.m_pad, n, C.n_pad, 128);
+    C.mA_lo = make_tma_bf16(op.Ab_lo.p, n, C.m_pad, C.m_pad, 128);
+  }
+}
 
 // w (FP64, m x ldc) = A~^T X  where X = rows of `src` (scaled by rowscale), split hi/lo
 static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w,
@@ -350,16 +400,16 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
                                                                                     C.n_pad, g.Xb.p);
   FSA_CHECK_LAUNCH();
   TcGemm t;
-  t.a[0] = &C.mAt; t.num_a = 1;
+  t.a[0] = &C.mAt; t.a[1] = &C.mAt_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mX; t.num_b = 1;
-  t.pairs = 1u;
+  t.pairs = C.lo ? (1u | 4u) : 1u;
   t.M = C.m_pad; t.N = 2 * ldc; t.K = (int)C.n; t.bn = 2 * ldc;
   t.halves = 1;
   t.splits = C.splits_w;
   int kb = (t.K + 63) / 64, per = (kb + t.splits - 1) / t.splits, splits = (kb + per - 1) / per;
   t.out = C.wpart; t.ldo = ldc; t.split_stride = (int64_t)C.m_pad * ldc;
   t.tag = tag;
-  t.alg_bytes = (double)H.m * C.n * 2.0 + 2.0 * C.c * C.n * 2.0 + (double)splits * H.m * C.c * 4.0;
+  t.alg_bytes = t.num_a * (double)H.m * C.n * 2.0 + 2.0 * C.c * C.n * 2.0 + (double)splits * H.m * C.c * 4.0;
   tc_gemm(t, H.err, s);
   k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
                                                                     t.split_stride, w, ldc, 0);
@@ -374,14 +424,14 @@ static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const ch
   k_split_q<<<grid_for((int64_t)ldc * C.m_pad, 256), 256, 0, s>>>(H.m, C.c, ldc, C.m_pad, q, g.qb.p);
   FSA_CHECK_LAUNCH();
   TcGemm t;
-  t.a[0] = &C.mA; t.num_a = 1;
+  t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mQ; t.num_b = 1;
-  t.pairs = 1u;
+  t.pairs = C.lo ? (1u | 4u) : 1u;
   t.M = (int)C.n; t.N = 2 * ldc; t.K = C.m_pad; t.bn = 2 * ldc;
   t.halves = 1;
   t.out = S; t.ldo = ldc;
   t.tag = tag;
-  t.alg_bytes = (double)C.n * H.m * 2.0 + 2.0 * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
+  t.alg_bytes = t.num_a * (double)C.n * H.m * 2.0 + 2.0 * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
   tc_gemm(t, H.err, s);
 }
 
@@ -415,14 +465,14 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   C.ldc = ldc; C.c = lay.c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
   g.Xb.ensure((size_t)2 * ldc * C.n_pad);
   g.qb.ensure((size_t)2 * ldc * C.m_pad);
-  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
-  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  set_operator_maps(op, n, C);
   C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
   C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
   C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);
   DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
   C.wpart = wpart_buf.p;
-  dim3 cgrid(lay.nblk), cblk(lay.threads);
+  dim3 cgrid(lay.nblk), cblk(lay.threads), eblk(lay.ethreads);
+  const size_t vsm = (size_t)lay.ethreads * sizeof(double);
   // probes: R = [y, A~ eps1 + D^1/2 eps2]
   {
     int l16 = round_up(l, 16);
@@ -433,9 +483,9 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     FSA_CHECK_LAUNCH();
     TmaMap mEh = make_tma_bf16(Ehi.p, l16, C.m_pad, C.m_pad, l16), mEl = make_tma_bf16(Elo.p, l16, C.m_pad, C.m_pad, l16);
     TcGemm t;
-    t.a[0] = &C.mA; t.num_a = 1;
+    t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
     t.b[0] = &mEh; t.b[1] = &mEl; t.num_b = 2;
-    t.pairs = 1u | 2u;
+    t.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
     t.M = (int)n; t.N = l16; t.K = C.m_pad; t.bn = l16;
     t.out = Zp.p; t.ldo = l16;
     t.tag = "build";
@@ -450,35 +500,35 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
   lowrank_mixed(H, C, g.R32.p, g.S32.p);
-  k_z_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+  kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
                                            g.part.p);
   FSA_CHECK_LAUNCH();
   k_cg_init<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.rz0.p, g.alpha_prev.p, g.beta_prev.p,
                                g.beta.p, g.active.p, g.iters.p, g.stop.p, H.err);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  k_spmm_fused<float, float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals32.p,
+  launch_spmm_fused<float, float>(lay, s,H.rowptr.p, H.col.p, op.vals32.p,
                                                      g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
   FSA_CHECK_LAUNCH();
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
   for (int it = 0; it < L; ++it) {
     k_cg_alpha<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.alpha.p, g.active.p, H.err);
     FSA_CHECK_LAUNCH();
-    k_ur_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
+    kv_ur_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
                                               op.Dinv32.p, nullptr, g.alpha.p, g.active.p, g.part.p);
     FSA_CHECK_LAUNCH();
     k_cg_resid<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rnorm.p, g.active.p, g.stop.p, o.cg_tol,
                                   o.fixed_iters > 0);
     FSA_CHECK_LAUNCH();
     lowrank_mixed(H, C, g.R32.p, g.S32.p);
-    k_z_update<float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+    kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
                                              g.part.p);
     FSA_CHECK_LAUNCH();
     k_cg_beta<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, it, L, g.part.p, g.rho.p, g.alpha.p, g.beta.p,
                                  g.alpha_prev.p, g.beta_prev.p, g.active.p, g.iters.p, g.stop.p, g.tdiag.p,
                                  g.toff.p, g.num_active.p, H.err);
     FSA_CHECK_LAUNCH();
-    k_spmm_fused<float, float><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals32.p,
+    launch_spmm_fused<float, float>(lay, s,H.rowptr.p, H.col.p, op.vals32.p,
                                                        g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
     FSA_CHECK_LAUNCH();
     if (o.fixed_iters <= 0) {
@@ -539,9 +589,9 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, E.p, m, m_pad, m_pad, Lhi.p, Llo.p);
       FSA_CHECK_LAUNCH();
       TcGemm f;
-      f.a[0] = &C.mA; f.num_a = 1;
+      f.a[0] = &C.mA; f.a[1] = &C.mA_lo; f.num_a = C.lo ? 2 : 1;
       f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
-      f.pairs = 1u | 2u;
+      f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
       f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
       f.out = B32.p; f.ldo = m_pad;
       FSA_CUDA(cudaStreamSynchronize(s));
@@ -560,6 +610,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       FSA_CHECK_LAUNCH();
       MixedCtx CB = C;
       CB.mAt = make_tma_bf16(Bt.p, m_pad, n, C.n_pad, 128);
+      CB.lo = false;
       mixed_AtX(H, CB, g.U32.p, nullptr, BX.p, "grad");
       mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p, "grad");
       FSA_CUDA(cudaStreamSynchronize(s));
@@ -646,8 +697,7 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
   g.qb.ensure((size_t)2 * ldc * C.m_pad);
   g.w.ensure((size_t)m * ldc);
   g.q.ensure((size_t)m * ldc);
-  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
-  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  set_operator_maps(op, n, C);
   C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
   C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
   C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);

@@ -17,6 +17,7 @@
 // (v = Sigma_dag h follows from h = z + beta h by linearity).
 #include "fsa_kernels.cuh"
 #include "fsa_solver.cuh"
+#include "fsa_vec.cuh"
 
 namespace fsa {
 
@@ -374,11 +375,14 @@ void CGLayout::setup(int64_t n_, int c_, int L_) {
   ldc = (c + 7) / 8 * 8;
   L = L_;
   threads = (ldc + 31) / 32 * 32;
-  int64_t target = 152 * 16;
-  int64_t rows_per = (n + target - 1) / target;
-  if (rows_per < 8) rows_per = 8;
-  chunk = rows_per;
-  nblk = (int)((n + chunk - 1) / chunk);
+  int64_t nb = (n + 127) / 128;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  nblk = (int)nb;
+  chunk = (n + nblk - 1) / nblk;
+  rpb = 256 / ldc;
+  if (rpb < 1) rpb = 1;
+  ethreads = rpb * ldc;
 }
 
 void ensure_cg(Handle& H, const CGLayout& lay, bool fp64) {
@@ -434,7 +438,7 @@ void ensure_operator(Handle& H, const fsa_theta& th, int precision) {
     return;
   op.valid = false;
   if (precision == FSA_FP64) build_operator_fp64(H, th);
-  else build_operator_mixed(H, th);
+  else build_operator_mixed(H, th, precision);
   check_err(H);
 }
 
@@ -462,7 +466,8 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   ensure_cg(H, lay, true);
   int ldc = lay.ldc;
   size_t nc = (size_t)n * ldc;
-  dim3 cgrid(lay.nblk), cblk(lay.threads);
+  dim3 cgrid(lay.nblk), cblk(lay.threads), eblk(lay.ethreads);
+  const size_t vsm = (size_t)lay.ethreads * sizeof(double);
   // probes: R = [y, A eps1 + D^1/2 eps2]
   {
     DevPtr<double> E1((size_t)m * l);
@@ -479,17 +484,17 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   FSA_CUDA(cudaMemsetAsync(g.V.p, 0, nc * sizeof(double), s));
   FSA_CUDA(cudaMemsetAsync(g.H.p, 0, nc * sizeof(double), s));
   // z0 = P^-1 r0
-  k_row_scale<double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R.p, op.Dinv.p, g.X.p);
+  kv_row_scale<double><<<cgrid, eblk, 0, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, op.Dinv.p, g.X.p);
   FSA_CHECK_LAUNCH();
   lowrank_fp64(H, lay, g.X.p, g.S.p);
-  k_z_update<double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
+  kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
   FSA_CHECK_LAUNCH();
   k_cg_init<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.rz0.p, g.alpha_prev.p, g.beta_prev.p,
                                g.beta.p, g.active.p, g.iters.p, g.stop.p, H.err);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W0.p, g.Z.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
   // h0 = z0, v0 = Sigma_dag h0
-  k_spmm_fused<double, double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals.p,
+  launch_spmm_fused<double, double>(lay, s,H.rowptr.p, H.col.p, op.vals.p,
                                                        g.Z.p, g.S.p, g.V.p, g.H.p, g.beta.p, g.part.p);
   FSA_CHECK_LAUNCH();
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
@@ -497,20 +502,20 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   for (int it = 0; it < L; ++it) {
     k_cg_alpha<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.alpha.p, g.active.p, H.err);
     FSA_CHECK_LAUNCH();
-    k_ur_update<double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.U.p, g.R.p, g.H.p, g.V.p, op.Dinv.p,
+    kv_ur_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.U.p, g.R.p, g.H.p, g.V.p, op.Dinv.p,
                                                g.X.p, g.alpha.p, g.active.p, g.part.p);
     FSA_CHECK_LAUNCH();
     k_cg_resid<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rnorm.p, g.active.p, g.stop.p, o.cg_tol,
                                   o.fixed_iters > 0);
     FSA_CHECK_LAUNCH();
     lowrank_fp64(H, lay, g.X.p, g.S.p);
-    k_z_update<double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
+    kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
     FSA_CHECK_LAUNCH();
     k_cg_beta<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, it, L, g.part.p, g.rho.p, g.alpha.p, g.beta.p,
                                  g.alpha_prev.p, g.beta_prev.p, g.active.p, g.iters.p, g.stop.p, g.tdiag.p,
                                  g.toff.p, g.num_active.p, H.err);
     FSA_CHECK_LAUNCH();
-    k_spmm_fused<double, double><<<cgrid, cblk, 0, s>>>(n, lay.c, ldc, lay.chunk, H.rowptr.p, H.col.p, op.vals.p,
+    launch_spmm_fused<double, double>(lay, s,H.rowptr.p, H.col.p, op.vals.p,
                                                          g.Z.p, g.S.p, g.V.p, g.H.p, g.beta.p, g.part.p);
     FSA_CHECK_LAUNCH();
     done_iters = it + 1;
@@ -616,7 +621,7 @@ LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o) 
 void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* out);
 
 void apply_operator(Handle& H, int which, const double* v, int k, double* out) {
-  if (H.op.precision == FSA_MIXED_BF16) return apply_operator_mixed(H, which, v, k, out);
+  if (H.op.precision != FSA_FP64) return apply_operator_mixed(H, which, v, k, out);
   Operator& op = H.op;
   cudaStream_t s = H.stream;
   int64_t n = H.n;

@@ -7,7 +7,9 @@ namespace fsa {
 struct CGLayout {
   int64_t n = 0;
   int c = 0, ldc = 0, L = 0, threads = 32, nblk = 1;
-  int64_t chunk = 1;
+  int64_t chunk = 1;      // rows per block (row-chunk kernels): nblk * chunk >= n
+  int rpb = 1;            // rows per block step of the flat element-wise kernels
+  int ethreads = 32;      // rpb * ldc threads per block
   void setup(int64_t n_, int c_, int L_);
 };
 
@@ -24,7 +26,7 @@ void cov_cross(Handle& H, int64_t np, const double* px, const double* py, int nq
 void build_mspace(Handle& H, const fsa_theta& th);
 void finish_core(Handle& H);
 void build_operator_fp64(Handle& H, const fsa_theta& th);
-void build_operator_mixed(Handle& H, const fsa_theta& th);
+void build_operator_mixed(Handle& H, const fsa_theta& th, int precision);
 void ensure_operator(Handle& H, const fsa_theta& th, int precision);
 void ensure_cg(Handle& H, const CGLayout& lay, bool fp64);
 void sum_log_D(Handle& H, const double* D, double* scal);

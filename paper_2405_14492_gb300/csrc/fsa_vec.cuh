@@ -1,0 +1,207 @@
+// Bandwidth-oriented block-vector kernels of the CG loop.
+//
+// Layout: n x ldc row-major.  Element-wise kernels run a flat grid-stride
+// loop whose stride (blocks x rows-per-block x ldc) is a multiple of ldc, so
+// every thread always touches the same column: loads and stores are fully
+// coalesced, and each thread keeps the partial dot product of its column.
+// Block partials are reduced over the block's row slots in a fixed order and
+// written to part[block][col]; the per-column CG scalars then sum the nblk
+// partials in a fixed order, so every dot product is bit-reproducible.
+//
+// The SpMM (tapered residual Sigma_s~ times the block) runs one warp per row:
+// the row's column indices and values are loaded once, coalesced, into the
+// lanes and broadcast with shuffles, so the gathers of neighbour rows are
+// independent and several stay in flight per lane.
+#pragma once
+#include "fsa_internal.cuh"
+#include "fsa_solver.cuh"
+
+namespace fsa {
+
+template <typename T> struct VAcc { using type = double; };
+template <> struct VAcc<float> { using type = float; };
+
+// block reduction of per-thread column partials -> part[blockIdx.x][col]
+__device__ __forceinline__ void vec_block_partials(double acc, int ldc, int rpb, double* __restrict__ red,
+                                                   double* __restrict__ part) {
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if ((int)threadIdx.x < ldc) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += red[r * ldc + threadIdx.x];
+    part[(int64_t)blockIdx.x * ldc + threadIdx.x] = s;
+  }
+}
+
+#define FSA_VEC_BEGIN                                                          \
+  extern __shared__ double red[];                                              \
+  const int col = threadIdx.x % ldc;                                           \
+  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / ldc;          \
+  const int64_t rstride = (int64_t)gridDim.x * rpb;                            \
+  double acc = 0.0;                                                            \
+  typename VAcc<T>::type sub = 0;                                              \
+  int cnt = 0;
+
+#define FSA_VEC_ACC(v)                                              \
+  do {                                                              \
+    sub += (v);                                                     \
+    if (++cnt == 32) { acc += (double)sub; sub = 0; cnt = 0; }      \
+  } while (0)
+
+#define FSA_VEC_END                      \
+  acc += (double)sub;                    \
+  vec_block_partials(acc, ldc, rpb, red, part);
+
+// U += a H ; R -= a V ; (X = R Dinv) ; part = ||R||^2
+template <typename T>
+__global__ void kv_ur_update(int64_t n, int c, int ldc, int rpb, T* __restrict__ U, T* __restrict__ R,
+                             const T* __restrict__ H, const T* __restrict__ V, const T* __restrict__ Dinv,
+                             T* __restrict__ X, const double* __restrict__ alpha, const int32_t* __restrict__ active,
+                             double* __restrict__ part) {
+  FSA_VEC_BEGIN
+  const T a = (col < c && active[col]) ? (T)alpha[col] : (T)0;
+  for (int64_t i = row0; i < n; i += rstride) {
+    const int64_t idx = i * ldc + col;
+    if (col < c) {
+      T r = R[idx];
+      if (a != (T)0) {
+        U[idx] = U[idx] + a * H[idx];
+        r = r - a * V[idx];
+        R[idx] = r;
+      }
+      if (X) X[idx] = r * Dinv[i];
+      FSA_VEC_ACC(r * r);
+    } else if (X) {
+      X[idx] = (T)0;
+    }
+  }
+  FSA_VEC_END
+}
+
+// Z = (R - S) Dinv ; part = r^T z
+template <typename T>
+__global__ void kv_z_update(int64_t n, int c, int ldc, int rpb, const T* __restrict__ R, const T* __restrict__ S,
+                            const T* __restrict__ Dinv, T* __restrict__ Z, double* __restrict__ part) {
+  FSA_VEC_BEGIN
+  for (int64_t i = row0; i < n; i += rstride) {
+    const int64_t idx = i * ldc + col;
+    if (col < c) {
+      T r = R[idx];
+      T z = (r - S[idx]) * Dinv[i];
+      Z[idx] = z;
+      FSA_VEC_ACC(r * z);
+    } else {
+      Z[idx] = (T)0;
+    }
+  }
+  FSA_VEC_END
+}
+
+// X = R Dinv
+template <typename T>
+__global__ void kv_row_scale(int64_t n, int c, int ldc, int rpb, const T* __restrict__ R, const T* __restrict__ Dinv,
+                             T* __restrict__ X) {
+  const int col = threadIdx.x % ldc;
+  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / ldc;
+  const int64_t rstride = (int64_t)gridDim.x * rpb;
+  for (int64_t i = row0; i < n; i += rstride) {
+    const int64_t idx = i * ldc + col;
+    X[idx] = col < c ? R[idx] * Dinv[i] : (T)0;
+  }
+}
+
+#undef FSA_VEC_BEGIN
+#undef FSA_VEC_ACC
+#undef FSA_VEC_END
+
+// V = Sigma_s~ Z + S + beta V ; H = Z + beta H ; part = h^T v
+// NS 32-column slots per lane (ldc <= 32 NS); 8 warps per block.
+template <typename T, typename VT, int NS>
+__global__ void __launch_bounds__(256) kv_spmm_fused(int64_t n, int c, int ldc, const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colidx,
+                                                     const VT* __restrict__ vals, const T* __restrict__ Z,
+                                                     const T* __restrict__ S, T* __restrict__ V, T* __restrict__ H,
+                                                     const double* __restrict__ beta, double* __restrict__ part) {
+  __shared__ double red[8][NS * 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  T b[NS];
+  double dot[NS];
+  typename VAcc<T>::type sub[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int col = lane + 32 * s;
+    b[s] = col < c ? (T)beta[col] : (T)0;
+    dot[s] = 0.0;
+    sub[s] = 0;
+  }
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
+    const int64_t rb = rowptr[i], re = rowptr[i + 1];
+    T acc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) acc[s] = 0;
+    for (int64_t base = rb; base < re; base += 32) {
+      const int m = (int)((re - base) < 32 ? (re - base) : 32);
+      const int myc = lane < m ? colidx[base + lane] : 0;
+      const T myv = lane < m ? (T)vals[base + lane] : (T)0;
+#pragma unroll 4
+      for (int t = 0; t < m; ++t) {
+        const int j = __shfl_sync(0xffffffffu, myc, t);
+        const T v = __shfl_sync(0xffffffffu, myv, t);
+        const T* zr = Z + (int64_t)j * ldc;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          int col = lane + 32 * s;
+          if (col < ldc) acc[s] += v * zr[col];
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      int col = lane + 32 * s;
+      if (col >= ldc) continue;
+      int64_t idx = i * ldc + col;
+      if (col < c) {
+        T v = acc[s] + S[idx] + (b[s] != (T)0 ? b[s] * V[idx] : (T)0);
+        T h = Z[idx] + (b[s] != (T)0 ? b[s] * H[idx] : (T)0);
+        V[idx] = v;
+        H[idx] = h;
+        sub[s] += h * v;
+      } else {
+        V[idx] = (T)0;
+        H[idx] = (T)0;
+      }
+    }
+    if (++cnt == 32) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) { dot[s] += (double)sub[s]; sub[s] = 0; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) red[wib][lane + 32 * s] = dot[s] + (double)sub[s];
+  __syncthreads();
+  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][col];
+    part[(int64_t)blockIdx.x * ldc + col] = t;
+  }
+}
+
+template <typename T, typename VT>
+inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t* rowptr, const int32_t* col,
+                              const VT* vals, const T* Z, const T* S, T* V, T* H, const double* beta,
+                              double* part) {
+  const int ns = (lay.ldc + 31) / 32;
+  switch (ns) {
+    case 1: kv_spmm_fused<T, VT, 1><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
+    case 2: kv_spmm_fused<T, VT, 2><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
+    case 3: kv_spmm_fused<T, VT, 3><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
+    case 4: kv_spmm_fused<T, VT, 4><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
+    default: throw Error{FSA_ERR_UNSUPPORTED, "block of more than 128 columns"};
+  }
+  FSA_CHECK_LAUNCH();
+}
+
+}  // namespace fsa

@@ -72,6 +72,40 @@ def test_mixed_operator_close_to_fp64(F):
     assert abs(ld16 - ld64) < 1e-3 * abs(ld64)
 
 
+def test_mixed_x2_operator_close_to_fp64(F):
+    """With A stored as a BF16 hi + lo pair the operator is FP32-accurate."""
+    n, m, nu, gamma = 20011, 200, 0.5, 0.015
+    locs = fi.uniform_locations(n, 72)
+    ind = locs[fi.inducing_subset(n, m, 72)]
+    th = (1.0, 0.05, 0.05)
+    V = np.random.default_rng(4).standard_normal((n, 5))
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        ref0 = h.matvec(th, V, 0, F.FSA_FP64)
+        ref1 = h.matvec(th, V, 1, F.FSA_FP64)
+        ld64 = h.logdet_precond(th, F.FSA_FP64)
+        got0 = h.matvec(th, V, 0, F.FSA_MIXED_BF16X2)
+        got1 = h.matvec(th, V, 1, F.FSA_MIXED_BF16X2)
+        ld32 = h.logdet_precond(th, F.FSA_MIXED_BF16X2)
+    assert rel(got0, ref0) < 1e-5
+    assert rel(got1, ref1) < 1e-4
+    assert abs(ld32 - ld64) < 1e-6 * abs(ld64)
+
+
+@pytest.mark.parametrize("n,m,nu,gamma,l,K", [(20011, 200, 0.5, 0.015, 16, 30), (30011, 300, 1.5, 0.012, 12, 25)])
+def test_mixed_x2_loglik_within_1e5_of_oracle(F, n, m, nu, gamma, l, K):
+    locs = fi.uniform_locations(n, 82)
+    ind = locs[fi.inducing_subset(n, m, 82)]
+    th = (1.0, 0.05, 0.01) if nu == 0.5 else (1.0, 0.03, 0.02)
+    y = fi.random_field(locs, nu, *th, 82)
+    ref = O.IterativeFSA(locs, ind, gamma, nu, th).loglik_grad(y, l, 6, 0.0, fixed_iters=K)
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        ll, g, info = h.loglik_grad(y, th, F.make_opts(num_probes=l, fixed_iters=K, seed=6,
+                                                       precision=F.FSA_MIXED_BF16X2))
+    assert abs(ll - ref["loglik"]) < 1e-5 * abs(ref["loglik"]), (ll, ref["loglik"])
+    assert np.linalg.norm(g - ref["grad"]) < 1e-2 * np.linalg.norm(ref["grad"]), (g, ref["grad"])
+
+
 @pytest.mark.parametrize("n,m,nu,gamma,l,K", [(20011, 200, 0.5, 0.015, 16, 30), (30011, 300, 1.5, 0.012, 12, 25)])
 def test_mixed_loglik_within_1e4_of_oracle(F, n, m, nu, gamma, l, K):
     locs = fi.uniform_locations(n, 81)
