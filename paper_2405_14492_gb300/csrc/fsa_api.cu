@@ -164,6 +164,9 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   fsa_opts o = resolve_opts(opts);
   if (o.num_probes < 1 || o.num_probes > 1000) return fail(Error{FSA_ERR_ARG, "num_probes must be in [1, 1000]"});
   if (o.want_grad && !grad) return fail(Error{FSA_ERR_ARG, "grad is NULL"});
+  if (o.cg_max_iter > 8000 || o.fixed_iters > 8000 || o.fixed_iters < 0)
+    return fail(Error{FSA_ERR_ARG, "cg_max_iter / fixed_iters must be <= 8000"});
+  if (!(o.cg_tol >= 0.0)) return fail(Error{FSA_ERR_ARG, "cg_tol must be >= 0"});
   if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
   Handle& H = h->h;

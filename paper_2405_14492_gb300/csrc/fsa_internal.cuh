@@ -109,6 +109,7 @@ struct CGState {
   DevPtr<double> quads;            // e1^T log(T) e1 per column
   DevPtr<double> qlwork;           // QL scratch (c x 2L)
   DevPtr<int32_t> num_active;      // device counter
+  DevPtr<unsigned> ticket;         // last-block counter of the fused scalar steps (kept at 0 between launches)
   int nblk = 0;
 };
 

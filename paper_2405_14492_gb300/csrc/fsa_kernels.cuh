@@ -267,14 +267,18 @@ static __global__ void k_cg_beta(int c, int ldc, int nblk, int l, int L, const d
 // Wilkinson-type shifts (Bowdler, Martin, Reinsch & Wilkinson 1968; EISPACK
 // tql1/tql2), carrying only the first row of the eigenvector matrix.
 // ---------------------------------------------------------------------------
+// One block per probe column (blockIdx.x + 1); the rotation chain is
+// sequential, so one thread works on d, e, z held in shared memory.
 static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, const double* __restrict__ tdiag,
                       const double* __restrict__ toff, double* __restrict__ work, double* __restrict__ quads,
                       unsigned* __restrict__ err) {
-  int col = 1 + blockIdx.x * blockDim.x + threadIdx.x;   // probe columns 1..c-1
-  if (col >= c) return;
+  extern __shared__ double qlsh[];
+  int col = 1 + blockIdx.x;   // probe columns 1..c-1
+  if (col >= c || threadIdx.x != 0) return;
+  (void)work;
   int k = iters[col];
   if (k <= 0) { quads[col] = 0.0; return; }
-  double* d = work + (int64_t)col * 3 * L;
+  double* d = qlsh;
   double* e = d + L;
   double* z = e + L;
   for (int i = 0; i < k; ++i) {
@@ -293,13 +297,13 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
       if (mm == l) break;
       if (++it > 100) { atomicOr(err, kErrNaN); break; }
       double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = hypot(g, 1.0);
+      double r = sqrt(g * g + 1.0);
       g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
       double s = 1.0, cs = 1.0, p = 0.0;
       bool deflated = false;
       for (int i = mm - 1; i >= l; --i) {
         double f = s * e[i], b = cs * e[i];
-        r = hypot(f, g);
+        r = sqrt(f * f + g * g);
         e[i + 1] = r;
         if (r == 0.0) {   // split: the rotation chain stops early
           d[i + 1] -= p;
@@ -307,8 +311,9 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
           deflated = true;
           break;
         }
-        s = f / r;
-        cs = g / r;
+        const double rinv = 1.0 / r;
+        s = f * rinv;
+        cs = g * rinv;
         g = d[i + 1] - p;
         r = (d[i] - g) * s + 2.0 * cs * b;
         p = s * r;
@@ -330,6 +335,19 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
     q += z[j] * z[j] * log(d[j]);
   }
   quads[col] = q;
+}
+
+// e1^T log(T) e1 for every probe column (L <= 8000 iterations)
+static inline void launch_slq(int c, int L, const int32_t* iters, const double* tdiag, const double* toff,
+                              double* quads, unsigned* err, cudaStream_t s) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_done = true;
+  }
+  if (c < 2) return;
+  k_slq<<<c - 1, 32, (size_t)3 * L * sizeof(double), s>>>(c, L, iters, tdiag, toff, nullptr, quads, err);
+  FSA_CHECK_LAUNCH();
 }
 
 }  // namespace fsa

@@ -260,6 +260,133 @@ __global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kin
   }
 }
 
+// dst = bf16(a - b)
+__global__ void k_sub_to_bf16(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
+                              __nv_bfloat16* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = __float2bfloat16_rn(a[t] - b[t]);
+}
+
+__device__ __forceinline__ float dot8_bf16(const uint4& x, const uint4& y) {
+  const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(&x);
+  const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&y);
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float2 u = __bfloat1622float2(a[k]), v = __bfloat1622float2(b[k]);
+    s = fmaf(u.x, v.x, s);
+    s = fmaf(u.y, v.y, s);
+  }
+  return s;
+}
+
+// Gradient, sparse part (Eq. NEGLLDNEGLLFSA with dSigma_dag of §2.2), one warp
+// per row i.  With G_ij = sum_k w_k X_ik Y_jk and the rho-derivative of the
+// low-rank entries dl_ij = b_i.a_j + a_i.(b_j - f_j)  (b = dK L^-T, f = A E):
+//   s0 += dval/ds1 G = (val_ij - nugget [i=j]) / s1 G
+//   sr += dval/drho G = (s1 r'(d) T(d) - dl_ij T(d)) G      (T(0) = 1, r'(0) = 0)
+//   s2 += [i = j] G
+// Rows a_i, b_i stay in registers (KC 16-byte chunks per lane); a_j and
+// q_j = b_j - f_j are gathered with 16-byte loads; X_i is in registers.
+template <int KC, int NS>
+__global__ void __launch_bounds__(256) k_grad_sparse_bf16(
+    int64_t n, int m_pad, int c, int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+    const double* __restrict__ vals, const double* __restrict__ xs, const double* __restrict__ ys,
+    const float* __restrict__ X, const float* __restrict__ Y, const __nv_bfloat16* __restrict__ A,
+    const __nv_bfloat16* __restrict__ B, const __nv_bfloat16* __restrict__ Q, int cov, double s1, double rho,
+    double nug, double gamma, double* __restrict__ part) {
+  __shared__ double red[3][8];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int nch = m_pad / 8;   // 16-byte chunks per row
+  const float inv_l = c > 1 ? 1.0f / (float)(c - 1) : 0.f;
+  double s0 = 0.0, sr = 0.0, s2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
+    const uint4* ai4 = reinterpret_cast<const uint4*>(A + i * m_pad);
+    const uint4* bi4 = reinterpret_cast<const uint4*>(B + i * m_pad);
+    uint4 ai[KC], bi[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      int ch = lane + 32 * k;
+      ai[k] = ch < nch ? ai4[ch] : make_uint4(0, 0, 0, 0);
+      bi[k] = ch < nch ? bi4[ch] : make_uint4(0, 0, 0, 0);
+    }
+    float xi[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      int col = lane + 32 * s;
+      xi[s] = col < c ? X[i * ldc + col] * (col == 0 ? -1.0f : inv_l) : 0.f;
+    }
+    const double xi0 = xs[i], yi0 = ys[i];
+    const int64_t rb = rowptr[i], re = rowptr[i + 1];
+    for (int64_t base = rb; base < re; base += 32) {
+      const int mcnt = (int)((re - base) < 32 ? (re - base) : 32);
+      const int myc = lane < mcnt ? colidx[base + lane] : 0;
+      for (int t = 0; t < mcnt; ++t) {
+        const int j = __shfl_sync(0xffffffffu, myc, t);
+        const uint4* aj4 = reinterpret_cast<const uint4*>(A + (int64_t)j * m_pad);
+        const uint4* qj4 = reinterpret_cast<const uint4*>(Q + (int64_t)j * m_pad);
+        float dl = 0.f;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          int ch = lane + 32 * k;
+          if (ch < nch) dl += dot8_bf16(bi[k], aj4[ch]) + dot8_bf16(ai[k], qj4[ch]);
+        }
+        float g = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          int col = lane + 32 * s;
+          if (col < c) g = fmaf(xi[s], Y[(int64_t)j * ldc + col], g);
+        }
+        dl = warp_sum(dl);
+        g = warp_sum(g);
+        if (lane == 0) {
+          const double gd = (double)g;
+          const double v = vals[base + t];
+          if (j == i) {
+            s0 += (v - nug) / s1 * gd;
+            sr += -(double)dl * gd;
+            s2 += gd;
+          } else {
+            double d = sqrt(sqdist_rn(xi0, yi0, xs[j], ys[j]));
+            double tp = wendland(d, gamma);
+            s0 += v / s1 * gd;
+            sr += (s1 * matern_dr(cov, d, rho) - (double)dl) * tp * gd;
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0) { red[0][wib] = s0; red[1][wib] = sr; red[2][wib] = s2; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    part[(int64_t)blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
+static void launch_grad_sparse_bf16v(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
+                                     const float* X, const float* Y, const __nv_bfloat16* A,
+                                     const __nv_bfloat16* B, const __nv_bfloat16* Q, const fsa_theta& th,
+                                     double* part) {
+  const int kc = (m_pad / 8 + 31) / 32, ns = (ldc + 31) / 32;
+  FSA_REQUIRE(kc >= 1 && kc <= 8 && ns >= 1 && ns <= 4, FSA_ERR_UNSUPPORTED, "gradient kernel: m or l too large");
+#define GS_CASE(KC_, NS_)                                                                                        \
+  if (kc == KC_ && ns == NS_) {                                                                                  \
+    k_grad_sparse_bf16<KC_, NS_><<<nblocks, 256, 0, H.stream>>>(H.n, m_pad, c, ldc, H.rowptr.p, H.col.p, vals,    \
+                                                                H.xs.p, H.ys.p, X, Y, A, B, Q, H.cov,            \
+                                                                th.sigma1_sq, th.rho, th.nugget, H.gamma, part); \
+    FSA_CHECK_LAUNCH();                                                                                          \
+    return;                                                                                                      \
+  }
+#define GS_KC(KC_) GS_CASE(KC_, 1) GS_CASE(KC_, 2) GS_CASE(KC_, 3) GS_CASE(KC_, 4)
+  GS_KC(1) GS_KC(2) GS_KC(3) GS_KC(4) GS_KC(5) GS_KC(6) GS_KC(7) GS_KC(8)
+#undef GS_KC
+#undef GS_CASE
+}
+
 // ---------------------------------------------------------------------------
 // operator build
 // ---------------------------------------------------------------------------
@@ -499,46 +626,33 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_CUDA(cudaMemsetAsync(g.U32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
+  CGScalars q = make_scalars(H, o, L);
   lowrank_mixed(H, C, g.R32.p, g.S32.p);
   kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
-                                           g.part.p);
-  FSA_CHECK_LAUNCH();
-  k_cg_init<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.rz0.p, g.alpha_prev.p, g.beta_prev.p,
-                               g.beta.p, g.active.p, g.iters.p, g.stop.p, H.err);
+                                              g.part.p, kStepInit, 0, q);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  launch_spmm_fused<float, float>(lay, s,H.rowptr.p, H.col.p, op.vals32.p,
-                                                     g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
-  FSA_CHECK_LAUNCH();
+  launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
+                                  g.beta.p, g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
   for (int it = 0; it < L; ++it) {
-    k_cg_alpha<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.alpha.p, g.active.p, H.err);
-    FSA_CHECK_LAUNCH();
     kv_ur_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
-                                              op.Dinv32.p, nullptr, g.alpha.p, g.active.p, g.part.p);
-    FSA_CHECK_LAUNCH();
-    k_cg_resid<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rnorm.p, g.active.p, g.stop.p, o.cg_tol,
-                                  o.fixed_iters > 0);
+                                                 op.Dinv32.p, nullptr, g.alpha.p, g.active.p, g.part.p, kStepResid,
+                                                 it, q);
     FSA_CHECK_LAUNCH();
     lowrank_mixed(H, C, g.R32.p, g.S32.p);
     kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
-                                             g.part.p);
+                                                g.part.p, kStepBeta, it, q);
     FSA_CHECK_LAUNCH();
-    k_cg_beta<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, it, L, g.part.p, g.rho.p, g.alpha.p, g.beta.p,
-                                 g.alpha_prev.p, g.beta_prev.p, g.active.p, g.iters.p, g.stop.p, g.tdiag.p,
-                                 g.toff.p, g.num_active.p, H.err);
-    FSA_CHECK_LAUNCH();
-    launch_spmm_fused<float, float>(lay, s,H.rowptr.p, H.col.p, op.vals32.p,
-                                                       g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p);
-    FSA_CHECK_LAUNCH();
-    if (o.fixed_iters <= 0) {
+    launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
+                                    g.beta.p, g.part.p, kStepAlpha, q);
+    if (o.fixed_iters <= 0 && should_poll(it)) {
       FSA_CUDA(cudaMemcpyAsync(pin_active, g.num_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       FSA_CUDA(cudaStreamSynchronize(s));
       if (*pin_active == 0) break;
     }
   }
-  k_slq<<<(lay.c + 63) / 64, 64, 0, s>>>(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.qlwork.p, g.quads.p, H.err);
-  FSA_CHECK_LAUNCH();
+  launch_slq(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.quads.p, H.err, s);
   DevPtr<double> ypart((size_t)lay.nblk * ldc);
   k_dot_col0<float><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U32.p, ypart.p);
   FSA_CHECK_LAUNCH();
@@ -593,12 +707,12 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
       f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
       f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
-      f.out = B32.p; f.ldo = m_pad;
-      FSA_CUDA(cudaStreamSynchronize(s));
-      // B32 now free for F
+      DevPtr<float> F32(nm);
+      f.out = F32.p; f.ldo = m_pad;
       f.tag = "grad";
       tc_gemm(f, H.err, s);
-      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Fb.p);
+      // Q = B - F, the gathered operand of the sparse gradient term
+      k_sub_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, F32.p, Fb.p);
       FSA_CHECK_LAUNCH();
       FSA_CUDA(cudaStreamSynchronize(s));
     }
@@ -618,7 +732,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
     int ngpart = 152 * 8;
     gbuf.alloc((size_t)ngpart * 3 + 2);
-    launch_grad_sparse_bf16(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th, gbuf.p);
+    launch_grad_sparse_bf16v(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th,
+                             gbuf.p);
     k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq,
                                              gbuf.p + (size_t)ngpart * 3);
     FSA_CHECK_LAUNCH();

@@ -404,6 +404,25 @@ void ensure_cg(Handle& H, const CGLayout& lay, bool fp64) {
   g.quads.ensure(cc);
   g.qlwork.ensure((size_t)lay.ldc * 3 * lay.L);
   g.num_active.ensure(1);
+  if (!g.ticket.p) {
+    g.ticket.alloc(1);
+    FSA_CUDA(cudaMemsetAsync(g.ticket.p, 0, sizeof(unsigned), H.stream));
+  }
+}
+
+CGScalars make_scalars(Handle& H, const fsa_opts& o, int L) {
+  CGState& g = H.cg;
+  CGScalars q;
+  q.rho = g.rho.p; q.rz0 = g.rz0.p; q.alpha = g.alpha.p; q.beta = g.beta.p;
+  q.alpha_prev = g.alpha_prev.p; q.beta_prev = g.beta_prev.p; q.rnorm = g.rnorm.p;
+  q.tdiag = g.tdiag.p; q.toff = g.toff.p;
+  q.active = g.active.p; q.iters = g.iters.p; q.stop = g.stop.p; q.num_active = g.num_active.p;
+  q.err = H.err;
+  q.ticket = g.ticket.p;
+  q.tol = o.cg_tol;
+  q.fixed = o.fixed_iters > 0 ? 1 : 0;
+  q.L = L;
+  return q;
 }
 
 }  // namespace fsa
@@ -483,52 +502,40 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   FSA_CUDA(cudaMemsetAsync(g.U.p, 0, nc * sizeof(double), s));
   FSA_CUDA(cudaMemsetAsync(g.V.p, 0, nc * sizeof(double), s));
   FSA_CUDA(cudaMemsetAsync(g.H.p, 0, nc * sizeof(double), s));
-  // z0 = P^-1 r0
+  // z0 = P^-1 r0 (scalars: rho, rz0, alpha_0 = 1, beta_0 = 0 fused into the z update)
+  CGScalars q = make_scalars(H, o, L);
   kv_row_scale<double><<<cgrid, eblk, 0, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, op.Dinv.p, g.X.p);
   FSA_CHECK_LAUNCH();
   lowrank_fp64(H, lay, g.X.p, g.S.p);
-  kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
-  FSA_CHECK_LAUNCH();
-  k_cg_init<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.rz0.p, g.alpha_prev.p, g.beta_prev.p,
-                               g.beta.p, g.active.p, g.iters.p, g.stop.p, H.err);
+  kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p,
+                                               kStepInit, 0, q);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W0.p, g.Z.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  // h0 = z0, v0 = Sigma_dag h0
-  launch_spmm_fused<double, double>(lay, s,H.rowptr.p, H.col.p, op.vals.p,
-                                                       g.Z.p, g.S.p, g.V.p, g.H.p, g.beta.p, g.part.p);
-  FSA_CHECK_LAUNCH();
+  // h0 = z0, v0 = Sigma_dag h0, alpha_1 = rho / h^T v
+  launch_spmm_fused<double, double>(lay, s, H.rowptr.p, H.col.p, op.vals.p, g.Z.p, g.S.p, g.V.p, g.H.p, g.beta.p,
+                                    g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
-  int done_iters = 0;
   for (int it = 0; it < L; ++it) {
-    k_cg_alpha<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rho.p, g.alpha.p, g.active.p, H.err);
-    FSA_CHECK_LAUNCH();
+    // u += alpha h ; r -= alpha v ; ||r|| and the stop test
     kv_ur_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.U.p, g.R.p, g.H.p, g.V.p, op.Dinv.p,
-                                               g.X.p, g.alpha.p, g.active.p, g.part.p);
-    FSA_CHECK_LAUNCH();
-    k_cg_resid<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, g.part.p, g.rnorm.p, g.active.p, g.stop.p, o.cg_tol,
-                                  o.fixed_iters > 0);
+                                                  g.X.p, g.alpha.p, g.active.p, g.part.p, kStepResid, it, q);
     FSA_CHECK_LAUNCH();
     lowrank_fp64(H, lay, g.X.p, g.S.p);
-    kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p);
+    // z = P^-1 r ; beta ; Lanczos T~ entries
+    kv_z_update<double><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R.p, g.S.p, op.Dinv.p, g.Z.p, g.part.p,
+                                                 kStepBeta, it, q);
     FSA_CHECK_LAUNCH();
-    k_cg_beta<<<1, cblk, 0, s>>>(lay.c, ldc, lay.nblk, it, L, g.part.p, g.rho.p, g.alpha.p, g.beta.p,
-                                 g.alpha_prev.p, g.beta_prev.p, g.active.p, g.iters.p, g.stop.p, g.tdiag.p,
-                                 g.toff.p, g.num_active.p, H.err);
-    FSA_CHECK_LAUNCH();
-    launch_spmm_fused<double, double>(lay, s,H.rowptr.p, H.col.p, op.vals.p,
-                                                         g.Z.p, g.S.p, g.V.p, g.H.p, g.beta.p, g.part.p);
-    FSA_CHECK_LAUNCH();
-    done_iters = it + 1;
-    if (o.fixed_iters <= 0) {
+    // h = z + beta h ; v = Sigma_dag z + beta v ; next alpha
+    launch_spmm_fused<double, double>(lay, s, H.rowptr.p, H.col.p, op.vals.p, g.Z.p, g.S.p, g.V.p, g.H.p,
+                                      g.beta.p, g.part.p, kStepAlpha, q);
+    if (o.fixed_iters <= 0 && should_poll(it)) {
       FSA_CUDA(cudaMemcpyAsync(pin_active, g.num_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       FSA_CUDA(cudaStreamSynchronize(s));
       if (*pin_active == 0) break;
     }
   }
-  (void)done_iters;
   // SLQ
-  k_slq<<<(lay.c + 63) / 64, 64, 0, s>>>(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.qlwork.p, g.quads.p, H.err);
-  FSA_CHECK_LAUNCH();
+  launch_slq(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.quads.p, H.err, s);
   // y^T u
   k_dot_col0<double><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U.p, g.part.p);
   FSA_CHECK_LAUNCH();

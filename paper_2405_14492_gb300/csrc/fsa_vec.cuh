@@ -21,6 +21,105 @@ namespace fsa {
 template <typename T> struct VAcc { using type = double; };
 template <> struct VAcc<float> { using type = float; };
 
+// ---------------------------------------------------------------------------
+// CG scalars fused into the producing kernels (Appendix A).  The last block
+// to finish (ticket counter) sums the per-block partials of every column in
+// a fixed order and applies the per-column scalar step, so results do not
+// depend on which block finishes last.
+// ---------------------------------------------------------------------------
+struct CGScalars {
+  double *rho, *rz0, *alpha, *beta, *alpha_prev, *beta_prev, *rnorm, *tdiag, *toff;
+  int32_t *active, *iters, *stop, *num_active;
+  unsigned* err;
+  unsigned* ticket;
+  double tol;
+  int fixed, L;
+};
+
+enum ScalarStep : int { kStepNone = 0, kStepInit = 1, kStepAlpha = 2, kStepResid = 3, kStepBeta = 4 };
+
+__device__ __forceinline__ void scalar_step(int step, int col, int c, double v, int l, CGScalars& q) {
+  if (col >= c) return;
+  if (step == kStepInit) {
+    if (!isfinite(v)) atomicOr(q.err, kErrNaN);
+    q.rho[col] = v;
+    q.rz0[col] = v;
+    q.alpha_prev[col] = 1.0;   // alpha_0 = 1
+    q.beta_prev[col] = 0.0;    // beta_0 = 0
+    q.beta[col] = 0.0;
+    q.active[col] = v > 0.0 ? 1 : 0;
+    q.iters[col] = 0;
+    q.stop[col] = 0;
+  } else if (step == kStepAlpha) {
+    double a = 0.0;
+    if (q.active[col]) {
+      a = q.rho[col] / v;
+      if (!isfinite(a) || !(v > 0.0)) { atomicOr(q.err, kErrNaN); a = 0.0; }
+    }
+    q.alpha[col] = a;
+  } else if (step == kStepResid) {
+    if (q.active[col]) {
+      double rn = sqrt(v);
+      q.rnorm[col] = rn;
+      q.stop[col] = (!q.fixed && rn < q.tol) ? 1 : 0;
+    }
+  } else if (step == kStepBeta) {
+    if (q.active[col]) {
+      double b = v / q.rho[col];
+      double a = q.alpha[col];
+      if (l < q.L) {   // Lanczos tridiagonal from the CG coefficients (Appendix A)
+        q.tdiag[(int64_t)col * q.L + l] = 1.0 / a + q.beta_prev[col] / q.alpha_prev[col];
+        if (l > 0) q.toff[(int64_t)col * q.L + l - 1] = sqrt(q.beta_prev[col]) / q.alpha_prev[col];
+      }
+      q.iters[col] = l + 1;
+      q.alpha_prev[col] = a;
+      q.beta_prev[col] = b;
+      q.rho[col] = v;
+      if (!isfinite(b)) { atomicOr(q.err, kErrNaN); b = 0.0; }
+      q.beta[col] = b;
+      if (q.stop[col] || v <= 0.0) q.active[col] = 0;
+    } else {
+      q.beta[col] = 0.0;
+    }
+  }
+}
+
+// called by every thread of every block after part[blockIdx.x][*] is written
+__device__ __forceinline__ void finish_scalars(int step, const double* __restrict__ part, int ldc, int c, int l,
+                                               CGScalars& q, double* __restrict__ red) {
+  if (step == kStepNone) return;
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(q.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int per = (int)blockDim.x / ldc;   // >= 1 by construction
+  const int col = threadIdx.x % ldc, slot = threadIdx.x / ldc;
+  const bool worker = slot < per;
+  double v = 0.0;
+  if (worker) {
+    double s = 0.0;
+    for (int b = slot; b < (int)gridDim.x; b += per) s += __ldcg(&part[(int64_t)b * ldc + col]);
+    red[slot * ldc + col] = s;
+  }
+  __syncthreads();
+  if (worker && slot == 0) {
+    for (int r = 0; r < per; ++r) v += red[r * ldc + col];
+    scalar_step(step, col, c, v, l, q);
+  }
+  if (step == kStepBeta) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int k = 0; k < c; ++k) s += q.active[k];
+      *q.num_active = s;
+    }
+  }
+  if (threadIdx.x == 0) *q.ticket = 0u;
+}
+
 // block reduction of per-thread column partials -> part[blockIdx.x][col]
 __device__ __forceinline__ void vec_block_partials(double acc, int ldc, int rpb, double* __restrict__ red,
                                                    double* __restrict__ part) {
@@ -50,14 +149,15 @@ __device__ __forceinline__ void vec_block_partials(double acc, int ldc, int rpb,
 
 #define FSA_VEC_END                      \
   acc += (double)sub;                    \
-  vec_block_partials(acc, ldc, rpb, red, part);
+  vec_block_partials(acc, ldc, rpb, red, part); \
+  finish_scalars(step, part, ldc, c, l, q, red);
 
 // U += a H ; R -= a V ; (X = R Dinv) ; part = ||R||^2
 template <typename T>
 __global__ void kv_ur_update(int64_t n, int c, int ldc, int rpb, T* __restrict__ U, T* __restrict__ R,
                              const T* __restrict__ H, const T* __restrict__ V, const T* __restrict__ Dinv,
                              T* __restrict__ X, const double* __restrict__ alpha, const int32_t* __restrict__ active,
-                             double* __restrict__ part) {
+                             double* __restrict__ part, int step, int l, CGScalars q) {
   FSA_VEC_BEGIN
   const T a = (col < c && active[col]) ? (T)alpha[col] : (T)0;
   for (int64_t i = row0; i < n; i += rstride) {
@@ -81,7 +181,8 @@ __global__ void kv_ur_update(int64_t n, int c, int ldc, int rpb, T* __restrict__
 // Z = (R - S) Dinv ; part = r^T z
 template <typename T>
 __global__ void kv_z_update(int64_t n, int c, int ldc, int rpb, const T* __restrict__ R, const T* __restrict__ S,
-                            const T* __restrict__ Dinv, T* __restrict__ Z, double* __restrict__ part) {
+                            const T* __restrict__ Dinv, T* __restrict__ Z, double* __restrict__ part, int step,
+                            int l, CGScalars q) {
   FSA_VEC_BEGIN
   for (int64_t i = row0; i < n; i += rstride) {
     const int64_t idx = i * ldc + col;
@@ -121,7 +222,8 @@ __global__ void __launch_bounds__(256) kv_spmm_fused(int64_t n, int c, int ldc, 
                                                      const int32_t* __restrict__ colidx,
                                                      const VT* __restrict__ vals, const T* __restrict__ Z,
                                                      const T* __restrict__ S, T* __restrict__ V, T* __restrict__ H,
-                                                     const double* __restrict__ beta, double* __restrict__ part) {
+                                                     const double* __restrict__ beta, double* __restrict__ part,
+                                                     int step, CGScalars q) {
   __shared__ double red[8][NS * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
@@ -187,18 +289,24 @@ __global__ void __launch_bounds__(256) kv_spmm_fused(int64_t n, int c, int ldc, 
     for (int w = 0; w < 8; ++w) t += red[w][col];
     part[(int64_t)blockIdx.x * ldc + col] = t;
   }
+  finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
 }
+
+CGScalars make_scalars(Handle& H, const fsa_opts& o, int L);
+
+// the host reads the active-column count after every iteration
+inline bool should_poll(int /*it*/) { return true; }
 
 template <typename T, typename VT>
 inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t* rowptr, const int32_t* col,
                               const VT* vals, const T* Z, const T* S, T* V, T* H, const double* beta,
-                              double* part) {
+                              double* part, int step, const CGScalars& q) {
   const int ns = (lay.ldc + 31) / 32;
   switch (ns) {
-    case 1: kv_spmm_fused<T, VT, 1><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
-    case 2: kv_spmm_fused<T, VT, 2><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
-    case 3: kv_spmm_fused<T, VT, 3><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
-    case 4: kv_spmm_fused<T, VT, 4><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part); break;
+    case 1: kv_spmm_fused<T, VT, 1><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q); break;
+    case 2: kv_spmm_fused<T, VT, 2><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q); break;
+    case 3: kv_spmm_fused<T, VT, 3><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q); break;
+    case 4: kv_spmm_fused<T, VT, 4><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q); break;
     default: throw Error{FSA_ERR_UNSUPPORTED, "block of more than 128 columns"};
   }
   FSA_CHECK_LAUNCH();
