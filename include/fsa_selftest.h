@@ -22,7 +22,8 @@ extern "C" {
  *   M, N, K      problem size (any M >= 1, N <= 256 multiple of 16 when halves,
  *                K >= 1; ragged edges exercise the TMA zero fill)
  *   num_a, num_b 1 or 2 operand tensors; pairs: bit 2a+b selects A_a B_b^T
- *   halves       1: output column j = acc[j] + acc[j + N/2]
+ *   halves       0: plain output; 1 or 2: output column j = acc[j] + acc[j + N/2];
+ *                3: output column j = acc[j] + acc[j + N/3] + acc[j + 2N/3]
  *   splits       requested split-K factor
  *   max_rel_err  receives max |got - ref| / sum |a b| over the output
  *   launched_splits receives the split count actually used (may be NULL)

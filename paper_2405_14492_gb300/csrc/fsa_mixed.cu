@@ -184,13 +184,24 @@ __global__ void k_reduce_splits(int splits, int rows, int cols, const float* __r
   }
 }
 
-// src (n x ldc FP32) optionally scaled by rowscale -> dst (2 ldc x n_pad BF16): rows
-// 0..ldc-1 hi, ldc..2ldc-1 lo; 64 points per block through shared memory
+// v = sum of nsplit BF16 pieces (2: ~16 significant bits, 3: the full FP32 24)
+__device__ __forceinline__ void split_n(double v, int nsplit, __nv_bfloat16* out) {
+  __nv_bfloat16 h = __double2bfloat16(v);
+  out[0] = h;
+  double r = v - (double)__bfloat162float(h);
+  __nv_bfloat16 mid = __double2bfloat16(r);
+  out[1] = mid;
+  if (nsplit == 3) out[2] = __double2bfloat16(r - (double)__bfloat162float(mid));
+}
+
+// src (n x ldc FP32) optionally scaled by rowscale -> dst (nsplit ldc x n_pad BF16):
+// plane p (rows p ldc .. p ldc + ldc - 1) holds the p-th BF16 piece; K-major
+// (points contiguous) for the B operand of A^T X; 64 points per block
 constexpr int kSTRows = 64;
-__global__ void k_split_transpose(int64_t n, int c, int ldc, const float* __restrict__ src,
+__global__ void k_split_transpose(int64_t n, int c, int ldc, int nsplit, const float* __restrict__ src,
                                   const float* __restrict__ rowscale, int64_t n_pad,
                                   __nv_bfloat16* __restrict__ dst) {
-  extern __shared__ __nv_bfloat16 tl[];   // [2 ldc][kSTRows + 2]
+  extern __shared__ __nv_bfloat16 tl[];   // [nsplit ldc][kSTRows + 2]
   const int W = kSTRows + 2;
   int64_t r0 = (int64_t)blockIdx.x * kSTRows;
   for (int t = threadIdx.x; t < kSTRows * ldc; t += blockDim.x) {
@@ -201,31 +212,29 @@ __global__ void k_split_transpose(int64_t n, int c, int ldc, const float* __rest
       v = src[r * ldc + cc];
       if (rowscale) v *= rowscale[r];
     }
-    __nv_bfloat16 h, l;
-    split_bf16(v, h, l);
-    tl[cc * W + rr] = h;
-    tl[(ldc + cc) * W + rr] = l;
+    __nv_bfloat16 pc[3];
+    split_n((double)v, nsplit, pc);
+    for (int p = 0; p < nsplit; ++p) tl[(p * ldc + cc) * W + rr] = pc[p];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 2 * ldc * kSTRows; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nsplit * ldc * kSTRows; t += blockDim.x) {
     int cc = t / kSTRows, rr = t % kSTRows;
     int64_t r = r0 + rr;
     if (r < n_pad) dst[(int64_t)cc * n_pad + r] = (r < n) ? tl[cc * W + rr] : __float2bfloat16(0.f);
   }
 }
 
-// q (m x ldc FP64) -> (2 ldc x m_pad) BF16 hi/lo, K-major (q transposed)
-__global__ void k_split_q(int m, int c, int ldc, int m_pad, const double* __restrict__ q,
+// q (m x ldc FP64) -> (nsplit ldc x m_pad) BF16 pieces, K-major (q transposed)
+__global__ void k_split_q(int m, int c, int ldc, int nsplit, int m_pad, const double* __restrict__ q,
                           __nv_bfloat16* __restrict__ dst) {
   int64_t total = (int64_t)ldc * m_pad;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int cc = (int)(t / m_pad), k = (int)(t % m_pad);
-    float v = (cc < c && k < m) ? (float)q[(int64_t)k * ldc + cc] : 0.f;
-    __nv_bfloat16 h, l;
-    split_bf16(v, h, l);
-    dst[(int64_t)cc * m_pad + k] = h;
-    dst[(int64_t)(ldc + cc) * m_pad + k] = l;
+    double v = (cc < c && k < m) ? q[(int64_t)k * ldc + cc] : 0.0;
+    __nv_bfloat16 pc[3];
+    split_n(v, nsplit, pc);
+    for (int p = 0; p < nsplit; ++p) dst[(int64_t)(p * ldc + cc) * m_pad + k] = pc[p];
   }
 }
 
@@ -503,8 +512,34 @@ struct MixedCtx {
   TmaMap mAt, mA, mX, mQ;
   TmaMap mAt_lo, mA_lo;     // low halves of A (FSA_MIXED_BF16X2)
   bool lo = false;
+  int nsplit = 2;           // BF16 pieces of the vector operands (3: FP32-exact)
   float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
 };
+
+// vector-operand split: three BF16 pieces (24 significant bits) while the
+// stacked operand fits one 256-wide MMA, else two
+static inline int pick_nsplit(int ldc) { return 3 * ldc <= 256 ? 3 : 2; }
+static inline int mixed_ldc(int c) {
+  int l16 = (c + 15) / 16 * 16;
+  return 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
+}
+
+static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C);
+
+static void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc) {
+  Operator& op = H.op;
+  CGState& g = H.cg;
+  C.ldc = ldc; C.c = c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
+  C.nsplit = pick_nsplit(ldc);
+  const int ns = C.nsplit * ldc;
+  FSA_REQUIRE(ns <= 256, FSA_ERR_UNSUPPORTED, "block too wide for the tensor-core products");
+  g.Xb.ensure((size_t)ns * C.n_pad);
+  g.qb.ensure((size_t)ns * C.m_pad);
+  set_operator_maps(op, n, C);
+  C.mX = make_tma_bf16(g.Xb.p, ns, n, C.n_pad, ns);
+  C.mQ = make_tma_bf16(g.qb.p, ns, C.m_pad, C.m_pad, ns);
+  C.splits_w = tc_pick_splits(C.m_pad, ns, (int)n, ns);
+}
 
 static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C) {
   C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
@@ -522,21 +557,22 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
-  size_t smem = (size_t)2 * ldc * (kSTRows + 2) * sizeof(__nv_bfloat16);
-  k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, src, rowscale,
-                                                                                    C.n_pad, g.Xb.p);
+  size_t smem = (size_t)C.nsplit * ldc * (kSTRows + 2) * sizeof(__nv_bfloat16);
+  k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, C.nsplit, src,
+                                                                                    rowscale, C.n_pad, g.Xb.p);
   FSA_CHECK_LAUNCH();
   TcGemm t;
   t.a[0] = &C.mAt; t.a[1] = &C.mAt_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mX; t.num_b = 1;
   t.pairs = C.lo ? (1u | 4u) : 1u;
-  t.M = C.m_pad; t.N = 2 * ldc; t.K = (int)C.n; t.bn = 2 * ldc;
-  t.halves = 1;
+  t.M = C.m_pad; t.N = C.nsplit * ldc; t.K = (int)C.n; t.bn = C.nsplit * ldc;
+  t.stack = C.nsplit;
   t.splits = C.splits_w;
   int kb = (t.K + 63) / 64, per = (kb + t.splits - 1) / t.splits, splits = (kb + per - 1) / per;
   t.out = C.wpart; t.ldo = ldc; t.split_stride = (int64_t)C.m_pad * ldc;
   t.tag = tag;
-  t.alg_bytes = t.num_a * (double)H.m * C.n * 2.0 + 2.0 * C.c * C.n * 2.0 + (double)splits * H.m * C.c * 4.0;
+  t.alg_bytes = t.num_a * (double)H.m * C.n * 2.0 + (double)C.nsplit * C.c * C.n * 2.0 +
+                (double)splits * H.m * C.c * 4.0;
   tc_gemm(t, H.err, s);
   k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
                                                                     t.split_stride, w, ldc, 0);
@@ -548,17 +584,17 @@ static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const ch
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
-  k_split_q<<<grid_for((int64_t)ldc * C.m_pad, 256), 256, 0, s>>>(H.m, C.c, ldc, C.m_pad, q, g.qb.p);
+  k_split_q<<<grid_for((int64_t)ldc * C.m_pad, 256), 256, 0, s>>>(H.m, C.c, ldc, C.nsplit, C.m_pad, q, g.qb.p);
   FSA_CHECK_LAUNCH();
   TcGemm t;
   t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mQ; t.num_b = 1;
   t.pairs = C.lo ? (1u | 4u) : 1u;
-  t.M = (int)C.n; t.N = 2 * ldc; t.K = C.m_pad; t.bn = 2 * ldc;
-  t.halves = 1;
+  t.M = (int)C.n; t.N = C.nsplit * ldc; t.K = C.m_pad; t.bn = C.nsplit * ldc;
+  t.stack = C.nsplit;
   t.out = S; t.ldo = ldc;
   t.tag = tag;
-  t.alg_bytes = t.num_a * (double)C.n * H.m * 2.0 + 2.0 * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
+  t.alg_bytes = t.num_a * (double)C.n * H.m * 2.0 + (double)C.nsplit * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
   tc_gemm(t, H.err, s);
 }
 
@@ -582,20 +618,14 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_REQUIRE(l + 1 <= 128, FSA_ERR_UNSUPPORTED, "mixed precision supports at most 127 probes");
   CGLayout lay;
   int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
-  lay.setup(n, l + 1, L);
+  lay.setup(n, l + 1, L, mixed_ldc(l + 1));
   ensure_cg(H, lay, false);
   int ldc = lay.ldc;
   size_t nc = (size_t)n * ldc;
   g.U32.ensure(nc); g.R32.ensure(nc); g.Z32.ensure(nc); g.H32.ensure(nc); g.V32.ensure(nc);
   g.S32.ensure(nc); g.W032.ensure(nc);
   MixedCtx C;
-  C.ldc = ldc; C.c = lay.c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
-  g.Xb.ensure((size_t)2 * ldc * C.n_pad);
-  g.qb.ensure((size_t)2 * ldc * C.m_pad);
-  set_operator_maps(op, n, C);
-  C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
-  C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
-  C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);
+  mixed_ctx_setup(H, C, n, lay.c, ldc);
   DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
   C.wpart = wpart_buf.p;
   dim3 cgrid(lay.nblk), cblk(lay.threads), eblk(lay.ethreads);
@@ -800,22 +830,16 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
   int m = H.m;
   FSA_REQUIRE(k <= 128, FSA_ERR_UNSUPPORTED, "mixed matvec supports at most 128 columns");
   CGLayout lay;
-  lay.setup(n, k, 1);
+  lay.setup(n, k, 1, mixed_ldc(k));
   int ldc = lay.ldc;
   size_t nc = (size_t)n * ldc;
   DevPtr<float> V32(nc), S32(nc), O32(nc);
   k_f64_to_f32_pad<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, k, ldc, v, V32.p);
   FSA_CHECK_LAUNCH();
   MixedCtx C;
-  C.ldc = ldc; C.c = k; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
-  g.Xb.ensure((size_t)2 * ldc * C.n_pad);
-  g.qb.ensure((size_t)2 * ldc * C.m_pad);
   g.w.ensure((size_t)m * ldc);
   g.q.ensure((size_t)m * ldc);
-  set_operator_maps(op, n, C);
-  C.mX = make_tma_bf16(g.Xb.p, 2 * ldc, n, C.n_pad, 2 * ldc);
-  C.mQ = make_tma_bf16(g.qb.p, 2 * ldc, C.m_pad, C.m_pad, 2 * ldc);
-  C.splits_w = tc_pick_splits(C.m_pad, 2 * ldc, (int)n, 2 * ldc);
+  mixed_ctx_setup(H, C, n, k, ldc);
   DevPtr<float> wpart((size_t)C.splits_w * C.m_pad * ldc);
   C.wpart = wpart.p;
   DevPtr<double> part((size_t)lay.nblk * ldc), beta(ldc);

@@ -28,16 +28,16 @@ struct Ops {
 
 // ref and error: one thread per output element
 __global__ void k_ref_check(int M, int N, int K, int64_t lda, int64_t ldb, Ops ops, int num_a, int num_b,
-                            unsigned pairs, int halves, const float* __restrict__ out, int64_t ldo,
+                            unsigned pairs, int stack, const float* __restrict__ out, int64_t ldo,
                             int64_t split_stride, int splits, double* __restrict__ err) {
-  int ncols = halves ? N / 2 : N;
+  int ncols = N / stack;
   int64_t total = (int64_t)M * ncols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(t / ncols), j = (int)(t % ncols);
     double ref = 0.0, mag = 0.0;
-    for (int h = 0; h < (halves ? 2 : 1); ++h) {
-      int jj = j + h * (N / 2);
+    for (int h = 0; h < stack; ++h) {
+      int jj = j + h * (N / stack);
       for (int a = 0; a < num_a; ++a)
         for (int b = 0; b < num_b; ++b) {
           if (!(pairs & (1u << (2 * a + b)))) continue;
@@ -65,6 +65,7 @@ extern "C" int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, u
                                     uint64_t seed, double* max_rel_err, int* launched_splits) {
   try {
     cudaStream_t s = nullptr;
+    const int stack = halves == 1 ? 2 : (halves >= 2 ? halves : 1);
     int64_t ldk = (K + 63) / 64 * 64;
     DevPtr<__nv_bfloat16> A0((size_t)M * ldk), A1((size_t)M * ldk), B0((size_t)N * ldk), B1((size_t)N * ldk);
     k_fill_bf16<<<256, 256, 0, s>>>(M, K, ldk, rng_key(seed, 11), 1.0f, A0.p);
@@ -73,9 +74,9 @@ extern "C" int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, u
     k_fill_bf16<<<256, 256, 0, s>>>(N, K, ldk, rng_key(seed, 14), 0.01f, B1.p);
     FSA_CHECK_LAUNCH();
     TmaMap ma0 = make_tma_bf16(A0.p, M, K, ldk, 128), ma1 = make_tma_bf16(A1.p, M, K, ldk, 128);
-    int bn = halves ? N : std::min(256, (N + 15) / 16 * 16);
+    int bn = stack > 1 ? N : std::min(256, (N + 15) / 16 * 16);
     TmaMap mb0 = make_tma_bf16(B0.p, N, K, ldk, bn), mb1 = make_tma_bf16(B1.p, N, K, ldk, bn);
-    int ncols = halves ? N / 2 : N;
+    int ncols = N / stack;
     int kb = (K + 63) / 64;
     int per = (kb + splits - 1) / splits;
     int act = (kb + per - 1) / per;
@@ -85,13 +86,13 @@ extern "C" int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, u
     TcGemm g;
     g.a[0] = &ma0; g.a[1] = &ma1; g.num_a = num_a;
     g.b[0] = &mb0; g.b[1] = &mb1; g.num_b = num_b;
-    g.pairs = pairs; g.M = M; g.N = N; g.K = K; g.bn = bn; g.splits = splits; g.halves = halves;
+    g.pairs = pairs; g.M = M; g.N = N; g.K = K; g.bn = bn; g.splits = splits; g.stack = stack;
     g.out = out.p; g.ldo = ncols; g.split_stride = (int64_t)M * ncols;
     tc_gemm(g, err.p, s);
     DevPtr<double> e(1);
     FSA_CUDA(cudaMemset(e.p, 0, sizeof(double)));
     Ops ops{{A0.p, A1.p}, {B0.p, B1.p}};
-    k_ref_check<<<512, 256, 0, s>>>(M, N, K, ldk, ldk, ops, num_a, num_b, pairs, halves, out.p, ncols,
+    k_ref_check<<<512, 256, 0, s>>>(M, N, K, ldk, ldk, ops, num_a, num_b, pairs, stack, out.p, ncols,
                                     (int64_t)M * ncols, act, e.p);
     FSA_CHECK_LAUNCH();
     unsigned herr = 0;

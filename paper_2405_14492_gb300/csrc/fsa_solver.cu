@@ -369,10 +369,10 @@ __global__ void k_assemble(int64_t n, int c, int exact_weight, const double* __r
 // ---------------------------------------------------------------------------
 // CG block set-up
 // ---------------------------------------------------------------------------
-void CGLayout::setup(int64_t n_, int c_, int L_) {
+void CGLayout::setup(int64_t n_, int c_, int L_, int ldc_) {
   n = n_;
   c = c_;
-  ldc = (c + 7) / 8 * 8;
+  ldc = ldc_ > 0 ? ldc_ : (c + 7) / 8 * 8;
   L = L_;
   threads = (ldc + 31) / 32 * 32;
   int64_t nb = (n + 127) / 128;

@@ -10,7 +10,7 @@ struct CGLayout {
   int64_t chunk = 1;      // rows per block (row-chunk kernels): nblk * chunk >= n
   int rpb = 1;            // rows per block step of the flat element-wise kernels
   int ethreads = 32;      // rpb * ldc threads per block
-  void setup(int64_t n_, int c_, int L_);
+  void setup(int64_t n_, int c_, int L_, int ldc_ = 0);   // ldc_ = 0: c rounded up to 8
 };
 
 struct LoglikResult {

@@ -35,7 +35,7 @@ struct Params {
   unsigned pairs;
   int M, bn, kblocks, kb_per_split, stages;
   uint32_t a_bytes, b_bytes, stage_bytes, tmem_cols, idesc;
-  int halves, n_valid;
+  int stack, n_valid;
   float* out;
   int64_t ldo, split_stride;
   unsigned* err;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
       float* orow = p.out + (int64_t)blockIdx.z * p.split_stride + (int64_t)row * p.ldo;
       const bool in = row < p.M && nk > 0;
-      if (!p.halves) {
+      if (p.stack <= 1) {
         for (int c0 = 0; c0 < p.bn; c0 += 8) {
           uint32_t r[8];
           tmem_ld8(taddr + c0, r);
@@ -244,17 +244,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           }
         }
       } else {
-        const int h = p.bn / 2;
+        // split vector operand stacked along N: sum the stack column blocks
+        const int h = p.bn / p.stack;
         for (int c0 = 0; c0 < h; c0 += 8) {
-          uint32_t r[8], t[8];
+          uint32_t r[8], t[8], u[8];
           tmem_ld8(taddr + c0, r);
           tmem_ld8(taddr + h + c0, t);
+          if (p.stack == 3) tmem_ld8(taddr + 2 * h + c0, u);
           tmem_wait_ld();
           if (in) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               int col = c0 + j;
-              if (col < p.n_valid) orow[col] = __uint_as_float(r[j]) + __uint_as_float(t[j]);
+              float v = __uint_as_float(r[j]) + __uint_as_float(t[j]);
+              if (p.stack == 3) v += __uint_as_float(u[j]);
+              if (col < p.n_valid) orow[col] = v;
             }
           }
         }
@@ -321,7 +325,10 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   FSA_REQUIRE(g.num_a >= 1 && g.num_a <= 2 && g.num_b >= 1 && g.num_b <= 2, FSA_ERR_ARG, "tc_gemm operand count");
   int bn = g.bn > 0 ? g.bn : std::min(256, (g.N + 15) / 16 * 16);
   FSA_REQUIRE(bn % 16 == 0 && bn >= 16 && bn <= 256, FSA_ERR_ARG, "tc_gemm N tile must be a multiple of 16 <= 256");
-  FSA_REQUIRE(!g.halves || (g.N == bn && (bn / 2) % 8 == 0), FSA_ERR_ARG, "tc_gemm halves needs N = bn, N/2 % 8 = 0");
+  const int stack = g.halves ? 2 : std::max(1, g.stack);
+  FSA_REQUIRE(stack <= 3, FSA_ERR_ARG, "tc_gemm stack must be 1, 2 or 3");
+  FSA_REQUIRE(stack == 1 || (g.N == bn && bn % stack == 0 && (bn / stack) % 8 == 0), FSA_ERR_ARG,
+              "tc_gemm stacked epilogue needs N = bn and N/stack a multiple of 8");
   FSA_REQUIRE(g.M > 0 && g.N > 0 && g.K > 0, FSA_ERR_ARG, "tc_gemm empty problem");
   tc::Params p;
   std::memset(&p, 0, sizeof(p));
@@ -346,8 +353,8 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   p.tmem_cols = cols;
   // instruction descriptor: D FP32, A BF16, B BF16, both K-major, N >> 3, M >> 4
   p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
-  p.halves = g.halves;
-  p.n_valid = g.n_valid > 0 ? g.n_valid : (g.halves ? bn / 2 : g.N);
+  p.stack = stack;
+  p.n_valid = g.n_valid > 0 ? g.n_valid : (stack > 1 ? bn / stack : g.N);
   p.out = g.out;
   p.ldo = g.ldo;
   p.split_stride = g.split_stride;

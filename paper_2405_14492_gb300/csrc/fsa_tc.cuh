@@ -34,7 +34,8 @@ struct TcGemm {
   int K = 0;                // reduction length
   int bn = 0;               // N tile (multiple of 16, <= 256); 0 = min(N rounded to 16, 256)
   int splits = 1;           // split-K factor (outputs at out + z * split_stride)
-  int halves = 0;           // epilogue: out[:, j] = acc[:, j] + acc[:, j + N/2]
+  int halves = 0;           // epilogue: out[:, j] = acc[:, j] + acc[:, j + N/2]  (same as stack = 2)
+  int stack = 1;            // epilogue: out[:, j] = sum_s acc[:, j + s N/stack], stack in {1, 2, 3}
   float* out = nullptr;
   int64_t ldo = 0;
   int64_t split_stride = 0;

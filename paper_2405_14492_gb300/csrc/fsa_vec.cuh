@@ -95,20 +95,23 @@ __device__ __forceinline__ void finish_scalars(int step, const double* __restric
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int per = (int)blockDim.x / ldc;   // >= 1 by construction
-  const int col = threadIdx.x % ldc, slot = threadIdx.x / ldc;
-  const bool worker = slot < per;
-  double v = 0.0;
-  if (worker) {
-    double s = 0.0;
-    for (int b = slot; b < (int)gridDim.x; b += per) s += __ldcg(&part[(int64_t)b * ldc + col]);
-    red[slot * ldc + col] = s;
+  // one warp per column: lanes sum strided partials, then a fixed shuffle tree
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  const int nb = (int)gridDim.x;
+  for (int col = warp; col < ldc; col += nw) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nb; b += 128) {
+      s0 += __ldcg(&part[(int64_t)b * ldc + col]);
+      s1 += __ldcg(&part[(int64_t)(b + 32) * ldc + col]);
+      s2 += __ldcg(&part[(int64_t)(b + 64) * ldc + col]);
+      s3 += __ldcg(&part[(int64_t)(b + 96) * ldc + col]);
+    }
+    for (; b < nb; b += 32) s0 += __ldcg(&part[(int64_t)b * ldc + col]);
+    double v = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) scalar_step(step, col, c, v, l, q);
   }
-  __syncthreads();
-  if (worker && slot == 0) {
-    for (int r = 0; r < per; ++r) v += red[r * ldc + col];
-    scalar_step(step, col, c, v, l, q);
-  }
+  (void)red;
   if (step == kStepBeta) {
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -42,6 +42,8 @@ def _selftest(M, N, K, na, nb, pairs, halves, splits, seed=1):
     (1024, 144, 20000, 1, 1, 1, 1, 38),    # split-K with halves (the A^T X shape)
     (70, 32, 2000, 1, 1, 1, 0, 5),         # split-K, ragged everything
     (4096, 48, 1024, 1, 1, 1, 1, 1),       # many M tiles (the A q shape)
+    (1024, 240, 20000, 2, 1, 5, 3, 38),    # A hi/lo with a three-piece stacked vector (the A^T X shape)
+    (3000, 240, 1024, 2, 1, 5, 3, 1),      # same for the A q shape, ragged M
 ])
 def test_tc_gemm_selftest(F, M, N, K, na, nb, pairs, halves, splits):
     st, err, act = _selftest(M, N, K, na, nb, pairs, halves, splits)
