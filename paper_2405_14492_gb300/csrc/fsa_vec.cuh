@@ -98,7 +98,8 @@ __device__ __forceinline__ void finish_scalars(int step, const double* __restric
   // one warp per column: lanes sum strided partials, then a fixed shuffle tree
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
   const int nb = (int)gridDim.x;
-  for (int col = warp; col < ldc; col += nw) {
+  // only complete warps take part (the block size rpb * ldc need not be a multiple of 32)
+  for (int col = warp; warp < nw && col < ldc; col += nw) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int b = lane;
     for (; b + 96 < nb; b += 128) {
