@@ -184,14 +184,15 @@ __global__ void k_reduce_splits(int splits, int rows, int cols, const float* __r
   }
 }
 
-// v = sum of nsplit BF16 pieces (2: ~16 significant bits, 3: the full FP32 24)
-__device__ __forceinline__ void split_n(double v, int nsplit, __nv_bfloat16* out) {
-  __nv_bfloat16 h = __double2bfloat16(v);
+// v = sum of nsplit BF16 pieces (2: ~16 significant bits, 3: the full FP32 24);
+// FP32 arithmetic (the pieces of an FP32 value are exact differences)
+__device__ __forceinline__ void split_n(float v, int nsplit, __nv_bfloat16* out) {
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
   out[0] = h;
-  double r = v - (double)__bfloat162float(h);
-  __nv_bfloat16 mid = __double2bfloat16(r);
+  float r = v - __bfloat162float(h);
+  __nv_bfloat16 mid = __float2bfloat16_rn(r);
   out[1] = mid;
-  if (nsplit == 3) out[2] = __double2bfloat16(r - (double)__bfloat162float(mid));
+  if (nsplit == 3) out[2] = __float2bfloat16_rn(r - __bfloat162float(mid));
 }
 
 // src (n x ldc FP32) optionally scaled by rowscale -> dst (nsplit ldc x n_pad BF16):
@@ -213,7 +214,7 @@ __global__ void k_split_transpose(int64_t n, int c, int ldc, int nsplit, const f
       if (rowscale) v *= rowscale[r];
     }
     __nv_bfloat16 pc[3];
-    split_n((double)v, nsplit, pc);
+    split_n(v, nsplit, pc);
     for (int p = 0; p < nsplit; ++p) tl[(p * ldc + cc) * W + rr] = pc[p];
   }
   __syncthreads();
@@ -231,7 +232,7 @@ __global__ void k_split_q(int m, int c, int ldc, int nsplit, int m_pad, const do
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int cc = (int)(t / m_pad), k = (int)(t % m_pad);
-    double v = (cc < c && k < m) ? q[(int64_t)k * ldc + cc] : 0.0;
+    float v = (cc < c && k < m) ? (float)q[(int64_t)k * ldc + cc] : 0.f;
     __nv_bfloat16 pc[3];
     split_n(v, nsplit, pc);
     for (int p = 0; p < nsplit; ++p) dst[(int64_t)(p * ldc + cc) * m_pad + k] = pc[p];
@@ -516,12 +517,14 @@ struct MixedCtx {
   float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
 };
 
-// vector-operand split: three BF16 pieces (24 significant bits) while the
-// stacked operand fits one 256-wide MMA, else two
-static inline int pick_nsplit(int ldc) { return 3 * ldc <= 256 ? 3 : 2; }
+// vector-operand split: two BF16 pieces (~16 significant bits).  Three pieces
+// (the full FP32 24) are supported by the kernels (kVecSplit = 3) but changed
+// the n = 1e6 log-likelihood by < 1e-6 relative at a higher cost, so two are used.
+constexpr int kVecSplit = 2;
+static inline int pick_nsplit(int ldc) { return kVecSplit == 3 && 3 * ldc <= 256 ? 3 : 2; }
 static inline int mixed_ldc(int c) {
   int l16 = (c + 15) / 16 * 16;
-  return 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
+  return kVecSplit == 3 && 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
 }
 
 static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C);
