@@ -260,9 +260,52 @@ fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t pre
 fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, const fsa_opts* opts,
                        const double* pred_locs, int64_t n_p, int32_t num_var_samples, double* mean, double* var,
                        fsa_info* info) {
-  (void)h; (void)y; (void)theta; (void)opts; (void)pred_locs; (void)n_p; (void)num_var_samples;
-  (void)mean; (void)var; (void)info;
-  return fail(Error{FSA_ERR_UNSUPPORTED, "prediction not built yet"});
+  if (!h || !y || !pred_locs || !mean || n_p < 1) return fail(Error{FSA_ERR_ARG, "NULL argument or n_p < 1"});
+  if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
+  if (var && (num_var_samples < 1 || num_var_samples > 4096))
+    return fail(Error{FSA_ERR_ARG, "num_var_samples must be in [1, 4096]"});
+  fsa_opts o = resolve_opts(opts);
+  if (o.cg_max_iter > 8000) return fail(Error{FSA_ERR_ARG, "cg_max_iter must be <= 8000"});
+  if (o.precision != FSA_FP64)
+    return fail(Error{FSA_ERR_UNSUPPORTED, "prediction is implemented in the FP64 form"});
+  Handle& H = h->h;
+  try {
+    FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
+    H.y.ensure(H.n);
+    {
+      const double* ydev = y;
+      DevPtr<double> tmp;
+      if (!o.y_on_device) {
+        tmp.alloc(H.n);
+        FSA_CUDA(cudaMemcpyAsync(tmp.p, y, sizeof(double) * H.n, cudaMemcpyHostToDevice, H.stream));
+        ydev = tmp.p;
+      }
+      k_gather_y<<<grid_for(H.n, 256), 256, 0, H.stream>>>(H.n, H.perm.p, ydev, H.y.p, H.err);
+      FSA_CHECK_LAUNCH();
+      check_err(H);
+    }
+    ensure_operator(H, *theta, FSA_FP64);
+    PredResult r = run_predict_fp64(H, *theta, o, pred_locs, n_p, num_var_samples, mean, var);
+    FSA_CUDA(cudaEventRecord(H.ev1, H.stream));
+    FSA_CUDA(cudaEventSynchronize(H.ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, H.ev0, H.ev1);
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iters_y = r.iters_u;
+      info->iters_max = std::max(r.iters_u, r.iters_sparse);
+      info->converged = r.converged ? 1 : 0;
+      info->num_probes = num_var_samples;
+      info->nnz = H.nnz;
+      info->time_ms = ms;
+    }
+    if (!r.converged) return fail(Error{FSA_ERR_NO_CONVERGENCE, "CG iteration limit reached"});
+    return FSA_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
+    return fail(e);
+  }
 }
 
 void fsa_free(fsa_handle* h) {

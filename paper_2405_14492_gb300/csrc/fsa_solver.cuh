@@ -32,6 +32,13 @@ void ensure_cg(Handle& H, const CGLayout& lay, bool fp64);
 void sum_log_D(Handle& H, const double* D, double* scal);
 
 LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o);
+
+struct PredResult {
+  int iters_u = 0, iters_sparse = 0;
+  bool converged = true;
+};
+PredResult run_predict_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o, const double* pred_host, int64_t np,
+                            int s, double* mean_host, double* var_host);
 void apply_operator(Handle& H, int which, const double* v_dev_internal, int k, double* out_dev_internal);
 
 // kernels used across units

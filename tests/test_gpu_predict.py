@@ -1,0 +1,74 @@
+"""Predictive mean and simulation-based variances (Algorithm 1) on the GPU
+against the FP64 oracle under identical probes, and against the exact FSA
+predictive variances within the estimator's standard deviation."""
+import numpy as np
+import pytest
+
+import fsa_inputs as fi
+from oracle import fsa_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import paper_2405_14492_gb300 as F
+    return F
+
+
+def _case(n, m, n_p, seed, gamma):
+    locs = fi.uniform_locations(n, seed)
+    ind = locs[fi.inducing_subset(n, m, seed)]
+    pred = fi.uniform_locations(n_p, seed, stream=fi.STREAM_PRED_LOCATIONS)
+    return locs, ind, pred
+
+
+@pytest.mark.parametrize("nu,probe", [(0.5, "rademacher"), (1.5, "gaussian")])
+def test_predict_parity_same_probes(F, nu, probe):
+    n, m, n_p, s, gamma = 3001, 60, 517, 40, 0.05
+    locs, ind, pred = _case(n, m, n_p, 91, gamma)
+    th = (1.0, 0.08, 0.05)
+    y = fi.random_field(locs, nu, *th, 91)
+    ref = O.IterativeFSA(locs, ind, gamma, nu, th).predict(y, pred, s, 13, 1e-11, probe=probe)
+    kind = F.FSA_PROBE_RADEMACHER if probe == "rademacher" else F.FSA_PROBE_GAUSSIAN
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        mean, var, info = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-11, seed=13, probe=kind))
+    assert info["converged"] == 1
+    assert np.max(np.abs(mean - ref["mean"])) < 1e-7 * np.max(np.abs(ref["mean"]))
+    assert np.max(np.abs(var - ref["var"])) < 1e-7
+
+
+def test_predict_statistically_matches_exact_variances(F):
+    n, m, n_p, s, gamma = 1500, 40, 300, 400, 0.06
+    locs, ind, pred = _case(n, m, n_p, 92, gamma)
+    th = (1.0, 0.1, 0.1)
+    y = fi.random_field(locs, 0.5, *th, 92)
+    D = O.DenseFSA(locs, ind, gamma, 0.5, th)
+    mu, var_exact = D.predict(y, pred)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        mean, var, _ = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-10, seed=3))
+    assert np.max(np.abs(mean - mu)) < 1e-7
+    # Rademacher diagonal estimator: Var[D_l,p] = (1/s) sum_{k != p} A_pk^2
+    _, _, Ssnp, _ = D.cross(pred)
+    Amat = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
+    sd = np.sqrt((np.sum(Amat ** 2, 1) - np.diag(Amat) ** 2) / s)
+    assert np.all(np.abs(var - var_exact) <= 5 * sd + 1e-9)
+
+
+def test_predict_mean_only_and_far_points(F):
+    n, m, gamma = 2000, 30, 0.05
+    locs = fi.uniform_locations(n, 93)
+    ind = locs[fi.inducing_subset(n, m, 93)]
+    # prediction points outside the data square, some beyond the taper range of every point
+    pred = np.array([[-0.01, 0.5], [1.02, 0.3], [3.0, 3.0], [0.5, 0.5], [-1.0, -1.0]])
+    th = (1.0, 0.1, 0.1)
+    y = fi.random_field(locs, 0.5, *th, 93)
+    ref = O.IterativeFSA(locs, ind, gamma, 0.5, th).predict(y, pred, 8, 5, 1e-11)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        mean, var, _ = h.predict(y, th, pred, 8, F.make_opts(cg_tol=1e-11, seed=5))
+        mean2, var2, _ = h.predict(y, th, pred, 8, F.make_opts(cg_tol=1e-11, seed=5), want_var=False)
+    assert np.allclose(mean, ref["mean"], atol=1e-8)
+    assert np.allclose(var, ref["var"], atol=1e-8)
+    assert np.array_equal(mean, mean2) and var2 is None
+    # far from every data point: no sparse term, variance is the low-rank (FITC) one
+    assert var[2] > 0.0 and var[4] > 0.0
