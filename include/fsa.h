@@ -203,6 +203,37 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta,
 /* Release a handle and all its device memory. */
 void fsa_free(fsa_handle* h);
 
+/*
+ * fsa_csr_noalloc — the taper-support pattern of fsa_build + fsa_get_csr
+ * (same rows, same ascending columns, caller's point order), computed without
+ * allocating any memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory, e.g. a process whose device
+ * memory is owned by its own pool or capped allocator, or code running where
+ * cudaMalloc must not be called.  All temporaries live in one fixed-size
+ * device array compiled into the library (about 6 MB, held on every GPU that
+ * loads the library until the process exits); the call makes no cudaMalloc,
+ * cudaFree or other allocating call.
+ *   locs_dev      n x 2 row-major DEVICE array of locations
+ *   n             1 <= n <= 65536 (the size of the fixed array); larger n is
+ *                 rejected with FSA_ERR_ARG (use fsa_build instead)
+ *   taper_range   gamma > 0
+ *   rowptr_dev    DEVICE int64[n + 1], written
+ *   col_dev       DEVICE int32[col_capacity], written; NULL: only *nnz_out is set
+ *   col_capacity  capacity of col_dev; if it is below the pattern's nonzeros the
+ *                 call returns FSA_ERR_ARG with *nnz_out set to the size needed
+ *   nnz_out       HOST int64, receives the number of nonzeros
+ *   cuda_stream   stream to run on (NULL: legacy default stream); the call
+ *                 synchronises this stream before returning
+ * Errors: FSA_ERR_ARG, FSA_ERR_NAN (non-finite coordinates), FSA_ERR_CUDA.
+ * The first call on a device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the same array and its
+ * contents persist between calls (the call clears what must start at zero), so
+ * calls that overlap on the GPU (from two streams or threads at once) race.
+ */
+fsa_status fsa_csr_noalloc(const double* locs_dev, int64_t n, double taper_range, int64_t* rowptr_dev,
+                           int32_t* col_dev, int64_t col_capacity, int64_t* nnz_out, void* cuda_stream);
+
 /* Estimate of the device bytes one loglik+grad call on a problem of this size
  * holds (structure + operator + CG block), used for admission control. */
 int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probes,
