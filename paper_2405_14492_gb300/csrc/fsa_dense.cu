@@ -16,7 +16,7 @@ namespace fsa {
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
 template <int TA, int TB>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, const double* __restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, const double* __restrict__ A, int64_t lda,
                                                     const double* __restrict__ B, int64_t ldb,
                                                     const double* __restrict__ scale, double* __restrict__ C,
                                                     int64_t ldc, double alpha, double beta, int kchunk,
@@ -122,7 +122,7 @@ void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
   double* part = nullptr;
   if (splits > 1) part = ws.scratch_f64((size_t)splits * M * N);
 #define LAUNCH_DG(a, b)                                                                               \
-  dgemm_kernel<a, b><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, scale, C, ldc, alpha, beta, kchunk, \
+  k_dgemm<a, b><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, scale, C, ldc, alpha, beta, kchunk, \
                                           part)
   if (!ta && !tb) LAUNCH_DG(0, 0);
   else if (!ta && tb) LAUNCH_DG(0, 1);

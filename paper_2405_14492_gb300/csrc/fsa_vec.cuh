@@ -13,6 +13,9 @@
 // lanes and broadcast with shuffles, so the gathers of neighbour rows are
 // independent and several stay in flight per lane.
 #pragma once
+#include <algorithm>
+#include <type_traits>
+
 #include "fsa_internal.cuh"
 #include "fsa_solver.cuh"
 
@@ -296,6 +299,94 @@ __global__ void __launch_bounds__(256) kv_spmm_fused(int64_t n, int c, int ldc, 
   finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
 }
 
+// FP32 form: lane L owns columns 4L..4L+3 (ldc <= 128, ldc % 4 == 0), so one
+// 16-byte load per active lane gathers a whole neighbour row.
+static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c, int ldc, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ colidx,
+                                                        const float* __restrict__ vals, const float* __restrict__ Z,
+                                                        const float* __restrict__ S, float* __restrict__ V,
+                                                        float* __restrict__ H, const double* __restrict__ beta,
+                                                        double* __restrict__ part, int step, CGScalars q) {
+  __shared__ double red[8][128];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int c4 = ldc >> 2;
+  const bool act = lane < c4;
+  const int col0 = 4 * lane;
+  float b[4];
+  float sub[4] = {0.f, 0.f, 0.f, 0.f};
+  double dot[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) b[k] = (act && col0 + k < c) ? (float)beta[col0 + k] : 0.f;
+  const bool use_b = (b[0] != 0.f) || (b[1] != 0.f) || (b[2] != 0.f) || (b[3] != 0.f);
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
+    const int64_t rb = rowptr[i], re = rowptr[i + 1];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t base = rb; base < re; base += 32) {
+      const int m = (int)((re - base) < 32 ? (re - base) : 32);
+      const int myc = lane < m ? colidx[base + lane] : 0;
+      const float myv = lane < m ? vals[base + lane] : 0.f;
+#pragma unroll 4
+      for (int t = 0; t < m; ++t) {
+        const int j = __shfl_sync(0xffffffffu, myc, t);
+        const float v = __shfl_sync(0xffffffffu, myv, t);
+        if (act) {
+          const float4 z = *reinterpret_cast<const float4*>(Z + (int64_t)j * ldc + col0);
+          acc.x = fmaf(v, z.x, acc.x);
+          acc.y = fmaf(v, z.y, acc.y);
+          acc.z = fmaf(v, z.z, acc.z);
+          acc.w = fmaf(v, z.w, acc.w);
+        }
+      }
+    }
+    if (act) {
+      const int64_t idx = i * ldc + col0;
+      const float4 sv = *reinterpret_cast<const float4*>(S + idx);
+      const float4 zi = *reinterpret_cast<const float4*>(Z + idx);
+      float4 vo = make_float4(acc.x + sv.x, acc.y + sv.y, acc.z + sv.z, acc.w + sv.w);
+      float4 ho = zi;
+      if (use_b) {
+        const float4 vv = *reinterpret_cast<const float4*>(V + idx);
+        const float4 hh = *reinterpret_cast<const float4*>(H + idx);
+        vo.x += b[0] * vv.x; vo.y += b[1] * vv.y; vo.z += b[2] * vv.z; vo.w += b[3] * vv.w;
+        ho.x += b[0] * hh.x; ho.y += b[1] * hh.y; ho.z += b[2] * hh.z; ho.w += b[3] * hh.w;
+      }
+      // columns >= c hold zeros in Z and S and get zero beta, so they stay zero
+      *reinterpret_cast<float4*>(V + idx) = vo;
+      *reinterpret_cast<float4*>(H + idx) = ho;
+      sub[0] += ho.x * vo.x; sub[1] += ho.y * vo.y; sub[2] += ho.z * vo.z; sub[3] += ho.w * vo.w;
+    }
+    if (++cnt == 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { dot[k] += (double)sub[k]; sub[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[wib][(4 * lane + k) & 127] = act ? dot[k] + (double)sub[k] : 0.0;
+  __syncthreads();
+  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][col];
+    part[(int64_t)blockIdx.x * ldc + col] = t;
+  }
+  finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
+}
+
+// grid of one full wave: SM count x resident blocks of the kernel
+static inline int spmm_f4_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_fused_f4, 256, 0);
+    blocks = sms * (per > 0 ? per : 1);
+  }
+  return blocks;
+}
+
 CGScalars make_scalars(Handle& H, const fsa_opts& o, int L);
 
 // the host reads the active-column count after every iteration
@@ -305,6 +396,14 @@ template <typename T, typename VT>
 inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t* rowptr, const int32_t* col,
                               const VT* vals, const T* Z, const T* S, T* V, T* H, const double* beta,
                               double* part, int step, const CGScalars& q) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<VT, float>::value) {
+    if (lay.ldc % 4 == 0 && lay.ldc <= 128) {
+      const int nb = std::min(lay.nblk, spmm_f4_blocks());
+      kv_spmm_fused_f4<<<nb, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q);
+      FSA_CHECK_LAUNCH();
+      return;
+    }
+  }
   const int ns = (lay.ldc + 31) / 32;
   switch (ns) {
     case 1: kv_spmm_fused<T, VT, 1><<<lay.nblk, 256, 0, s>>>(lay.n, lay.c, lay.ldc, rowptr, col, vals, Z, S, V, H, beta, part, step, q); break;
