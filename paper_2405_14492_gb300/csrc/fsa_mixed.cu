@@ -631,8 +631,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   mixed_ctx_setup(H, C, n, lay.c, ldc);
   DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
   C.wpart = wpart_buf.p;
-  dim3 cgrid(lay.nblk), cblk(lay.threads), eblk(lay.ethreads);
-  const size_t vsm = (size_t)lay.ethreads * sizeof(double);
+  FSA_REQUIRE(ldc % 4 == 0 && ldc <= 128, FSA_ERR_UNSUPPORTED, "mixed block width must be a multiple of 4, at most 128");
+  const Vec4Launch v4 = vec4_launch(lay);
   // probes: R = [y, A~ eps1 + D^1/2 eps2]
   {
     int l16 = round_up(l, 16);
@@ -661,21 +661,20 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
   CGScalars q = make_scalars(H, o, L);
   lowrank_mixed(H, C, g.R32.p, g.S32.p);
-  kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
-                                              g.part.p, kStepInit, 0, q);
+  kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+                                                      g.part.p, kStepInit, 0, q);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
   launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
                                   g.beta.p, g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
   for (int it = 0; it < L; ++it) {
-    kv_ur_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
-                                                 op.Dinv32.p, nullptr, g.alpha.p, g.active.p, g.part.p, kStepResid,
-                                                 it, q);
+    kv4_ur_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
+                                                         g.alpha.p, g.active.p, g.part.p, kStepResid, it, q);
     FSA_CHECK_LAUNCH();
     lowrank_mixed(H, C, g.R32.p, g.S32.p);
-    kv_z_update<float><<<cgrid, eblk, vsm, s>>>(n, lay.c, ldc, lay.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
-                                                g.part.p, kStepBeta, it, q);
+    kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
+                                                        g.Z32.p, g.part.p, kStepBeta, it, q);
     FSA_CHECK_LAUNCH();
     launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
                                     g.beta.p, g.part.p, kStepAlpha, q);

@@ -315,7 +315,8 @@ int tc_pick_splits(int M, int N, int K, int bn) {
   int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + bn - 1) / bn);
   int kblocks = (K + tc::BK - 1) / tc::BK;
   if (tiles >= 152) return 1;
-  int s = (2 * 152 + tiles - 1) / tiles;
+  // at most two CTAs per SM in one wave: a partly filled second wave costs a whole tile time
+  int s = (2 * 152) / tiles;
   int maxs = kblocks / 8;
   if (s > maxs) s = maxs;
   return s < 1 ? 1 : s;

@@ -323,11 +323,22 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
   for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
     const int64_t rb = rowptr[i], re = rowptr[i + 1];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the row's own operands are loaded up front, in flight with the gathers
+    const int64_t idx = i * ldc + col0;
+    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f), zi = sv, vv = sv, hh = sv;
+    if (act) {
+      sv = *reinterpret_cast<const float4*>(S + idx);
+      zi = *reinterpret_cast<const float4*>(Z + idx);
+      if (use_b) {
+        vv = *reinterpret_cast<const float4*>(V + idx);
+        hh = *reinterpret_cast<const float4*>(H + idx);
+      }
+    }
     for (int64_t base = rb; base < re; base += 32) {
       const int m = (int)((re - base) < 32 ? (re - base) : 32);
       const int myc = lane < m ? colidx[base + lane] : 0;
       const float myv = lane < m ? vals[base + lane] : 0.f;
-#pragma unroll 4
+#pragma unroll 8
       for (int t = 0; t < m; ++t) {
         const int j = __shfl_sync(0xffffffffu, myc, t);
         const float v = __shfl_sync(0xffffffffu, myv, t);
@@ -341,14 +352,9 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
       }
     }
     if (act) {
-      const int64_t idx = i * ldc + col0;
-      const float4 sv = *reinterpret_cast<const float4*>(S + idx);
-      const float4 zi = *reinterpret_cast<const float4*>(Z + idx);
       float4 vo = make_float4(acc.x + sv.x, acc.y + sv.y, acc.z + sv.z, acc.w + sv.w);
       float4 ho = zi;
       if (use_b) {
-        const float4 vv = *reinterpret_cast<const float4*>(V + idx);
-        const float4 hh = *reinterpret_cast<const float4*>(H + idx);
         vo.x += b[0] * vv.x; vo.y += b[1] * vv.y; vo.z += b[2] * vv.z; vo.w += b[3] * vv.w;
         ho.x += b[0] * hh.x; ho.y += b[1] * hh.y; ho.z += b[2] * hh.z; ho.w += b[3] * hh.w;
       }
@@ -372,6 +378,111 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
     part[(int64_t)blockIdx.x * ldc + col] = t;
   }
   finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 element-wise kernels with 16-byte accesses: thread -> 4 consecutive
+// columns (c4 = ldc/4 threads per row, rpb rows per block step), row loop
+// unrolled so that several independent loads are in flight per thread.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void vec4_block_partials(const double (&acc)[4], int ldc, int c4, int rpb,
+                                                    double* __restrict__ red, double* __restrict__ part) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[threadIdx.x * 4 + k] = acc[k];
+  __syncthreads();
+  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += red[(r * c4 + col / 4) * 4 + (col & 3)];
+    part[(int64_t)blockIdx.x * ldc + col] = s;
+  }
+}
+
+// U += a H ; R -= a V ; part = ||R||^2
+static __global__ void kv4_ur_update(int64_t n, int c, int ldc, int rpb, float* __restrict__ U, float* __restrict__ R,
+                                     const float* __restrict__ H, const float* __restrict__ V,
+                                     const double* __restrict__ alpha, const int32_t* __restrict__ active,
+                                     double* __restrict__ part, int step, int l, CGScalars q) {
+  extern __shared__ double red4[];
+  const int c4 = ldc >> 2;
+  const int cq = threadIdx.x % c4, col0 = 4 * cq;
+  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / c4;
+  const int64_t rstride = (int64_t)gridDim.x * rpb;
+  float a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = (col0 + k < c && active[col0 + k]) ? (float)alpha[col0 + k] : 0.f;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float sub[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+#pragma unroll 4
+  for (int64_t i = row0; i < n; i += rstride) {
+    const int64_t idx = i * ldc + col0;
+    float4 r = *reinterpret_cast<const float4*>(R + idx);
+    const float4 h = *reinterpret_cast<const float4*>(H + idx);
+    const float4 v = *reinterpret_cast<const float4*>(V + idx);
+    float4 u = *reinterpret_cast<const float4*>(U + idx);
+    u.x = fmaf(a[0], h.x, u.x); u.y = fmaf(a[1], h.y, u.y); u.z = fmaf(a[2], h.z, u.z); u.w = fmaf(a[3], h.w, u.w);
+    r.x = fmaf(-a[0], v.x, r.x); r.y = fmaf(-a[1], v.y, r.y); r.z = fmaf(-a[2], v.z, r.z); r.w = fmaf(-a[3], v.w, r.w);
+    *reinterpret_cast<float4*>(U + idx) = u;
+    *reinterpret_cast<float4*>(R + idx) = r;
+    sub[0] += r.x * r.x; sub[1] += r.y * r.y; sub[2] += r.z * r.z; sub[3] += r.w * r.w;
+    if (++cnt == 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { acc[k] += (double)sub[k]; sub[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] += (double)sub[k];
+  vec4_block_partials(acc, ldc, c4, rpb, red4, part);
+  finish_scalars(step, part, ldc, c, l, q, red4);
+}
+
+// Z = (R - S) Dinv ; part = r^T z
+static __global__ void kv4_z_update(int64_t n, int c, int ldc, int rpb, const float* __restrict__ R,
+                                    const float* __restrict__ S, const float* __restrict__ Dinv,
+                                    float* __restrict__ Z, double* __restrict__ part, int step, int l, CGScalars q) {
+  extern __shared__ double red4[];
+  const int c4 = ldc >> 2;
+  const int cq = threadIdx.x % c4, col0 = 4 * cq;
+  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / c4;
+  const int64_t rstride = (int64_t)gridDim.x * rpb;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float sub[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+#pragma unroll 4
+  for (int64_t i = row0; i < n; i += rstride) {
+    const int64_t idx = i * ldc + col0;
+    const float4 r = *reinterpret_cast<const float4*>(R + idx);
+    const float4 sv = *reinterpret_cast<const float4*>(S + idx);
+    const float d = Dinv[i];
+    // columns >= c hold zeros in R and S, so Z is zero there
+    float4 z = make_float4((r.x - sv.x) * d, (r.y - sv.y) * d, (r.z - sv.z) * d, (r.w - sv.w) * d);
+    *reinterpret_cast<float4*>(Z + idx) = z;
+    sub[0] += r.x * z.x; sub[1] += r.y * z.y; sub[2] += r.z * z.z; sub[3] += r.w * z.w;
+    if (++cnt == 32) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { acc[k] += (double)sub[k]; sub[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] += (double)sub[k];
+  vec4_block_partials(acc, ldc, c4, rpb, red4, part);
+  finish_scalars(step, part, ldc, c, l, q, red4);
+}
+
+struct Vec4Launch {
+  int blocks, threads, rpb;
+  size_t smem;
+};
+static inline Vec4Launch vec4_launch(const CGLayout& lay) {
+  Vec4Launch v;
+  const int c4 = lay.ldc / 4;
+  v.rpb = std::max(1, 256 / c4);
+  v.threads = v.rpb * c4;
+  v.blocks = lay.nblk;
+  v.smem = (size_t)v.threads * 4 * sizeof(double);
+  return v;
 }
 
 // grid of one full wave: SM count x resident blocks of the kernel
