@@ -311,6 +311,8 @@ def run_gpu(args):
         if "bf16_single_form" in result:
             result["bf16_single_form"]["loglik_rel_err_vs_fp64"] = abs(result["bf16_single_form"]["loglik"] - ll64) / abs(ll64)
     h.close()
+    if rank == 0 and args.serve_requests > 0:
+        result["serving"] = run_serving(args, F)
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, ns, v, iters = oracle_sample_eval(w, locs, ind, y, args.cpu_sample)
         result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -321,6 +323,95 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# serving leg: the Poisson request stream through the persistent server
+# ----------------------------------------------------------------------------
+def _make_request_inputs(args):
+    num, idx = args
+    return fi.serving_stream(num)[idx].make()
+
+
+def _serving_opts(F, req, precision):
+    if req.kind == "loglik":
+        return F.make_opts(num_probes=req.num_probes, cg_tol=1e-3, precision=precision, seed=req.seed)
+    return F.make_opts(num_probes=req.num_probes, cg_tol=1e-3, precision=F.FSA_FP64, seed=req.seed)
+
+
+def _submit_request(F, srv, req, data, precision):
+    locs, ind, y, pred = data
+    th = (req.sigma1_sq, req.rho, req.nugget)
+    opts = _serving_opts(F, req, precision)
+    if req.kind == "loglik":
+        return srv.submit_loglik(locs, ind, req.taper_range(), req.nu, y, th, opts)
+    return srv.submit_predict(locs, ind, req.taper_range(), req.nu, y, th, pred, req.num_var_samples, opts)
+
+
+def _run_alone(F, req, data, precision):
+    locs, ind, y, pred = data
+    th = (req.sigma1_sq, req.rho, req.nugget)
+    opts = _serving_opts(F, req, precision)
+    with F.FSAHandle(locs, ind, req.taper_range(), req.nu) as h:
+        if req.kind == "loglik":
+            return h.loglik_grad(y, th, opts)[0]
+        h.predict(y, th, pred, req.num_var_samples, opts)
+        return None
+
+
+def run_serving(args, F):
+    """Replays the request stream (Poisson arrivals) against one server and
+    reports latency percentiles and completed evaluations per second, beside
+    the plain FP64 one-request-at-a-time GPU form on an evenly spaced sample of
+    the same requests."""
+    import multiprocessing as mp
+
+    reqs = fi.serving_stream(args.serve_requests)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
+        data = pool.map(_make_request_inputs, [(args.serve_requests, k) for k in range(len(reqs))], chunksize=4)
+    prec = F.FSA_MIXED_BF16X2
+    with F.FSAServer(max_slots=args.serve_slots) as srv:
+        # warm-up: one request of each kind, not counted
+        warm = [next(r for r in reqs if r.kind == k) for k in ("loglik", "predict")]
+        for r in warm:
+            srv.wait(_submit_request(F, srv, r, data[r.index], prec), 600.0)
+        base = srv.stats()
+        tickets = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            dt = t0 + r.arrival_s - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(_submit_request(F, srv, r, data[r.index], prec))
+        res = [srv.wait(t, 3600.0) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = [r for r in res if r["status"] in (0, 4)]
+    served = {"requests": len(reqs), "arrival_rate_per_s": 200.0, "slots": args.serve_slots,
+              "completed": len(ok), "failed": len(res) - len(ok),
+              "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")),
+              "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")),
+              "mean_run_ms": float(np.mean([r["run_ms"] for r in res])),
+              "evals_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 2),
+              "loglik_precision": "bf16x2", "predict_precision": "fp64",
+              "peak_running": st["peak_running"], "peak_footprint_gb": round(st["peak_in_use_bytes"] / 1e9, 2),
+              "budget_gb": round(st["budget_bytes"] / 1e9, 1), "warmup_requests": base["completed"]}
+    # one-request-at-a-time FP64 GPU form on an evenly spaced sample
+    sample = reqs[:: max(1, len(reqs) // args.serve_fp64_sample)][: args.serve_fp64_sample]
+    t0 = time.perf_counter()
+    ll64 = {}
+    for r in sample:
+        ll64[r.index] = _run_alone(F, r, data[r.index], F.FSA_FP64)
+    t64 = time.perf_counter() - t0
+    errs = [abs(res[r.index]["loglik"] - ll64[r.index]) / abs(ll64[r.index])
+            for r in sample if r.kind == "loglik" and ll64[r.index]]
+    served["fp64_one_at_a_time"] = {"requests": len(sample), "evals_per_s": round(len(sample) / t64, 3),
+                                    "sample": f"every {max(1, len(reqs) // args.serve_fp64_sample)}th request"}
+    served["speedup_vs_fp64_one_at_a_time"] = round(served["evals_per_s"] / (len(sample) / t64), 2)
+    served["loglik_rel_err_vs_fp64_max"] = float(max(errs)) if errs else None
+    return served
 
 
 def main():
@@ -336,6 +427,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--ref-sample", type=int, default=2500)
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-fp64-sample", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -144,3 +144,67 @@ PRED_N2E5 = Workload("pred-n2e5-np1e5-m800", n=200_000, m=800, nu=0.5, sigma1_sq
                      n_pred=100_000, num_var_samples=100)
 
 WORKLOADS = {w.name: w for w in (SMALL_EXP_N2K, MATERN15_N1E5, EXP_N1E6, PRED_N2E5)}
+
+
+# ----------------------------------------------------------------------------
+# Serving stream: independent problems of mixed size arriving as a Poisson process
+# ----------------------------------------------------------------------------
+STREAM_SERVING = 8
+SERVING_SEED = BASE_SEED + 5
+
+
+@dataclass
+class ServingRequest:
+    index: int
+    arrival_s: float        # arrival time after the stream starts
+    kind: str               # "loglik" (likelihood + gradient) or "predict"
+    n: int
+    m: int
+    rho: float
+    nugget: float
+    sigma1_sq: float = 1.0
+    nu: float = 0.5
+    nnz_per_row: float = 20.0
+    num_probes: int = 50
+    n_pred: int = 0
+    num_var_samples: int = 0
+
+    @property
+    def seed(self) -> int:
+        return SERVING_SEED * 1000 + self.index
+
+    def taper_range(self) -> float:
+        return taper_range_for(self.nnz_per_row, self.n)
+
+    def make(self, features: int = 64):
+        """Locations, inducing points, response (and prediction locations)."""
+        locs = uniform_locations(self.n, self.seed)
+        ind = locs[inducing_subset(self.n, self.m, self.seed)].copy()
+        y = random_field(locs, self.nu, self.sigma1_sq, self.rho, self.nugget, self.seed, features=features)
+        pred = uniform_locations(self.n_pred, self.seed, STREAM_PRED_LOCATIONS) if self.n_pred else None
+        return locs, ind, y, pred
+
+
+def serving_stream(num_requests: int = 512, rate_per_s: float = 200.0, seed: int = SERVING_SEED):
+    """Requests with Poisson arrivals at ``rate_per_s``; n log-uniform in
+    [5e3, 2e5], m uniform in {100, ..., 1000}, range log-uniform in
+    [0.01, 0.2], nugget log-uniform in [0.01, 0.5], unit marginal variance,
+    exponential covariance, taper for about 20 nonzeros per row, 50 probes;
+    an even mix of likelihood+gradient and prediction calls, the latter with
+    n/2 prediction locations and 50 variance samples."""
+    rng = _rng(seed, STREAM_SERVING)
+    gaps = rng.exponential(1.0 / rate_per_s, num_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    n = np.exp(rng.uniform(math.log(5e3), math.log(2e5), num_requests)).astype(np.int64)
+    m = rng.integers(100, 1001, num_requests)
+    rho = np.exp(rng.uniform(math.log(0.01), math.log(0.2), num_requests))
+    nug = np.exp(rng.uniform(math.log(0.01), math.log(0.5), num_requests))
+    kinds = np.array(["loglik", "predict"] * ((num_requests + 1) // 2))[:num_requests]
+    kinds = kinds[rng.permutation(num_requests)]
+    out = []
+    for k in range(num_requests):
+        pred = kinds[k] == "predict"
+        out.append(ServingRequest(index=k, arrival_s=float(arrivals[k]), kind=str(kinds[k]), n=int(n[k]),
+                                  m=int(min(m[k], n[k])), rho=float(rho[k]), nugget=float(nug[k]),
+                                  n_pred=int(n[k] // 2) if pred else 0, num_var_samples=50 if pred else 0))
+    return out

@@ -239,6 +239,106 @@ fsa_status fsa_csr_noalloc(const double* locs_dev, int64_t n, double taper_range
 int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probes,
                             int32_t precision);
 
+/* ------------------------------------------------------------------------
+ * Serving: a persistent request loop on one GPU with continuous batching.
+ * The paper evaluates one problem at a time; the server runs many
+ * independent problems (different n, m, theta) at once.  Each request is
+ * exactly one fsa_build followed by one fsa_loglik_grad or fsa_predict, and
+ * its result is bit-for-bit the one those calls give alone.
+ *
+ * Scheduling: requests wait in arrival order.  A request is admitted when one
+ * of the max_slots slots is idle and its device-memory footprint estimate
+ * fits in what the running requests leave of the budget; a later request
+ * that fits may go ahead of an earlier one that does not, at most 8 times
+ * for the oldest waiting request.  A running request keeps its CSR pattern,
+ * Sigma_m Cholesky, operator and CG block resident on the device; the slots
+ * run on separate CUDA streams, so the work of all admitted requests overlaps
+ * on the GPU.  A request whose estimate exceeds the whole budget is refused
+ * at submission with FSA_ERR_OOM.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  FSA_REQ_LOGLIK_GRAD = 0,   /* fsa_loglik_grad */
+  FSA_REQ_PREDICT = 1        /* fsa_predict */
+} fsa_request_kind;
+
+typedef struct {
+  int32_t device;            /* CUDA device ordinal */
+  int32_t max_slots;         /* requests running at once, 1..64 (default 4) */
+  int64_t hbm_budget_bytes;  /* admission limit on the summed footprint estimates of the
+                                running requests; <= 0: 85 % of the device memory free at
+                                creation (default) */
+} fsa_server_cfg;
+
+typedef struct {
+  int32_t kind;              /* fsa_request_kind */
+  const double* locs;        /* n x 2 row-major host array (copied at submission) */
+  int64_t n;
+  const double* inducing;    /* m x 2 row-major host array (copied) */
+  int32_t m;
+  double taper_range;
+  int32_t cov;               /* fsa_cov */
+  const double* y;           /* n host values (copied) */
+  fsa_theta theta;
+  fsa_opts opts;             /* y_on_device must be 0 */
+  const double* pred_locs;   /* FSA_REQ_PREDICT: n_p x 2 host array (copied) */
+  int64_t n_p;
+  int32_t num_var_samples;
+  double* mean;              /* FSA_REQ_PREDICT outputs: caller-owned host arrays of n_p
+                                doubles, written before the result becomes ready; they must
+                                stay valid until then (var may be NULL: means only) */
+  double* var;
+} fsa_request;
+
+typedef struct {
+  int32_t status;            /* fsa_status of the request's own build and solve */
+  int32_t kind;
+  double loglik;             /* FSA_REQ_LOGLIK_GRAD: as fsa_loglik_grad */
+  double grad[3];
+  fsa_info info;
+  double queue_ms;           /* submission -> admission */
+  double run_ms;             /* admission -> completion (build, solve, release) */
+  double latency_ms;         /* submission -> completion */
+  int64_t footprint_bytes;   /* admission estimate */
+  int32_t slot;
+  char message[160];         /* error text of a failed request */
+} fsa_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, pending;
+  int32_t running, peak_running;
+  int64_t budget_bytes, in_use_bytes, peak_in_use_bytes;
+  double p50_ms, p99_ms, mean_ms;   /* latency percentiles (nearest rank) of completed requests */
+  double completed_per_s;           /* completed / (last completion - first submission) */
+} fsa_server_stats;
+
+typedef struct fsa_server fsa_server;
+
+/* Defaults: device 0, 4 slots, budget 85 % of free device memory. */
+void fsa_default_server_cfg(fsa_server_cfg* cfg);
+
+/* Starts the slot threads and streams.  Errors: FSA_ERR_ARG, FSA_ERR_CUDA. */
+fsa_status fsa_server_create(const fsa_server_cfg* cfg, fsa_server** out);
+
+/* Queues a request; *ticket identifies it.  Inputs are copied before the call
+ * returns.  Errors: FSA_ERR_ARG, FSA_ERR_OOM (estimate above the whole budget). */
+fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* ticket);
+
+/* FSA_OK: *out holds the result (its own status in out->status) and the
+ * ticket is released; FSA_ERR_BUSY: still waiting or running; FSA_ERR_ARG:
+ * unknown or already retrieved ticket. */
+fsa_status fsa_serve_poll(fsa_server* s, uint64_t ticket, fsa_result* out);
+
+/* As fsa_serve_poll, but blocks up to timeout_s seconds (< 0: no limit);
+ * FSA_ERR_TIMEOUT when the limit passes first. */
+fsa_status fsa_serve_wait(fsa_server* s, uint64_t ticket, double timeout_s, fsa_result* out);
+
+/* Counters and latency percentiles over the server's life so far. */
+fsa_status fsa_server_get_stats(fsa_server* s, fsa_server_stats* out);
+
+/* Blocks until every submitted request has completed, then stops the slots
+ * and frees the server; results not retrieved are discarded. */
+void fsa_server_destroy(fsa_server* s);
+
 #ifdef __cplusplus
 }
 #endif

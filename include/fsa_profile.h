@@ -36,6 +36,12 @@ void fsa_profile_reset(void);
  * Returns 0, or a negative value if the tag is unknown or nothing recorded. */
 int fsa_profile_collect(const char* tag, int64_t* launches, double* ms, double* bytes);
 
+/* High-water mark, in bytes, of the device memory the library's calls held at
+ * once on the current device since the last reset (every library allocation
+ * comes from the device's stream-ordered memory pool); reset != 0 restarts it
+ * at the current use.  Returns -1 if the pool cannot be queried. */
+int64_t fsa_pool_used_high(int reset);
+
 #ifdef __cplusplus
 }
 #endif

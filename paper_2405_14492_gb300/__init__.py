@@ -15,7 +15,7 @@ from . import _native as N
 from ._native import (FSA_EXPONENTIAL, FSA_FP64, FSA_MATERN_1_5, FSA_MIXED_BF16, FSA_MIXED_BF16X2,
                       FSA_PROBE_GAUSSIAN, FSA_PROBE_RADEMACHER, FsaError, FsaInfo, FsaOpts, FsaTheta)
 
-__all__ = ["FSAHandle", "FSALogLik", "FsaError", "FSA_EXPONENTIAL", "FSA_MATERN_1_5", "FSA_FP64",
+__all__ = ["FSAHandle", "FSAServer", "FSALogLik", "FsaError", "FSA_EXPONENTIAL", "FSA_MATERN_1_5", "FSA_FP64",
            "FSA_MIXED_BF16", "FSA_MIXED_BF16X2", "FSA_PROBE_RADEMACHER", "FSA_PROBE_GAUSSIAN", "make_opts",
            "cov_code"]
 
@@ -129,6 +129,102 @@ class FSAHandle:
         if getattr(self, "_h", None):
             N.lib().fsa_free(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class FSAServer:
+    """Persistent serving loop on one GPU with continuous batching
+    (``fsa_server_create`` / ``fsa_serve_submit`` / ``fsa_serve_poll`` /
+    ``fsa_serve_wait``).  Each request is one build plus one likelihood or
+    prediction call; the server admits requests by slot and device-memory
+    footprint and runs the admitted ones concurrently on its slot streams."""
+
+    def __init__(self, max_slots: int = 4, hbm_budget_bytes: int = 0, device: int = 0):
+        cfg = N.FsaServerCfg()
+        N.lib().fsa_default_server_cfg(C.byref(cfg))
+        cfg.device, cfg.max_slots, cfg.hbm_budget_bytes = device, max_slots, int(hbm_budget_bytes)
+        s = C.c_void_p()
+        N.check(N.lib().fsa_server_create(C.byref(cfg), C.byref(s)))
+        self._s = s
+        self._outs = {}   # ticket -> prediction output arrays (kept alive until retrieved)
+
+    def _submit(self, kind, locs, inducing, taper_range, nu, y, theta, opts, pred_locs=None,
+                num_var_samples=0, want_var=True):
+        locs, inducing, y = _f64(locs), _f64(inducing), _f64(y)
+        q = N.FsaRequest()
+        q.kind = kind
+        q.locs, q.n = locs.ctypes.data, locs.shape[0]
+        q.inducing, q.m = inducing.ctypes.data, inducing.shape[0]
+        q.taper_range, q.cov = float(taper_range), cov_code(nu)
+        q.y = y.ctypes.data
+        q.theta = _theta(theta)
+        q.opts = opts or make_opts()
+        outs = None
+        if kind == N.FSA_REQ_PREDICT:
+            pl = _f64(pred_locs)
+            mean = np.empty(pl.shape[0])
+            var = np.empty(pl.shape[0]) if want_var else None
+            q.pred_locs, q.n_p, q.num_var_samples = pl.ctypes.data, pl.shape[0], int(num_var_samples)
+            q.mean = mean.ctypes.data
+            q.var = var.ctypes.data if want_var else None
+            outs = (mean, var)
+        t = C.c_uint64()
+        N.check(N.lib().fsa_serve_submit(self._s, C.byref(q), C.byref(t)))
+        if outs is not None:
+            self._outs[t.value] = outs
+        return t.value
+
+    def submit_loglik(self, locs, inducing, taper_range, nu, y, theta, opts: FsaOpts | None = None) -> int:
+        return self._submit(N.FSA_REQ_LOGLIK_GRAD, locs, inducing, taper_range, nu, y, theta, opts)
+
+    def submit_predict(self, locs, inducing, taper_range, nu, y, theta, pred_locs, num_var_samples=50,
+                       opts: FsaOpts | None = None, want_var=True) -> int:
+        return self._submit(N.FSA_REQ_PREDICT, locs, inducing, taper_range, nu, y, theta, opts, pred_locs,
+                            num_var_samples, want_var)
+
+    def _result(self, ticket, r: "N.FsaResult"):
+        d = {"status": r.status, "kind": r.kind, "loglik": r.loglik, "grad": np.array(list(r.grad)),
+             "info": r.info.as_dict(), "queue_ms": r.queue_ms, "run_ms": r.run_ms, "latency_ms": r.latency_ms,
+             "footprint_bytes": r.footprint_bytes, "slot": r.slot, "message": r.message.decode()}
+        if ticket in self._outs:
+            d["mean"], d["var"] = self._outs.pop(ticket)
+        return d
+
+    def poll(self, ticket):
+        """The result dict, or None while the request waits or runs."""
+        r = N.FsaResult()
+        st = N.lib().fsa_serve_poll(self._s, ticket, C.byref(r))
+        if st == 7:
+            return None
+        N.check(st)
+        return self._result(ticket, r)
+
+    def wait(self, ticket, timeout_s: float = -1.0):
+        r = N.FsaResult()
+        N.check(N.lib().fsa_serve_wait(self._s, ticket, float(timeout_s), C.byref(r)))
+        return self._result(ticket, r)
+
+    def stats(self) -> dict:
+        st = N.FsaServerStats()
+        N.check(N.lib().fsa_server_get_stats(self._s, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_s", None):
+            N.lib().fsa_server_destroy(self._s)
+            self._s = None
+            self._outs.clear()
 
     def __del__(self):
         try:

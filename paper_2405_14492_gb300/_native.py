@@ -43,6 +43,36 @@ class FsaInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+FSA_REQ_LOGLIK_GRAD, FSA_REQ_PREDICT = 0, 1
+
+
+class FsaServerCfg(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+class FsaRequest(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("locs", C.c_void_p), ("n", C.c_int64), ("inducing", C.c_void_p),
+                ("m", C.c_int32), ("taper_range", C.c_double), ("cov", C.c_int32), ("y", C.c_void_p),
+                ("theta", FsaTheta), ("opts", FsaOpts), ("pred_locs", C.c_void_p), ("n_p", C.c_int64),
+                ("num_var_samples", C.c_int32), ("mean", C.c_void_p), ("var", C.c_void_p)]
+
+
+class FsaResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("loglik", C.c_double), ("grad", C.c_double * 3),
+                ("info", FsaInfo), ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("footprint_bytes", C.c_int64), ("slot", C.c_int32), ("message", C.c_char * 160)]
+
+
+class FsaServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("pending", C.c_int64),
+                ("running", C.c_int32), ("peak_running", C.c_int32), ("budget_bytes", C.c_int64),
+                ("in_use_bytes", C.c_int64), ("peak_in_use_bytes", C.c_int64), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("completed_per_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FsaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -71,6 +101,14 @@ def _declare(lib):
                                   P, P, C.POINTER(FsaInfo)]),
         "fsa_free": (None, [P]),
         "fsa_footprint_bytes": (C.c_int64, [C.c_int64, C.c_int32, C.c_int64, C.c_int32, C.c_int32]),
+        "fsa_default_server_cfg": (None, [C.POINTER(FsaServerCfg)]),
+        "fsa_server_create": (C.c_int, [C.POINTER(FsaServerCfg), C.POINTER(P)]),
+        "fsa_serve_submit": (C.c_int, [P, C.POINTER(FsaRequest), C.POINTER(C.c_uint64)]),
+        "fsa_serve_poll": (C.c_int, [P, C.c_uint64, C.POINTER(FsaResult)]),
+        "fsa_serve_wait": (C.c_int, [P, C.c_uint64, C.c_double, C.POINTER(FsaResult)]),
+        "fsa_server_get_stats": (C.c_int, [P, C.POINTER(FsaServerStats)]),
+        "fsa_server_destroy": (None, [P]),
+        "fsa_pool_used_high": (C.c_int64, [C.c_int]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(lib, name):

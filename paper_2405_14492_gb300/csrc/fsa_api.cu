@@ -2,13 +2,73 @@
 // catches library errors and returns a status; nothing throws across the ABI.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "fsa_solver.cuh"
+#include "fsa_profile.h"
 
 namespace fsa {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// ---------------------------------------------------------------------------
+// stream-ordered allocation: per-thread stream, pool configured once per device
+// ---------------------------------------------------------------------------
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+
+static void configure_pool() {
+  static std::mutex mu;
+  static bool done[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    // keep freed blocks in the pool between calls instead of unmapping them at every synchronisation
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+cudaStream_t current_alloc_stream() { return g_alloc_stream; }
+AllocStreamScope::AllocStreamScope(cudaStream_t s) : prev(g_alloc_stream) {
+  configure_pool();
+  g_alloc_stream = s;
+}
+AllocStreamScope::~AllocStreamScope() { g_alloc_stream = prev; }
+
+void release_pool_memory() {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+    cudaMemPoolTrimTo(pool, 0);
+}
+
+// small pinned host buffers (CG polling), recycled: freeing pinned memory
+// would synchronise the device
+static std::mutex g_pin_mu;
+static std::vector<double*> g_pin_free;
+static double* pinned_acquire() {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      double* p = g_pin_free.back();
+      g_pin_free.pop_back();
+      return p;
+    }
+  }
+  double* p = nullptr;
+  FSA_CUDA(cudaMallocHost(&p, 64 * sizeof(double)));
+  return p;
+}
+static void pinned_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
 
 static __global__ void k_to_internal(int64_t n, int k, const int64_t* __restrict__ perm,
                                      const double* __restrict__ src, double* __restrict__ dst) {
@@ -67,6 +127,22 @@ struct fsa_handle {
   Handle h;
 };
 
+namespace fsa {
+// Releases a handle: its buffers are freed in the order of its stream, the
+// stream is drained, and (trim) unused pool memory goes back to the driver.
+void free_handle(fsa_handle* h, bool trim) {
+  Handle& H = h->h;
+  cudaStream_t s = H.stream;
+  pinned_release(H.host_pinned);
+  H.host_pinned = nullptr;
+  if (H.ev0) cudaEventDestroy(H.ev0);
+  if (H.ev1) cudaEventDestroy(H.ev1);
+  delete h;
+  cudaStreamSynchronize(s);
+  if (trim) release_pool_memory();
+}
+}  // namespace fsa
+
 extern "C" {
 
 void fsa_default_opts(fsa_opts* o) {
@@ -102,6 +178,22 @@ const char* fsa_status_string(fsa_status s) {
 
 const char* fsa_last_error(void) { return g_last_error.c_str(); }
 
+int64_t fsa_pool_used_high(int reset) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  uint64_t v = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v) != cudaSuccess) return -1;
+  if (reset) {
+    uint64_t zero = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+  }
+  return (int64_t)v;
+}
+
 fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int32_t m, double taper_range,
                      int32_t cov, void* cuda_stream, fsa_handle** out) {
   if (!out) return fail(Error{FSA_ERR_ARG, "out is NULL"});
@@ -121,10 +213,11 @@ fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int3
     H.gamma = taper_range;
     H.cov = cov;
     H.stream = (cudaStream_t)cuda_stream;
+    AllocStreamScope scope(H.stream);
     H.err_buf.alloc(1);
     H.err = H.err_buf.p;
     FSA_CUDA(cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream));
-    FSA_CUDA(cudaMallocHost(&H.host_pinned, 64 * sizeof(double)));
+    H.host_pinned = pinned_acquire();
     FSA_CUDA(cudaEventCreate(&H.ev0));
     FSA_CUDA(cudaEventCreate(&H.ev1));
     std::vector<double> ix(m), iy(m);
@@ -150,6 +243,7 @@ int64_t fsa_nnz(const fsa_handle* h) { return h ? h->h.nnz : -1; }
 fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col) {
   if (!h || !rowptr || !col) return fail(Error{FSA_ERR_ARG, "NULL argument"});
   try {
+    AllocStreamScope scope(h->h.stream);
     export_csr(h->h, rowptr, col);
     return FSA_OK;
   } catch (const Error& e) {
@@ -170,6 +264,7 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
   Handle& H = h->h;
+  AllocStreamScope scope(H.stream);
   try {
     FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
     H.y.ensure(H.n);
@@ -222,6 +317,7 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
   if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
   if (precision < FSA_FP64 || precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   Handle& H = h->h;
+  AllocStreamScope scope(H.stream);
   try {
     ensure_operator(H, *theta, precision);
     size_t nk = (size_t)H.n * k;
@@ -245,6 +341,7 @@ fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t pre
   if (!theta_ok(theta)) return fail(Error{FSA_ERR_ARG, "theta must be finite and > 0"});
   if (precision < FSA_FP64 || precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   Handle& H = h->h;
+  AllocStreamScope scope(H.stream);
   try {
     ensure_operator(H, *theta, precision);
     double sc[3];
@@ -269,6 +366,7 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
   if (o.precision != FSA_FP64)
     return fail(Error{FSA_ERR_UNSUPPORTED, "prediction is implemented in the FP64 form"});
   Handle& H = h->h;
+  AllocStreamScope scope(H.stream);
   try {
     FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
     H.y.ensure(H.n);
@@ -310,30 +408,21 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
 
 void fsa_free(fsa_handle* h) {
   if (!h) return;
-  Handle& H = h->h;
-  if (H.stream) cudaStreamSynchronize(H.stream);
-  if (H.host_pinned) cudaFreeHost(H.host_pinned);
-  if (H.ev0) cudaEventDestroy(H.ev0);
-  if (H.ev1) cudaEventDestroy(H.ev1);
-  delete h;
+  fsa::free_handle(h, true);
 }
 
 int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probes, int32_t precision) {
-  int64_t c = (num_probes + 1 + 7) / 8 * 8;
-  int64_t mp = (m + 63) / 64 * 64;
-  int64_t b = 0;
-  b += n * 2 * 8 + n * 8 * 3 + nnz * 4;                  // coordinates, perm, rowptr, col
-  b += (int64_t)m * m * 8 * 4;                           // m x m FP64 matrices
-  if (precision == FSA_FP64) {
-    b += n * (int64_t)m * 8 * 2;                         // A + build temporary
-    b += nnz * 8 + n * 16;                               // values, D
-    b += n * c * 8 * 8;                                  // CG block
-  } else {
-    b += n * mp * 2 * 2 + n * (int64_t)m * 4;            // A, A^T (BF16), build temporary (FP32)
-    b += nnz * 4 + n * 16;
-    b += n * c * 4 * 8 + n * c * 2 * 2 * 2;              // CG block, split operands
-  }
-  return b;
+  // peak of one fsa_build + fsa_loglik_grad: pattern and coordinates, m x m
+  // matrices, the n x m operator with its build or gradient temporaries
+  // (whichever is larger), and the n x ldc CG block; plus 25 % and a fixed
+  // allowance for split-K partials and scratch
+  const int64_t c = (int64_t)num_probes + 1, ldc = (c + 7) / 8 * 8, mp = ((int64_t)m + 63) / 64 * 64;
+  int64_t b = 64 * n + 16 * nnz + 128 * (int64_t)m * m + ((int64_t)64 << 20);
+  if (precision == FSA_FP64)
+    b += 32 * n * (int64_t)m + 72 * n * ldc;
+  else
+    b += (precision == FSA_MIXED_BF16X2 ? 20 : 16) * n * mp + 40 * n * ldc;
+  return b + b / 4;
 }
 
 }  // extern "C"

@@ -11,27 +11,43 @@ namespace fsa {
 // ---------------------------------------------------------------------------
 // device memory
 // ---------------------------------------------------------------------------
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync from the
+// device's memory pool) on the stream of the call that allocates it: a free
+// waits for that stream's earlier work only, never for the whole device, so
+// calls on different streams (the serving slots) overlap on the GPU.  The
+// stream is a per-thread setting made by the entry points (AllocStreamScope);
+// a buffer remembers the stream it was allocated on and is freed on it.
+cudaStream_t current_alloc_stream();
+struct AllocStreamScope {
+  cudaStream_t prev;
+  explicit AllocStreamScope(cudaStream_t s);
+  ~AllocStreamScope();
+};
+void release_pool_memory();   // returns unused pool memory of the current device to the driver
+
 template <typename T>
 struct DevPtr {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t s = nullptr;
   DevPtr() = default;
   explicit DevPtr(size_t k) { alloc(k); }
   DevPtr(const DevPtr&) = delete;
   DevPtr& operator=(const DevPtr&) = delete;
-  DevPtr(DevPtr&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevPtr(DevPtr&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
   DevPtr& operator=(DevPtr&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
     return *this;
   }
   void alloc(size_t k) {
     release();
     if (k == 0) k = 1;
-    cudaError_t e = cudaMalloc(&p, k * sizeof(T));
+    s = current_alloc_stream();
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), k * sizeof(T), s);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       p = nullptr;
-      throw Error{FSA_ERR_OOM, "cudaMalloc of " + std::to_string(k * sizeof(T)) + " bytes failed"};
+      throw Error{FSA_ERR_OOM, "device allocation of " + std::to_string(k * sizeof(T)) + " bytes failed"};
     }
     n = k;
   }
@@ -39,7 +55,7 @@ struct DevPtr {
     if (k > n || p == nullptr) alloc(k);
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     n = 0;
   }

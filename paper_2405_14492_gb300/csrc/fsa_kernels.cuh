@@ -340,11 +340,9 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
 // e1^T log(T) e1 for every probe column (L <= 8000 iterations)
 static inline void launch_slq(int c, int L, const int32_t* iters, const double* tdiag, const double* toff,
                               double* quads, unsigned* err, cudaStream_t s) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_done = true;
-  }
+  static const bool attr_done =
+      cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) == cudaSuccess;
+  (void)attr_done;
   if (c < 2) return;
   k_slq<<<c - 1, 32, (size_t)3 * L * sizeof(double), s>>>(c, L, iters, tdiag, toff, nullptr, quads, err);
   FSA_CHECK_LAUNCH();

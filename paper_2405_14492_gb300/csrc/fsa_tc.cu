@@ -402,11 +402,11 @@ struct ProfRec {
   double bytes;
 };
 static std::mutex g_prof_mu;
-static bool g_prof_on = false;
+static std::atomic<bool> g_prof_on{false};
 static std::vector<ProfRec> g_prof;
 static std::vector<cudaEvent_t> g_prof_pool;
 
-bool profile_on() { return g_prof_on; }
+bool profile_on() { return g_prof_on.load(std::memory_order_relaxed); }
 
 cudaEvent_t profile_event() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -431,7 +431,7 @@ extern "C" {
 
 uint64_t fsa_launch_count(void) { return fsa::g_launches.load(); }
 
-void fsa_profile_enable(int on) { fsa::g_prof_on = on != 0; }
+void fsa_profile_enable(int on) { fsa::g_prof_on.store(on != 0); }
 
 void fsa_profile_reset(void) {
   std::lock_guard<std::mutex> lk(fsa::g_prof_mu);

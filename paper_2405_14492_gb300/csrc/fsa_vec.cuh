@@ -487,14 +487,13 @@ static inline Vec4Launch vec4_launch(const CGLayout& lay) {
 
 // grid of one full wave: SM count x resident blocks of the kernel
 static inline int spmm_f4_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
+  static const int blocks = [] {
     int dev = 0, sms = 152, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_fused_f4, 256, 0);
-    blocks = sms * (per > 0 ? per : 1);
-  }
+    return sms * (per > 0 ? per : 1);
+  }();
   return blocks;
 }
 

@@ -67,3 +67,50 @@ def test_argument_errors_need_no_gpu(libpath):
     st = N.lib().fsa_build(N.ptr(locs), 10, N.ptr(bad), 3, 0.1, 0, None, ctypes.byref(h))
     assert st == 5
     assert b"inducing" in N.lib().fsa_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path, libpath):
+    """The ctypes mirrors of the ABI structs have the C sizes and offsets
+    (a C program built from include/fsa.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2405_14492_gb300 import _native as N
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fsa_theta": N.FsaTheta, "fsa_opts": N.FsaOpts, "fsa_info": N.FsaInfo,
+               "fsa_server_cfg": N.FsaServerCfg, "fsa_request": N.FsaRequest, "fsa_result": N.FsaResult,
+               "fsa_server_stats": N.FsaServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fsa.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (cname, field, got, val)
+
+
+def test_serving_without_a_gpu_fails_cleanly(libpath):
+    """Server creation reports a CUDA error status (no crash) where no GPU is present."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2405_14492_gb300 import _native as N
+    s = ctypes.c_void_p()
+    cfg = N.FsaServerCfg()
+    N.lib().fsa_default_server_cfg(ctypes.byref(cfg))
+    assert cfg.max_slots == 4 and cfg.hbm_budget_bytes == 0
+    cfg.max_slots = 0
+    assert N.lib().fsa_server_create(ctypes.byref(cfg), ctypes.byref(s)) == 1
+    cfg.max_slots = 2
+    assert N.lib().fsa_server_create(ctypes.byref(cfg), ctypes.byref(s)) == 8
+    assert s.value is None
