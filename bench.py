@@ -427,7 +427,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
     ap.add_argument("--ref-sample", type=int, default=2500)
-    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-fp64-sample", type=int, default=32)
     args = ap.parse_args()

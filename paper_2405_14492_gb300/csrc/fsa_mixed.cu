@@ -20,6 +20,12 @@
 
 namespace fsa {
 
+// k-blocks (64 rows each) of one FP32 accumulation span of the Woodbury core
+// on the tensor cores (512 rows; the spans are reduced in FP64)
+constexpr int kCoreSpanBlocks = 8;
+constexpr int kCoreSpans = 64;      // spans per launch
+
+
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(v);
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
@@ -173,12 +179,13 @@ __global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __
 
 // out[r][c] = sum_s part[s][r][c] (+1 on the diagonal), FP64
 __global__ void k_reduce_splits(int splits, int rows, int cols, const float* __restrict__ part, int64_t ldp,
-                                int64_t split_stride, double* __restrict__ out, int64_t ldo, int add_identity) {
+                                int64_t split_stride, double* __restrict__ out, int64_t ldo, int add_identity,
+                                int accumulate = 0) {
   int64_t total = (int64_t)rows * cols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(t / cols), c = (int)(t % cols);
-    double s = (add_identity && r == c) ? 1.0 : 0.0;
+    double s = accumulate ? out[(int64_t)r * ldo + c] : ((add_identity && r == c) ? 1.0 : 0.0);
     for (int z = 0; z < splits; ++z) s += (double)part[(int64_t)z * split_stride + (int64_t)r * ldp + c];
     out[(int64_t)r * ldo + c] = s;
   }
@@ -483,17 +490,27 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
     g.a[0] = &mAt; g.a[1] = &mAtl; g.num_a = lo ? 2 : 1;
     g.b[0] = &mYh; g.b[1] = &mYl; g.num_b = 2;
     g.pairs = lo ? (1u | 2u | 4u) : (1u | 2u);
-    g.M = m_pad; g.N = m_pad; g.K = (int)n; g.bn = 128;
-    g.splits = tc_pick_splits(g.M, g.N, g.K, g.bn);
-    int kb = (g.K + 63) / 64, per = (kb + g.splits - 1) / g.splits, splits = (kb + per - 1) / per;
-    DevPtr<float> part((size_t)splits * m_pad * m_pad);
+    g.M = m_pad; g.N = m_pad; g.bn = 128;
+    // M - I = A~^T D^-1 A~ has entries up to n / min(D) while the identity is
+    // what the small eigenvalues of M keep: FP32 accumulation runs over spans
+    // of kCoreSpanBlocks k-blocks only and the spans are summed in FP64, in
+    // launches of kCoreSpans spans (bounded partial buffer), in a fixed order
+    const int kb = (int)((n + 63) / 64);
+    const int spans = std::min(kCoreSpans, (kb + kCoreSpanBlocks - 1) / kCoreSpanBlocks);
+    DevPtr<float> part((size_t)spans * m_pad * m_pad);
+    op.Mp.ensure((size_t)m * m);
     g.out = part.p; g.ldo = m_pad; g.split_stride = (int64_t)m_pad * m_pad;
     g.tag = "build";
-    tc_gemm(g, H.err, s);
-    op.Mp.ensure((size_t)m * m);
-    k_reduce_splits<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(splits, m, m, part.p, m_pad, g.split_stride,
-                                                                  op.Mp.p, m, 1);
-    FSA_CHECK_LAUNCH();
+    for (int b0 = 0, first = 1; b0 < kb; b0 += spans * kCoreSpanBlocks, first = 0) {
+      const int nb = std::min(kb - b0, spans * kCoreSpanBlocks);
+      g.k0 = b0 * 64;
+      g.K = nb * 64;
+      g.splits = (nb + kCoreSpanBlocks - 1) / kCoreSpanBlocks;
+      tc_gemm(g, H.err, s);
+      k_reduce_splits<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(g.splits, m, m, part.p, m_pad, g.split_stride,
+                                                                    op.Mp.p, m, 1, first ? 0 : 1);
+      FSA_CHECK_LAUNCH();
+    }
     FSA_CUDA(cudaStreamSynchronize(s));
   }
   check_err(H);

@@ -33,7 +33,7 @@ struct Params {
   CUtensorMap mb[2];
   int num_a, num_b;
   unsigned pairs;
-  int M, bn, kblocks, kb_per_split, stages;
+  int M, bn, kb_base, kblocks, kb_per_split, stages;   // k-blocks [kb_base, kblocks)
   uint32_t a_bytes, b_bytes, stage_bytes, tmem_cols, idesc;
   int stack, n_valid;
   float* out;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
   const int n0 = blockIdx.y * p.bn;
-  const int kb0 = blockIdx.z * p.kb_per_split;
+  const int kb0 = p.kb_base + blockIdx.z * p.kb_per_split;
   const int kb1 = min(p.kblocks, kb0 + p.kb_per_split);
   const int nk = kb1 - kb0;
   const int S = p.stages;
@@ -340,10 +340,13 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   p.pairs = g.pairs;
   p.M = g.M;
   p.bn = bn;
-  p.kblocks = (g.K + tc::BK - 1) / tc::BK;
-  int splits = std::max(1, std::min(g.splits, p.kblocks));
-  p.kb_per_split = (p.kblocks + splits - 1) / splits;
-  splits = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
+  FSA_REQUIRE(g.k0 >= 0 && g.k0 % tc::BK == 0, FSA_ERR_ARG, "tc_gemm k0 must be a multiple of 64");
+  const int count = (g.K + tc::BK - 1) / tc::BK;
+  p.kb_base = g.k0 / tc::BK;
+  p.kblocks = p.kb_base + count;
+  int splits = std::max(1, std::min(g.splits, count));
+  p.kb_per_split = (count + splits - 1) / splits;
+  splits = (count + p.kb_per_split - 1) / p.kb_per_split;
   p.a_bytes = tc::BM * tc::BK * 2;
   p.b_bytes = (uint32_t)bn * tc::BK * 2;
   p.stage_bytes = p.num_a * p.a_bytes + p.num_b * p.b_bytes;

@@ -31,7 +31,8 @@ struct TcGemm {
   unsigned pairs = 1;       // bit (2*ia + ib): multiply A_ia with B_ib
   int M = 0;                // rows of D
   int N = 0;                // columns of D (per launch; tiled by bn)
-  int K = 0;                // reduction length
+  int K = 0;                // reduction length (from k0)
+  int k0 = 0;               // first reduction index (a multiple of 64)
   int bn = 0;               // N tile (multiple of 16, <= 256); 0 = min(N rounded to 16, 256)
   int splits = 1;           // split-K factor (outputs at out + z * split_stride)
   int halves = 0;           // epilogue: out[:, j] = acc[:, j] + acc[:, j + N/2]  (same as stack = 2)

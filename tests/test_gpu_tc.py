@@ -122,3 +122,24 @@ def test_mixed_loglik_within_1e4_of_oracle(F, n, m, nu, gamma, l, K):
     assert abs(ll64 - ref["loglik"]) < 1e-6 * abs(ref["loglik"])
     assert abs(ll - ref["loglik"]) < 1e-4 * abs(ref["loglik"]), (ll, ref["loglik"])
     assert np.linalg.norm(g - ref["grad"]) < 2e-2 * np.linalg.norm(ref["grad"]), (g, ref["grad"])
+
+
+def test_mixed_x2_woodbury_core_accurate_at_large_n(F):
+    """n = 2e5 with a long range and small nugget: M - I = A~^T D^-1 A~ has
+    entries ~1e4 while the small eigenvalues of M = I + A~^T D^-1 A~ sit near
+    1, so an FP32 sum over the whole n would lose the identity.  The mixed
+    form must stay within 1e-4 of the FP64 form (same probes, same fixed
+    iteration count), for the log det of the preconditioner and the
+    log-likelihood."""
+    n, m, rho, nug = 199_791, 738, 0.081, 0.028
+    locs = fi.uniform_locations(n, 8032)
+    ind = locs[fi.inducing_subset(n, m, 8032)]
+    gamma = fi.taper_range_for(20, n)
+    th = (1.0, rho, nug)
+    y = fi.random_field(locs, 0.5, *th, 8032, features=64)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        o = dict(num_probes=16, fixed_iters=40, seed=3, want_grad=False)
+        ll64, _, i64 = h.loglik_grad(y, th, F.make_opts(**o))
+        ll2, _, i2 = h.loglik_grad(y, th, F.make_opts(precision=F.FSA_MIXED_BF16X2, **o))
+    assert abs(i2["logdet_precond"] - i64["logdet_precond"]) < 1e-5 * abs(i64["logdet_precond"])
+    assert abs(ll2 - ll64) < 1e-4 * abs(ll64), (ll2, ll64)
