@@ -11,6 +11,8 @@
 
 #include <stdint.h>
 
+#include "fsa.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -32,6 +34,22 @@ extern "C" {
  */
 int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, unsigned pairs, int halves, int splits,
                          uint64_t seed, double* max_rel_err, int* launched_splits);
+
+/*
+ * fsa_selftest_spmm — the FP32 tapered-residual SpMM of the mixed CG loop
+ * (V = Sigma_s~ Z + S, H = Z; paper §3.1) in its two forms on the handle's
+ * pattern and the FSA_MIXED_BF16X2 operator of theta: the shared-memory tile
+ * kernel and the row kernel, on the same seeded block of ncols (1..127)
+ * columns.  Both sum each row's products in the same order, so the outputs
+ * agree bit for bit.
+ *   max_abs_diff  receives max |tile - row| over V and H
+ *   staged_tiles  receives the number of tiles that fit the staging capacity
+ *                 (the rest run from global memory); may be NULL
+ *   total_tiles   receives the number of tiles; may be NULL
+ * Returns FSA_OK or an fsa_status.  Runs on the handle's stream.
+ */
+int fsa_selftest_spmm(fsa_handle* h, const fsa_theta* theta, int ncols, uint64_t seed, double* max_abs_diff,
+                      int* staged_tiles, int* total_tiles);
 
 #ifdef __cplusplus
 }

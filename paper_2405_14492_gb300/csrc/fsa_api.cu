@@ -123,9 +123,6 @@ static fsa_opts resolve_opts(const fsa_opts* o) {
 
 using namespace fsa;
 
-struct fsa_handle {
-  Handle h;
-};
 
 namespace fsa {
 // Releases a handle: its buffers are freed in the order of its stream, the

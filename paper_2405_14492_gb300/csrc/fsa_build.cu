@@ -3,6 +3,9 @@
 // cell side >= gamma, a deterministic counting sort of the points by cell
 // (internal order: cell id, then original index), and a two-pass CSR build
 // (count, exclusive scan, fill) over the 3x3 cell stencil.
+#include <algorithm>
+#include <vector>
+
 #include "fsa_internal.cuh"
 
 namespace fsa {
@@ -277,6 +280,28 @@ Grid make_grid(const double bb[4], double gamma, int64_t n) {
   return g;
 }
 
+void build_tiles(Handle& H);
+
+// per nonzero of a tile's rows: the row of its column within the tile's
+// staged ranges (range 0, then 1, then 2), or -1 outside them
+__global__ void k_tile_scol(const int64_t* __restrict__ tiles, const int64_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, int32_t* __restrict__ scol,
+                            int32_t* __restrict__ bad) {
+  const int64_t* d = tiles + (int64_t)blockIdx.x * 8;
+  const int64_t e0 = rowptr[d[0]], e1 = rowptr[d[1]];
+  const int64_t n0 = d[3] - d[2], n1 = d[5] - d[4], n2 = d[7] - d[6];
+  for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
+    const int64_t j = col[t];
+    int64_t r = -1;
+    if (j >= d[4] && j < d[5]) r = n0 + (j - d[4]);
+    else if (j >= d[2] && j < d[3]) r = j - d[2];
+    else if (j >= d[6] && j < d[7]) r = n0 + n1 + (j - d[6]);
+    (void)n2;
+    scol[t] = (int32_t)r;
+    if (r < 0) bad[blockIdx.x] = 1;
+  }
+}
+
 void build_structure(Handle& H, const double* locs_host) {
   cudaStream_t s = H.stream;
   int64_t n = H.n;
@@ -336,7 +361,75 @@ void build_structure(Handle& H, const double* locs_host) {
   neighbour_kernel<true><<<gb, 256, 0, s>>>(H.xs.p, H.ys.p, n, H.xs.p, H.ys.p, H.cell_start.p,
                                             H.cell_count.p, H.grid, g2, nullptr, H.rowptr.p, H.col.p);
   FSA_CHECK_LAUNCH();
+  build_tiles(H);
   FSA_CUDA(cudaStreamSynchronize(s));
+}
+
+// SpMM tiles (host): each grid row of cells is cut into runs of cells holding
+// about kTileRows points; the taper neighbours of a run's points lie in the
+// run's cells widened by one on each side, in the rows above, at and below
+// (cell side >= gamma), i.e. in three contiguous ranges of the internal order.
+void build_tiles(Handle& H) {
+  constexpr int64_t kTileRows = 40;
+  const int ncx = H.grid.ncx, ncy = H.grid.ncy;
+  const int64_t ncells = (int64_t)ncx * ncy;
+  std::vector<int32_t> start(ncells), count(ncells);
+  FSA_CUDA(cudaMemcpyAsync(start.data(), H.cell_start.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaMemcpyAsync(count.data(), H.cell_count.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaStreamSynchronize(H.stream));
+  auto range = [&](int cy, int cxa, int cxb, int64_t* out) {
+    if (cy < 0 || cy >= ncy) { out[0] = out[1] = 0; return; }
+    const int a = std::max(cxa - 1, 0), b = std::min(cxb + 1, ncx - 1);
+    const int64_t c0 = (int64_t)cy * ncx + a, c1 = (int64_t)cy * ncx + b;
+    out[0] = start[c0];
+    out[1] = (int64_t)start[c1] + count[c1];
+  };
+  std::vector<int64_t> t;
+  int64_t max_staged = 0;
+  for (int cy = 0; cy < ncy; ++cy) {
+    int cxa = 0;
+    int64_t acc = 0;
+    for (int cx = 0; cx < ncx; ++cx) {
+      acc += count[(int64_t)cy * ncx + cx];
+      if (acc >= kTileRows || cx == ncx - 1) {
+        if (acc > 0) {
+          int64_t d[8];
+          d[0] = start[(int64_t)cy * ncx + cxa];
+          d[1] = (int64_t)start[(int64_t)cy * ncx + cx] + count[(int64_t)cy * ncx + cx];
+          range(cy - 1, cxa, cx, d + 2);
+          range(cy, cxa, cx, d + 4);
+          range(cy + 1, cxa, cx, d + 6);
+          max_staged = std::max(max_staged, (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]));
+          t.insert(t.end(), d, d + 8);
+        }
+        cxa = cx + 1;
+        acc = 0;
+      }
+    }
+  }
+  H.ntiles = (int)(t.size() / 8);
+  H.max_staged = max_staged;
+  H.tiles.alloc(std::max<size_t>(t.size(), 8));
+  if (!t.empty())
+    FSA_CUDA(cudaMemcpyAsync(H.tiles.p, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, H.stream));
+  // largest tile (rows, nonzeros) from the row pointers
+  std::vector<int64_t> rp(H.n + 1);
+  FSA_CUDA(cudaMemcpyAsync(rp.data(), H.rowptr.p, sizeof(int64_t) * (H.n + 1), cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaStreamSynchronize(H.stream));
+  int64_t mr = 0, me = 0;
+  for (int k = 0; k < H.ntiles; ++k) {
+    mr = std::max(mr, t[8 * k + 1] - t[8 * k]);
+    me = std::max(me, rp[t[8 * k + 1]] - rp[t[8 * k]]);
+  }
+  H.max_tile_rows = mr;
+  H.max_tile_nnz = me;
+  H.scol.alloc(std::max<int64_t>(H.nnz, 1));
+  H.tile_bad.alloc(std::max(H.ntiles, 1));
+  FSA_CUDA(cudaMemsetAsync(H.tile_bad.p, 0, sizeof(int32_t) * std::max(H.ntiles, 1), H.stream));
+  if (H.ntiles > 0) {
+    k_tile_scol<<<H.ntiles, 256, 0, H.stream>>>(H.tiles.p, H.rowptr.p, H.col.p, H.scol.p, H.tile_bad.p);
+    FSA_CHECK_LAUNCH();
+  }
 }
 
 void build_cross_structure(Handle& H, const double* qx, const double* qy, int64_t nq,

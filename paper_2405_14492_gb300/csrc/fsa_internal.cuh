@@ -140,6 +140,16 @@ struct Handle {
   DevPtr<int64_t> perm, iperm, rowptr;     // perm[internal] = original
   DevPtr<int32_t> col, cell_start, cell_count;
   int64_t nnz = 0;
+  // SpMM tiles: runs of cells of one grid row (about kTileRows points) whose
+  // taper neighbours all lie in three contiguous index ranges (the same cells
+  // +-1 in the rows above, at and below).  Per tile 8 int64: p0, p1 (its
+  // rows), then [begin, end) of the three ranges.
+  DevPtr<int64_t> tiles;
+  DevPtr<int32_t> scol;                    // per nonzero: row of its column in the tile's staged ranges
+  DevPtr<int32_t> tile_bad;                // 1: a column of the tile lies outside its ranges
+  int ntiles = 0;
+  int64_t max_staged = 0;                  // largest sum of the three range lengths
+  int64_t max_tile_rows = 0, max_tile_nnz = 0;
   DevPtr<unsigned> err_buf;
   unsigned* err = nullptr;
   Operator op;
@@ -175,3 +185,9 @@ unsigned read_err(Handle& H);   // synchronises the stream
 void check_err(Handle& H);      // throws on a set error bit
 
 }  // namespace fsa
+
+// the opaque handle of the C ABI
+struct fsa_handle {
+  fsa::Handle h;
+};
+

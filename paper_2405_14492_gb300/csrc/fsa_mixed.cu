@@ -204,31 +204,56 @@ __device__ __forceinline__ void split_n(float v, int nsplit, __nv_bfloat16* out)
 
 // src (n x ldc FP32) optionally scaled by rowscale -> dst (nsplit ldc x n_pad BF16):
 // plane p (rows p ldc .. p ldc + ldc - 1) holds the p-th BF16 piece; K-major
-// (points contiguous) for the B operand of A^T X; 64 points per block
+// (points contiguous) for the B operand of A^T X.  A block transposes a tile
+// of kSTRows points: coalesced 16-byte loads of the FP32 rows into shared
+// memory (row stride ldc + 1 words against bank conflicts), then each thread
+// splits 8 consecutive points of one column and writes each piece as one
+// 16-byte store (8 threads cover 128 contiguous bytes of a column).
 constexpr int kSTRows = 64;
-__global__ void k_split_transpose(int64_t n, int c, int ldc, int nsplit, const float* __restrict__ src,
-                                  const float* __restrict__ rowscale, int64_t n_pad,
-                                  __nv_bfloat16* __restrict__ dst) {
-  extern __shared__ __nv_bfloat16 tl[];   // [nsplit ldc][kSTRows + 2]
-  const int W = kSTRows + 2;
-  int64_t r0 = (int64_t)blockIdx.x * kSTRows;
-  for (int t = threadIdx.x; t < kSTRows * ldc; t += blockDim.x) {
-    int rr = t / ldc, cc = t % ldc;
-    int64_t r = r0 + rr;
-    float v = 0.f;
-    if (r < n && cc < c) {
-      v = src[r * ldc + cc];
-      if (rowscale) v *= rowscale[r];
-    }
-    __nv_bfloat16 pc[3];
-    split_n(v, nsplit, pc);
-    for (int p = 0; p < nsplit; ++p) tl[(p * ldc + cc) * W + rr] = pc[p];
+__global__ void __launch_bounds__(256) k_split_transpose(int64_t n, int c, int ldc, int nsplit,
+                                                         const float* __restrict__ src,
+                                                         const float* __restrict__ rowscale, int64_t n_pad,
+                                                         __nv_bfloat16* __restrict__ dst) {
+  extern __shared__ float tf[];   // [kSTRows][ldc + 1] then rowscale[kSTRows]
+  const int ls = ldc + 1;
+  float* rs = tf + kSTRows * ls;
+  const int64_t r0 = (int64_t)blockIdx.x * kSTRows;
+  const int c4 = ldc >> 2;
+  for (int t = threadIdx.x; t < kSTRows * c4; t += blockDim.x) {
+    const int rr = t / c4, q = t - (t / c4) * c4;
+    const int64_t r = r0 + rr;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < n) v = *reinterpret_cast<const float4*>(src + r * ldc + 4 * q);
+    float* d = tf + rr * ls + 4 * q;
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  }
+  for (int t = threadIdx.x; t < kSTRows; t += blockDim.x) {
+    const int64_t r = r0 + t;
+    rs[t] = (r < n) ? (rowscale ? rowscale[r] : 1.f) : 0.f;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nsplit * ldc * kSTRows; t += blockDim.x) {
-    int cc = t / kSTRows, rr = t % kSTRows;
-    int64_t r = r0 + rr;
-    if (r < n_pad) dst[(int64_t)cc * n_pad + r] = (r < n) ? tl[cc * W + rr] : __float2bfloat16(0.f);
+  for (int t = threadIdx.x; t < ldc * (kSTRows / 8); t += blockDim.x) {
+    const int g = t & 7, cc = t >> 3;
+    if (r0 + 8 * g >= n_pad) continue;
+    uint32_t w[3][4];   // 8 BF16 per piece, packed in pairs
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      __nv_bfloat16 e[3], o[3];
+      const float ve = cc < c ? tf[(8 * g + k) * ls + cc] * rs[8 * g + k] : 0.f;
+      const float vo = cc < c ? tf[(8 * g + k + 1) * ls + cc] * rs[8 * g + k + 1] : 0.f;
+      split_n(ve, nsplit, e);
+      split_n(vo, nsplit, o);
+      if (nsplit != 3) { e[2] = e[1]; o[2] = o[1]; }
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+        w[p][k / 2] = (uint32_t)__bfloat16_as_ushort(e[p]) | ((uint32_t)__bfloat16_as_ushort(o[p]) << 16);
+    }
+    const int64_t base = (int64_t)cc * n_pad + r0 + 8 * g;
+    *reinterpret_cast<uint4*>(dst + base) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+    *reinterpret_cast<uint4*>(dst + base + (int64_t)ldc * n_pad) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+    if (nsplit == 3)
+      *reinterpret_cast<uint4*>(dst + base + (int64_t)2 * ldc * n_pad) =
+          make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
   }
 }
 
@@ -577,7 +602,7 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
-  size_t smem = (size_t)C.nsplit * ldc * (kSTRows + 2) * sizeof(__nv_bfloat16);
+  size_t smem = (size_t)(kSTRows * (ldc + 1) + kSTRows) * sizeof(float);
   k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, C.nsplit, src,
                                                                                     rowscale, C.n_pad, g.Xb.p);
   FSA_CHECK_LAUNCH();
@@ -682,8 +707,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
                                                       g.part.p, kStepInit, 0, q);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
-                                  g.beta.p, g.part.p, kStepAlpha, q);
+  const StagedLaunch sl = staged_launch(H, ldc);
+  launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
   for (int it = 0; it < L; ++it) {
     kv4_ur_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
@@ -693,8 +718,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
                                                         g.Z32.p, g.part.p, kStepBeta, it, q);
     FSA_CHECK_LAUNCH();
-    launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p,
-                                    g.beta.p, g.part.p, kStepAlpha, q);
+    launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha,
+                    q);
     if (o.fixed_iters <= 0 && should_poll(it)) {
       FSA_CUDA(cudaMemcpyAsync(pin_active, g.num_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       FSA_CUDA(cudaStreamSynchronize(s));
@@ -878,10 +903,9 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
     DevPtr<float> Hd(nc);
     FSA_CUDA(cudaMemsetAsync(Hd.p, 0, nc * sizeof(float), s));
     FSA_CUDA(cudaMemsetAsync(O32.p, 0, nc * sizeof(float), s));
-    k_spmm_fused<float, float><<<lay.nblk, lay.threads, 0, s>>>(n, k, ldc, lay.chunk, H.rowptr.p, H.col.p,
-                                                                 op.vals32.p, V32.p, S32.p, O32.p, Hd.p, beta.p,
-                                                                 part.p);
-    FSA_CHECK_LAUNCH();
+    CGScalars none{};
+    launch_spmm_f32(H, lay, staged_launch(H, ldc), s, op.vals32.p, V32.p, S32.p, O32.p, Hd.p, beta.p, part.p,
+                    kStepNone, none);
   }
   k_f32_to_f64_unpad<<<grid_for(n * k, 256), 256, 0, s>>>(n, k, ldc, O32.p, out);
   FSA_CHECK_LAUNCH();

@@ -380,6 +380,212 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
   finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
 }
 
+// FP32 form over the cell-grid tiles with shared-memory staging: a block
+// copies its tile's three neighbour ranges of Z (contiguous runs of rows) and
+// the tile's (staged column, value) pairs into shared memory with coalesced
+// loads, then each warp runs its rows from shared memory: per nonzero one
+// broadcast load of the pair, one 16-byte load of the neighbour's columns per
+// lane and four FMAs (lane L owns columns 4L..4L+3).  A tile that exceeds the
+// staging capacity, or holds a column outside its ranges (the cell-grid
+// pattern produces none), runs the row kernel's global gathers instead.
+static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
+    int ntiles, const int64_t* __restrict__ tiles, const int32_t* __restrict__ tile_bad, int cap_rows, int cap_nnz,
+    int cap_trows, int c, int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+    const int32_t* __restrict__ scol, const float* __restrict__ vals, const float* __restrict__ Z,
+    const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H, const double* __restrict__ beta,
+    double* __restrict__ part, int step, CGScalars q) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int c4 = ldc >> 2;
+  float4* zs = reinterpret_cast<float4*>(smraw);                               // cap_rows x c4
+  int2* prs = reinterpret_cast<int2*>(smraw + (size_t)cap_rows * c4 * 16);    // cap_nnz pairs
+  int* ro = reinterpret_cast<int*>(prs + cap_nnz);                             // cap_trows + 1 offsets
+  __shared__ int64_t td[8];
+  __shared__ int bad_sh;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // lane -> (row slot, chunk pair): L lanes per row, R rows per warp step;
+  // the lane owns float4 chunks q0 = 2 ch and q1 = 2 ch + 1 of its row
+  const int L = (c4 + 1) >> 1, R = 32 / L;
+  const int slot = lane / L, ch = lane - (lane / L) * L;
+  const bool lane_on = slot < R;
+  const int q0 = 2 * ch, q1 = 2 * ch + 1;
+  const bool has1 = q1 < c4;
+  const float4* Z4 = reinterpret_cast<const float4*>(Z);
+  __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
+  __shared__ int any_b;
+  float sub[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  double dot[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (threadIdx.x == 0) any_b = 0;
+  __syncthreads();
+  for (int col = threadIdx.x; col < 136; col += blockDim.x) {
+    const float bv = col < c ? (float)beta[col] : 0.f;
+    bsh[col] = bv;
+    if (bv != 0.f) any_b = 1;
+  }
+  __syncthreads();
+  const bool use_b = any_b != 0;
+  int cnt = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();   // the previous tile's reads of shared memory are done
+    if (threadIdx.x < 8) td[threadIdx.x] = tiles[(int64_t)tile * 8 + threadIdx.x];
+    if (threadIdx.x == 0) bad_sh = tile_bad[tile];
+    __syncthreads();
+    const int64_t p0 = td[0], p1 = td[1];
+    const int64_t e0 = rowptr[p0], e1 = rowptr[p1];
+    const int nr = (int)(p1 - p0), ne = (int)(e1 - e0);
+    const int r0b = (int)td[2], r1b = (int)td[4], r2b = (int)td[6];
+    const int n0 = (int)(td[3] - td[2]), n1 = (int)(td[5] - td[4]), n2 = (int)(td[7] - td[6]);
+    const bool staged = !bad_sh && n0 + n1 + n2 <= cap_rows && ne <= cap_nnz && nr <= cap_trows;
+    if (staged) {
+      const int x0 = n0 * c4, x1 = x0 + n1 * c4, x2 = x1 + n2 * c4;
+      for (int x = threadIdx.x; x < x2; x += blockDim.x) {
+        const int64_t src = x < x0 ? (int64_t)r0b * c4 + x
+                                   : (x < x1 ? (int64_t)r1b * c4 + (x - x0) : (int64_t)r2b * c4 + (x - x1));
+        zs[x] = Z4[src];
+      }
+      for (int x = threadIdx.x; x < ne; x += blockDim.x)
+        prs[x] = make_int2(scol[e0 + x], __float_as_int(vals[e0 + x]));
+      for (int x = threadIdx.x; x <= nr; x += blockDim.x) ro[x] = (int)(rowptr[p0 + x] - e0);
+    }
+    __syncthreads();
+    for (int rbase = wib * R; rbase < nr; rbase += 8 * R) {
+      const int r = rbase + slot;
+      const bool on = lane_on && r < nr;
+      const int64_t i = p0 + r;
+      const int64_t i0 = i * c4;
+      float4 sv0 = make_float4(0.f, 0.f, 0.f, 0.f), sv1 = sv0, zi0 = sv0, zi1 = sv0;
+      if (on) {   // the row's own operand S is loaded up front, in flight with the row's products
+        const float4* S4 = reinterpret_cast<const float4*>(S);
+        sv0 = S4[i0 + q0];
+        if (has1) sv1 = S4[i0 + q1];
+      }
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      if (on) {
+        if (staged) {
+          const int tb = ro[r], te = ro[r + 1];
+          // q1 may run one chunk past the row for odd c4: it reads the next
+          // staged row (in bounds, kept off the output)
+#pragma unroll 4
+          for (int t = tb; t < te; ++t) {
+            const int2 pv = prs[t];
+            const float v = __int_as_float(pv.y);
+            const float4 z0 = zs[pv.x * c4 + q0];
+            const float4 z1 = zs[pv.x * c4 + q1];
+            a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
+            a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
+            a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
+            a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
+          }
+          const int zr = (n0 + (int)(i - r1b)) * c4;
+          zi0 = zs[zr + q0];
+          if (has1) zi1 = zs[zr + q1];
+        } else {
+          zi0 = Z4[i0 + q0];
+          if (has1) zi1 = Z4[i0 + q1];
+          const int64_t rb = rowptr[i], re = rowptr[i + 1];
+          for (int64_t t = rb; t < re; ++t) {
+            const int64_t j = colidx[t];
+            const float v = vals[t];
+            const float4 z0 = Z4[j * c4 + q0];
+            const float4 z1 = has1 ? Z4[j * c4 + q1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
+            a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
+            a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
+            a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
+          }
+        }
+        float4 vo0 = make_float4(a0.x + sv0.x, a0.y + sv0.y, a0.z + sv0.z, a0.w + sv0.w);
+        float4 vo1 = make_float4(a1.x + sv1.x, a1.y + sv1.y, a1.z + sv1.z, a1.w + sv1.w);
+        float4 ho0 = zi0, ho1 = zi1;
+        if (use_b) {
+          const float4* V4 = reinterpret_cast<const float4*>(V);
+          const float4* H4 = reinterpret_cast<const float4*>(H);
+          const float* b = bsh + 4 * q0;
+          const float4 vv0 = V4[i0 + q0], hh0 = H4[i0 + q0];
+          vo0.x += b[0] * vv0.x; vo0.y += b[1] * vv0.y; vo0.z += b[2] * vv0.z; vo0.w += b[3] * vv0.w;
+          ho0.x += b[0] * hh0.x; ho0.y += b[1] * hh0.y; ho0.z += b[2] * hh0.z; ho0.w += b[3] * hh0.w;
+          if (has1) {
+            const float4 vv1 = V4[i0 + q1], hh1 = H4[i0 + q1];
+            vo1.x += b[4] * vv1.x; vo1.y += b[5] * vv1.y; vo1.z += b[6] * vv1.z; vo1.w += b[7] * vv1.w;
+            ho1.x += b[4] * hh1.x; ho1.y += b[5] * hh1.y; ho1.z += b[6] * hh1.z; ho1.w += b[7] * hh1.w;
+          }
+        }
+        float4* Vw = reinterpret_cast<float4*>(V);
+        float4* Hw = reinterpret_cast<float4*>(H);
+        Vw[i0 + q0] = vo0;
+        Hw[i0 + q0] = ho0;
+        sub[0] += ho0.x * vo0.x; sub[1] += ho0.y * vo0.y; sub[2] += ho0.z * vo0.z; sub[3] += ho0.w * vo0.w;
+        if (has1) {
+          Vw[i0 + q1] = vo1;
+          Hw[i0 + q1] = ho1;
+          sub[4] += ho1.x * vo1.x; sub[5] += ho1.y * vo1.y; sub[6] += ho1.z * vo1.z; sub[7] += ho1.w * vo1.w;
+        }
+      }
+      if (++cnt == 32) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { dot[k] += (double)sub[k]; sub[k] = 0.f; }
+        cnt = 0;
+      }
+    }
+  }
+  // fixed-order sum over the warp's row slots (lanes ch, ch + L, ...), then
+  // over the 8 warps in the (now free) staging buffer
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dot[k] += (double)sub[k];
+  for (int sl = 1; sl < R; ++sl) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double o = __shfl_sync(0xffffffffu, dot[k], (ch + sl * L) & 31);
+      if (slot == 0) dot[k] += o;
+    }
+  }
+  double* red = reinterpret_cast<double*>(smraw);
+  __syncthreads();
+  if (slot == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int col = 4 * q0 + k;
+      if (col < 128) red[wib * 128 + col] = (col < ldc) ? dot[k] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w * 128 + col];
+    part[(int64_t)blockIdx.x * ldc + col] = t;
+  }
+  finish_scalars(step, part, ldc, c, 0, q, red);
+}
+
+// launch shape of kv_spmm_staged for a block width: staging capacities
+// (rows of Z within kStageBytes, the largest tile's nonzeros and rows) and a
+// one-wave grid
+struct StagedLaunch {
+  int blocks = 0, cap_rows = 0, cap_nnz = 0, cap_trows = 0;
+  size_t smem = 0;
+};
+constexpr size_t kStageBytes = 56 * 1024;
+constexpr size_t kStageMaxSmem = 100 * 1024;
+static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
+  static const bool attr =
+      cudaFuncSetAttribute(kv_spmm_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageMaxSmem) ==
+      cudaSuccess;
+  (void)attr;
+  StagedLaunch L;
+  const int64_t cap = (int64_t)(kStageBytes / ((size_t)ldc * sizeof(float)));
+  L.cap_rows = (int)std::min<int64_t>(cap, std::max<int64_t>(Hd.max_staged, 1));
+  L.cap_nnz = (int)std::min<int64_t>(2048, std::max<int64_t>(Hd.max_tile_nnz, 1));
+  L.cap_trows = (int)std::min<int64_t>(512, std::max<int64_t>(Hd.max_tile_rows, 1));
+  size_t bytes = (size_t)(L.cap_rows + 1) * ldc * sizeof(float) + (size_t)L.cap_nnz * 8 +
+                 (size_t)(L.cap_trows + 1) * 4;
+  L.smem = std::max<size_t>((bytes + 15) / 16 * 16, 8 * 128 * sizeof(double));
+  int dev = 0, sms = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_staged, 256, L.smem);
+  L.blocks = std::max(1, std::min(Hd.ntiles, sms * std::max(per, 1)));
+  return L;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 element-wise kernels with 16-byte accesses: thread -> 4 consecutive
 // columns (c4 = ldc/4 threads per row, rpb rows per block step), row loop
@@ -523,6 +729,21 @@ inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t
     default: throw Error{FSA_ERR_UNSUPPORTED, "block of more than 128 columns"};
   }
   FSA_CHECK_LAUNCH();
+}
+
+// FP32 SpMM of the CG loop: the staged tile kernel when the handle has tiles,
+// the row kernel otherwise
+inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedLaunch& L, cudaStream_t s,
+                            const float* vals, const float* Z, const float* S, float* V, float* Hv,
+                            const double* beta, double* part, int step, const CGScalars& q) {
+  if (Hd.ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0) {
+    kv_spmm_staged<<<std::min(L.blocks, lay.nblk), 256, L.smem, s>>>(
+        Hd.ntiles, Hd.tiles.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, lay.c, lay.ldc, Hd.rowptr.p,
+        Hd.col.p, Hd.scol.p, vals, Z, S, V, Hv, beta, part, step, q);
+    FSA_CHECK_LAUNCH();
+    return;
+  }
+  launch_spmm_fused<float, float>(lay, s, Hd.rowptr.p, Hd.col.p, vals, Z, S, V, Hv, beta, part, step, q);
 }
 
 }  // namespace fsa

@@ -143,3 +143,53 @@ def test_mixed_x2_woodbury_core_accurate_at_large_n(F):
         ll2, _, i2 = h.loglik_grad(y, th, F.make_opts(precision=F.FSA_MIXED_BF16X2, **o))
     assert abs(i2["logdet_precond"] - i64["logdet_precond"]) < 1e-5 * abs(i64["logdet_precond"])
     assert abs(ll2 - ll64) < 1e-4 * abs(ll64), (ll2, ll64)
+
+
+def test_mixed_x2_loglik_clustered_points(F):
+    """Points with a dense cluster (a few hundred in one taper cell) beside a
+    uniform background: the SpMM stages most tiles in shared memory and runs
+    the overfull ones from global memory; both paths meet the oracle."""
+    rng = np.random.default_rng(4321)
+    n_bg, n_cl = 12000, 600
+    locs = np.vstack([fi.uniform_locations(n_bg, 83), 0.5 + 0.003 * rng.random((n_cl, 2))])
+    n = locs.shape[0]
+    m, nu, gamma, l, K = 150, 0.5, 0.02, 8, 25
+    ind = locs[fi.inducing_subset(n, m, 83)]
+    th = (1.0, 0.05, 0.05)
+    y = fi.random_field(locs, nu, *th, 83)
+    ref = O.IterativeFSA(locs, ind, gamma, nu, th).loglik_grad(y, l, 4, 0.0, fixed_iters=K)
+    with F.FSAHandle(locs, ind, gamma, nu) as h:
+        diff, staged, total = _spmm_selftest(h, th, 40)
+        ll, g, info = h.loglik_grad(y, th, F.make_opts(num_probes=l, fixed_iters=K, seed=4,
+                                                       precision=F.FSA_MIXED_BF16X2))
+    # the tile kernel (shared-memory and global tiles) equals the row kernel bit for bit
+    assert diff == 0.0 and 0 < staged < total, (diff, staged, total)
+    # a dense cluster is the ill-conditioned case: the log-likelihood stays within 1e-4
+    assert abs(ll - ref["loglik"]) < 1e-4 * abs(ref["loglik"]), (ll, ref["loglik"])
+    assert np.linalg.norm(g - ref["grad"]) < 1e-2 * np.linalg.norm(ref["grad"])
+
+
+def _spmm_selftest(h, th, ncols, seed=1):
+    import ctypes
+    from paper_2405_14492_gb300 import _native as N
+    f = N.lib().fsa_selftest_spmm
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(N.FsaTheta), ctypes.c_int, ctypes.c_uint64,
+                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    d, st, tot = ctypes.c_double(-1), ctypes.c_int(-1), ctypes.c_int(-1)
+    t = N.FsaTheta(*th)
+    N.check(f(h._h, ctypes.byref(t), ncols, seed, ctypes.byref(d), ctypes.byref(st), ctypes.byref(tot)))
+    return d.value, st.value, tot.value
+
+
+@pytest.mark.parametrize("n,gamma,ncols", [(20011, 0.015, 65), (50021, 0.0071, 17), (3001, 0.05, 127)])
+def test_spmm_tile_kernel_equals_row_kernel(F, n, gamma, ncols):
+    """The shared-memory tile SpMM gives the row kernel's result bit for bit
+    (same per-row summation order), for block widths from 17 to 127 columns."""
+    locs = fi.uniform_locations(n, 84)
+    ind = locs[fi.inducing_subset(n, 60, 84)]
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        diff, staged, total = _spmm_selftest(h, (1.0, 0.05, 0.05), ncols)
+    assert diff == 0.0
+    # at 128 columns the staging capacity holds fewer rows than these tiles span
+    assert total > 0 and (staged > 0 or ncols > 100)
