@@ -10,6 +10,10 @@
  *   "pcg_Aq"   per-CG-iteration  s = A~ q
  *   "build"    operator build    A = Sigma_nm L^-T, M = I + A~^T D^-1 A~, probes
  *   "grad"     gradient          B = dK L^-T, F = A~ E, projections
+ * and every tiled SpMM of the mixed CG loop:
+ *   "pcg_spmm" per-CG-iteration  V = Sigma_s~ Z + S + beta V, H = Z + beta H
+ *              (bytes: 8 per nonzero, the row pointers, Z and S read, V and H
+ *              read and written)
  * Timing adds one event pair per GEMM launch; it is meant for measurement
  * runs.  Not thread-safe across concurrent callers.
  */

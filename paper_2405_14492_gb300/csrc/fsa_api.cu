@@ -134,7 +134,12 @@ void free_handle(fsa_handle* h, bool trim) {
   H.host_pinned = nullptr;
   if (H.ev0) cudaEventDestroy(H.ev0);
   if (H.ev1) cudaEventDestroy(H.ev1);
+  if (H.side) cudaStreamSynchronize(H.side);
+  if (H.ev_fork) cudaEventDestroy(H.ev_fork);
+  if (H.ev_join) cudaEventDestroy(H.ev_join);
+  cudaStream_t side = H.side;
   delete h;
+  if (side) cudaStreamDestroy(side);
   cudaStreamSynchronize(s);
   if (trim) release_pool_memory();
 }

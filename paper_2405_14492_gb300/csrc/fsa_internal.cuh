@@ -159,6 +159,9 @@ struct Handle {
   DevPtr<double> outs;                     // device results [loglik, logdet, quad, g0, g1, g2, se, ...]
   double* host_pinned = nullptr;           // pinned mirror of small results
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // side stream for work that overlaps the main stream (SLQ beside the gradient)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // ---------------------------------------------------------------------------

@@ -72,17 +72,28 @@ __global__ void k_split_f64(int rows, int cols, const double* __restrict__ src, 
   }
 }
 
-__global__ void k_f32_to_bf16(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+// destination index of element t of a row-major rows x cols source: the same
+// (cols == 0) or the blocked K-major layout with K = the column
+__device__ __forceinline__ int64_t dst_index(int64_t t, int64_t rows, int cols) {
+  if (cols == 0) return t;
+  const int64_t r = t / cols;
+  return blocked_index(r, t - r * cols, rows);
+}
+
+__global__ void k_f32_to_bf16(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                              int64_t rows = 0, int cols = 0) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x)
-    dst[t] = __float2bfloat16_rn(src[t]);
+    dst[dst_index(t, rows, cols)] = __float2bfloat16_rn(src[t]);
 }
 
 __global__ void k_f32_split(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
-                            __nv_bfloat16* __restrict__ lo) {
+                            __nv_bfloat16* __restrict__ lo, int64_t rows = 0, int cols = 0) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    split_bf16(src[t], hi[t], lo[t]);
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = dst_index(t, rows, cols);
+    split_bf16(src[t], hi[d], lo[d]);
+  }
 }
 
 __device__ __forceinline__ float2 ld_pair(const __nv_bfloat162* hi, const __nv_bfloat162* lo, int k) {
@@ -96,21 +107,25 @@ __device__ __forceinline__ float2 ld_pair(const __nv_bfloat162* hi, const __nv_b
 }
 
 // dst (cols x ld_dst) = src^T, src rows x cols (ld_src); 32 x 32 tiles through shared memory
+// dst = src^T; blocked != 0: dst in the blocked K-major layout (K = the src
+// row index, cols rows), else row-major with leading dimension ld_dst
 __global__ void k_transpose_bf16(int64_t rows, int cols, const __nv_bfloat16* __restrict__ src, int64_t ld_src,
-                                 __nv_bfloat16* __restrict__ dst, int64_t ld_dst) {
+                                 __nv_bfloat16* __restrict__ dst, int64_t ld_dst, int blocked, int src_blocked = 0) {
   __shared__ __nv_bfloat16 tile[32][34];
   int64_t r0 = (int64_t)blockIdx.x * 32;
   int c0 = blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
     int64_t r = r0 + k;
     int c = c0 + threadIdx.x;
-    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[r * ld_src + c] : __float2bfloat16(0.f);
+    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[src_blocked ? blocked_index(r, c, rows) : r * ld_src + c]
+                                                  : __float2bfloat16(0.f);
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += 8) {
     int c = c0 + k;
     int64_t r = r0 + threadIdx.x;
-    if (c < cols && r < rows) dst[(int64_t)c * ld_dst + r] = tile[threadIdx.x][k];
+    if (c < cols && r < rows)
+      dst[blocked ? blocked_index(c, r, cols) : (int64_t)c * ld_dst + r] = tile[threadIdx.x][k];
   }
 }
 
@@ -128,18 +143,20 @@ __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restri
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int np2 = m_pad / 2;
+  // A~ (and its low half) in the blocked K-major layout: pair k of row i is
+  // pair (k & 31) of 64-element block k >> 5 at ((k >> 5) n + i) 64
+  const __nv_bfloat162* A2 = reinterpret_cast<const __nv_bfloat162*>(A);
+  const __nv_bfloat162* A2l = Alo ? reinterpret_cast<const __nv_bfloat162*>(Alo) : nullptr;
   for (int64_t i = warp; i < n; i += nwarps) {
-    const __nv_bfloat162* ai = reinterpret_cast<const __nv_bfloat162*>(A + i * m_pad);
-    const __nv_bfloat162* ali = Alo ? reinterpret_cast<const __nv_bfloat162*>(Alo + i * m_pad) : nullptr;
     double xi = xs[i], yi = ys[i];
     for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
       int j = col[t];
-      const __nv_bfloat162* aj = reinterpret_cast<const __nv_bfloat162*>(A + (int64_t)j * m_pad);
-      const __nv_bfloat162* alj = Alo ? reinterpret_cast<const __nv_bfloat162*>(Alo + (int64_t)j * m_pad) : nullptr;
       float s = 0.f;
       for (int k = lane; k < np2; k += 32) {
-        float2 a = ld_pair(ai, ali, k);
-        float2 b = ld_pair(aj, alj, k);
+        const int64_t bi = ((int64_t)(k >> 5) * n + i) * 32 + (k & 31);
+        const int64_t bj = ((int64_t)(k >> 5) * n + j) * 32 + (k & 31);
+        float2 a = ld_pair(A2 + bi, A2l ? A2l + bi : nullptr, 0);
+        float2 b = ld_pair(A2 + bj, A2l ? A2l + bj : nullptr, 0);
         s = fmaf(a.x, b.x, s);
         s = fmaf(a.y, b.y, s);
       }
@@ -164,13 +181,14 @@ __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restri
 }
 
 // Y^T = (D^-1 A~)^T split hi/lo, from A~^T (m_pad x n_pad)
+// (all four in the blocked K-major layout: element t holds point (t / (64 m_pad)) 64 + t % 64)
 __global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __nv_bfloat16* __restrict__ At,
                                    const __nv_bfloat16* __restrict__ At_lo, const float* __restrict__ Dinv,
                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   int64_t total = (int64_t)m_pad * n_pad;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t % n_pad;
+    int64_t i = (t / (64 * (int64_t)m_pad)) * 64 + (t & 63);
     float a = __bfloat162float(At[t]) + (At_lo ? __bfloat162float(At_lo[t]) : 0.f);
     float v = i < n ? a * Dinv[i] : 0.f;
     split_bf16(v, hi[t], lo[t]);
@@ -202,9 +220,9 @@ __device__ __forceinline__ void split_n(float v, int nsplit, __nv_bfloat16* out)
   if (nsplit == 3) out[2] = __float2bfloat16_rn(r - __bfloat162float(mid));
 }
 
-// src (n x ldc FP32) optionally scaled by rowscale -> dst (nsplit ldc x n_pad BF16):
-// plane p (rows p ldc .. p ldc + ldc - 1) holds the p-th BF16 piece; K-major
-// (points contiguous) for the B operand of A^T X.  A block transposes a tile
+// src (n x ldc FP32) optionally scaled by rowscale -> dst (nsplit ldc x n_pad BF16,
+// blocked K-major layout): plane p (rows p ldc .. p ldc + ldc - 1) holds the
+// p-th BF16 piece; K = the point index, for the B operand of A^T X.  A block transposes a tile
 // of kSTRows points: coalesced 16-byte loads of the FP32 rows into shared
 // memory (row stride ldc + 1 words against bank conflicts), then each thread
 // splits 8 consecutive points of one column and writes each piece as one
@@ -248,12 +266,13 @@ __global__ void __launch_bounds__(256) k_split_transpose(int64_t n, int c, int l
       for (int p = 0; p < 3; ++p)
         w[p][k / 2] = (uint32_t)__bfloat16_as_ushort(e[p]) | ((uint32_t)__bfloat16_as_ushort(o[p]) << 16);
     }
-    const int64_t base = (int64_t)cc * n_pad + r0 + 8 * g;
+    // blocked K-major output: this tile is K block blockIdx.x, rows p ldc + cc
+    const int64_t ns = (int64_t)nsplit * ldc;
+    const int64_t base = ((int64_t)blockIdx.x * ns + cc) * 64 + 8 * g;
     *reinterpret_cast<uint4*>(dst + base) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
-    *reinterpret_cast<uint4*>(dst + base + (int64_t)ldc * n_pad) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+    *reinterpret_cast<uint4*>(dst + base + (int64_t)ldc * 64) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
     if (nsplit == 3)
-      *reinterpret_cast<uint4*>(dst + base + (int64_t)2 * ldc * n_pad) =
-          make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+      *reinterpret_cast<uint4*>(dst + base + (int64_t)2 * ldc * 64) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
   }
 }
 
@@ -344,14 +363,16 @@ __global__ void __launch_bounds__(256) k_grad_sparse_bf16(
   const int nch = m_pad / 8;   // 16-byte chunks per row
   const float inv_l = c > 1 ? 1.0f / (float)(c - 1) : 0.f;
   double s0 = 0.0, sr = 0.0, s2 = 0.0;
+  // A~ is in the blocked K-major layout: 16-byte chunk ch of row r is chunk
+  // (ch & 7) of 64-element block ch >> 3, at ((ch >> 3) n + r) 8 + (ch & 7)
+  const uint4* A4 = reinterpret_cast<const uint4*>(A);
   for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
-    const uint4* ai4 = reinterpret_cast<const uint4*>(A + i * m_pad);
     const uint4* bi4 = reinterpret_cast<const uint4*>(B + i * m_pad);
     uint4 ai[KC], bi[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       int ch = lane + 32 * k;
-      ai[k] = ch < nch ? ai4[ch] : make_uint4(0, 0, 0, 0);
+      ai[k] = ch < nch ? A4[((int64_t)(ch >> 3) * n + i) * 8 + (ch & 7)] : make_uint4(0, 0, 0, 0);
       bi[k] = ch < nch ? bi4[ch] : make_uint4(0, 0, 0, 0);
     }
     float xi[NS];
@@ -367,13 +388,12 @@ __global__ void __launch_bounds__(256) k_grad_sparse_bf16(
       const int myc = lane < mcnt ? colidx[base + lane] : 0;
       for (int t = 0; t < mcnt; ++t) {
         const int j = __shfl_sync(0xffffffffu, myc, t);
-        const uint4* aj4 = reinterpret_cast<const uint4*>(A + (int64_t)j * m_pad);
         const uint4* qj4 = reinterpret_cast<const uint4*>(Q + (int64_t)j * m_pad);
         float dl = 0.f;
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
           int ch = lane + 32 * k;
-          if (ch < nch) dl += dot8_bf16(bi[k], aj4[ch]) + dot8_bf16(ai[k], qj4[ch]);
+          if (ch < nch) dl += dot8_bf16(bi[k], A4[((int64_t)(ch >> 3) * n + j) * 8 + (ch & 7)]) + dot8_bf16(ai[k], qj4[ch]);
         }
         float g = 0.f;
 #pragma unroll
@@ -471,9 +491,9 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
     op.Ab.ensure(nm);
     if (lo) {
       op.Ab_lo.ensure(nm);
-      k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, op.Ab_lo.p);
+      k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, op.Ab_lo.p, n, m_pad);
     } else {
-      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p);
+      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, n, m_pad);
     }
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
@@ -481,12 +501,12 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   dim3 tgrid((unsigned)((n + 31) / 32), (m_pad + 31) / 32), tblk(32, 8);
   op.Atb.ensure((size_t)m_pad * n_pad);
   FSA_CUDA(cudaMemsetAsync(op.Atb.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
-  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab.p, m_pad, op.Atb.p, n_pad);
+  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab.p, m_pad, op.Atb.p, n_pad, 1, 1);
   FSA_CHECK_LAUNCH();
   if (lo) {
     op.Atb_lo.ensure((size_t)m_pad * n_pad);
     FSA_CUDA(cudaMemsetAsync(op.Atb_lo.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
-    k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab_lo.p, m_pad, op.Atb_lo.p, n_pad);
+    k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab_lo.p, m_pad, op.Atb_lo.p, n_pad, 1, 1);
     FSA_CHECK_LAUNCH();
   }
   const __nv_bfloat16* Alo = lo ? op.Ab_lo.p : nullptr;
@@ -508,9 +528,9 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
     k_scale_cols_split<<<grid_for((int64_t)mn, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, Atlo, op.Dinv32.p,
                                                                     Yhi.p, Ylo.p);
     FSA_CHECK_LAUNCH();
-    TmaMap mAt = make_tma_bf16(op.Atb.p, m_pad, n, n_pad, 128);
-    TmaMap mAtl = lo ? make_tma_bf16(op.Atb_lo.p, m_pad, n, n_pad, 128) : mAt;
-    TmaMap mYh = make_tma_bf16(Yhi.p, m_pad, n, n_pad, 128), mYl = make_tma_bf16(Ylo.p, m_pad, n, n_pad, 128);
+    TmaMap mAt = make_tma_bf16_blocked(op.Atb.p, m_pad, n_pad, 128);
+    TmaMap mAtl = lo ? make_tma_bf16_blocked(op.Atb_lo.p, m_pad, n_pad, 128) : mAt;
+    TmaMap mYh = make_tma_bf16_blocked(Yhi.p, m_pad, n_pad, 128), mYl = make_tma_bf16_blocked(Ylo.p, m_pad, n_pad, 128);
     TcGemm g;
     g.a[0] = &mAt; g.a[1] = &mAtl; g.num_a = lo ? 2 : 1;
     g.b[0] = &mYh; g.b[1] = &mYl; g.num_b = 2;
@@ -581,18 +601,18 @@ static void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc) {
   g.Xb.ensure((size_t)ns * C.n_pad);
   g.qb.ensure((size_t)ns * C.m_pad);
   set_operator_maps(op, n, C);
-  C.mX = make_tma_bf16(g.Xb.p, ns, n, C.n_pad, ns);
+  C.mX = make_tma_bf16_blocked(g.Xb.p, ns, C.n_pad, ns);
   C.mQ = make_tma_bf16(g.qb.p, ns, C.m_pad, C.m_pad, ns);
   C.splits_w = tc_pick_splits(C.m_pad, ns, (int)n, ns);
 }
 
 static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C) {
-  C.mAt = make_tma_bf16(op.Atb.p, C.m_pad, n, C.n_pad, 128);
-  C.mA = make_tma_bf16(op.Ab.p, n, C.m_pad, C.m_pad, 128);
+  C.mAt = make_tma_bf16_blocked(op.Atb.p, C.m_pad, C.n_pad, 128);
+  C.mA = make_tma_bf16_blocked(op.Ab.p, n, C.m_pad, 128);
   C.lo = op.has_lo;
   if (C.lo) {
-    C.mAt_lo = make_tma_bf16(op.Atb_lo.p, C.m_pad, n, C.n_pad, 128);
-    C.mA_lo = make_tma_bf16(op.Ab_lo.p, n, C.m_pad, C.m_pad, 128);
+    C.mAt_lo = make_tma_bf16_blocked(op.Atb_lo.p, C.m_pad, C.n_pad, 128);
+    C.mA_lo = make_tma_bf16_blocked(op.Ab_lo.p, n, C.m_pad, 128);
   }
 }
 
@@ -726,7 +746,17 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       if (*pin_active == 0) break;
     }
   }
-  launch_slq(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.quads.p, H.err, s);
+  // the Lanczos eigen-quadrature depends only on the tridiagonals: it runs on
+  // the side stream (one thread per probe column) beside the gradient work
+  if (!H.side) {
+    FSA_CUDA(cudaStreamCreateWithFlags(&H.side, cudaStreamNonBlocking));
+    FSA_CUDA(cudaEventCreateWithFlags(&H.ev_fork, cudaEventDisableTiming));
+    FSA_CUDA(cudaEventCreateWithFlags(&H.ev_join, cudaEventDisableTiming));
+  }
+  FSA_CUDA(cudaEventRecord(H.ev_fork, s));
+  FSA_CUDA(cudaStreamWaitEvent(H.side, H.ev_fork, 0));
+  launch_slq(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.quads.p, H.err, H.side);
+  FSA_CUDA(cudaEventRecord(H.ev_join, H.side));
   DevPtr<double> ypart((size_t)lay.nblk * ldc);
   k_dot_col0<float><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U32.p, ypart.p);
   FSA_CHECK_LAUNCH();
@@ -794,10 +824,10 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       DevPtr<__nv_bfloat16> Bt((size_t)m_pad * C.n_pad);
       FSA_CUDA(cudaMemsetAsync(Bt.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * C.n_pad, s));
       k_transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (m_pad + 31) / 32), dim3(32, 8), 0, s>>>(n, m_pad, Bb.p,
-                                                                                              m_pad, Bt.p, C.n_pad);
+                                                                                              m_pad, Bt.p, C.n_pad, 1);
       FSA_CHECK_LAUNCH();
       MixedCtx CB = C;
-      CB.mAt = make_tma_bf16(Bt.p, m_pad, n, C.n_pad, 128);
+      CB.mAt = make_tma_bf16_blocked(Bt.p, m_pad, C.n_pad, 128);
       CB.lo = false;
       mixed_AtX(H, CB, g.U32.p, nullptr, BX.p, "grad");
       mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p, "grad");
@@ -811,11 +841,13 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq,
                                              gbuf.p + (size_t)ngpart * 3);
     FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
                                 gbuf.p, ngpart, gbuf.p + (size_t)ngpart * 3, 1, H.outs.p);
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
   } else {
+    FSA_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
                                 nullptr, 0, nullptr, 0, H.outs.p);
     FSA_CHECK_LAUNCH();

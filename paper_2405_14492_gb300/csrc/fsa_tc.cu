@@ -34,6 +34,7 @@ struct Params {
   int num_a, num_b;
   unsigned pairs;
   int M, bn, kb_base, kblocks, kb_per_split, stages;   // k-blocks [kb_base, kblocks)
+  uint32_t blk;                                         // bit a: A_a blocked; bit 2 + b: B_b blocked
   uint32_t a_bytes, b_bytes, stage_bytes, tmem_cols, idesc;
   int stack, n_valid;
   float* out;
@@ -84,6 +85,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// one operand box of K block kb: 64 K columns x the rows from row0
+__device__ __forceinline__ void load_operand(void* dst, const CUtensorMap* map, bool blocked, uint64_t* bar, int kb,
+                                             int row0) {
+  if (blocked)
+    tma_load_3d(dst, map, bar, 0, row0, kb);
+  else
+    tma_load_2d(dst, map, bar, kb * BK, row0);
 }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
@@ -174,10 +192,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         }
         uint8_t* st = smem + (size_t)s * p.stage_bytes;
         mbar_expect_tx(&full_bar[s], p.stage_bytes);
-        int kx = (kb0 + i) * BK;
-        for (int a = 0; a < p.num_a; ++a) tma_load_2d(st + a * p.a_bytes, &p.ma[a], &full_bar[s], kx, m0);
+        const int kb = kb0 + i;
+        for (int a = 0; a < p.num_a; ++a)
+          load_operand(st + a * p.a_bytes, &p.ma[a], (p.blk >> a) & 1u, &full_bar[s], kb, m0);
         for (int b = 0; b < p.num_b; ++b)
-          tma_load_2d(st + p.num_a * p.a_bytes + b * p.b_bytes, &p.mb[b], &full_bar[s], kx, n0);
+          load_operand(st + p.num_a * p.a_bytes + b * p.b_bytes, &p.mb[b], (p.blk >> (2 + b)) & 1u, &full_bar[s], kb,
+                       n0);
         issued = i + 1;
       }
       // drain: every copy issued by this thread has landed before the CTA exits
@@ -295,6 +315,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
+TmaMap make_tma_bf16_blocked(const __nv_bfloat16* ptr, int64_t rows, int64_t kpad, int box_rows) {
+  FSA_REQUIRE(((uintptr_t)ptr & 15) == 0, FSA_ERR_ARG, "TMA base not 16-byte aligned");
+  FSA_REQUIRE(kpad % 64 == 0 && kpad > 0, FSA_ERR_ARG, "blocked TMA layout needs K a multiple of 64");
+  FSA_REQUIRE(box_rows >= 8 && box_rows <= 256, FSA_ERR_ARG, "TMA box rows out of range");
+  TmaMap t;
+  t.blocked = 1;
+  cuuint64_t gdim[3] = {64, (cuuint64_t)rows, (cuuint64_t)(kpad / 64)};
+  cuuint64_t gstride[2] = {128, (cuuint64_t)rows * 128};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = get_encode()(&t.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(ptr), gdim,
+                            gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  FSA_REQUIRE(r == CUDA_SUCCESS, FSA_ERR_CUDA, "cuTensorMapEncodeTiled (blocked) failed: " + std::to_string((int)r));
+  return t;
+}
+
 TmaMap make_tma_bf16(const __nv_bfloat16* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
   FSA_REQUIRE(((uintptr_t)ptr & 15) == 0, FSA_ERR_ARG, "TMA base not 16-byte aligned");
   FSA_REQUIRE((ld * 2) % 16 == 0, FSA_ERR_ARG, "TMA row stride not a multiple of 16 bytes");
@@ -333,8 +370,14 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   FSA_REQUIRE(g.M > 0 && g.N > 0 && g.K > 0, FSA_ERR_ARG, "tc_gemm empty problem");
   tc::Params p;
   std::memset(&p, 0, sizeof(p));
-  for (int a = 0; a < g.num_a; ++a) p.ma[a] = g.a[a]->map;
-  for (int b = 0; b < g.num_b; ++b) p.mb[b] = g.b[b]->map;
+  for (int a = 0; a < g.num_a; ++a) {
+    p.ma[a] = g.a[a]->map;
+    if (g.a[a]->blocked) p.blk |= 1u << a;
+  }
+  for (int b = 0; b < g.num_b; ++b) {
+    p.mb[b] = g.b[b]->map;
+    if (g.b[b]->blocked) p.blk |= 4u << b;
+  }
   p.num_a = g.num_a;
   p.num_b = g.num_b;
   p.pairs = g.pairs;

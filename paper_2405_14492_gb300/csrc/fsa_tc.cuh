@@ -18,11 +18,24 @@ namespace fsa {
 
 struct TmaMap {
   CUtensorMap map;
+  int blocked = 0;   // 1: the blocked K-major layout below (3-D map)
 };
 
 // 2-D K-major BF16 tensor map: rows x cols (cols contiguous, leading dimension
 // ld elements, ld * 2 bytes a multiple of 16), box = 64 cols x box_rows rows.
 TmaMap make_tma_bf16(const __nv_bfloat16* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+
+// Blocked K-major layout of a rows x kpad matrix (kpad a multiple of 64): K is
+// cut into blocks of 64, and block kb stores columns 64 kb .. 64 kb + 63 of
+// all rows, row after row, so that the box of box_rows consecutive rows of one
+// K block is one contiguous range of memory (the operands whose K is the
+// point index n: a row-major n-long row would put the rows of a box 2n bytes
+// apart).  Element (r, k) sits at blocked_index(r, k, rows).  Everything in
+// columns k >= K must be stored as zeros (the map does not fill them).
+TmaMap make_tma_bf16_blocked(const __nv_bfloat16* ptr, int64_t rows, int64_t kpad, int box_rows);
+__host__ __device__ __forceinline__ int64_t blocked_index(int64_t r, int64_t k, int64_t rows) {
+  return ((k >> 6) * rows + r) * 64 + (k & 63);
+}
 
 struct TcGemm {
   const TmaMap* a[2] = {nullptr, nullptr};

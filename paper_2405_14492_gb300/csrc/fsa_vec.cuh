@@ -18,6 +18,7 @@
 
 #include "fsa_internal.cuh"
 #include "fsa_solver.cuh"
+#include "fsa_tc.cuh"
 
 namespace fsa {
 
@@ -737,10 +738,25 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
                             const float* vals, const float* Z, const float* S, float* V, float* Hv,
                             const double* beta, double* part, int step, const CGScalars& q) {
   if (Hd.ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0) {
+    // timed under the profiling hooks (tag pcg_spmm); algorithmic bytes: the
+    // pattern (staged column + value per nonzero, row pointers), Z and S read
+    // once, V and H read and written once
+    const bool prof = profile_on() && step != kStepNone;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+      e0 = profile_event();
+      e1 = profile_event();
+      FSA_CUDA(cudaEventRecord(e0, s));
+    }
     kv_spmm_staged<<<std::min(L.blocks, lay.nblk), 256, L.smem, s>>>(
         Hd.ntiles, Hd.tiles.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, lay.c, lay.ldc, Hd.rowptr.p,
         Hd.col.p, Hd.scol.p, vals, Z, S, V, Hv, beta, part, step, q);
     FSA_CHECK_LAUNCH();
+    if (prof) {
+      FSA_CUDA(cudaEventRecord(e1, s));
+      const double nb = (double)Hd.n * lay.ldc * sizeof(float);
+      profile_record("pcg_spmm", e0, e1, (double)Hd.nnz * 8.0 + (double)(Hd.n + 1) * 8.0 + 6.0 * nb);
+    }
     return;
   }
   launch_spmm_fused<float, float>(lay, s, Hd.rowptr.p, Hd.col.p, vals, Z, S, V, Hv, beta, part, step, q);
