@@ -88,7 +88,8 @@ __device__ __forceinline__ void scalar_step(int step, int col, int c, double v, 
   }
 }
 
-// called by every thread of every block after part[blockIdx.x][*] is written
+// called by every thread of every block after part[blockIdx.x][*] is written;
+// red: shared scratch of at least blockDim.x doubles
 __device__ __forceinline__ void finish_scalars(int step, const double* __restrict__ part, int ldc, int c, int l,
                                                CGScalars& q, double* __restrict__ red) {
   if (step == kStepNone) return;
@@ -99,24 +100,30 @@ __device__ __forceinline__ void finish_scalars(int step, const double* __restric
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // one warp per column: lanes sum strided partials, then a fixed shuffle tree
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  // coalesced fixed-order sum of the nb partial rows: thread (group g, column
+  // col) adds rows g, g + RG, ... in order (four running sums); the RG group
+  // sums are then added in group order
   const int nb = (int)gridDim.x;
-  // only complete warps take part (the block size rpb * ldc need not be a multiple of 32)
-  for (int col = warp; warp < nw && col < ldc; col += nw) {
+  const int RG = ((int)blockDim.x / ldc) > 1 ? (int)blockDim.x / ldc : 1;
+  for (int t = threadIdx.x; t < RG * ldc; t += blockDim.x) {
+    const int col = t % ldc, g = t / ldc;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = lane;
-    for (; b + 96 < nb; b += 128) {
+    int b = g;
+    for (; b + 3 * RG < nb; b += 4 * RG) {
       s0 += __ldcg(&part[(int64_t)b * ldc + col]);
-      s1 += __ldcg(&part[(int64_t)(b + 32) * ldc + col]);
-      s2 += __ldcg(&part[(int64_t)(b + 64) * ldc + col]);
-      s3 += __ldcg(&part[(int64_t)(b + 96) * ldc + col]);
+      s1 += __ldcg(&part[(int64_t)(b + RG) * ldc + col]);
+      s2 += __ldcg(&part[(int64_t)(b + 2 * RG) * ldc + col]);
+      s3 += __ldcg(&part[(int64_t)(b + 3 * RG) * ldc + col]);
     }
-    for (; b < nb; b += 32) s0 += __ldcg(&part[(int64_t)b * ldc + col]);
-    double v = warp_sum((s0 + s1) + (s2 + s3));
-    if (lane == 0) scalar_step(step, col, c, v, l, q);
+    for (; b < nb; b += RG) s0 += __ldcg(&part[(int64_t)b * ldc + col]);
+    red[t] = (s0 + s1) + (s2 + s3);
   }
-  (void)red;
+  __syncthreads();
+  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < RG; ++g) v += red[g * ldc + col];
+    scalar_step(step, col, c, v, l, q);
+  }
   if (step == kStepBeta) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -404,11 +411,13 @@ static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
   __shared__ int bad_sh;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // lane -> (row slot, chunk pair): L lanes per row, R rows per warp step;
-  // the lane owns float4 chunks q0 = 2 ch and q1 = 2 ch + 1 of its row
+  // the lane owns float4 chunks q0 = ch and q1 = ch + L of its row, so that
+  // the L lanes of a row read L consecutive 16-byte words (no bank conflicts
+  // within a row)
   const int L = (c4 + 1) >> 1, R = 32 / L;
   const int slot = lane / L, ch = lane - (lane / L) * L;
   const bool lane_on = slot < R;
-  const int q0 = 2 * ch, q1 = 2 * ch + 1;
+  const int q0 = ch, q1 = ch + L;
   const bool has1 = q1 < c4;
   const float4* Z4 = reinterpret_cast<const float4*>(Z);
   __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
@@ -464,7 +473,7 @@ static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
         if (staged) {
           const int tb = ro[r], te = ro[r + 1];
           // q1 may run one chunk past the row for odd c4: it reads the next
-          // staged row (in bounds, kept off the output)
+          // staged row (in bounds: one spare row is allocated; kept off the output)
 #pragma unroll 4
           for (int t = tb; t < te; ++t) {
             const int2 pv = prs[t];
@@ -505,9 +514,10 @@ static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
           vo0.x += b[0] * vv0.x; vo0.y += b[1] * vv0.y; vo0.z += b[2] * vv0.z; vo0.w += b[3] * vv0.w;
           ho0.x += b[0] * hh0.x; ho0.y += b[1] * hh0.y; ho0.z += b[2] * hh0.z; ho0.w += b[3] * hh0.w;
           if (has1) {
+            const float* b1 = bsh + 4 * q1;
             const float4 vv1 = V4[i0 + q1], hh1 = H4[i0 + q1];
-            vo1.x += b[4] * vv1.x; vo1.y += b[5] * vv1.y; vo1.z += b[6] * vv1.z; vo1.w += b[7] * vv1.w;
-            ho1.x += b[4] * hh1.x; ho1.y += b[5] * hh1.y; ho1.z += b[6] * hh1.z; ho1.w += b[7] * hh1.w;
+            vo1.x += b1[0] * vv1.x; vo1.y += b1[1] * vv1.y; vo1.z += b1[2] * vv1.z; vo1.w += b1[3] * vv1.w;
+            ho1.x += b1[0] * hh1.x; ho1.y += b1[1] * hh1.y; ho1.z += b1[2] * hh1.z; ho1.w += b1[3] * hh1.w;
           }
         }
         float4* Vw = reinterpret_cast<float4*>(V);
@@ -544,7 +554,7 @@ static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
   if (slot == 0) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int col = 4 * q0 + k;
+      const int col = k < 4 ? 4 * q0 + k : 4 * q1 + (k - 4);
       if (col < 128) red[wib * 128 + col] = (col < ldc) ? dot[k] : 0.0;
     }
   }
