@@ -37,11 +37,12 @@ int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, unsigned pai
 
 /*
  * fsa_selftest_spmm — the FP32 tapered-residual SpMM of the mixed CG loop
- * (V = Sigma_s~ Z + S, H = Z; paper §3.1) in its two forms on the handle's
- * pattern and the FSA_MIXED_BF16X2 operator of theta: the shared-memory tile
- * kernel and the row kernel, on the same seeded block of ncols (1..127)
- * columns.  Both sum each row's products in the same order, so the outputs
- * agree bit for bit.
+ * (V = Sigma_s~ Z + S + beta V, H = Z + beta H; paper §3.1, Appendix A) in
+ * its two forms on the handle's pattern and the FSA_MIXED_BF16X2 operator of
+ * theta: the pipelined shared-memory tile kernel and the row kernel, on the
+ * same seeded block of ncols (1..127) columns, once with beta = 0 and once
+ * with a seeded beta in (0, 1) on seeded V, H.  Both sum each row's products
+ * in the same order, so the outputs agree bit for bit.
  *   max_abs_diff  receives max |tile - row| over V and H
  *   staged_tiles  receives the number of tiles that fit the staging capacity
  *                 (the rest run from global memory); may be NULL
@@ -50,6 +51,26 @@ int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, unsigned pai
  */
 int fsa_selftest_spmm(fsa_handle* h, const fsa_theta* theta, int ncols, uint64_t seed, double* max_abs_diff,
                       int* staged_tiles, int* total_tiles);
+
+/*
+ * fsa_selftest_sddmm — the two sampled dense products of the mixed form in
+ * their tile form (A~ rows staged in shared memory per cell-grid tile) against
+ * their row form (one warp per row, global gathers), on the handle's pattern:
+ *   - the tapered residual values val_ij = (c(s_i,s_j) - a_i.a_j) T(d_ij) and
+ *     D_s (paper §2.1, Eq. eqfitcp) of the operator of theta in precision
+ *     FSA_MIXED_BF16 or FSA_MIXED_BF16X2;
+ *   - the sparse part of the gradient (paper §2.2) on seeded X, Y (ncols
+ *     columns, 1..127) and seeded BF16 B, Q (n x m_pad).
+ *   cap_rows   0: automatic staging capacity; > 0: at most that many staged
+ *              rows per tile (larger tiles take the global-memory path)
+ *   val_err    receives [max |tile - row| / max |row| over the values,
+ *              the same over D_s]
+ *   grad_tile, grad_row  receive the three sums (sigma1^2, rho, nugget parts)
+ * The operator is rebuilt on the handle's next use.  Returns FSA_OK or an
+ * fsa_status.  Runs on the handle's stream.
+ */
+int fsa_selftest_sddmm(fsa_handle* h, const fsa_theta* theta, int precision, int ncols, int cap_rows, uint64_t seed,
+                       double* val_err, double* grad_tile, double* grad_row);
 
 #ifdef __cplusplus
 }

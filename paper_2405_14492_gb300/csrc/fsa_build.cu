@@ -350,7 +350,7 @@ void build_structure(Handle& H, const double* locs_host) {
   neighbour_kernel<false><<<gb, 256, 0, s>>>(H.xs.p, H.ys.p, n, H.xs.p, H.ys.p, H.cell_start.p,
                                              H.cell_count.p, H.grid, g2, counts.p, nullptr, nullptr);
   FSA_CHECK_LAUNCH();
-  H.rowptr.alloc(n + 1);
+  H.rowptr.alloc(n + 2);   // one spare entry: the SpMM copies row pointers in 16-byte units
   exclusive_scan<int64_t>(counts.p, H.rowptr.p, n + 1, s);
   int64_t nnz = 0;
   FSA_CUDA(cudaMemcpyAsync(&nnz, H.rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -370,7 +370,7 @@ void build_structure(Handle& H, const double* locs_host) {
 // run's cells widened by one on each side, in the rows above, at and below
 // (cell side >= gamma), i.e. in three contiguous ranges of the internal order.
 void build_tiles(Handle& H) {
-  constexpr int64_t kTileRows = 40;
+  constexpr int64_t kTileRows = 32;
   const int ncx = H.grid.ncx, ncy = H.grid.ncy;
   const int64_t ncells = (int64_t)ncx * ncy;
   std::vector<int32_t> start(ncells), count(ncells);
@@ -423,7 +423,27 @@ void build_tiles(Handle& H) {
   }
   H.max_tile_rows = mr;
   H.max_tile_nnz = me;
-  H.scol.alloc(std::max<int64_t>(H.nnz, 1));
+  // the pipelined SpMM's record: p0, rows, (begin, length) of the three
+  // ranges, first nonzero (low, high 32 bits), nonzeros, unused
+  FSA_REQUIRE(H.n < ((int64_t)1 << 31), FSA_ERR_ARG, "more than 2^31 - 1 points");
+  std::vector<int32_t> pt((size_t)std::max(H.ntiles, 1) * 12, 0);
+  for (int k = 0; k < H.ntiles; ++k) {
+    const int64_t* d = &t[8 * (size_t)k];
+    int32_t* o = &pt[12 * (size_t)k];
+    const int64_t e0 = rp[d[0]];
+    o[0] = (int32_t)d[0];
+    o[1] = (int32_t)(d[1] - d[0]);
+    for (int r = 0; r < 3; ++r) {
+      o[2 + 2 * r] = (int32_t)d[2 + 2 * r];
+      o[3 + 2 * r] = (int32_t)(d[3 + 2 * r] - d[2 + 2 * r]);
+    }
+    o[8] = (int32_t)(uint32_t)((uint64_t)e0 & 0xffffffffu);
+    o[9] = (int32_t)(e0 >> 32);
+    o[10] = (int32_t)(rp[d[1]] - e0);
+  }
+  H.ptile.alloc(pt.size());
+  FSA_CUDA(cudaMemcpyAsync(H.ptile.p, pt.data(), sizeof(int32_t) * pt.size(), cudaMemcpyHostToDevice, H.stream));
+  H.scol.alloc(H.nnz + 4);   // spare entries: the SpMM copies in 16-byte units
   H.tile_bad.alloc(std::max(H.ntiles, 1));
   FSA_CUDA(cudaMemsetAsync(H.tile_bad.p, 0, sizeof(int32_t) * std::max(H.ntiles, 1), H.stream));
   if (H.ntiles > 0) {

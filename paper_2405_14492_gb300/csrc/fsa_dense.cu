@@ -137,6 +137,87 @@ void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
 }
 
 // ---------------------------------------------------------------------------
+// C (M x N, ld ldc) = A (M x K, ld lda) B (K x N, ld ldb), N <= 128 a multiple
+// of 8, FP64: the tall-times-narrow product of the preconditioner apply
+// (q = M_P^-1 w, N = the CG block width).  A block owns 32 rows and every
+// column (thread: one row, columns tx, tx + 8, ...), so no column tile is
+// padded; the K loop is split so that the grid fills the GPU several times
+// over, and the split partials are summed in a fixed order.
+// ---------------------------------------------------------------------------
+template <int NJ>
+__global__ void __launch_bounds__(256) k_dgemm_tall(int M, int K, const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ B, int64_t ldb, int kchunk,
+                                                    double* __restrict__ out, int64_t ldo, int64_t zstride) {
+  constexpr int N = 8 * NJ;
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][N];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int i0 = blockIdx.x * 32;
+  const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
+  double acc[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) acc[j] = 0.0;
+  for (int k0 = kbeg; k0 < kend; k0 += 32) {
+    for (int t = threadIdx.x; t < 32 * 32; t += 256) {
+      const int r = t >> 5, kk = t & 31;
+      const int gi = i0 + r, gk = k0 + kk;
+      As[r][kk] = (gi < M && gk < kend) ? A[(int64_t)gi * lda + gk] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 32 * N; t += 256) {
+      const int kk = t / N, j = t - kk * N;
+      const int gk = k0 + kk;
+      Bs[kk][j] = gk < kend ? B[(int64_t)gk * ldb + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double a = As[ty][kk];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) acc[j] = fma(a, Bs[kk][tx + 8 * j], acc[j]);
+    }
+    __syncthreads();
+  }
+  const int gi = i0 + ty;
+  if (gi < M) {
+    double* o = out + (int64_t)blockIdx.y * zstride + (int64_t)gi * ldo;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) o[tx + 8 * j] = acc[j];
+  }
+}
+
+void dgemm_tall(Workspace& ws, cudaStream_t s, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return;
+  if (N % 8 != 0 || N > 128 || K <= 0) {
+    dgemm(ws, s, false, false, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, nullptr);
+    return;
+  }
+  const int rt = (M + 31) / 32;
+  int splits = std::max(1, std::min((4 * 152 + rt - 1) / rt, (K + 31) / 32));
+  const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
+  splits = (K + kchunk - 1) / kchunk;
+  double* out = C;
+  int64_t ldo = ldc, zs = 0;
+  if (splits > 1) {
+    out = ws.scratch_f64((size_t)splits * M * N);
+    ldo = N;
+    zs = (int64_t)M * N;
+  }
+  dim3 grid((unsigned)rt, (unsigned)splits);
+  switch (N / 8) {
+#define DT_CASE(J) case J: k_dgemm_tall<J><<<grid, 256, 0, s>>>(M, K, A, lda, B, ldb, kchunk, out, ldo, zs); break;
+    DT_CASE(1) DT_CASE(2) DT_CASE(3) DT_CASE(4) DT_CASE(5) DT_CASE(6) DT_CASE(7) DT_CASE(8)
+    DT_CASE(9) DT_CASE(10) DT_CASE(11) DT_CASE(12) DT_CASE(13) DT_CASE(14) DT_CASE(15) DT_CASE(16)
+#undef DT_CASE
+  }
+  FSA_CHECK_LAUNCH();
+  if (splits > 1) {
+    splitk_reduce_kernel<<<grid_for((int64_t)M * N, 256), 256, 0, s>>>(M, N, splits, out, C, ldc, 1.0, 0.0);
+    FSA_CHECK_LAUNCH();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Cholesky, lower, in place (row-major, ld = lda), blocked right-looking.
 // A pivot <= 0 (or NaN) sets kErrNotPD; the factor then continues with a
 // unit pivot so that the kernels stay finite.

@@ -145,6 +145,7 @@ struct Handle {
   // +-1 in the rows above, at and below).  Per tile 8 int64: p0, p1 (its
   // rows), then [begin, end) of the three ranges.
   DevPtr<int64_t> tiles;
+  DevPtr<int32_t> ptile;                   // per tile 12 int32 for the pipelined SpMM (see build_tiles)
   DevPtr<int32_t> scol;                    // per nonzero: row of its column in the tile's staged ranges
   DevPtr<int32_t> tile_bad;                // 1: a column of the tile lies outside its ranges
   int ntiles = 0;
@@ -178,6 +179,10 @@ void export_csr(Handle& H, int64_t* rowptr_host, int32_t* col_host);
 void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
            int64_t ldc, const double* scale);
+// C = A B for a narrow B (N <= 128 columns, a multiple of 8; else the general
+// form): every column in one block, K split across the GPU
+void dgemm_tall(Workspace& ws, cudaStream_t s, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc);
 void cholesky(double* A, int64_t lda, int m, unsigned* err, cudaStream_t s);
 void trsm_lower(Workspace& ws, const double* L, int64_t ldl, int m, double* B, int64_t ldb, int r,
                 cudaStream_t s);

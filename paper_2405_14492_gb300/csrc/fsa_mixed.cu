@@ -449,6 +449,20 @@ static void launch_grad_sparse_bf16v(Handle& H, int nblocks, int m_pad, int c, i
 #undef GS_CASE
 }
 
+void grad_sparse_rows(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals, const float* X,
+                      const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q,
+                      const fsa_theta& th, double* part) {
+  launch_grad_sparse_bf16v(H, nblocks, m_pad, c, ldc, vals, X, Y, A, B, Q, th, part);
+}
+
+void csr_values_rows(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad) {
+  Operator& op = H.op;
+  k_csr_values_mixed<<<grid_for(H.n * 32, 256, 152 * 64), 256, 0, H.stream>>>(
+      H.n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, A, Alo, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma,
+      op.vals.p, op.vals32.p, op.D.p, op.D32.p, op.Dinv32.p);
+  FSA_CHECK_LAUNCH();
+}
+
 // ---------------------------------------------------------------------------
 // operator build
 // ---------------------------------------------------------------------------
@@ -513,14 +527,11 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   const __nv_bfloat16* Atlo = lo ? op.Atb_lo.p : nullptr;
   // residual values, D
   op.vals.ensure(H.nnz);
-  op.vals32.ensure(H.nnz);
+  op.vals32.ensure(H.nnz + 4);   // spare entries: the SpMM copies in 16-byte units
   op.D.ensure(n);
   op.D32.ensure(n);
   op.Dinv32.ensure(n);
-  k_csr_values_mixed<<<grid_for(n * 32, 256, 152 * 64), 256, 0, s>>>(
-      n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, op.Ab.p, Alo, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma,
-      op.vals.p, op.vals32.p, op.D.p, op.D32.p, op.Dinv32.p);
-  FSA_CHECK_LAUNCH();
+  if (!csr_values_tiles(H, th, op.Ab.p, Alo, m_pad)) csr_values_rows(H, th, op.Ab.p, Alo, m_pad);
   // Woodbury core M = I + A^T D^-1 A on the tensor cores (split-K, FP64 reduction)
   {
     size_t mn = (size_t)m_pad * n_pad;
@@ -668,8 +679,7 @@ static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
   CGState& g = H.cg;
   Operator& op = H.op;
   mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
-  dgemm(H.ws, H.stream, false, false, H.m, C.c, H.m, 1.0, op.Minv.p, H.m, g.w.p, C.ldc, 0.0, g.q.p, C.ldc,
-        nullptr);
+  dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
   mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
 }
 
@@ -836,14 +846,19 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
     int ngpart = 152 * 8;
     gbuf.alloc((size_t)ngpart * 3 + 2);
-    launch_grad_sparse_bf16v(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th,
-                             gbuf.p);
+    int nused = grad_sparse_tiles(H, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th, gbuf.p,
+                                  ngpart);
+    if (nused == 0) {
+      launch_grad_sparse_bf16v(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th,
+                               gbuf.p);
+      nused = ngpart;
+    }
     k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq,
                                              gbuf.p + (size_t)ngpart * 3);
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
-                                gbuf.p, ngpart, gbuf.p + (size_t)ngpart * 3, 1, H.outs.p);
+                                gbuf.p, nused, gbuf.p + (size_t)ngpart * 3, 1, H.outs.p);
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
   } else {

@@ -1,6 +1,7 @@
 // Self-test of the FP32 SpMM of the mixed CG loop (declared in
-// include/fsa_selftest.h): the shared-memory tile kernel against the row
-// kernel on the same handle, operator and seeded block.
+// include/fsa_selftest.h): the pipelined shared-memory tile kernel against the
+// row kernel on the same handle, operator and seeded block, with beta = 0 and
+// with a seeded nonzero beta.
 #include <cstring>
 #include <vector>
 
@@ -17,6 +18,12 @@ static __global__ void k_fill_f32(int64_t n, int cols, int ld, uint64_t key, flo
     if (c < cols) v = (float)(rng_at(key, (uint64_t)t) >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
     out[t] = v;
   }
+}
+
+// beta in (0, 1) for the first cols columns, 0 beyond
+static __global__ void k_fill_beta(int cols, int ld, uint64_t key, double* __restrict__ beta) {
+  for (int c = threadIdx.x; c < ld; c += blockDim.x)
+    beta[c] = c < cols ? ((double)(rng_at(key, (uint64_t)c) >> 11) + 1.0) * 0x1.0p-53 : 0.0;
 }
 
 // max |a - b| of non-negative differences, as ordered bit patterns
@@ -66,6 +73,20 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
     k_max_abs_diff<<<grid_for((int64_t)nc, 256), 256, 0, s>>>((int64_t)nc, V1.p, V2.p, mx.p);
     k_max_abs_diff<<<grid_for((int64_t)nc, 256), 256, 0, s>>>((int64_t)nc, H1.p, H2.p, mx.p);
     FSA_CHECK_LAUNCH();
+    // second pass with a nonzero beta (V = Sigma_s~ Z + S + beta V, H = Z + beta H)
+    // on seeded V, H: both forms start from the same copies
+    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(H.n, ncols, ldc, rng_key(seed, 13), V1.p);
+    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(H.n, ncols, ldc, rng_key(seed, 14), H1.p);
+    k_fill_beta<<<1, 128, 0, s>>>(ncols, ldc, rng_key(seed, 15), beta.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaMemcpyAsync(V2.p, V1.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    FSA_CUDA(cudaMemcpyAsync(H2.p, H1.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    launch_spmm_f32(H, lay, sl, s, H.op.vals32.p, Z.p, S.p, V1.p, H1.p, beta.p, part.p, kStepNone, none);
+    launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, H.op.vals32.p, Z.p, S.p, V2.p, H2.p, beta.p,
+                                    part.p, kStepNone, none);
+    k_max_abs_diff<<<grid_for((int64_t)nc, 256), 256, 0, s>>>((int64_t)nc, V1.p, V2.p, mx.p);
+    k_max_abs_diff<<<grid_for((int64_t)nc, 256), 256, 0, s>>>((int64_t)nc, H1.p, H2.p, mx.p);
+    FSA_CHECK_LAUNCH();
     unsigned long long bits = 0;
     FSA_CUDA(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
     // which tiles fit the staging capacity (the kernel's own test)
@@ -89,6 +110,102 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
     *max_abs_diff = d;
     if (staged_tiles) *staged_tiles = staged;
     if (total_tiles) *total_tiles = H.ntiles;
+    return FSA_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    set_error(e.msg);
+    return e.code;
+  }
+}
+
+namespace fsa {
+
+static __global__ void k_fill_bf16(int64_t total, uint64_t key, __nv_bfloat16* __restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = __float2bfloat16_rn((float)(rng_at(key, (uint64_t)t) >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f);
+}
+
+// max |a - b| and max |b| over FP64 arrays (non-negative doubles as ordered bit patterns)
+static __global__ void k_max_abs_diff_f64(int64_t total, const double* __restrict__ a, const double* __restrict__ b,
+                                          unsigned long long* __restrict__ out) {
+  double mx = 0.0, mb = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double d = fabs(a[t] - b[t]);
+    if (!(d <= mx)) mx = (d != d) ? INFINITY : d;
+    mb = fmax(mb, fabs(b[t]));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+  atomicMax(out + 1, (unsigned long long)__double_as_longlong(mb));
+}
+
+}  // namespace fsa
+
+extern "C" int fsa_selftest_sddmm(fsa_handle* hh, const fsa_theta* theta, int precision, int ncols, int cap_rows,
+                                  uint64_t seed, double* val_err, double* grad_tile, double* grad_row) {
+  if (!hh || !theta || !val_err || !grad_tile || !grad_row || ncols < 1 || ncols > 127 || cap_rows < 0 ||
+      (precision != FSA_MIXED_BF16 && precision != FSA_MIXED_BF16X2)) {
+    set_error("fsa_selftest_sddmm: bad argument");
+    return FSA_ERR_ARG;
+  }
+  Handle& H = hh->h;
+  AllocStreamScope scope(H.stream);
+  try {
+    cudaStream_t s = H.stream;
+    ensure_operator(H, *theta, precision);
+    Operator& op = H.op;
+    const int64_t n = H.n, nnz = H.nnz;
+    const int m_pad = op.m_pad;
+    const __nv_bfloat16* Alo = op.has_lo ? op.Ab_lo.p : nullptr;
+    // residual values and D: tile form (capped staging) against the row form
+    FSA_REQUIRE(csr_values_tiles(H, *theta, op.Ab.p, Alo, m_pad, cap_rows), FSA_ERR_UNSUPPORTED,
+                "tile form unavailable for this handle");
+    DevPtr<double> vt(nnz), Dt(n);
+    FSA_CUDA(cudaMemcpyAsync(vt.p, op.vals.p, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    FSA_CUDA(cudaMemcpyAsync(Dt.p, op.D.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    csr_values_rows(H, *theta, op.Ab.p, Alo, m_pad);
+    op.valid = false;   // the operator now holds the row form's values: rebuilt on next use
+    DevPtr<unsigned long long> mx(4);
+    FSA_CUDA(cudaMemsetAsync(mx.p, 0, 4 * sizeof(unsigned long long), s));
+    k_max_abs_diff_f64<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, vt.p, op.vals.p, mx.p);
+    k_max_abs_diff_f64<<<grid_for(n, 256), 256, 0, s>>>(n, Dt.p, op.D.p, mx.p + 2);
+    FSA_CHECK_LAUNCH();
+    // gradient sparse part on seeded X, Y, B, Q
+    const int ldc = (ncols + 7) / 8 * 8;
+    const size_t nc = (size_t)n * ldc, nm = (size_t)n * m_pad;
+    DevPtr<float> X(nc), Y(nc);
+    DevPtr<__nv_bfloat16> B(nm), Q(nm);
+    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, ncols, ldc, rng_key(seed, 21), X.p);
+    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, ncols, ldc, rng_key(seed, 22), Y.p);
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 23), B.p);
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 24), Q.p);
+    FSA_CHECK_LAUNCH();
+    const int nb = 152 * 8;
+    DevPtr<double> pt((size_t)nb * 3), pr((size_t)nb * 3);
+    const int used = grad_sparse_tiles(H, m_pad, ncols, ldc, op.vals.p, X.p, Y.p, op.Ab.p, B.p, Q.p, *theta, pt.p, nb,
+                                       cap_rows);
+    FSA_REQUIRE(used > 0, FSA_ERR_UNSUPPORTED, "tile form unavailable for this handle");
+    grad_sparse_rows(H, nb, m_pad, ncols, ldc, op.vals.p, X.p, Y.p, op.Ab.p, B.p, Q.p, *theta, pr.p);
+    std::vector<double> ht((size_t)used * 3), hr((size_t)nb * 3);
+    unsigned long long bits[4];
+    FSA_CUDA(cudaMemcpyAsync(ht.data(), pt.p, sizeof(double) * ht.size(), cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaMemcpyAsync(hr.data(), pr.p, sizeof(double) * hr.size(), cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaMemcpyAsync(bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaStreamSynchronize(s));
+    check_err(H);
+    for (int k = 0; k < 3; ++k) {
+      double a = 0.0, b = 0.0;
+      for (int u = 0; u < used; ++u) a += ht[(size_t)u * 3 + k];
+      for (int u = 0; u < nb; ++u) b += hr[(size_t)u * 3 + k];
+      grad_tile[k] = a;
+      grad_row[k] = b;
+    }
+    double d[4];
+    std::memcpy(d, bits, sizeof(d));
+    // max-norm relative differences of the values and of D
+    val_err[0] = d[1] > 0 ? d[0] / d[1] : d[0];
+    val_err[1] = d[3] > 0 ? d[2] / d[3] : d[2];
     return FSA_OK;
   } catch (const Error& e) {
     cudaGetLastError();

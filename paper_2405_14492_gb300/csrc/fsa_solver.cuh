@@ -58,6 +58,21 @@ __global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* _
                               const T* __restrict__ Y, const AT* __restrict__ A, const AT* __restrict__ B,
                               const AT* __restrict__ F, int64_t lda, int cov, double s1, double rho, double nug,
                               double gamma, double* __restrict__ part);
+// tile forms of the mixed residual values and of the gradient's sparse part
+// (shared-memory staging of A~ over the cell-grid tiles); false / 0 when the
+// handle has no tiles or the shapes do not fit, and the caller runs the row
+// form.  cap_rows_max > 0 caps the staged rows per tile (tiles above it run
+// from global memory).  grad_sparse_tiles returns the blocks (partials) written.
+bool csr_values_tiles(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad,
+                      int cap_rows_max = 0);
+int grad_sparse_tiles(Handle& H, int m_pad, int c, int ldc, const double* vals, const float* X, const float* Y,
+                      const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q, const fsa_theta& th,
+                      double* part, int max_blocks, int cap_rows_max = 0);
+// row forms (one warp per row, global gathers) of the same two products
+void csr_values_rows(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad);
+void grad_sparse_rows(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals, const float* X,
+                      const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q,
+                      const fsa_theta& th, double* part);
 __global__ void k_grad_lowrank(int m, int c, int ldc, const double* __restrict__ AX, const double* __restrict__ AY,
                                const double* __restrict__ BX, const double* __restrict__ BY,
                                const double* __restrict__ EAY, double s1, double* __restrict__ out2);

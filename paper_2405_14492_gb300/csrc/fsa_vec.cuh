@@ -388,212 +388,375 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
   finish_scalars(step, part, ldc, c, 0, q, &red[0][0]);
 }
 
-// FP32 form over the cell-grid tiles with shared-memory staging: a block
-// copies its tile's three neighbour ranges of Z (contiguous runs of rows) and
-// the tile's (staged column, value) pairs into shared memory with coalesced
-// loads, then each warp runs its rows from shared memory: per nonzero one
-// broadcast load of the pair, one 16-byte load of the neighbour's columns per
-// lane and four FMAs (lane L owns columns 4L..4L+3).  A tile that exceeds the
-// staging capacity, or holds a column outside its ranges (the cell-grid
-// pattern produces none), runs the row kernel's global gathers instead.
-static __global__ void __launch_bounds__(256, 3) kv_spmm_staged(
-    int ntiles, const int64_t* __restrict__ tiles, const int32_t* __restrict__ tile_bad, int cap_rows, int cap_nnz,
-    int cap_trows, int c, int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-    const int32_t* __restrict__ scol, const float* __restrict__ vals, const float* __restrict__ Z,
-    const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H, const double* __restrict__ beta,
-    double* __restrict__ part, int step, CGScalars q) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+// asynchronous global -> shared copies (cp.async): the copies of a tile are
+// issued without passing through registers and complete as one group
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// mbarrier and bulk-copy (TMA, non-tensor) primitives of the SpMM pipeline;
+// every wait is bounded (kSpSpin polls), after which the caller records
+// kErrTimeout and stops
+constexpr uint32_t kSpSpin = 1u << 26;
+__device__ __forceinline__ uint32_t sp_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void sp_mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sp_smem(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void sp_mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sp_smem(b)) : "memory");
+}
+__device__ __forceinline__ void sp_mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sp_smem(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool sp_mbar_wait(uint64_t* b, uint32_t parity, const unsigned* gerr) {
+  for (uint32_t i = 0; i < kSpSpin; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sp_smem(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 4095u) == 4095u && (*(volatile const unsigned*)gerr & kErrTimeout)) return false;
+  }
+  return false;
+}
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
+__device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sp_smem(dst)),
+               "l"(src), "r"(bytes), "r"(sp_smem(bar))
+               : "memory");
+}
+
+// FP32 form over the cell-grid tiles, warp-specialised: one persistent block
+// per SM runs its tiles (blockIdx.x, + gridDim.x, ...) through a ring of
+// kSpStages shared-memory stages.  The producer lane (last warp) fills a
+// stage with at most six bulk copies (TMA, completion counted in bytes on the
+// stage's full barrier): the tile's three neighbour ranges of Z (contiguous
+// runs of rows), its staged columns and values, and its row pointers (the
+// last three rounded out to 16-byte boundaries; the arrays are padded for
+// it).  The consumer warps wait on the full barrier, compute the tile and
+// release the stage on its empty barrier; no block-wide barrier per tile.
+// Each consumer warp runs R rows at once, L lanes per row (lane owns float4
+// chunks ch and ch + L), per nonzero one broadcast load of the pair and one
+// 16-byte shared load per chunk; the row operands S, V, H of the next tile
+// are loaded into registers while a tile is computed.  Every row sums its
+// products in CSR order, exactly as the row kernel.  A tile that exceeds the
+// stage capacity, or holds a column outside its ranges (the cell-grid pattern
+// produces none), gathers from global memory.
+// Tile record (int32 x 12): p0, rows, then (begin, length) of the three
+// ranges, first nonzero (lo, hi words), nonzeros, unused.
+constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpStages = 3, kTileWords = 12;
+constexpr int kSpMeta = 8;   // per stage: p0, nr, n0, r1b, staged, pair offset, row-pointer offset, unused
+
+struct PipeRow {   // a row's own operands S, V, H (two float4 chunks each)
+  float4 s0, s1, v0, v1, h0, h1;
+};
+
+struct SpStage {   // byte offsets inside one stage
+  int sc, sv, rp, bytes;
+};
+
+static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
+    int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, int cap_rows,
+    int cap_nnz, int cap_trows, SpStage so, int c, int ldc, const int64_t* __restrict__ rowptr,
+    const int32_t* __restrict__ colidx, const int32_t* __restrict__ scol, const float* __restrict__ vals,
+    const float* __restrict__ Z, const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H,
+    const double* __restrict__ beta, double* __restrict__ part, int step, CGScalars q) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t full_bar[kSpStages], empty_bar[kSpStages];
+  __shared__ int smeta[kSpStages][kSpMeta];
+  __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
+  __shared__ int any_b;
+  __shared__ double wdot[kSpConsumers][128];   // per consumer warp: running h^T v partials per column
+  const int tid = threadIdx.x;
   const int c4 = ldc >> 2;
-  float4* zs = reinterpret_cast<float4*>(smraw);                               // cap_rows x c4
-  int2* prs = reinterpret_cast<int2*>(smraw + (size_t)cap_rows * c4 * 16);    // cap_nnz pairs
-  int* ro = reinterpret_cast<int*>(prs + cap_nnz);                             // cap_trows + 1 offsets
-  __shared__ int64_t td[8];
-  __shared__ int bad_sh;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // lane -> (row slot, chunk pair): L lanes per row, R rows per warp step;
-  // the lane owns float4 chunks q0 = ch and q1 = ch + L of its row, so that
-  // the L lanes of a row read L consecutive 16-byte words (no bank conflicts
-  // within a row)
+  const int lane = tid & 31, wib = tid >> 5;
   const int L = (c4 + 1) >> 1, R = 32 / L;
   const int slot = lane / L, ch = lane - (lane / L) * L;
   const bool lane_on = slot < R;
   const int q0 = ch, q1 = ch + L;
   const bool has1 = q1 < c4;
   const float4* Z4 = reinterpret_cast<const float4*>(Z);
-  __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
-  __shared__ int any_b;
+  const float4* S4 = reinterpret_cast<const float4*>(S);
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  const float4* H4 = reinterpret_cast<const float4*>(H);
   float sub[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  double dot[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (threadIdx.x == 0) any_b = 0;
+  for (int x = tid; x < kSpConsumers * 128; x += kSpThreads) (&wdot[0][0])[x] = 0.0;
+  if (tid == 0) {
+    any_b = 0;
+    for (int s = 0; s < kSpStages; ++s) {
+      sp_mbar_init(&full_bar[s], 1);
+      sp_mbar_init(&empty_bar[s], kSpConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   __syncthreads();
-  for (int col = threadIdx.x; col < 136; col += blockDim.x) {
+  for (int col = tid; col < 136; col += kSpThreads) {
     const float bv = col < c ? (float)beta[col] : 0.f;
     bsh[col] = bv;
     if (bv != 0.f) any_b = 1;
   }
   __syncthreads();
   const bool use_b = any_b != 0;
-  int cnt = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    __syncthreads();   // the previous tile's reads of shared memory are done
-    if (threadIdx.x < 8) td[threadIdx.x] = tiles[(int64_t)tile * 8 + threadIdx.x];
-    if (threadIdx.x == 0) bad_sh = tile_bad[tile];
-    __syncthreads();
-    const int64_t p0 = td[0], p1 = td[1];
-    const int64_t e0 = rowptr[p0], e1 = rowptr[p1];
-    const int nr = (int)(p1 - p0), ne = (int)(e1 - e0);
-    const int r0b = (int)td[2], r1b = (int)td[4], r2b = (int)td[6];
-    const int n0 = (int)(td[3] - td[2]), n1 = (int)(td[5] - td[4]), n2 = (int)(td[7] - td[6]);
-    const bool staged = !bad_sh && n0 + n1 + n2 <= cap_rows && ne <= cap_nnz && nr <= cap_trows;
-    if (staged) {
-      const int x0 = n0 * c4, x1 = x0 + n1 * c4, x2 = x1 + n2 * c4;
-      for (int x = threadIdx.x; x < x2; x += blockDim.x) {
-        const int64_t src = x < x0 ? (int64_t)r0b * c4 + x
-                                   : (x < x1 ? (int64_t)r1b * c4 + (x - x0) : (int64_t)r2b * c4 + (x - x1));
-        zs[x] = Z4[src];
-      }
-      for (int x = threadIdx.x; x < ne; x += blockDim.x)
-        prs[x] = make_int2(scol[e0 + x], __float_as_int(vals[e0 + x]));
-      for (int x = threadIdx.x; x <= nr; x += blockDim.x) ro[x] = (int)(rowptr[p0 + x] - e0);
-    }
-    __syncthreads();
-    for (int rbase = wib * R; rbase < nr; rbase += 8 * R) {
-      const int r = rbase + slot;
-      const bool on = lane_on && r < nr;
-      const int64_t i = p0 + r;
-      const int64_t i0 = i * c4;
-      float4 sv0 = make_float4(0.f, 0.f, 0.f, 0.f), sv1 = sv0, zi0 = sv0, zi1 = sv0;
-      if (on) {   // the row's own operand S is loaded up front, in flight with the row's products
-        const float4* S4 = reinterpret_cast<const float4*>(S);
-        sv0 = S4[i0 + q0];
-        if (has1) sv1 = S4[i0 + q1];
-      }
-      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-      if (on) {
+  // this block's tiles: k -> blockIdx.x + k * gridDim.x (gridDim.x <= ntiles)
+  const int nk = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (wib == kSpConsumers) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % kSpStages;
+        const uint32_t ph = (uint32_t)(k / kSpStages) & 1u;
+        if (k >= kSpStages && !sp_mbar_wait(&empty_bar[s], ph ^ 1u, q.err)) {
+          atomicOr(q.err, kErrTimeout);
+          break;
+        }
+        const int64_t t = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+        const int32_t* rec = ptile + t * kTileWords;
+        const int p0 = rec[0], nr = rec[1], r0b = rec[2], n0 = rec[3], r1b = rec[4], n1 = rec[5], r2b = rec[6],
+                  n2 = rec[7], ne = rec[10];
+        const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
+        const int64_t ea = e0 & ~(int64_t)3, eb = (e0 + ne + 3) & ~(int64_t)3;
+        const int64_t pa = (int64_t)p0 & ~(int64_t)1, pb = ((int64_t)p0 + nr + 2) & ~(int64_t)1;
+        const bool staged = !tile_bad[t] && n0 + n1 + n2 <= cap_rows && eb - ea <= cap_nnz + 8 &&
+                            pb - pa <= cap_trows + 4;
+        int* mt = smeta[s];
+        mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0;
+        mt[5] = (int)(e0 - ea); mt[6] = (int)(p0 - pa);
         if (staged) {
-          const int tb = ro[r], te = ro[r + 1];
-          // q1 may run one chunk past the row for odd c4: it reads the next
-          // staged row (in bounds: one spare row is allocated; kept off the output)
-#pragma unroll 4
-          for (int t = tb; t < te; ++t) {
-            const int2 pv = prs[t];
-            const float v = __int_as_float(pv.y);
-            const float4 z0 = zs[pv.x * c4 + q0];
-            const float4 z1 = zs[pv.x * c4 + q1];
-            a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
-            a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
-            a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
-            a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
-          }
-          const int zr = (n0 + (int)(i - r1b)) * c4;
-          zi0 = zs[zr + q0];
-          if (has1) zi1 = zs[zr + q1];
+          unsigned char* sb = smraw + (size_t)s * so.bytes;
+          const uint32_t rb = (uint32_t)ldc * 4u;
+          const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bp = (uint32_t)(eb - ea) * 4u,
+                         br = (uint32_t)(pb - pa) * 8u;
+          sp_mbar_expect_tx(&full_bar[s], bz + 2u * bp + br);
+          if (n0 > 0) sp_bulk_load(sb, Z + (int64_t)r0b * ldc, (uint32_t)n0 * rb, &full_bar[s]);
+          if (n1 > 0) sp_bulk_load(sb + (size_t)n0 * rb, Z + (int64_t)r1b * ldc, (uint32_t)n1 * rb, &full_bar[s]);
+          if (n2 > 0)
+            sp_bulk_load(sb + (size_t)(n0 + n1) * rb, Z + (int64_t)r2b * ldc, (uint32_t)n2 * rb, &full_bar[s]);
+          sp_bulk_load(sb + so.sc, scol + ea, bp, &full_bar[s]);
+          sp_bulk_load(sb + so.sv, vals + ea, bp, &full_bar[s]);
+          sp_bulk_load(sb + so.rp, rowptr + pa, br, &full_bar[s]);
         } else {
-          zi0 = Z4[i0 + q0];
-          if (has1) zi1 = Z4[i0 + q1];
-          const int64_t rb = rowptr[i], re = rowptr[i + 1];
-          for (int64_t t = rb; t < re; ++t) {
-            const int64_t j = colidx[t];
-            const float v = vals[t];
-            const float4 z0 = Z4[j * c4 + q0];
-            const float4 z1 = has1 ? Z4[j * c4 + q1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
-            a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
-            a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
-            a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
-          }
+          sp_mbar_arrive(&full_bar[s]);
         }
-        float4 vo0 = make_float4(a0.x + sv0.x, a0.y + sv0.y, a0.z + sv0.z, a0.w + sv0.w);
-        float4 vo1 = make_float4(a1.x + sv1.x, a1.y + sv1.y, a1.z + sv1.z, a1.w + sv1.w);
-        float4 ho0 = zi0, ho1 = zi1;
-        if (use_b) {
-          const float4* V4 = reinterpret_cast<const float4*>(V);
-          const float4* H4 = reinterpret_cast<const float4*>(H);
-          const float* b = bsh + 4 * q0;
-          const float4 vv0 = V4[i0 + q0], hh0 = H4[i0 + q0];
-          vo0.x += b[0] * vv0.x; vo0.y += b[1] * vv0.y; vo0.z += b[2] * vv0.z; vo0.w += b[3] * vv0.w;
-          ho0.x += b[0] * hh0.x; ho0.y += b[1] * hh0.y; ho0.z += b[2] * hh0.z; ho0.w += b[3] * hh0.w;
-          if (has1) {
-            const float* b1 = bsh + 4 * q1;
-            const float4 vv1 = V4[i0 + q1], hh1 = H4[i0 + q1];
-            vo1.x += b1[0] * vv1.x; vo1.y += b1[1] * vv1.y; vo1.z += b1[2] * vv1.z; vo1.w += b1[3] * vv1.w;
-            ho1.x += b1[0] * hh1.x; ho1.y += b1[1] * hh1.y; ho1.z += b1[2] * hh1.z; ho1.w += b1[3] * hh1.w;
-          }
-        }
-        float4* Vw = reinterpret_cast<float4*>(V);
-        float4* Hw = reinterpret_cast<float4*>(H);
-        Vw[i0 + q0] = vo0;
-        Hw[i0 + q0] = ho0;
-        sub[0] += ho0.x * vo0.x; sub[1] += ho0.y * vo0.y; sub[2] += ho0.z * vo0.z; sub[3] += ho0.w * vo0.w;
+        issued = k + 1;
+      }
+      // no copy may still be in flight when the block exits: wait (bounded)
+      // for the last fill of every stage
+      for (int s = 0; s < kSpStages && s < issued; ++s) {
+        const int klast = s + ((issued - 1 - s) / kSpStages) * kSpStages;
+        if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / kSpStages) & 1u, q.err)) atomicOr(q.err, kErrTimeout);
+      }
+    }
+  } else {
+    // ---------------- consumers ----------------
+    auto load_rows = [&](int p0, int nr, int r, PipeRow& pr) {
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      pr.s0 = pr.s1 = pr.v0 = pr.v1 = pr.h0 = pr.h1 = zero;
+      if (!lane_on || r >= nr) return;
+      const int64_t i0 = (int64_t)(p0 + r) * c4;
+      pr.s0 = S4[i0 + q0];
+      if (has1) pr.s1 = S4[i0 + q1];
+      if (use_b) {
+        pr.v0 = V4[i0 + q0];
+        pr.h0 = H4[i0 + q0];
         if (has1) {
-          Vw[i0 + q1] = vo1;
-          Hw[i0 + q1] = ho1;
-          sub[4] += ho1.x * vo1.x; sub[5] += ho1.y * vo1.y; sub[6] += ho1.z * vo1.z; sub[7] += ho1.w * vo1.w;
+          pr.v1 = V4[i0 + q1];
+          pr.h1 = H4[i0 + q1];
         }
       }
-      if (++cnt == 32) {
+    };
+    auto flush = [&]() {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) { dot[k] += (double)sub[k]; sub[k] = 0.f; }
-        cnt = 0;
+      for (int kk = 0; kk < 8; ++kk) {
+        double v = (double)sub[kk];
+        for (int sl = 1; sl < R; ++sl) {
+          const double o = __shfl_sync(0xffffffffu, v, (ch + sl * L) & 31);
+          if (slot == 0) v += o;
+        }
+        const int col = kk < 4 ? 4 * q0 + kk : 4 * q1 + (kk - 4);
+        if (slot == 0 && col < ldc && col < 128) wdot[wib][col] += v;
+        sub[kk] = 0.f;
+      }
+    };
+    // cur: the first pass's row operands of tile k; nxt: those of tile k + 1
+    PipeRow cur, nxt;
+    const int r_first = wib * R + slot;
+    int p0n = 0, nrn = 0;   // record of tile k + 1
+    {
+      const int32_t* rec0 = ptile + (int64_t)blockIdx.x * kTileWords;
+      load_rows(rec0[0], rec0[1], r_first, cur);
+      if (nk > 1) {
+        const int32_t* rec1 = ptile + ((int64_t)blockIdx.x + gridDim.x) * kTileWords;
+        p0n = rec1[0];
+        nrn = rec1[1];
       }
     }
-  }
-  // fixed-order sum over the warp's row slots (lanes ch, ch + L, ...), then
-  // over the 8 warps in the (now free) staging buffer
-#pragma unroll
-  for (int k = 0; k < 8; ++k) dot[k] += (double)sub[k];
-  for (int sl = 1; sl < R; ++sl) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const double o = __shfl_sync(0xffffffffu, dot[k], (ch + sl * L) & 31);
-      if (slot == 0) dot[k] += o;
+    int cnt = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % kSpStages;
+      // warp-uniform outcome (the flush shuffles need every lane)
+      if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / kSpStages) & 1u, q.err))) {
+        if (lane == 0) atomicOr(q.err, kErrTimeout);
+        break;
+      }
+      load_rows(p0n, k + 1 < nk ? nrn : 0, r_first, nxt);
+      int p0nn = 0, nrnn = 0;
+      if (k + 2 < nk) {
+        const int32_t* rec2 = ptile + ((int64_t)blockIdx.x + (int64_t)(k + 2) * gridDim.x) * kTileWords;
+        p0nn = rec2[0];
+        nrnn = rec2[1];
+      }
+      const int* mt = smeta[s];
+      const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3];
+      const bool staged = mt[4] != 0;
+      const int dsc = mt[5], drp = mt[6];
+      const unsigned char* sb = smraw + (size_t)s * so.bytes;
+      const float4* zs = reinterpret_cast<const float4*>(sb);
+      const int32_t* sc = reinterpret_cast<const int32_t*>(sb + so.sc) + dsc;
+      const float* sv = reinterpret_cast<const float*>(sb + so.sv) + dsc;
+      const int64_t* rp = reinterpret_cast<const int64_t*>(sb + so.rp) + drp;
+      for (int rbase = wib * R, pass = 0; rbase < nr; rbase += kSpConsumers * R, ++pass) {
+        const int r = rbase + slot;
+        const bool on = lane_on && r < nr;
+        const int64_t i = (int64_t)p0 + r;
+        const int64_t i0 = i * c4;
+        if (pass > 0) load_rows(p0, nr, r, cur);   // later passes load their rows directly
+        const PipeRow& pr = cur;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, zi0 = a0, zi1 = a0;
+        if (on) {
+          if (staged) {
+            const int64_t eb = rp[0];
+            const int tb = (int)(rp[r] - eb), te = (int)(rp[r + 1] - eb);
+            // q1 may run one chunk past the row for odd c4: it reads the next
+            // staged row (in bounds: one spare row is allocated; kept off the output)
+#pragma unroll 4
+            for (int t = tb; t < te; ++t) {
+              const float v = sv[t];
+              const int zr = sc[t] * c4;
+              const float4 z0 = zs[zr + q0];
+              const float4 z1 = zs[zr + q1];
+              a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
+              a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
+              a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
+              a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
+            }
+            const int zr = (n0 + (int)(i - r1b)) * c4;
+            zi0 = zs[zr + q0];
+            if (has1) zi1 = zs[zr + q1];
+          } else {
+            zi0 = Z4[i0 + q0];
+            if (has1) zi1 = Z4[i0 + q1];
+            const int64_t rb = rowptr[i], re = rowptr[i + 1];
+            for (int64_t t = rb; t < re; ++t) {
+              const int64_t j = colidx[t];
+              const float v = vals[t];
+              const float4 z0 = Z4[j * c4 + q0];
+              const float4 z1 = has1 ? Z4[j * c4 + q1] : make_float4(0.f, 0.f, 0.f, 0.f);
+              a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
+              a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
+              a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
+              a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
+            }
+          }
+          float4 vo0 = make_float4(a0.x + pr.s0.x, a0.y + pr.s0.y, a0.z + pr.s0.z, a0.w + pr.s0.w);
+          float4 vo1 = make_float4(a1.x + pr.s1.x, a1.y + pr.s1.y, a1.z + pr.s1.z, a1.w + pr.s1.w);
+          float4 ho0 = zi0, ho1 = zi1;
+          if (use_b) {
+            const float* b = bsh + 4 * q0;
+            vo0.x += b[0] * pr.v0.x; vo0.y += b[1] * pr.v0.y; vo0.z += b[2] * pr.v0.z; vo0.w += b[3] * pr.v0.w;
+            ho0.x += b[0] * pr.h0.x; ho0.y += b[1] * pr.h0.y; ho0.z += b[2] * pr.h0.z; ho0.w += b[3] * pr.h0.w;
+            if (has1) {
+              const float* b1 = bsh + 4 * q1;
+              vo1.x += b1[0] * pr.v1.x; vo1.y += b1[1] * pr.v1.y; vo1.z += b1[2] * pr.v1.z; vo1.w += b1[3] * pr.v1.w;
+              ho1.x += b1[0] * pr.h1.x; ho1.y += b1[1] * pr.h1.y; ho1.z += b1[2] * pr.h1.z; ho1.w += b1[3] * pr.h1.w;
+            }
+          }
+          float4* Vw = reinterpret_cast<float4*>(V);
+          float4* Hw = reinterpret_cast<float4*>(H);
+          Vw[i0 + q0] = vo0;
+          Hw[i0 + q0] = ho0;
+          sub[0] += ho0.x * vo0.x; sub[1] += ho0.y * vo0.y; sub[2] += ho0.z * vo0.z; sub[3] += ho0.w * vo0.w;
+          if (has1) {
+            Vw[i0 + q1] = vo1;
+            Hw[i0 + q1] = ho1;
+            sub[4] += ho1.x * vo1.x; sub[5] += ho1.y * vo1.y; sub[6] += ho1.z * vo1.z; sub[7] += ho1.w * vo1.w;
+          }
+        }
+        if (++cnt == 32) {
+          flush();
+          cnt = 0;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) sp_mbar_arrive(&empty_bar[s]);   // this warp is done with stage s
+      cur = nxt;
+      p0n = p0nn;
+      nrn = nrnn;
     }
-  }
-  double* red = reinterpret_cast<double*>(smraw);
-  __syncthreads();
-  if (slot == 0) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int col = k < 4 ? 4 * q0 + k : 4 * q1 + (k - 4);
-      if (col < 128) red[wib * 128 + col] = (col < ldc) ? dot[k] : 0.0;
-    }
+    flush();
   }
   __syncthreads();
-  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
+  for (int col = tid; col < ldc; col += kSpThreads) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w * 128 + col];
+    for (int w = 0; w < kSpConsumers; ++w) t += wdot[w][col];
     part[(int64_t)blockIdx.x * ldc + col] = t;
   }
-  finish_scalars(step, part, ldc, c, 0, q, red);
+  finish_scalars(step, part, ldc, c, 0, q, &wdot[0][0]);
 }
 
-// launch shape of kv_spmm_staged for a block width: staging capacities
-// (rows of Z within kStageBytes, the largest tile's nonzeros and rows) and a
-// one-wave grid
+// launch shape of kv_spmm_tma for a block width: per-stage capacities (the
+// largest tile's rows and nonzeros, rows of Z within what is left of the
+// stage budget) and one block per SM
 struct StagedLaunch {
   int blocks = 0, cap_rows = 0, cap_nnz = 0, cap_trows = 0;
+  SpStage so{};
   size_t smem = 0;
 };
-constexpr size_t kStageBytes = 56 * 1024;
-constexpr size_t kStageMaxSmem = 100 * 1024;
+constexpr size_t kSpSmemMax = 204 * 1024;
 static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
   static const bool attr =
-      cudaFuncSetAttribute(kv_spmm_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageMaxSmem) ==
+      cudaFuncSetAttribute(kv_spmm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmemMax) ==
       cudaSuccess;
   (void)attr;
+  auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
   StagedLaunch L;
-  const int64_t cap = (int64_t)(kStageBytes / ((size_t)ldc * sizeof(float)));
-  L.cap_rows = (int)std::min<int64_t>(cap, std::max<int64_t>(Hd.max_staged, 1));
-  L.cap_nnz = (int)std::min<int64_t>(2048, std::max<int64_t>(Hd.max_tile_nnz, 1));
-  L.cap_trows = (int)std::min<int64_t>(512, std::max<int64_t>(Hd.max_tile_rows, 1));
-  size_t bytes = (size_t)(L.cap_rows + 1) * ldc * sizeof(float) + (size_t)L.cap_nnz * 8 +
-                 (size_t)(L.cap_trows + 1) * 4;
-  L.smem = std::max<size_t>((bytes + 15) / 16 * 16, 8 * 128 * sizeof(double));
+  const size_t budget = kSpSmemMax / kSpStages / 128 * 128;
+  L.cap_trows = (int)std::min<int64_t>(1024, std::max<int64_t>(Hd.max_tile_rows, 1));
+  L.cap_nnz = (int)std::min<int64_t>(4096, std::max<int64_t>(Hd.max_tile_nnz, 1));
+  const size_t fixed = 2 * r16((size_t)(L.cap_nnz + 8) * 4) + r16((size_t)(L.cap_trows + 4) * 8);
+  const size_t row_bytes = (size_t)ldc * sizeof(float);
+  const int64_t fit = budget > fixed + 128 ? (int64_t)((budget - fixed - 128) / row_bytes) - 1 : 0;
+  L.cap_rows = (int)std::max<int64_t>(0, std::min<int64_t>(fit, std::max<int64_t>(Hd.max_staged, 1)));
+  L.so.sc = (int)((((size_t)(L.cap_rows + 1) * row_bytes) + 127) / 128 * 128);
+  L.so.sv = L.so.sc + (int)r16((size_t)(L.cap_nnz + 8) * 4);
+  L.so.rp = L.so.sv + (int)r16((size_t)(L.cap_nnz + 8) * 4);
+  L.so.bytes = (int)(((size_t)L.so.rp + r16((size_t)(L.cap_trows + 4) * 8) + 127) / 128 * 128);
+  L.smem = (size_t)L.so.bytes * kSpStages;
   int dev = 0, sms = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_staged, 256, L.smem);
-  L.blocks = std::max(1, std::min(Hd.ntiles, sms * std::max(per, 1)));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_tma, kSpThreads, L.smem);
+  L.blocks = (L.cap_rows > 0 && L.smem <= kSpSmemMax && per > 0) ? std::min(Hd.ntiles, sms * per) : 0;
   return L;
 }
 
@@ -758,8 +921,8 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
       e1 = profile_event();
       FSA_CUDA(cudaEventRecord(e0, s));
     }
-    kv_spmm_staged<<<std::min(L.blocks, lay.nblk), 256, L.smem, s>>>(
-        Hd.ntiles, Hd.tiles.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, lay.c, lay.ldc, Hd.rowptr.p,
+    kv_spmm_tma<<<std::min(L.blocks, lay.nblk), kSpThreads, L.smem, s>>>(
+        Hd.ntiles, Hd.ptile.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, L.so, lay.c, lay.ldc, Hd.rowptr.p,
         Hd.col.p, Hd.scol.p, vals, Z, S, V, Hv, beta, part, step, q);
     FSA_CHECK_LAUNCH();
     if (prof) {
