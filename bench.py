@@ -237,7 +237,7 @@ def run_gpu(args):
     value = world * args.steps / (elapsed_ms / 1000.0)
     # dominant kernel: the per-iteration tensor-core GEMMs
     prof = {}
-    for tag in ("pcg_Aq", "pcg_AtX", "pcg_spmm", "build", "grad"):
+    for tag in ("pcg_Aq", "pcg_AtX", "pcg_spmm", "pcg_ur", "pcg_z", "pcg_split", "build", "grad"):
         nl, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         if lib.fsa_profile_collect(tag.encode(), ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(by)) == 0:
             prof[tag] = {"launches": nl.value, "ms": ms.value, "bytes": by.value}
@@ -257,7 +257,7 @@ def run_gpu(args):
         if "pcg_spmm" in prof:
             d2 = prof["pcg_spmm"]
             ach = d2["bytes"] / d2["launches"] / (d2["ms"] / d2["launches"] / 1000.0) / 1e9
-            roof["spmm"] = {"kernel": "kv_spmm_staged", "bound": "hbm", "achieved": round(ach, 1),
+            roof["spmm"] = {"kernel": "kv_spmm_tma", "bound": "hbm", "achieved": round(ach, 1),
                             "frac": round(ach / peaks["hbm_gbs"], 4), "alg_bytes_per_launch": d2["bytes"] / d2["launches"],
                             "avg_launch_ms": d2["ms"] / d2["launches"], "launches": d2["launches"],
                             "share_of_step": round(d2["ms"] / elapsed_ms, 4)}

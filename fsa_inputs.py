@@ -143,7 +143,13 @@ PRED_N2E5 = Workload("pred-n2e5-np1e5-m800", n=200_000, m=800, nu=0.5, sigma1_sq
                      nugget=0.05, nnz_per_row=25, num_probes=50, cg_tol=1e-3, seed=BASE_SEED + 4,
                      n_pred=100_000, num_var_samples=100)
 
-WORKLOADS = {w.name: w for w in (SMALL_EXP_N2K, MATERN15_N1E5, EXP_N1E6, PRED_N2E5)}
+# The headline's points, taper and probes with few inducing points: the same
+# SpMM and element-wise CG kernels on a device footprint of a few GB (the
+# profiling case of those kernels).
+EXP_N1E6_M128 = Workload("exp-n1e6-m128", n=1_000_000, m=128, nu=0.5, sigma1_sq=1.0, rho=0.02,
+                         nugget=0.01, nnz_per_row=20, num_probes=64, cg_tol=1e-3, seed=BASE_SEED + 3)
+
+WORKLOADS = {w.name: w for w in (SMALL_EXP_N2K, MATERN15_N1E5, EXP_N1E6, PRED_N2E5, EXP_N1E6_M128)}
 
 
 # ----------------------------------------------------------------------------

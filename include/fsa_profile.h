@@ -14,6 +14,10 @@
  *   "pcg_spmm" per-CG-iteration  V = Sigma_s~ Z + S + beta V, H = Z + beta H
  *              (bytes: 8 per nonzero, the row pointers, Z and S read, V and H
  *              read and written)
+ * and the element-wise kernels of the mixed CG loop:
+ *   "pcg_ur"    U += alpha H, R -= alpha V, |R|^2   (U, R read and written; H, V read)
+ *   "pcg_z"     Z = D^-1 (R - S), r^T z             (R, S read, Z written, D^-1 read)
+ *   "pcg_split" D^-1 R -> BF16 pieces, transposed   (block read, pieces written)
  * Timing adds one event pair per GEMM launch; it is meant for measurement
  * runs.  Not thread-safe across concurrent callers.
  */

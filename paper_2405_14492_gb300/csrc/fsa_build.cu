@@ -370,7 +370,7 @@ void build_structure(Handle& H, const double* locs_host) {
 // run's cells widened by one on each side, in the rows above, at and below
 // (cell side >= gamma), i.e. in three contiguous ranges of the internal order.
 void build_tiles(Handle& H) {
-  constexpr int64_t kTileRows = 32;
+  constexpr int64_t kTileRows = 24;
   const int ncx = H.grid.ncx, ncy = H.grid.ncy;
   const int64_t ncells = (int64_t)ncx * ncy;
   std::vector<int32_t> start(ncells), count(ncells);

@@ -303,7 +303,11 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
       bool deflated = false;
       for (int i = mm - 1; i >= l; --i) {
         double f = s * e[i], b = cs * e[i];
-        r = sqrt(f * f + g * g);
+        // r = |(f, g)| and 1/r from one reciprocal square root (the FP64
+        // divide and square root are long dependent chains on this path)
+        const double hh = f * f + g * g;
+        const double rinv = hh > 0.0 ? rsqrt(hh) : 0.0;
+        r = hh * rinv;
         e[i + 1] = r;
         if (r == 0.0) {   // split: the rotation chain stops early
           d[i + 1] -= p;
@@ -311,7 +315,6 @@ static __global__ void k_slq(int c, int L, const int32_t* __restrict__ iters, co
           deflated = true;
           break;
         }
-        const double rinv = 1.0 / r;
         s = f * rinv;
         cs = g * rinv;
         g = d[i + 1] - p;

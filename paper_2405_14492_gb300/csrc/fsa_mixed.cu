@@ -634,9 +634,13 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   CGState& g = H.cg;
   int ldc = C.ldc;
   size_t smem = (size_t)(kSTRows * (ldc + 1) + kSTRows) * sizeof(float);
-  k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, C.nsplit, src,
-                                                                                    rowscale, C.n_pad, g.Xb.p);
-  FSA_CHECK_LAUNCH();
+  {
+    // FP32 block read once, nsplit BF16 pieces written
+    ProfScope ps("pcg_split", (double)C.n * ldc * (4.0 + 2.0 * C.nsplit), s, tag && tag[0] == 'p');
+    k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, C.nsplit,
+                                                                                      src, rowscale, C.n_pad, g.Xb.p);
+    FSA_CHECK_LAUNCH();
+  }
   TcGemm t;
   t.a[0] = &C.mAt; t.a[1] = &C.mAt_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mX; t.num_b = 1;
@@ -740,14 +744,22 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   const StagedLaunch sl = staged_launch(H, ldc);
   launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
+  const double blk_bytes = (double)n * ldc * sizeof(float);
   for (int it = 0; it < L; ++it) {
-    kv4_ur_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.U32.p, g.R32.p, g.H32.p, g.V32.p,
-                                                         g.alpha.p, g.active.p, g.part.p, kStepResid, it, q);
-    FSA_CHECK_LAUNCH();
+    {
+      ProfScope ps("pcg_ur", 6.0 * blk_bytes, s);   // U, R read and written; H, V read
+      kv4_ur_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.U32.p, g.R32.p, g.H32.p,
+                                                           g.V32.p, g.alpha.p, g.active.p, g.part.p, kStepResid, it,
+                                                           q);
+      FSA_CHECK_LAUNCH();
+    }
     lowrank_mixed(H, C, g.R32.p, g.S32.p);
-    kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
-                                                        g.Z32.p, g.part.p, kStepBeta, it, q);
-    FSA_CHECK_LAUNCH();
+    {
+      ProfScope ps("pcg_z", 3.0 * blk_bytes + 4.0 * n, s);   // R, S read, Z written; D^-1
+      kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
+                                                          g.Z32.p, g.part.p, kStepBeta, it, q);
+      FSA_CHECK_LAUNCH();
+    }
     launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha,
                     q);
     if (o.fixed_iters <= 0 && should_poll(it)) {
@@ -951,6 +963,7 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
     FSA_CUDA(cudaMemsetAsync(Hd.p, 0, nc * sizeof(float), s));
     FSA_CUDA(cudaMemsetAsync(O32.p, 0, nc * sizeof(float), s));
     CGScalars none{};
+    none.err = H.err;   // bounded waits in the SpMM report a timeout here
     launch_spmm_f32(H, lay, staged_launch(H, ldc), s, op.vals32.p, V32.p, S32.p, O32.p, Hd.p, beta.p, part.p,
                     kStepNone, none);
   }

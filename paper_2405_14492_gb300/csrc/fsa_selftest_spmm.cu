@@ -66,6 +66,7 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
     FSA_CUDA(cudaMemsetAsync(beta.p, 0, sizeof(double) * ldc, s));
     FSA_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), s));
     CGScalars none{};
+    none.err = H.err;   // bounded waits in the SpMM report a timeout here
     const StagedLaunch sl = staged_launch(H, ldc);
     launch_spmm_f32(H, lay, sl, s, H.op.vals32.p, Z.p, S.p, V1.p, H1.p, beta.p, part.p, kStepNone, none);
     launch_spmm_fused<float, float>(lay, s, H.rowptr.p, H.col.p, H.op.vals32.p, Z.p, S.p, V2.p, H2.p, beta.p,

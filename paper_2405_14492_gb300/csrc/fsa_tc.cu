@@ -55,6 +55,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -295,6 +299,191 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   }
 }
 
+// Persistent form for problems of many M tiles (one N tile, no split-K): one
+// CTA per SM loops over the M tiles blockIdx.x, + gridDim.x, ...  The TMA
+// producer runs ahead through the stage ring across tile boundaries; the
+// accumulator is double-buffered in TMEM (two column ranges of tmem_cols / 2),
+// so the epilogue of tile j (tcgen05.ld + stores) overlaps the MMAs of tile
+// j + 1.  Barriers: full/empty per stage (as above), acc_full[b] (MMA commit)
+// and acc_empty[b] (one arrival per epilogue warp).  Every wait is bounded.
+__global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_constant__ Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = p.kblocks - p.kb_base;
+  const int S = p.stages;
+  const int ntiles = (p.M + BM - 1) / BM;
+  const int nt = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const uint32_t half = p.tmem_cols / 2;   // columns of one accumulator buffer
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = (*(volatile const unsigned*)p.err & kErrTimeout) ? 1 : 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      int it = 0;
+      for (int j = 0; j < nt && !abort_sh; ++j) {
+        const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * BM;
+        for (int i = 0; i < nk && !abort_sh; ++i, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_sh, p.err)) {
+            atomicOr(p.err, kErrTimeout);
+            abort_sh = 1;
+            break;
+          }
+          uint8_t* st = smem + (size_t)s * p.stage_bytes;
+          mbar_expect_tx(&full_bar[s], p.stage_bytes);
+          const int kb = p.kb_base + i;
+          for (int a = 0; a < p.num_a; ++a)
+            load_operand(st + a * p.a_bytes, &p.ma[a], (p.blk >> a) & 1u, &full_bar[s], kb, m0);
+          for (int b = 0; b < p.num_b; ++b)
+            load_operand(st + p.num_a * p.a_bytes + b * p.b_bytes, &p.mb[b], (p.blk >> (2 + b)) & 1u, &full_bar[s],
+                         kb, 0);
+        }
+      }
+      // drain: every copy issued by this thread has landed before the CTA exits
+      for (int s = 0; s < S && s < it; ++s) {
+        const int last = s + ((it - 1 - s) / S) * S;
+        mbar_wait(&full_bar[s], (uint32_t)(last / S) & 1u, nullptr, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      int it = 0;
+      for (int j = 0; j < nt && !abort_sh; ++j) {
+        const int b = j & 1;
+        // the epilogue has drained this buffer (use j >> 1 of it; fresh buffers pass)
+        if (!mbar_wait(&acc_empty[b], ((uint32_t)(j >> 1) & 1u) ^ 1u, &abort_sh, p.err)) {
+          atomicOr(p.err, kErrTimeout);
+          abort_sh = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t acc = tmem + (uint32_t)b * half;
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!mbar_wait(&full_bar[s], ph, &abort_sh, p.err)) {
+            atomicOr(p.err, kErrTimeout);
+            abort_sh = 1;
+            break;
+          }
+          fence_after();
+          const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
+          int pidx = 0;
+          for (int a = 0; a < p.num_a; ++a) {
+            for (int bb = 0; bb < p.num_b; ++bb) {
+              if (!(p.pairs & (1u << (2 * a + bb)))) continue;
+              const uint64_t da = smem_desc(st + a * p.a_bytes);
+              const uint64_t db = smem_desc(st + p.num_a * p.a_bytes + bb * p.b_bytes);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(acc, da + 2 * kk, db + 2 * kk, p.idesc, (i > 0 || pidx > 0 || kk > 0) ? 1u : 0u);
+              ++pidx;
+            }
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        if (abort_sh) break;
+        mma_commit(&acc_full[b]);
+      }
+      mma_commit(&done_bar);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    for (int j = 0; j < nt; ++j) {
+      const int b = j & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)(j >> 1) & 1u, &abort_sh, p.err));
+      if (!ok) {
+        if (lane == 0) atomicOr(p.err, kErrTimeout);
+        abort_sh = 1;
+        break;
+      }
+      fence_after();
+      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * BM;
+      const int row = m0 + q * 32 + lane;
+      const uint32_t taddr = tmem + (uint32_t)b * half + ((uint32_t)(q * 32) << 16);
+      float* orow = p.out + (int64_t)row * p.ldo;
+      const bool in = row < p.M && nk > 0;
+      if (p.stack <= 1) {
+        for (int c0 = 0; c0 < p.bn; c0 += 8) {
+          uint32_t r[8];
+          tmem_ld8(taddr + c0, r);
+          tmem_wait_ld();
+          if (in) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int col = c0 + jj;
+              if (col < p.n_valid) orow[col] = __uint_as_float(r[jj]);
+            }
+          }
+        }
+      } else {
+        const int h = p.bn / p.stack;
+        for (int c0 = 0; c0 < h; c0 += 8) {
+          uint32_t r[8], t[8], u[8];
+          tmem_ld8(taddr + c0, r);
+          tmem_ld8(taddr + h + c0, t);
+          if (p.stack == 3) tmem_ld8(taddr + 2 * h + c0, u);
+          tmem_wait_ld();
+          if (in) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int col = c0 + jj;
+              float v = __uint_as_float(r[jj]) + __uint_as_float(t[jj]);
+              if (p.stack == 3) v += __uint_as_float(u[jj]);
+              if (col < p.n_valid) orow[col] = v;
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    // the accumulators are released only after every MMA of this CTA has completed
+    mbar_wait(&done_bar, 0, nullptr, nullptr);
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -407,12 +596,26 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   p.split_stride = g.split_stride;
   p.err = err;
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
+  static int sms = 0;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(tc::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc::gemm_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   });
   FSA_REQUIRE(smem <= 200 * 1024, FSA_ERR_ARG, "tc_gemm stage ring too large");
   dim3 grid((g.M + tc::BM - 1) / tc::BM, (g.N + bn - 1) / bn, splits);
+  // many M tiles of one N tile: the persistent form (one CTA per SM, a deeper
+  // stage ring, double-buffered accumulators)
+  const bool persistent = splits == 1 && grid.y == 1 && sms > 0 && (int)grid.x >= 2 * sms && 2 * cols <= 512;
+  if (persistent) {
+    p.tmem_cols = 2 * cols;
+    p.stages = std::max(2, std::min(tc::kMaxStages, (199 * 1024) / (int)p.stage_bytes));
+    smem = std::max<size_t>((size_t)p.stages * p.stage_bytes + 1024, 120 * 1024);   // one CTA per SM (TMEM)
+    grid = dim3((unsigned)sms, 1, 1);
+  }
   const bool prof = g.tag && profile_on();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof) {
@@ -420,7 +623,10 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
     e1 = profile_event();
     FSA_CUDA(cudaEventRecord(e0, s));
   }
-  tc::gemm_kernel<<<grid, tc::kThreads, smem, s>>>(p);
+  if (persistent)
+    tc::gemm_persistent<<<grid, tc::kThreads, smem, s>>>(p);
+  else
+    tc::gemm_kernel<<<grid, tc::kThreads, smem, s>>>(p);
   FSA_CHECK_LAUNCH();
   if (prof) {
     FSA_CUDA(cudaEventRecord(e1, s));

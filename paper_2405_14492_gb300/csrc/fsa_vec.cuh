@@ -433,9 +433,13 @@ __device__ __forceinline__ bool sp_mbar_wait(uint64_t* b, uint32_t parity, const
         : "r"(sp_smem(b)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((i & 4095u) == 4095u && (*(volatile const unsigned*)gerr & kErrTimeout)) return false;
+    if (gerr && (i & 4095u) == 4095u && (*(volatile const unsigned*)gerr & kErrTimeout)) return false;
   }
   return false;
+}
+// records a timed-out wait in the error word (when the launch has one)
+__device__ __forceinline__ void sp_flag(unsigned* err) {
+  if (err) atomicOr(err, kErrTimeout);
 }
 // bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
 __device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -447,31 +451,27 @@ __device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_
 
 // FP32 form over the cell-grid tiles, warp-specialised: one persistent block
 // per SM runs its tiles (blockIdx.x, + gridDim.x, ...) through a ring of
-// kSpStages shared-memory stages.  The producer lane (last warp) fills a
-// stage with at most six bulk copies (TMA, completion counted in bytes on the
-// stage's full barrier): the tile's three neighbour ranges of Z (contiguous
-// runs of rows), its staged columns and values, and its row pointers (the
-// last three rounded out to 16-byte boundaries; the arrays are padded for
-// it).  The consumer warps wait on the full barrier, compute the tile and
-// release the stage on its empty barrier; no block-wide barrier per tile.
-// Each consumer warp runs R rows at once, L lanes per row (lane owns float4
-// chunks ch and ch + L), per nonzero one broadcast load of the pair and one
-// 16-byte shared load per chunk; the row operands S, V, H of the next tile
-// are loaded into registers while a tile is computed.  Every row sums its
-// products in CSR order, exactly as the row kernel.  A tile that exceeds the
-// stage capacity, or holds a column outside its ranges (the cell-grid pattern
-// produces none), gathers from global memory.
+// shared-memory stages.  The producer lane (last warp) fills a stage with
+// bulk copies (TMA, completion counted in bytes on the stage's full
+// barrier): the tile's three neighbour ranges of Z (contiguous runs of rows),
+// its own rows of S, V and H (contiguous; V and H only when some beta is
+// nonzero), its staged columns and values and its row pointers (the last
+// three rounded out to 16-byte boundaries; the arrays are padded for it).
+// The consumer warps wait on the full barrier, compute the tile entirely from
+// shared memory, store V and H, and release the stage on its empty barrier;
+// there is no block-wide barrier per tile.  Each consumer warp runs R rows at
+// once, L lanes per row (lane owns float4 chunks ch and ch + L), per nonzero
+// one broadcast load of the pair and one 16-byte shared load per chunk; every
+// row sums its products in CSR order, exactly as the row kernel.  A tile that
+// exceeds the stage capacity, or holds a column outside its ranges (the
+// cell-grid pattern produces none), gathers from global memory.
 // Tile record (int32 x 12): p0, rows, then (begin, length) of the three
 // ranges, first nonzero (lo, hi words), nonzeros, unused.
-constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpStages = 3, kTileWords = 12;
+constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpMaxStages = 3, kTileWords = 12;
 constexpr int kSpMeta = 8;   // per stage: p0, nr, n0, r1b, staged, pair offset, row-pointer offset, unused
 
-struct PipeRow {   // a row's own operands S, V, H (two float4 chunks each)
-  float4 s0, s1, v0, v1, h0, h1;
-};
-
-struct SpStage {   // byte offsets inside one stage
-  int sc, sv, rp, bytes;
+struct SpStage {   // byte offsets inside one stage, the stage size and the number of stages
+  int s, v, h, sc, sv, rp, bytes, count;
 };
 
 static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
@@ -481,8 +481,8 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     const float* __restrict__ Z, const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H,
     const double* __restrict__ beta, double* __restrict__ part, int step, CGScalars q) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full_bar[kSpStages], empty_bar[kSpStages];
-  __shared__ int smeta[kSpStages][kSpMeta];
+  __shared__ __align__(8) uint64_t full_bar[kSpMaxStages], empty_bar[kSpMaxStages];
+  __shared__ int smeta[kSpMaxStages][kSpMeta];
   __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
   __shared__ int any_b;
   __shared__ double wdot[kSpConsumers][128];   // per consumer warp: running h^T v partials per column
@@ -494,6 +494,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   const bool lane_on = slot < R;
   const int q0 = ch, q1 = ch + L;
   const bool has1 = q1 < c4;
+  const int nst = so.count;
   const float4* Z4 = reinterpret_cast<const float4*>(Z);
   const float4* S4 = reinterpret_cast<const float4*>(S);
   const float4* V4 = reinterpret_cast<const float4*>(V);
@@ -502,7 +503,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   for (int x = tid; x < kSpConsumers * 128; x += kSpThreads) (&wdot[0][0])[x] = 0.0;
   if (tid == 0) {
     any_b = 0;
-    for (int s = 0; s < kSpStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       sp_mbar_init(&full_bar[s], 1);
       sp_mbar_init(&empty_bar[s], kSpConsumers);
     }
@@ -524,10 +525,10 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     if (lane == 0) {
       int issued = 0;
       for (int k = 0; k < nk; ++k) {
-        const int s = k % kSpStages;
-        const uint32_t ph = (uint32_t)(k / kSpStages) & 1u;
-        if (k >= kSpStages && !sp_mbar_wait(&empty_bar[s], ph ^ 1u, q.err)) {
-          atomicOr(q.err, kErrTimeout);
+        const int s = k % nst;
+        const uint32_t ph = (uint32_t)(k / nst) & 1u;
+        if (k >= nst && !sp_mbar_wait(&empty_bar[s], ph ^ 1u, q.err)) {
+          sp_flag(q.err);
           break;
         }
         const int64_t t = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
@@ -537,21 +538,26 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
         const int64_t ea = e0 & ~(int64_t)3, eb = (e0 + ne + 3) & ~(int64_t)3;
         const int64_t pa = (int64_t)p0 & ~(int64_t)1, pb = ((int64_t)p0 + nr + 2) & ~(int64_t)1;
-        const bool staged = !tile_bad[t] && n0 + n1 + n2 <= cap_rows && eb - ea <= cap_nnz + 8 &&
-                            pb - pa <= cap_trows + 4;
+        const bool staged = !tile_bad[t] && n0 + n1 + n2 <= cap_rows && nr <= cap_trows &&
+                            eb - ea <= cap_nnz + 8 && pb - pa <= cap_trows + 4;
         int* mt = smeta[s];
         mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0;
         mt[5] = (int)(e0 - ea); mt[6] = (int)(p0 - pa);
         if (staged) {
           unsigned char* sb = smraw + (size_t)s * so.bytes;
           const uint32_t rb = (uint32_t)ldc * 4u;
-          const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bp = (uint32_t)(eb - ea) * 4u,
-                         br = (uint32_t)(pb - pa) * 8u;
-          sp_mbar_expect_tx(&full_bar[s], bz + 2u * bp + br);
+          const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bo = (uint32_t)nr * rb,
+                         bp = (uint32_t)(eb - ea) * 4u, br = (uint32_t)(pb - pa) * 8u;
+          sp_mbar_expect_tx(&full_bar[s], bz + (use_b ? 3u : 1u) * bo + 2u * bp + br);
           if (n0 > 0) sp_bulk_load(sb, Z + (int64_t)r0b * ldc, (uint32_t)n0 * rb, &full_bar[s]);
           if (n1 > 0) sp_bulk_load(sb + (size_t)n0 * rb, Z + (int64_t)r1b * ldc, (uint32_t)n1 * rb, &full_bar[s]);
           if (n2 > 0)
             sp_bulk_load(sb + (size_t)(n0 + n1) * rb, Z + (int64_t)r2b * ldc, (uint32_t)n2 * rb, &full_bar[s]);
+          sp_bulk_load(sb + so.s, S + (int64_t)p0 * ldc, bo, &full_bar[s]);
+          if (use_b) {
+            sp_bulk_load(sb + so.v, V + (int64_t)p0 * ldc, bo, &full_bar[s]);
+            sp_bulk_load(sb + so.h, H + (int64_t)p0 * ldc, bo, &full_bar[s]);
+          }
           sp_bulk_load(sb + so.sc, scol + ea, bp, &full_bar[s]);
           sp_bulk_load(sb + so.sv, vals + ea, bp, &full_bar[s]);
           sp_bulk_load(sb + so.rp, rowptr + pa, br, &full_bar[s]);
@@ -562,29 +568,13 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
       }
       // no copy may still be in flight when the block exits: wait (bounded)
       // for the last fill of every stage
-      for (int s = 0; s < kSpStages && s < issued; ++s) {
-        const int klast = s + ((issued - 1 - s) / kSpStages) * kSpStages;
-        if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / kSpStages) & 1u, q.err)) atomicOr(q.err, kErrTimeout);
+      for (int s = 0; s < nst && s < issued; ++s) {
+        const int klast = s + ((issued - 1 - s) / nst) * nst;
+        if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / nst) & 1u, q.err)) sp_flag(q.err);
       }
     }
   } else {
     // ---------------- consumers ----------------
-    auto load_rows = [&](int p0, int nr, int r, PipeRow& pr) {
-      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-      pr.s0 = pr.s1 = pr.v0 = pr.v1 = pr.h0 = pr.h1 = zero;
-      if (!lane_on || r >= nr) return;
-      const int64_t i0 = (int64_t)(p0 + r) * c4;
-      pr.s0 = S4[i0 + q0];
-      if (has1) pr.s1 = S4[i0 + q1];
-      if (use_b) {
-        pr.v0 = V4[i0 + q0];
-        pr.h0 = H4[i0 + q0];
-        if (has1) {
-          pr.v1 = V4[i0 + q1];
-          pr.h1 = H4[i0 + q1];
-        }
-      }
-    };
     auto flush = [&]() {
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
@@ -598,33 +588,13 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         sub[kk] = 0.f;
       }
     };
-    // cur: the first pass's row operands of tile k; nxt: those of tile k + 1
-    PipeRow cur, nxt;
-    const int r_first = wib * R + slot;
-    int p0n = 0, nrn = 0;   // record of tile k + 1
-    {
-      const int32_t* rec0 = ptile + (int64_t)blockIdx.x * kTileWords;
-      load_rows(rec0[0], rec0[1], r_first, cur);
-      if (nk > 1) {
-        const int32_t* rec1 = ptile + ((int64_t)blockIdx.x + gridDim.x) * kTileWords;
-        p0n = rec1[0];
-        nrn = rec1[1];
-      }
-    }
     int cnt = 0;
     for (int k = 0; k < nk; ++k) {
-      const int s = k % kSpStages;
+      const int s = k % nst;
       // warp-uniform outcome (the flush shuffles need every lane)
-      if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / kSpStages) & 1u, q.err))) {
-        if (lane == 0) atomicOr(q.err, kErrTimeout);
+      if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / nst) & 1u, q.err))) {
+        if (lane == 0) sp_flag(q.err);
         break;
-      }
-      load_rows(p0n, k + 1 < nk ? nrn : 0, r_first, nxt);
-      int p0nn = 0, nrnn = 0;
-      if (k + 2 < nk) {
-        const int32_t* rec2 = ptile + ((int64_t)blockIdx.x + (int64_t)(k + 2) * gridDim.x) * kTileWords;
-        p0nn = rec2[0];
-        nrnn = rec2[1];
       }
       const int* mt = smeta[s];
       const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3];
@@ -632,18 +602,20 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
       const int dsc = mt[5], drp = mt[6];
       const unsigned char* sb = smraw + (size_t)s * so.bytes;
       const float4* zs = reinterpret_cast<const float4*>(sb);
+      const float4* ss = reinterpret_cast<const float4*>(sb + so.s);
+      const float4* vs = reinterpret_cast<const float4*>(sb + so.v);
+      const float4* hs = reinterpret_cast<const float4*>(sb + so.h);
       const int32_t* sc = reinterpret_cast<const int32_t*>(sb + so.sc) + dsc;
       const float* sv = reinterpret_cast<const float*>(sb + so.sv) + dsc;
       const int64_t* rp = reinterpret_cast<const int64_t*>(sb + so.rp) + drp;
-      for (int rbase = wib * R, pass = 0; rbase < nr; rbase += kSpConsumers * R, ++pass) {
+      for (int rbase = wib * R; rbase < nr; rbase += kSpConsumers * R) {
         const int r = rbase + slot;
         const bool on = lane_on && r < nr;
         const int64_t i = (int64_t)p0 + r;
         const int64_t i0 = i * c4;
-        if (pass > 0) load_rows(p0, nr, r, cur);   // later passes load their rows directly
-        const PipeRow& pr = cur;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, zi0 = a0, zi1 = a0;
         if (on) {
+          float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, zi0 = a0, zi1 = a0;
+          float4 s0 = a0, s1 = a0, v0 = a0, v1 = a0, h0 = a0, h1 = a0;
           if (staged) {
             const int64_t eb = rp[0];
             const int tb = (int)(rp[r] - eb), te = (int)(rp[r + 1] - eb);
@@ -662,10 +634,22 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
             }
             const int zr = (n0 + (int)(i - r1b)) * c4;
             zi0 = zs[zr + q0];
-            if (has1) zi1 = zs[zr + q1];
+            s0 = ss[r * c4 + q0];
+            if (use_b) { v0 = vs[r * c4 + q0]; h0 = hs[r * c4 + q0]; }
+            if (has1) {
+              zi1 = zs[zr + q1];
+              s1 = ss[r * c4 + q1];
+              if (use_b) { v1 = vs[r * c4 + q1]; h1 = hs[r * c4 + q1]; }
+            }
           } else {
             zi0 = Z4[i0 + q0];
-            if (has1) zi1 = Z4[i0 + q1];
+            s0 = S4[i0 + q0];
+            if (use_b) { v0 = V4[i0 + q0]; h0 = H4[i0 + q0]; }
+            if (has1) {
+              zi1 = Z4[i0 + q1];
+              s1 = S4[i0 + q1];
+              if (use_b) { v1 = V4[i0 + q1]; h1 = H4[i0 + q1]; }
+            }
             const int64_t rb = rowptr[i], re = rowptr[i + 1];
             for (int64_t t = rb; t < re; ++t) {
               const int64_t j = colidx[t];
@@ -678,17 +662,17 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
               a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
             }
           }
-          float4 vo0 = make_float4(a0.x + pr.s0.x, a0.y + pr.s0.y, a0.z + pr.s0.z, a0.w + pr.s0.w);
-          float4 vo1 = make_float4(a1.x + pr.s1.x, a1.y + pr.s1.y, a1.z + pr.s1.z, a1.w + pr.s1.w);
+          float4 vo0 = make_float4(a0.x + s0.x, a0.y + s0.y, a0.z + s0.z, a0.w + s0.w);
+          float4 vo1 = make_float4(a1.x + s1.x, a1.y + s1.y, a1.z + s1.z, a1.w + s1.w);
           float4 ho0 = zi0, ho1 = zi1;
           if (use_b) {
             const float* b = bsh + 4 * q0;
-            vo0.x += b[0] * pr.v0.x; vo0.y += b[1] * pr.v0.y; vo0.z += b[2] * pr.v0.z; vo0.w += b[3] * pr.v0.w;
-            ho0.x += b[0] * pr.h0.x; ho0.y += b[1] * pr.h0.y; ho0.z += b[2] * pr.h0.z; ho0.w += b[3] * pr.h0.w;
+            vo0.x += b[0] * v0.x; vo0.y += b[1] * v0.y; vo0.z += b[2] * v0.z; vo0.w += b[3] * v0.w;
+            ho0.x += b[0] * h0.x; ho0.y += b[1] * h0.y; ho0.z += b[2] * h0.z; ho0.w += b[3] * h0.w;
             if (has1) {
               const float* b1 = bsh + 4 * q1;
-              vo1.x += b1[0] * pr.v1.x; vo1.y += b1[1] * pr.v1.y; vo1.z += b1[2] * pr.v1.z; vo1.w += b1[3] * pr.v1.w;
-              ho1.x += b1[0] * pr.h1.x; ho1.y += b1[1] * pr.h1.y; ho1.z += b1[2] * pr.h1.z; ho1.w += b1[3] * pr.h1.w;
+              vo1.x += b1[0] * v1.x; vo1.y += b1[1] * v1.y; vo1.z += b1[2] * v1.z; vo1.w += b1[3] * v1.w;
+              ho1.x += b1[0] * h1.x; ho1.y += b1[1] * h1.y; ho1.z += b1[2] * h1.z; ho1.w += b1[3] * h1.w;
             }
           }
           float4* Vw = reinterpret_cast<float4*>(V);
@@ -709,9 +693,6 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
       }
       __syncwarp();
       if (lane == 0) sp_mbar_arrive(&empty_bar[s]);   // this warp is done with stage s
-      cur = nxt;
-      p0n = p0nn;
-      nrn = nrnn;
     }
     flush();
   }
@@ -725,8 +706,9 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
 }
 
 // launch shape of kv_spmm_tma for a block width: per-stage capacities (the
-// largest tile's rows and nonzeros, rows of Z within what is left of the
-// stage budget) and one block per SM
+// largest tile's rows and nonzeros up to 48 rows and 40 nonzeros per row;
+// rows of Z within what is left of the budget), three stages when they fit
+// the budget, else two, one block per SM
 struct StagedLaunch {
   int blocks = 0, cap_rows = 0, cap_nnz = 0, cap_trows = 0;
   SpStage so{};
@@ -739,19 +721,32 @@ static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
       cudaSuccess;
   (void)attr;
   auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
+  auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
   StagedLaunch L;
-  const size_t budget = kSpSmemMax / kSpStages / 128 * 128;
-  L.cap_trows = (int)std::min<int64_t>(1024, std::max<int64_t>(Hd.max_tile_rows, 1));
-  L.cap_nnz = (int)std::min<int64_t>(4096, std::max<int64_t>(Hd.max_tile_nnz, 1));
-  const size_t fixed = 2 * r16((size_t)(L.cap_nnz + 8) * 4) + r16((size_t)(L.cap_trows + 4) * 8);
+  // a tile beyond these capacities (a dense cluster of points) runs from global
+  // memory; the tiles of evenly spread points stay within them
+  L.cap_trows = (int)std::min<int64_t>(48, std::max<int64_t>(Hd.max_tile_rows, 1));
+  L.cap_nnz = (int)std::min<int64_t>((int64_t)L.cap_trows * 40, std::max<int64_t>(Hd.max_tile_nnz, 1));
   const size_t row_bytes = (size_t)ldc * sizeof(float);
-  const int64_t fit = budget > fixed + 128 ? (int64_t)((budget - fixed - 128) / row_bytes) - 1 : 0;
-  L.cap_rows = (int)std::max<int64_t>(0, std::min<int64_t>(fit, std::max<int64_t>(Hd.max_staged, 1)));
-  L.so.sc = (int)((((size_t)(L.cap_rows + 1) * row_bytes) + 127) / 128 * 128);
-  L.so.sv = L.so.sc + (int)r16((size_t)(L.cap_nnz + 8) * 4);
-  L.so.rp = L.so.sv + (int)r16((size_t)(L.cap_nnz + 8) * 4);
-  L.so.bytes = (int)(((size_t)L.so.rp + r16((size_t)(L.cap_trows + 4) * 8) + 127) / 128 * 128);
-  L.smem = (size_t)L.so.bytes * kSpStages;
+  const size_t fixed = 3 * (size_t)L.cap_trows * row_bytes + 2 * r16((size_t)(L.cap_nnz + 8) * 4) +
+                       r16((size_t)(L.cap_trows + 4) * 8) + 256;
+  const int64_t want = std::max<int64_t>(Hd.max_staged, 1);
+  for (int nst = kSpMaxStages; nst >= 2; --nst) {
+    const size_t budget = kSpSmemMax / nst / 128 * 128;
+    const int64_t fit = budget > fixed ? (int64_t)((budget - fixed) / row_bytes) - 1 : 0;
+    L.cap_rows = (int)std::max<int64_t>(0, std::min<int64_t>(fit, want));
+    L.so.count = nst;
+    if (L.cap_rows >= want) break;
+  }
+  size_t off = r128((size_t)(L.cap_rows + 1) * row_bytes);
+  L.so.s = (int)off; off += (size_t)L.cap_trows * row_bytes;
+  L.so.v = (int)off; off += (size_t)L.cap_trows * row_bytes;
+  L.so.h = (int)off; off += (size_t)L.cap_trows * row_bytes;
+  L.so.sc = (int)r16(off); off = L.so.sc + r16((size_t)(L.cap_nnz + 8) * 4);
+  L.so.sv = (int)off; off += r16((size_t)(L.cap_nnz + 8) * 4);
+  L.so.rp = (int)off; off += r16((size_t)(L.cap_trows + 4) * 8);
+  L.so.bytes = (int)r128(off);
+  L.smem = (size_t)L.so.bytes * L.so.count;
   int dev = 0, sms = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -850,6 +845,28 @@ static __global__ void kv4_z_update(int64_t n, int c, int ldc, int rpb, const fl
   vec4_block_partials(acc, ldc, c4, rpb, red4, part);
   finish_scalars(step, part, ldc, c, l, q, red4);
 }
+
+// CUDA-event timing of one launch under the profiling hooks (fsa_profile.h):
+// records the tag's algorithmic bytes with the launch's device time
+struct ProfScope {
+  const char* tag;
+  double bytes;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(const char* t, double b, cudaStream_t st, bool want = true) : tag(t), bytes(b), s(st) {
+    if (want && profile_on()) {
+      e0 = profile_event();
+      e1 = profile_event();
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~ProfScope() {
+    if (e0) {
+      cudaEventRecord(e1, s);
+      profile_record(tag, e0, e1, bytes);
+    }
+  }
+};
 
 struct Vec4Launch {
   int blocks, threads, rpb;

@@ -44,6 +44,9 @@ def _selftest(M, N, K, na, nb, pairs, halves, splits, seed=1):
     (4096, 48, 1024, 1, 1, 1, 1, 1),       # many M tiles (the A q shape)
     (1024, 240, 20000, 2, 1, 5, 3, 38),    # A hi/lo with a three-piece stacked vector (the A^T X shape)
     (3000, 240, 1024, 2, 1, 5, 3, 1),      # same for the A q shape, ragged M
+    (50000, 144, 1024, 2, 1, 5, 2, 1),     # persistent form (>= 2 tiles per SM): A q with A hi/lo, ragged M
+    (40000, 256, 128, 1, 1, 1, 0, 1),      # persistent form, full 256-column tile, two K blocks
+    (39001, 48, 64, 1, 1, 1, 1, 1),        # persistent form, one K block per tile
 ])
 def test_tc_gemm_selftest(F, M, N, K, na, nb, pairs, halves, splits):
     st, err, act = _selftest(M, N, K, na, nb, pairs, halves, splits)
