@@ -99,6 +99,7 @@ struct Operator {
   DevPtr<__nv_bfloat16> Ab_lo, Atb_lo;   // low halves (FSA_MIXED_BF16X2): A = Ab + Ab_lo
   bool has_lo = false;
   DevPtr<float> vals32;
+  DevPtr<int2> pairs32;   // per nonzero (staged column in its SpMM tile, FP32 value bits)
   DevPtr<float> D32, Dinv32;
   int m_pad = 0;
   int64_t n_pad = 0;
@@ -137,6 +138,7 @@ struct Handle {
   cudaStream_t stream = nullptr;
   Grid grid;
   DevPtr<double> xs, ys, ind_x, ind_y;     // internal-order coordinates; inducing points
+  DevPtr<float4> xy32, ixy32;              // the same as FP32 hi/lo pairs (x_hi, x_lo, y_hi, y_lo)
   DevPtr<int64_t> perm, iperm, rowptr;     // perm[internal] = original
   DevPtr<int32_t> col, cell_start, cell_count;
   int64_t nnz = 0;

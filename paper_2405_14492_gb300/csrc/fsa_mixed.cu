@@ -31,31 +31,60 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// Sigma_nm (or its rho-derivative) in FP32, split hi/lo BF16, n x m_pad (zero padded)
-__global__ void k_cov_nm_split(int64_t n, int m, int m_pad, const double* __restrict__ xs,
-                               const double* __restrict__ ys, const double* __restrict__ ix,
-                               const double* __restrict__ iy, int cov, float s1, float rho, int deriv,
+// coordinates as FP32 hi/lo pairs: x = x_hi + x_lo to ~2^-48 relative
+__global__ void k_coord_split(int64_t n, const double* __restrict__ xs, const double* __restrict__ ys,
+                              float4* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float xh = (float)xs[i], yh = (float)ys[i];
+    out[i] = make_float4(xh, (float)(xs[i] - (double)xh), yh, (float)(ys[i] - (double)yh));
+  }
+}
+
+// Sigma_nm (or its rho-derivative) in FP32, split hi/lo BF16, n x m_pad (zero
+// padded).  Thread = one inducing point k (its coordinates in registers),
+// looping over rows; the coordinate differences come from the FP32 hi/lo
+// pairs, (x_hi,i - x_hi,k) + (x_lo,i - x_lo,k), each within a rounding of
+// the exact difference, so no FP64 arithmetic is needed per element.
+__global__ void k_cov_nm_split(int64_t n, int m, int m_pad, const float4* __restrict__ pxy,
+                               const float4* __restrict__ ixy, int cov, float s1, float rho, int deriv,
                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  int64_t total = n * m_pad;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t / m_pad;
-    int k = (int)(t - i * m_pad);
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= m_pad) return;
+  const float4 q = k < m ? ixy[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float irho = 1.0f / rho;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     float v = 0.f;
     if (k < m) {
-      float dx = (float)(xs[i] - ix[k]), dy = (float)(ys[i] - iy[k]);
-      float d = sqrtf(dx * dx + dy * dy);
+      const float4 p = pxy[i];
+      const float dx = (p.x - q.x) + (p.y - q.y), dy = (p.z - q.z) + (p.w - q.w);
+      const float d = sqrtf(dx * dx + dy * dy);
       if (cov == 0) {
-        float e = expf(-d / rho);
-        v = deriv ? s1 * (d / (rho * rho)) * e : s1 * e;
+        const float e = expf(-d * irho);
+        v = deriv ? s1 * (d * irho * irho) * e : s1 * e;
       } else {
-        float x = 1.7320508f * d / rho;
-        float e = expf(-x);
-        v = deriv ? s1 * (x * x / rho) * e : s1 * (1.f + x) * e;
+        const float x = 1.7320508f * d * irho;
+        const float e = expf(-x);
+        v = deriv ? s1 * (x * x * irho) * e : s1 * (1.f + x) * e;
       }
     }
-    split_bf16(v, hi[t], lo[t]);
+    split_bf16(v, hi[i * m_pad + k], lo[i * m_pad + k]);
   }
+}
+
+static void cov_nm_split(Handle& H, int m_pad, const fsa_theta& th, int deriv, __nv_bfloat16* hi,
+                         __nv_bfloat16* lo) {
+  cudaStream_t s = H.stream;
+  if (!H.xy32.p || H.xy32.n < (size_t)H.n) {
+    H.xy32.alloc(H.n);
+    H.ixy32.alloc(H.m);
+    k_coord_split<<<grid_for(H.n, 256), 256, 0, s>>>(H.n, H.xs.p, H.ys.p, H.xy32.p);
+    k_coord_split<<<grid_for(H.m, 256), 256, 0, s>>>(H.m, H.ind_x.p, H.ind_y.p, H.ixy32.p);
+    FSA_CHECK_LAUNCH();
+  }
+  dim3 grid((unsigned)std::min<int64_t>(H.n, 152 * 16), (unsigned)((m_pad + 255) / 256));
+  k_cov_nm_split<<<grid, 256, 0, s>>>(H.n, H.m, m_pad, H.xy32.p, H.ixy32.p, H.cov, (float)th.sigma1_sq,
+                                      (float)th.rho, deriv, hi, lo);
+  FSA_CHECK_LAUNCH();
 }
 
 // FP64 rows x cols (ld) -> BF16 hi/lo rows_pad x cols_pad (zero padded)
@@ -321,6 +350,13 @@ __global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kin
   }
 }
 
+// pairs[t] = (scol[t], bits of vals32[t])
+__global__ void k_pack_pairs(int64_t nnz, const int32_t* __restrict__ scol, const float* __restrict__ vals32,
+                             int2* __restrict__ pairs) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+    pairs[t] = make_int2(scol[t], __float_as_int(vals32[t]));
+}
+
 // dst = bf16(a - b)
 __global__ void k_sub_to_bf16(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
                               __nv_bfloat16* __restrict__ dst) {
@@ -485,10 +521,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   {
     DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
     DevPtr<float> A32(nm);
-    k_cov_nm_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>(n, m, m_pad, H.xs.p, H.ys.p, H.ind_x.p, H.ind_y.p,
-                                                                H.cov, (float)th.sigma1_sq, (float)th.rho, 0,
-                                                                Khi.p, Klo.p);
-    FSA_CHECK_LAUNCH();
+    cov_nm_split(H, m_pad, th, 0, Khi.p, Klo.p);
     k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
                                                                        Llo.p);
     FSA_CHECK_LAUNCH();
@@ -532,6 +565,10 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   op.D32.ensure(n);
   op.Dinv32.ensure(n);
   if (!csr_values_tiles(H, th, op.Ab.p, Alo, m_pad)) csr_values_rows(H, th, op.Ab.p, Alo, m_pad);
+  // the SpMM's (staged column, value) pairs, read by one bulk copy per tile
+  op.pairs32.ensure(H.nnz + 2);   // spare entries: the SpMM copies in 16-byte units
+  k_pack_pairs<<<grid_for(H.nnz, 256), 256, 0, s>>>(H.nnz, H.scol.p, op.vals32.p, op.pairs32.p);
+  FSA_CHECK_LAUNCH();
   // Woodbury core M = I + A^T D^-1 A on the tensor cores (split-K, FP64 reduction)
   {
     size_t mn = (size_t)m_pad * n_pad;
@@ -659,8 +696,21 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   FSA_CHECK_LAUNCH();
 }
 
-// S (FP32 n x ldc) = A~ q, q FP64 m x ldc
-static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag) {
+// the CG's preconditioner step fused into the epilogue of S = A~ q:
+// Z = D^-1 (R - S) and r^T z with the scalar step
+struct ZFuse {
+  const float* R;
+  const float* Dinv;
+  float* Z;
+  int c, l, step;
+  double* part;
+  CGScalars q;
+};
+
+// S (FP32 n x ldc) = A~ q, q FP64 m x ldc; with zf, also the fused step when
+// the launch takes the persistent form (returns whether it did)
+static bool mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag,
+                     const ZFuse* zf = nullptr) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
@@ -675,16 +725,26 @@ static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const ch
   t.out = S; t.ldo = ldc;
   t.tag = tag;
   t.alg_bytes = t.num_a * (double)C.n * H.m * 2.0 + (double)C.nsplit * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
+  int fused = 0;
+  if (zf) {
+    t.zR = zf->R; t.zDinv = zf->Dinv; t.zZ = zf->Z;
+    t.z_c = zf->c; t.z_l = zf->l; t.z_step = zf->step; t.z_part = zf->part; t.z_q = zf->q;
+    t.z_fused = &fused;
+    // the fused form also reads R and D^-1 and writes Z (one block each)
+    t.alg_bytes += 2.0 * (double)C.n * C.ldc * 4.0 + (double)C.n * 4.0;
+  }
   tc_gemm(t, H.err, s);
+  return fused != 0;
 }
 
-// S = A~ M^-1 A~^T (D^-1 R)
-static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
+// S = A~ M^-1 A~^T (D^-1 R); with zf, also Z = D^-1 (R - S) and its scalar
+// step when the last product takes the persistent form (returns whether it did)
+static bool lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S, const ZFuse* zf = nullptr) {
   CGState& g = H.cg;
   Operator& op = H.op;
   mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
   dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
-  mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
+  return mixed_Aq(H, C, g.q.p, S, "pcg_Aq", zf);
 }
 
 LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
@@ -708,7 +768,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
   C.wpart = wpart_buf.p;
   FSA_REQUIRE(ldc % 4 == 0 && ldc <= 128, FSA_ERR_UNSUPPORTED, "mixed block width must be a multiple of 4, at most 128");
-  const Vec4Launch v4 = vec4_launch(lay);
+  const Vec4Launch v4 = vec4_launch(lay, reinterpret_cast<const void*>(kv4_ur_update));
+  const Vec4Launch v4z = vec4_launch(lay, reinterpret_cast<const void*>(kv4_z_update));
   // probes: R = [y, A~ eps1 + D^1/2 eps2]
   {
     int l16 = round_up(l, 16);
@@ -737,7 +798,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
   CGScalars q = make_scalars(H, o, L);
   lowrank_mixed(H, C, g.R32.p, g.S32.p);
-  kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+  kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
                                                       g.part.p, kStepInit, 0, q);
   FSA_CHECK_LAUNCH();
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -753,10 +814,10 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
                                                            q);
       FSA_CHECK_LAUNCH();
     }
-    lowrank_mixed(H, C, g.R32.p, g.S32.p);
-    {
+    const ZFuse zf{g.R32.p, op.Dinv32.p, g.Z32.p, lay.c, it, kStepBeta, g.part.p, q};
+    if (!lowrank_mixed(H, C, g.R32.p, g.S32.p, &zf)) {
       ProfScope ps("pcg_z", 3.0 * blk_bytes + 4.0 * n, s);   // R, S read, Z written; D^-1
-      kv4_z_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
+      kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
                                                           g.Z32.p, g.part.p, kStepBeta, it, q);
       FSA_CHECK_LAUNCH();
     }
@@ -801,10 +862,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       // B = dK L^-T (split products), and B^T for the m-space projections
       DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
       DevPtr<float> B32(nm);
-      k_cov_nm_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>(n, m, m_pad, H.xs.p, H.ys.p, H.ind_x.p, H.ind_y.p,
-                                                                  H.cov, (float)th.sigma1_sq, (float)th.rho, 1,
-                                                                  Khi.p, Klo.p);
-      FSA_CHECK_LAUNCH();
+      cov_nm_split(H, m_pad, th, 1, Khi.p, Klo.p);
       k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
                                                                          Llo.p);
       FSA_CHECK_LAUNCH();

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "fsa_internal.cuh"
+#include "fsa_scalars.cuh"
 #include "fsa_solver.cuh"
 #include "fsa_tc.cuh"
 
@@ -24,116 +25,6 @@ namespace fsa {
 
 template <typename T> struct VAcc { using type = double; };
 template <> struct VAcc<float> { using type = float; };
-
-// ---------------------------------------------------------------------------
-// CG scalars fused into the producing kernels (Appendix A).  The last block
-// to finish (ticket counter) sums the per-block partials of every column in
-// a fixed order and applies the per-column scalar step, so results do not
-// depend on which block finishes last.
-// ---------------------------------------------------------------------------
-struct CGScalars {
-  double *rho, *rz0, *alpha, *beta, *alpha_prev, *beta_prev, *rnorm, *tdiag, *toff;
-  int32_t *active, *iters, *stop, *num_active;
-  unsigned* err;
-  unsigned* ticket;
-  double tol;
-  int fixed, L;
-};
-
-enum ScalarStep : int { kStepNone = 0, kStepInit = 1, kStepAlpha = 2, kStepResid = 3, kStepBeta = 4 };
-
-__device__ __forceinline__ void scalar_step(int step, int col, int c, double v, int l, CGScalars& q) {
-  if (col >= c) return;
-  if (step == kStepInit) {
-    if (!isfinite(v)) atomicOr(q.err, kErrNaN);
-    q.rho[col] = v;
-    q.rz0[col] = v;
-    q.alpha_prev[col] = 1.0;   // alpha_0 = 1
-    q.beta_prev[col] = 0.0;    // beta_0 = 0
-    q.beta[col] = 0.0;
-    q.active[col] = v > 0.0 ? 1 : 0;
-    q.iters[col] = 0;
-    q.stop[col] = 0;
-  } else if (step == kStepAlpha) {
-    double a = 0.0;
-    if (q.active[col]) {
-      a = q.rho[col] / v;
-      if (!isfinite(a) || !(v > 0.0)) { atomicOr(q.err, kErrNaN); a = 0.0; }
-    }
-    q.alpha[col] = a;
-  } else if (step == kStepResid) {
-    if (q.active[col]) {
-      double rn = sqrt(v);
-      q.rnorm[col] = rn;
-      q.stop[col] = (!q.fixed && rn < q.tol) ? 1 : 0;
-    }
-  } else if (step == kStepBeta) {
-    if (q.active[col]) {
-      double b = v / q.rho[col];
-      double a = q.alpha[col];
-      if (l < q.L) {   // Lanczos tridiagonal from the CG coefficients (Appendix A)
-        q.tdiag[(int64_t)col * q.L + l] = 1.0 / a + q.beta_prev[col] / q.alpha_prev[col];
-        if (l > 0) q.toff[(int64_t)col * q.L + l - 1] = sqrt(q.beta_prev[col]) / q.alpha_prev[col];
-      }
-      q.iters[col] = l + 1;
-      q.alpha_prev[col] = a;
-      q.beta_prev[col] = b;
-      q.rho[col] = v;
-      if (!isfinite(b)) { atomicOr(q.err, kErrNaN); b = 0.0; }
-      q.beta[col] = b;
-      if (q.stop[col] || v <= 0.0) q.active[col] = 0;
-    } else {
-      q.beta[col] = 0.0;
-    }
-  }
-}
-
-// called by every thread of every block after part[blockIdx.x][*] is written;
-// red: shared scratch of at least blockDim.x doubles
-__device__ __forceinline__ void finish_scalars(int step, const double* __restrict__ part, int ldc, int c, int l,
-                                               CGScalars& q, double* __restrict__ red) {
-  if (step == kStepNone) return;
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(q.ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // coalesced fixed-order sum of the nb partial rows: thread (group g, column
-  // col) adds rows g, g + RG, ... in order (four running sums); the RG group
-  // sums are then added in group order
-  const int nb = (int)gridDim.x;
-  const int RG = ((int)blockDim.x / ldc) > 1 ? (int)blockDim.x / ldc : 1;
-  for (int t = threadIdx.x; t < RG * ldc; t += blockDim.x) {
-    const int col = t % ldc, g = t / ldc;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = g;
-    for (; b + 3 * RG < nb; b += 4 * RG) {
-      s0 += __ldcg(&part[(int64_t)b * ldc + col]);
-      s1 += __ldcg(&part[(int64_t)(b + RG) * ldc + col]);
-      s2 += __ldcg(&part[(int64_t)(b + 2 * RG) * ldc + col]);
-      s3 += __ldcg(&part[(int64_t)(b + 3 * RG) * ldc + col]);
-    }
-    for (; b < nb; b += RG) s0 += __ldcg(&part[(int64_t)b * ldc + col]);
-    red[t] = (s0 + s1) + (s2 + s3);
-  }
-  __syncthreads();
-  for (int col = threadIdx.x; col < ldc; col += blockDim.x) {
-    double v = 0.0;
-    for (int g = 0; g < RG; ++g) v += red[g * ldc + col];
-    scalar_step(step, col, c, v, l, q);
-  }
-  if (step == kStepBeta) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int s = 0;
-      for (int k = 0; k < c; ++k) s += q.active[k];
-      *q.num_active = s;
-    }
-  }
-  if (threadIdx.x == 0) *q.ticket = 0u;
-}
 
 // block reduction of per-thread column partials -> part[blockIdx.x][col]
 __device__ __forceinline__ void vec_block_partials(double acc, int ldc, int rpb, double* __restrict__ red,
@@ -455,13 +346,13 @@ __device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_
 // bulk copies (TMA, completion counted in bytes on the stage's full
 // barrier): the tile's three neighbour ranges of Z (contiguous runs of rows),
 // its own rows of S, V and H (contiguous; V and H only when some beta is
-// nonzero), its staged columns and values and its row pointers (the last
-// three rounded out to 16-byte boundaries; the arrays are padded for it).
+// nonzero), its (staged column, value) pairs and its row pointers (the last
+// two rounded out to 16-byte boundaries; the arrays are padded for it).
 // The consumer warps wait on the full barrier, compute the tile entirely from
 // shared memory, store V and H, and release the stage on its empty barrier;
 // there is no block-wide barrier per tile.  Each consumer warp runs R rows at
 // once, L lanes per row (lane owns float4 chunks ch and ch + L), per nonzero
-// one broadcast load of the pair and one 16-byte shared load per chunk; every
+// one broadcast 8-byte load of the pair and one 16-byte shared load per chunk; every
 // row sums its products in CSR order, exactly as the row kernel.  A tile that
 // exceeds the stage capacity, or holds a column outside its ranges (the
 // cell-grid pattern produces none), gathers from global memory.
@@ -471,13 +362,13 @@ constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpMaxSta
 constexpr int kSpMeta = 8;   // per stage: p0, nr, n0, r1b, staged, pair offset, row-pointer offset, unused
 
 struct SpStage {   // byte offsets inside one stage, the stage size and the number of stages
-  int s, v, h, sc, sv, rp, bytes, count;
+  int s, v, h, sp, rp, bytes, count;
 };
 
 static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, int cap_rows,
     int cap_nnz, int cap_trows, SpStage so, int c, int ldc, const int64_t* __restrict__ rowptr,
-    const int32_t* __restrict__ colidx, const int32_t* __restrict__ scol, const float* __restrict__ vals,
+    const int32_t* __restrict__ colidx, const int2* __restrict__ pairs, const float* __restrict__ vals,
     const float* __restrict__ Z, const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H,
     const double* __restrict__ beta, double* __restrict__ part, int step, CGScalars q) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -536,10 +427,10 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         const int p0 = rec[0], nr = rec[1], r0b = rec[2], n0 = rec[3], r1b = rec[4], n1 = rec[5], r2b = rec[6],
                   n2 = rec[7], ne = rec[10];
         const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
-        const int64_t ea = e0 & ~(int64_t)3, eb = (e0 + ne + 3) & ~(int64_t)3;
+        const int64_t ea = e0 & ~(int64_t)1, eb = (e0 + ne + 1) & ~(int64_t)1;
         const int64_t pa = (int64_t)p0 & ~(int64_t)1, pb = ((int64_t)p0 + nr + 2) & ~(int64_t)1;
         const bool staged = !tile_bad[t] && n0 + n1 + n2 <= cap_rows && nr <= cap_trows &&
-                            eb - ea <= cap_nnz + 8 && pb - pa <= cap_trows + 4;
+                            eb - ea <= cap_nnz + 2 && pb - pa <= cap_trows + 4;
         int* mt = smeta[s];
         mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0;
         mt[5] = (int)(e0 - ea); mt[6] = (int)(p0 - pa);
@@ -547,8 +438,8 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
           unsigned char* sb = smraw + (size_t)s * so.bytes;
           const uint32_t rb = (uint32_t)ldc * 4u;
           const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bo = (uint32_t)nr * rb,
-                         bp = (uint32_t)(eb - ea) * 4u, br = (uint32_t)(pb - pa) * 8u;
-          sp_mbar_expect_tx(&full_bar[s], bz + (use_b ? 3u : 1u) * bo + 2u * bp + br);
+                         bp = (uint32_t)(eb - ea) * 8u, br = (uint32_t)(pb - pa) * 8u;
+          sp_mbar_expect_tx(&full_bar[s], bz + (use_b ? 3u : 1u) * bo + bp + br);
           if (n0 > 0) sp_bulk_load(sb, Z + (int64_t)r0b * ldc, (uint32_t)n0 * rb, &full_bar[s]);
           if (n1 > 0) sp_bulk_load(sb + (size_t)n0 * rb, Z + (int64_t)r1b * ldc, (uint32_t)n1 * rb, &full_bar[s]);
           if (n2 > 0)
@@ -558,8 +449,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
             sp_bulk_load(sb + so.v, V + (int64_t)p0 * ldc, bo, &full_bar[s]);
             sp_bulk_load(sb + so.h, H + (int64_t)p0 * ldc, bo, &full_bar[s]);
           }
-          sp_bulk_load(sb + so.sc, scol + ea, bp, &full_bar[s]);
-          sp_bulk_load(sb + so.sv, vals + ea, bp, &full_bar[s]);
+          sp_bulk_load(sb + so.sp, pairs + ea, bp, &full_bar[s]);
           sp_bulk_load(sb + so.rp, rowptr + pa, br, &full_bar[s]);
         } else {
           sp_mbar_arrive(&full_bar[s]);
@@ -605,8 +495,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
       const float4* ss = reinterpret_cast<const float4*>(sb + so.s);
       const float4* vs = reinterpret_cast<const float4*>(sb + so.v);
       const float4* hs = reinterpret_cast<const float4*>(sb + so.h);
-      const int32_t* sc = reinterpret_cast<const int32_t*>(sb + so.sc) + dsc;
-      const float* sv = reinterpret_cast<const float*>(sb + so.sv) + dsc;
+      const int2* sp = reinterpret_cast<const int2*>(sb + so.sp) + dsc;
       const int64_t* rp = reinterpret_cast<const int64_t*>(sb + so.rp) + drp;
       for (int rbase = wib * R; rbase < nr; rbase += kSpConsumers * R) {
         const int r = rbase + slot;
@@ -623,8 +512,9 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
             // staged row (in bounds: one spare row is allocated; kept off the output)
 #pragma unroll 4
             for (int t = tb; t < te; ++t) {
-              const float v = sv[t];
-              const int zr = sc[t] * c4;
+              const int2 pv = sp[t];
+              const float v = __int_as_float(pv.y);
+              const int zr = pv.x * c4;
               const float4 z0 = zs[zr + q0];
               const float4 z1 = zs[zr + q1];
               a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
@@ -728,7 +618,7 @@ static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
   L.cap_trows = (int)std::min<int64_t>(48, std::max<int64_t>(Hd.max_tile_rows, 1));
   L.cap_nnz = (int)std::min<int64_t>((int64_t)L.cap_trows * 40, std::max<int64_t>(Hd.max_tile_nnz, 1));
   const size_t row_bytes = (size_t)ldc * sizeof(float);
-  const size_t fixed = 3 * (size_t)L.cap_trows * row_bytes + 2 * r16((size_t)(L.cap_nnz + 8) * 4) +
+  const size_t fixed = 3 * (size_t)L.cap_trows * row_bytes + r16((size_t)(L.cap_nnz + 2) * 8) +
                        r16((size_t)(L.cap_trows + 4) * 8) + 256;
   const int64_t want = std::max<int64_t>(Hd.max_staged, 1);
   for (int nst = kSpMaxStages; nst >= 2; --nst) {
@@ -738,12 +628,11 @@ static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
     L.so.count = nst;
     if (L.cap_rows >= want) break;
   }
-  size_t off = r128((size_t)(L.cap_rows + 1) * row_bytes);
+  size_t off = r128((size_t)(L.cap_rows + 1) * row_bytes);   // one spare row (see the kernel)
   L.so.s = (int)off; off += (size_t)L.cap_trows * row_bytes;
   L.so.v = (int)off; off += (size_t)L.cap_trows * row_bytes;
   L.so.h = (int)off; off += (size_t)L.cap_trows * row_bytes;
-  L.so.sc = (int)r16(off); off = L.so.sc + r16((size_t)(L.cap_nnz + 8) * 4);
-  L.so.sv = (int)off; off += r16((size_t)(L.cap_nnz + 8) * 4);
+  L.so.sp = (int)r16(off); off = L.so.sp + r16((size_t)(L.cap_nnz + 2) * 8);
   L.so.rp = (int)off; off += r16((size_t)(L.cap_trows + 4) * 8);
   L.so.bytes = (int)r128(off);
   L.smem = (size_t)L.so.bytes * L.so.count;
@@ -872,13 +761,19 @@ struct Vec4Launch {
   int blocks, threads, rpb;
   size_t smem;
 };
-static inline Vec4Launch vec4_launch(const CGLayout& lay) {
+// one full wave of the kernel (SM count x its resident blocks, at most the
+// layout's partial rows): a second, partly filled wave would leave SMs idle
+static inline Vec4Launch vec4_launch(const CGLayout& lay, const void* kernel) {
   Vec4Launch v;
   const int c4 = lay.ldc / 4;
   v.rpb = std::max(1, 256 / c4);
   v.threads = v.rpb * c4;
-  v.blocks = lay.nblk;
   v.smem = (size_t)v.threads * 4 * sizeof(double);
+  int dev = 0, sms = 152, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, v.threads, v.smem);
+  v.blocks = per > 0 ? std::min(lay.nblk, sms * per) : lay.nblk;
   return v;
 }
 
@@ -927,7 +822,8 @@ inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t
 inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedLaunch& L, cudaStream_t s,
                             const float* vals, const float* Z, const float* S, float* V, float* Hv,
                             const double* beta, double* part, int step, const CGScalars& q) {
-  if (Hd.ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0) {
+  if (Hd.ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0 && vals == Hd.op.vals32.p &&
+      Hd.op.pairs32.p) {
     // timed under the profiling hooks (tag pcg_spmm); algorithmic bytes: the
     // pattern (staged column + value per nonzero, row pointers), Z and S read
     // once, V and H read and written once
@@ -940,7 +836,7 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
     }
     kv_spmm_tma<<<std::min(L.blocks, lay.nblk), kSpThreads, L.smem, s>>>(
         Hd.ntiles, Hd.ptile.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, L.so, lay.c, lay.ldc, Hd.rowptr.p,
-        Hd.col.p, Hd.scol.p, vals, Z, S, V, Hv, beta, part, step, q);
+        Hd.col.p, Hd.op.pairs32.p, vals, Z, S, V, Hv, beta, part, step, q);
     FSA_CHECK_LAUNCH();
     if (prof) {
       FSA_CUDA(cudaEventRecord(e1, s));
