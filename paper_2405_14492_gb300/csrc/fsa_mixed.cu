@@ -696,21 +696,8 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   FSA_CHECK_LAUNCH();
 }
 
-// the CG's preconditioner step fused into the epilogue of S = A~ q:
-// Z = D^-1 (R - S) and r^T z with the scalar step
-struct ZFuse {
-  const float* R;
-  const float* Dinv;
-  float* Z;
-  int c, l, step;
-  double* part;
-  CGScalars q;
-};
-
-// S (FP32 n x ldc) = A~ q, q FP64 m x ldc; with zf, also the fused step when
-// the launch takes the persistent form (returns whether it did)
-static bool mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag,
-                     const ZFuse* zf = nullptr) {
+// S (FP32 n x ldc) = A~ q, q FP64 m x ldc
+static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
@@ -725,26 +712,16 @@ static bool mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const ch
   t.out = S; t.ldo = ldc;
   t.tag = tag;
   t.alg_bytes = t.num_a * (double)C.n * H.m * 2.0 + (double)C.nsplit * C.c * H.m * 2.0 + (double)C.n * C.c * 4.0;
-  int fused = 0;
-  if (zf) {
-    t.zR = zf->R; t.zDinv = zf->Dinv; t.zZ = zf->Z;
-    t.z_c = zf->c; t.z_l = zf->l; t.z_step = zf->step; t.z_part = zf->part; t.z_q = zf->q;
-    t.z_fused = &fused;
-    // the fused form also reads R and D^-1 and writes Z (one block each)
-    t.alg_bytes += 2.0 * (double)C.n * C.ldc * 4.0 + (double)C.n * 4.0;
-  }
   tc_gemm(t, H.err, s);
-  return fused != 0;
 }
 
-// S = A~ M^-1 A~^T (D^-1 R); with zf, also Z = D^-1 (R - S) and its scalar
-// step when the last product takes the persistent form (returns whether it did)
-static bool lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S, const ZFuse* zf = nullptr) {
+// S = A~ M^-1 A~^T (D^-1 R)
+static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
   CGState& g = H.cg;
   Operator& op = H.op;
   mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
   dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
-  return mixed_Aq(H, C, g.q.p, S, "pcg_Aq", zf);
+  mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
 }
 
 LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
@@ -814,8 +791,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
                                                            q);
       FSA_CHECK_LAUNCH();
     }
-    const ZFuse zf{g.R32.p, op.Dinv32.p, g.Z32.p, lay.c, it, kStepBeta, g.part.p, q};
-    if (!lowrank_mixed(H, C, g.R32.p, g.S32.p, &zf)) {
+    lowrank_mixed(H, C, g.R32.p, g.S32.p);
+    {
       ProfScope ps("pcg_z", 3.0 * blk_bytes + 4.0 * n, s);   // R, S read, Z written; D^-1
       kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
                                                           g.Z32.p, g.part.p, kStepBeta, it, q);

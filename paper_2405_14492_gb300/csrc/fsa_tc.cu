@@ -40,13 +40,6 @@ struct Params {
   float* out;
   int64_t ldo, split_stride;
   unsigned* err;
-  // fused preconditioner step (persistent form): Z = D^-1 (R - S), r^T z
-  const float* zR;
-  const float* zDinv;
-  float* zZ;
-  int z_c, z_l, z_step;
-  double* z_part;
-  CGScalars z_q;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -320,8 +313,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
-  __shared__ double zacc[4][128];   // fused step: per epilogue warp, r^T z partials per column
-  for (int x = threadIdx.x; x < 4 * 128; x += kThreads) (&zacc[0][0])[x] = 0.0;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -461,51 +452,19 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
         }
       } else {
         const int h = p.bn / p.stack;
-        const float dinv = (p.zZ && in) ? p.zDinv[row] : 0.f;
         for (int c0 = 0; c0 < h; c0 += 8) {
           uint32_t r[8], t[8], u[8];
           tmem_ld8(taddr + c0, r);
           tmem_ld8(taddr + h + c0, t);
           if (p.stack == 3) tmem_ld8(taddr + 2 * h + c0, u);
           tmem_wait_ld();
-          float v[8];
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            v[jj] = __uint_as_float(r[jj]) + __uint_as_float(t[jj]);
-            if (p.stack == 3) v[jj] += __uint_as_float(u[jj]);
-          }
           if (in) {
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
               const int col = c0 + jj;
-              if (col < p.n_valid) orow[col] = v[jj];
-            }
-          }
-          if (p.zZ) {
-            // Z = D^-1 (R - S) for this row's 8 columns (n_valid = ldo, a
-            // multiple of 8: whole 16-byte chunks), and the column sums of
-            // r z over the warp's 32 rows (rows past M contribute 0)
-            float rv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (in) {
-              const float4* r4 = reinterpret_cast<const float4*>(p.zR + (int64_t)row * p.ldo + c0);
-              const float4 ra = r4[0], rb = r4[1];
-              rv[0] = ra.x; rv[1] = ra.y; rv[2] = ra.z; rv[3] = ra.w;
-              rv[4] = rb.x; rv[5] = rb.y; rv[6] = rb.z; rv[7] = rb.w;
-            }
-            float zv[8];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) zv[jj] = (rv[jj] - v[jj]) * dinv;
-            if (in) {
-              float4* z4 = reinterpret_cast<float4*>(p.zZ + (int64_t)row * p.ldo + c0);
-              z4[0] = make_float4(zv[0], zv[1], zv[2], zv[3]);
-              z4[1] = make_float4(zv[4], zv[5], zv[6], zv[7]);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              float pr = in ? rv[jj] * zv[jj] : 0.f;
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
-              if (lane == 0) zacc[q][c0 + jj] += (double)pr;
+              float v = __uint_as_float(r[jj]) + __uint_as_float(t[jj]);
+              if (p.stack == 3) v += __uint_as_float(u[jj]);
+              if (col < p.n_valid) orow[col] = v;
             }
           }
         }
@@ -522,14 +481,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
     mbar_wait(&done_bar, 0, nullptr, nullptr);
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
-  }
-  if (p.zZ) {
-    // this CTA's r^T z partials (the four epilogue warps in order), then the
-    // fixed-order reduction over the CTAs and the CG scalar step
-    for (int col = threadIdx.x; col < (int)p.ldo; col += kThreads)
-      p.z_part[(int64_t)blockIdx.x * p.ldo + col] = ((zacc[0][col] + zacc[1][col]) + zacc[2][col]) + zacc[3][col];
-    CGScalars q = p.z_q;
-    finish_scalars(p.z_step, p.z_part, (int)p.ldo, p.z_c, p.z_l, q, &zacc[0][0]);
   }
 }
 
@@ -644,7 +595,6 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   p.ldo = g.ldo;
   p.split_stride = g.split_stride;
   p.err = err;
-  p.zR = nullptr; p.zDinv = nullptr; p.zZ = nullptr; p.z_part = nullptr;
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
   static int sms = 0;
   static std::once_flag attr_once;
@@ -665,12 +615,7 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
     p.stages = std::max(2, std::min(tc::kMaxStages, (199 * 1024) / (int)p.stage_bytes));
     smem = std::max<size_t>((size_t)p.stages * p.stage_bytes + 1024, 120 * 1024);   // one CTA per SM (TMEM)
     grid = dim3((unsigned)sms, 1, 1);
-    if (g.zZ && stack > 1 && p.n_valid == g.ldo && g.ldo % 8 == 0 && g.ldo <= 128) {
-      p.zR = g.zR; p.zDinv = g.zDinv; p.zZ = g.zZ;
-      p.z_c = g.z_c; p.z_l = g.z_l; p.z_step = g.z_step; p.z_part = g.z_part; p.z_q = g.z_q;
-    }
   }
-  if (g.z_fused) *g.z_fused = p.zZ ? 1 : 0;
   const bool prof = g.tag && profile_on();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof) {

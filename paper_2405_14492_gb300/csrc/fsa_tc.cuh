@@ -13,7 +13,6 @@
 #include <cuda.h>
 
 #include "fsa_internal.cuh"
-#include "fsa_scalars.cuh"
 
 namespace fsa {
 
@@ -55,16 +54,6 @@ struct TcGemm {
   int64_t ldo = 0;
   int64_t split_stride = 0;
   int n_valid = 0;          // columns of out written (<= N or N/2)
-  // optional fused epilogue of the CG's preconditioner step (S = A~ q launches
-  // of the persistent form only): Z = D^-1 (R - S) and the partials of r^T z,
-  // reduced with the scalar step z_step (z_fused receives 1 when applied)
-  const float* zR = nullptr;
-  const float* zDinv = nullptr;
-  float* zZ = nullptr;
-  int z_c = 0, z_l = 0, z_step = 0;
-  double* z_part = nullptr;
-  CGScalars z_q{};
-  int* z_fused = nullptr;
   const char* tag = nullptr;  // profiling tag (fsa_profile.h)
   double alg_bytes = 0;       // algorithmic bytes of this launch (0: from the shapes)
 };
