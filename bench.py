@@ -90,16 +90,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _tc_source_hash():
+def _source_hash(name):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2405_14492_gb300", "csrc", "fsa_tc.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2405_14492_gb300", "csrc", name), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_for(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    from the current tensor-core kernel source (else None)."""
+    from the current source of that kernel (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
@@ -107,7 +107,7 @@ def _traffic_for(kernel_tag):
     except (OSError, ValueError):
         return None
     e = d.get(kernel_tag)
-    if not e or e.get("source_sha") != _tc_source_hash():
+    if not e or e.get("source_sha") != _source_hash(e.get("source", "fsa_tc.cu")):
         return None
     return e.get("dram_bytes_per_launch_full")
 
@@ -269,6 +269,7 @@ def run_gpu(args):
             d2 = prof["pcg_spmm"]
             ach = d2["bytes"] / d2["launches"] / (d2["ms"] / d2["launches"] / 1000.0) / 1e9
             roof["spmm"] = {"kernel": "kv_spmm_tma", "bound": "hbm", "achieved": round(ach, 1),
+                            "traffic": _traffic_for("pcg_spmm"),
                             "frac": round(ach / peaks["hbm_gbs"], 4), "alg_bytes_per_launch": d2["bytes"] / d2["launches"],
                             "avg_launch_ms": d2["ms"] / d2["launches"], "launches": d2["launches"],
                             "share_of_step": round(d2["ms"] / elapsed_ms, 4)}

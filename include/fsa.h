@@ -92,6 +92,10 @@ typedef struct {
   int32_t slq_exact_weight; /* 1: weight z^T P^-1 z instead of the paper's n */
   int32_t want_grad;     /* 0: log-likelihood only */
   int32_t y_on_device;   /* 1: y is a DEVICE pointer (n doubles, caller order) */
+  int32_t pred_control_variate; /* fsa_predict: 0 plain D_l of Algorithm 1; 1 D_l with the
+                                   diagonal preconditioner D_s as control variate and the
+                                   per-point coefficient c_opt; 2 the same with c = 1
+                                   (appendix "Preconditioner as control variate") */
 } fsa_opts;
 
 typedef struct {
@@ -111,7 +115,7 @@ typedef struct {
 typedef struct fsa_handle fsa_handle;
 
 /* Defaults: num_probes 50, cg_tol 1e-3, cg_max_iter 1000, fixed_iters 0,
- * FSA_FP64, Rademacher, seed 14492, want_grad 1. */
+ * FSA_FP64, Rademacher, seed 14492, want_grad 1, pred_control_variate 0. */
 void fsa_default_opts(fsa_opts* opts);
 
 /* Human-readable name of a status code (static string). */

@@ -525,9 +525,17 @@ class IterativeFSA:
         return Kp, St, (rowptr, col)
 
     def predict(self, y, pred, num_samples, seed, tol, max_iter=1000, probe="rademacher",
-                u=None, Zp=None):
+                u=None, Zp=None, control_variate=None):
         """Predictive mean (§2.3) and simulation-based variances (Algorithm 1).
-        ``Zp`` replaces the random probes (used by deterministic checks)."""
+        ``Zp`` replaces the random probes (used by deterministic checks).
+        ``control_variate`` ("copt" or "c1") estimates the diagonal D_l with the
+        diagonal preconditioner P_s = D_s as control variate (appendix
+        "Preconditioner as control variate"): per point p, with
+        a_k = z_k o (S Sigma_s~^-1 S^T z_k) and b_k = z_k o (S P_s^-1 S^T z_k),
+            D_l = (1/l) sum_k (a_k - c b_k) + c diag(S P_s^-1 S^T),
+        c = c_opt = sum_k (a_k - mean_k a_k) b_k / sum_k b_k^2 (the appendix's
+        formula as printed, elementwise per point; 0 where sum_k b_k^2 = 0), or
+        c = 1 ("c1")."""
         s1, rho, nug = self.theta
         n_p = pred.shape[0]
         Kp, St, _ = self.cross_structures(pred)
@@ -548,8 +556,21 @@ class IterativeFSA:
         if Zp is None:
             draw = rademacher if probe == "rademacher" else gaussian
             Zp = draw(seed, STREAM_PRED, np.arange(n_p), n_p, num_samples)
-        X = pcg_lanczos(lambda V_: self.Ss @ V_, self.apply_Dinv, St.T @ Zp, tol, max_iter)["U"]
-        Dl = np.mean(Zp * (St @ X), axis=1)
+        StZ = St.T @ Zp
+        X = pcg_lanczos(lambda V_: self.Ss @ V_, self.apply_Dinv, StZ, tol, max_iter)["U"]
+        a = Zp * (St @ X)
+        Dl = np.mean(a, axis=1)
+        c = None
+        if control_variate is not None:
+            b = Zp * (St @ (StZ / self.D[:, None]))            # z o S P_s^-1 S^T z
+            exact_b = np.asarray(St.multiply(St) @ (1.0 / self.D)).ravel()   # diag(S P_s^-1 S^T)
+            if control_variate == "c1":
+                c = np.ones(n_p)
+            else:
+                den = np.sum(b * b, axis=1)
+                num = np.sum((a - Dl[:, None]) * b, axis=1)
+                c = np.divide(num, den, out=np.zeros(n_p), where=den > 0)
+            Dl = np.mean(a - c[:, None] * b, axis=1) + c * exact_b
         var = s1 + nug - D1 - 2.0 * D2 + D3 - Dl
-        return dict(mean=mean, var=var, D1=D1, D2=D2, D3=D3, Dl=Dl, u=u, Zp=Zp)
+        return dict(mean=mean, var=var, D1=D1, D2=D2, D3=D3, Dl=Dl, u=u, Zp=Zp, c=c)
 

@@ -28,13 +28,17 @@ def cov_code(nu: float) -> int:
     raise ValueError("nu must be 0.5 or 1.5")
 
 
+FSA_PRED_CV_NONE, FSA_PRED_CV_COPT, FSA_PRED_CV_C1 = 0, 1, 2
+
+
 def make_opts(num_probes=50, cg_tol=1e-3, cg_max_iter=1000, fixed_iters=0, precision=FSA_FP64,
               probe=FSA_PROBE_RADEMACHER, seed=14492, slq_exact_weight=False, want_grad=True,
-              y_on_device=False) -> FsaOpts:
+              y_on_device=False, pred_control_variate=FSA_PRED_CV_NONE) -> FsaOpts:
     o = N.default_opts()
     o.num_probes, o.cg_tol, o.cg_max_iter, o.fixed_iters = num_probes, cg_tol, cg_max_iter, fixed_iters
     o.precision, o.probe, o.seed = precision, probe, seed
     o.slq_exact_weight, o.want_grad, o.y_on_device = int(slq_exact_weight), int(want_grad), int(y_on_device)
+    o.pred_control_variate = int(pred_control_variate)
     return o
 
 

@@ -30,7 +30,7 @@ class FsaOpts(C.Structure):
     _fields_ = [("num_probes", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("fixed_iters", C.c_int32), ("precision", C.c_int32), ("probe", C.c_int32),
                 ("seed", C.c_uint64), ("slq_exact_weight", C.c_int32), ("want_grad", C.c_int32),
-                ("y_on_device", C.c_int32)]
+                ("y_on_device", C.c_int32), ("pred_control_variate", C.c_int32)]
 
 
 class FsaInfo(C.Structure):

@@ -367,6 +367,8 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
   if (o.cg_max_iter > 8000) return fail(Error{FSA_ERR_ARG, "cg_max_iter must be <= 8000"});
   if (o.precision != FSA_FP64)
     return fail(Error{FSA_ERR_UNSUPPORTED, "prediction is implemented in the FP64 form"});
+  if (o.pred_control_variate < 0 || o.pred_control_variate > 2)
+    return fail(Error{FSA_ERR_ARG, "pred_control_variate must be 0, 1 or 2"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
   try {

@@ -257,6 +257,52 @@ __global__ void k_pred_assemble(int64_t np, double s1, double nug, const double*
   }
 }
 
+// dst (n x k) = D^-1 o src (n x k, leading dimension lds)
+__global__ void k_scale_rows(int64_t n, int k, const double* __restrict__ Dv, const double* __restrict__ src,
+                             int64_t lds, double* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / k;
+    const int j = (int)(t - i * k);
+    dst[t] = src[i * lds + j] / Dv[i];
+  }
+}
+
+// D_l with the diagonal preconditioner P_s = D_s as control variate
+// (appendix "Preconditioner as control variate"), per prediction point p:
+//   a_k = z_pk (S Sigma_s~^-1 S^T z_k)_p,  b_k = z_pk (S D_s^-1 S^T z_k)_p,
+//   D_l = (1/s) sum_k (a_k - c b_k) + c sum_j S_pj^2 / D_j,
+// c = sum_k (a_k - mean a) b_k / sum_k b_k^2 (mode 1; 0 where the
+// denominator vanishes) or c = 1 (mode 2)
+__global__ void k_dl_control_variate(int64_t np, int s, int mode, const double* __restrict__ Zp,
+                                     const double* __restrict__ SY, const double* __restrict__ SU,
+                                     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                     const double* __restrict__ vals, const double* __restrict__ Dv,
+                                     double* __restrict__ Dl) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const double* z = Zp + p * s;
+    const double* ty = SY + p * s;
+    const double* tu = SU + p * s;
+    double sa = 0.0;
+    for (int k = 0; k < s; ++k) sa += z[k] * ty[k];
+    const double abar = sa / s;
+    double c = 1.0;
+    if (mode == 1) {
+      double num = 0.0, den = 0.0;
+      for (int k = 0; k < s; ++k) {
+        const double b = z[k] * tu[k];
+        num += (z[k] * ty[k] - abar) * b;
+        den += b * b;
+      }
+      c = den > 0.0 ? num / den : 0.0;
+    }
+    double sd = 0.0;
+    for (int k = 0; k < s; ++k) sd += z[k] * ty[k] - c * (z[k] * tu[k]);
+    double eb = 0.0;
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; ++e) eb += vals[e] * vals[e] / Dv[col[e]];
+    Dl[p] = sd / s + c * eb;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // driver
 // ---------------------------------------------------------------------------
@@ -370,13 +416,25 @@ PredResult run_predict_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o, c
     dgemm(H.ws, st, false, false, (int)np, m, m, 1.0, V.p, m, Minv.p, m, 0.0, T.p, m, nullptr);
     k_rowdot<<<grid_for(np * 32, 256, 152 * 64), 256, 0, st>>>(np, m, T.p, m, V.p, m, 1.0, D3.p);
     FSA_CHECK_LAUNCH();
-    // Dl = (1/s) sum_k z_pk (S Ys)_pk
+    // Dl = (1/s) sum_k z_pk (S Ys)_pk, or its control-variate form
     {
       DevPtr<double> SY((size_t)np * s);
       k_cross_spmm<<<grid_for(np * s, 256), 256, 0, st>>>(np, s, srow.p, scol.p, svals.p, Ys, cb, SY.p, s);
       FSA_CHECK_LAUNCH();
-      k_rowdot<<<grid_for(np * 32, 256, 152 * 64), 256, 0, st>>>(np, s, Zp.p, s, SY.p, s, 1.0 / s, Dl.p);
-      FSA_CHECK_LAUNCH();
+      if (o.pred_control_variate == 0) {
+        k_rowdot<<<grid_for(np * 32, 256, 152 * 64), 256, 0, st>>>(np, s, Zp.p, s, SY.p, s, 1.0 / s, Dl.p);
+        FSA_CHECK_LAUNCH();
+      } else {
+        // S D_s^-1 S^T Z from the probe right-hand sides S^T Z (columns m.. of RHS)
+        DevPtr<double> DZ((size_t)n * s), SU((size_t)np * s);
+        k_scale_rows<<<grid_for(n * s, 256), 256, 0, st>>>(n, s, op.D.p, RHS.p + m, cb, DZ.p);
+        FSA_CHECK_LAUNCH();
+        k_cross_spmm<<<grid_for(np * s, 256), 256, 0, st>>>(np, s, srow.p, scol.p, svals.p, DZ.p, s, SU.p, s);
+        FSA_CHECK_LAUNCH();
+        k_dl_control_variate<<<grid_for(np, 128), 128, 0, st>>>(np, s, o.pred_control_variate, Zp.p, SY.p, SU.p,
+                                                               srow.p, scol.p, svals.p, op.D.p, Dl.p);
+        FSA_CHECK_LAUNCH();
+      }
       k_pred_assemble<<<grid_for(np, 256), 256, 0, st>>>(np, th.sigma1_sq, th.nugget, mlr.p, su.p, D1.p, D2.p, D3.p,
                                                          Dl.p, mean.p, var.p);
       FSA_CHECK_LAUNCH();

@@ -72,3 +72,45 @@ def test_predict_mean_only_and_far_points(F):
     assert np.array_equal(mean, mean2) and var2 is None
     # far from every data point: no sparse term, variance is the low-rank (FITC) one
     assert var[2] > 0.0 and var[4] > 0.0
+
+
+@pytest.mark.parametrize("cv,name", [(1, "copt"), (2, "c1")])
+def test_predict_control_variate_parity_same_probes(F, cv, name):
+    """D_l with the diagonal preconditioner as control variate (appendix
+    "Preconditioner as control variate") against the oracle, same probes."""
+    n, m, n_p, s, gamma = 3001, 60, 517, 40, 0.05
+    locs, ind, pred = _case(n, m, n_p, 94, gamma)
+    th = (1.0, 0.08, 0.05)
+    y = fi.random_field(locs, 0.5, *th, 94)
+    ref = O.IterativeFSA(locs, ind, gamma, 0.5, th).predict(y, pred, s, 17, 1e-11, control_variate=name)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        mean, var, info = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-11, seed=17, pred_control_variate=cv))
+    assert info["converged"] == 1
+    assert np.max(np.abs(mean - ref["mean"])) < 1e-7 * np.max(np.abs(ref["mean"]))
+    assert np.max(np.abs(var - ref["var"])) < 1e-7
+
+
+def test_predict_control_variate_reduces_error_to_exact(F):
+    """With c = 1 the estimate is unbiased with Var[D_l,p] = (1/s) sum_{k != p}
+    (A - B)_pk^2, A = S Sigma_s~^-1 S^T, B = S D_s^-1 S^T; it stays within five
+    of those standard deviations of the exact FSA variances.  With the
+    coefficient c_opt the error to the exact variances is smaller than the
+    plain estimator's on the same probes (here c = 1 alone is not: the
+    diagonal preconditioner's term has variance of its own)."""
+    n, m, n_p, s, gamma = 1500, 40, 300, 100, 0.06
+    locs, ind, pred = _case(n, m, n_p, 95, gamma)
+    th = (1.0, 0.1, 0.1)
+    y = fi.random_field(locs, 0.5, *th, 95)
+    D = O.DenseFSA(locs, ind, gamma, 0.5, th)
+    _, var_exact = D.predict(y, pred)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        _, var_cv, _ = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-10, seed=4, pred_control_variate=2))
+        _, var_co, _ = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-10, seed=4, pred_control_variate=1))
+        _, var_pl, _ = h.predict(y, th, pred, s, F.make_opts(cg_tol=1e-10, seed=4))
+    _, _, Ssnp, _ = D.cross(pred)
+    A = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
+    B = Ssnp.T @ (Ssnp / np.diag(D.Ss)[:, None])
+    E = A - B
+    sd = np.sqrt((np.sum(E ** 2, 1) - np.diag(E) ** 2) / s)
+    assert np.all(np.abs(var_cv - var_exact) <= 5 * sd + 1e-9)
+    assert np.sqrt(np.mean((var_co - var_exact) ** 2)) < 0.8 * np.sqrt(np.mean((var_pl - var_exact) ** 2))

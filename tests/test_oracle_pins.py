@@ -346,3 +346,66 @@ def test_algorithm1_random_probes_unbiased_within_tolerance():
     Amat = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
     sd = np.sqrt((np.sum(Amat ** 2, 1) - np.diag(Amat) ** 2) / s)
     assert np.all(np.abs(out["var"] - var) <= 5 * sd + 1e-9)
+
+
+def test_control_variate_with_full_basis_probes_stays_exact():
+    """With probes sqrt(s) e_j the sample mean of b_k = z_k o (S P_s^-1 S^T z_k)
+    equals diag(S P_s^-1 S^T) exactly, so the control-variate estimator of D_l
+    (appendix "Preconditioner as control variate") stays exact for any c."""
+    locs, ind, g, nu, th = _problem(n=120, m=15)
+    pred = fi.uniform_locations(30, 3, stream=7)
+    y = np.random.default_rng(11).standard_normal(120)
+    _, var = O.DenseFSA(locs, ind, g, nu, th).predict(y, pred)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    for cv in ("copt", "c1"):
+        out = It.predict(y, pred, 30, 0, 1e-12, Zp=math.sqrt(30) * np.eye(30), control_variate=cv)
+        assert np.allclose(out["var"], var, atol=1e-8)
+
+
+def test_control_variate_c1_unbiased_with_reduced_variance():
+    """c = 1: D_l = mean(a - b) + diag(S P_s^-1 S^T) is unbiased, and for
+    Rademacher probes Var[D_l,p] = (1/s) sum_{k != p} (A - B)_pk^2 with
+    A = S Sigma_s~^-1 S^T and B = S D_s^-1 S^T (built densely here)."""
+    locs, ind, g, nu, th = _problem(n=200, m=20)
+    pred = fi.uniform_locations(60, 4, stream=7)
+    y = np.random.default_rng(12).standard_normal(200)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    _, var = D.predict(y, pred)
+    s = 400
+    out = It.predict(y, pred, s, 77, 1e-12, control_variate="c1")
+    _, _, Ssnp, _ = D.cross(pred)
+    Amat = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
+    Bmat = Ssnp.T @ (Ssnp / np.diag(D.Ss)[:, None])
+    E = Amat - Bmat
+    sd_cv = np.sqrt((np.sum(E ** 2, 1) - np.diag(E) ** 2) / s)
+    sd_plain = np.sqrt((np.sum(Amat ** 2, 1) - np.diag(Amat) ** 2) / s)
+    assert np.all(np.abs(out["var"] - var) <= 5 * sd_cv + 1e-9)
+    assert np.all(out["c"] == 1.0)
+    # the diagonal preconditioner captures most of the estimator's variance here
+    assert np.mean(sd_cv) < 0.7 * np.mean(sd_plain)
+
+
+def test_control_variate_copt_is_the_least_squares_coefficient():
+    """c_opt of each point is the least-squares slope of (a_k - mean a) on b_k
+    through the origin, i.e. the c minimising sum_k (a_k - mean a - c b_k)^2."""
+    locs, ind, g, nu, th = _problem(n=150, m=20)
+    pred = fi.uniform_locations(25, 5, stream=7)
+    y = np.random.default_rng(13).standard_normal(150)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    s = 12
+    Zp = O.rademacher(9, O.STREAM_PRED, np.arange(25), 25, s)
+    out = It.predict(y, pred, s, 9, 1e-12, Zp=Zp, control_variate="copt")
+    plain = It.predict(y, pred, s, 9, 1e-12, Zp=Zp)
+    _, St, _ = It.cross_structures(pred)
+    X = np.linalg.solve(It.Ss.toarray(), St.T @ Zp)
+    a = Zp * (St @ X)
+    b = Zp * (St @ ((St.T @ Zp) / It.D[:, None]))
+    for p in range(25):
+        if np.sum(b[p] ** 2) == 0:
+            assert out["c"][p] == 0.0
+            continue
+        slope = np.linalg.lstsq(b[p][:, None], a[p] - a[p].mean(), rcond=None)[0][0]
+        assert abs(out["c"][p] - slope) <= 1e-8 * (1 + abs(slope))
+    # the plain estimate is the c = 0 member of the family
+    assert np.allclose(plain["Dl"], a.mean(1), atol=1e-10)
