@@ -104,7 +104,12 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
     for (int k = 0; k < H.ntiles; ++k) {
       const int64_t* d = &td[(size_t)k * 8];
       const int64_t rows = (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]);
-      if (!bad[k] && rows <= sl.cap_rows && rp[d[1]] - rp[d[0]] <= sl.cap_nnz && d[1] - d[0] <= sl.cap_trows) ++staged;
+      const int64_t e0 = rp[d[0]], ne = rp[d[1]] - e0, p0 = d[0], nr = d[1] - d[0];
+      const int64_t npairs = ((e0 + ne + 1) & ~(int64_t)1) - (e0 & ~(int64_t)1);
+      const int64_t nrp = ((p0 + nr + 2) & ~(int64_t)1) - (p0 & ~(int64_t)1);
+      // with V and H staged (the nonzero-beta pass; the larger layout)
+      const SpTileLayout lay = sp_tile_layout((int)rows, (int)nr, npairs, nrp, ldc, true);
+      if (!bad[k] && lay.bytes <= sl.ring.bytes) ++staged;
     }
     double d;
     std::memcpy(&d, &bits, sizeof(d));

@@ -341,39 +341,64 @@ __device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_
 }
 
 // FP32 form over the cell-grid tiles, warp-specialised: one persistent block
-// per SM runs its tiles (blockIdx.x, + gridDim.x, ...) through a ring of
-// shared-memory stages.  The producer lane (last warp) fills a stage with
-// bulk copies (TMA, completion counted in bytes on the stage's full
-// barrier): the tile's three neighbour ranges of Z (contiguous runs of rows),
-// its own rows of S, V and H (contiguous; V and H only when some beta is
-// nonzero), its (staged column, value) pairs and its row pointers (the last
-// two rounded out to 16-byte boundaries; the arrays are padded for it).
+// per SM runs its tiles (blockIdx.x, + gridDim.x, ...) through a byte ring of
+// shared memory in which consecutive tiles are placed back to back (each at
+// its own size, so that about three average tiles are in flight).  The
+// producer lane (last warp) places a tile and fills it with bulk copies (TMA,
+// completion counted in bytes on the tile slot's full barrier): its three
+// neighbour ranges of Z (contiguous runs of rows), its own rows of S, V and H
+// (contiguous; V and H only when some beta is nonzero), its (staged column,
+// value) pairs and its row pointers (the last two rounded out to 16-byte
+// boundaries; the arrays are padded for it).  Before placing a tile the
+// producer waits for the release (empty barrier) of the newest earlier tile
+// whose bytes it would overwrite, and of the tile that last used the slot.
 // The consumer warps wait on the full barrier, compute the tile entirely from
-// shared memory, store V and H, and release the stage on its empty barrier;
+// shared memory, store V and H, and release the slot on its empty barrier;
 // there is no block-wide barrier per tile.  Each consumer warp runs R rows at
 // once, L lanes per row (lane owns float4 chunks ch and ch + L), per nonzero
-// one broadcast 8-byte load of the pair and one 16-byte shared load per chunk; every
-// row sums its products in CSR order, exactly as the row kernel.  A tile that
-// exceeds the stage capacity, or holds a column outside its ranges (the
-// cell-grid pattern produces none), gathers from global memory.
+// one broadcast 8-byte load of the pair and one 16-byte shared load per chunk;
+// every row sums its products in CSR order, exactly as the row kernel.  A tile
+// larger than the ring, or holding a column outside its ranges (the cell-grid
+// pattern produces none), gathers from global memory.
 // Tile record (int32 x 12): p0, rows, then (begin, length) of the three
 // ranges, first nonzero (lo, hi words), nonzeros, unused.
-constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpMaxStages = 3, kTileWords = 12;
-constexpr int kSpMeta = 8;   // per stage: p0, nr, n0, r1b, staged, pair offset, row-pointer offset, unused
+constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpSlots = 4, kTileWords = 12;
+constexpr int kSpMeta = 16;   // per slot: p0, nr, n0, r1b, staged, pair and row-pointer offsets, byte offsets
 
-struct SpStage {   // byte offsets inside one stage, the stage size and the number of stages
-  int s, v, h, sp, rp, bytes, count;
+// shared-memory bytes of a staged tile and the offsets of its parts from the
+// tile's start: Z rows (+ one spare row), S, V, H rows, pairs, row pointers
+struct SpTileLayout {
+  int s, v, h, sp, rp, bytes;
+};
+__host__ __device__ __forceinline__ SpTileLayout sp_tile_layout(int zrows, int nr, int64_t npairs, int64_t nrp,
+                                                                 int ldc, bool use_b) {
+  const int64_t rb = (int64_t)ldc * 4;
+  SpTileLayout l;
+  int64_t off = (int64_t)(zrows + 1) * rb;
+  l.s = (int)off; off += (int64_t)nr * rb;
+  l.v = (int)off; if (use_b) off += (int64_t)nr * rb;
+  l.h = (int)off; if (use_b) off += (int64_t)nr * rb;
+  off = (off + 15) / 16 * 16;
+  l.sp = (int)off; off += npairs * 8;
+  l.rp = (int)off; off += nrp * 8;
+  const int64_t bytes = (off + 127) / 128 * 128;
+  l.bytes = bytes > (int64_t)1 << 30 ? 1 << 30 : (int)bytes;
+  return l;
+}
+
+struct SpRing {   // the ring's size in bytes
+  int bytes;
 };
 
 static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
-    int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, int cap_rows,
-    int cap_nnz, int cap_trows, SpStage so, int c, int ldc, const int64_t* __restrict__ rowptr,
-    const int32_t* __restrict__ colidx, const int2* __restrict__ pairs, const float* __restrict__ vals,
-    const float* __restrict__ Z, const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H,
-    const double* __restrict__ beta, double* __restrict__ part, int step, CGScalars q) {
+    int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, SpRing ring, int c,
+    int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+    const int2* __restrict__ pairs, const float* __restrict__ vals, const float* __restrict__ Z,
+    const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H, const double* __restrict__ beta,
+    double* __restrict__ part, int step, CGScalars q) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full_bar[kSpMaxStages], empty_bar[kSpMaxStages];
-  __shared__ int smeta[kSpMaxStages][kSpMeta];
+  __shared__ __align__(8) uint64_t full_bar[kSpSlots], empty_bar[kSpSlots];
+  __shared__ int smeta[kSpSlots][kSpMeta];
   __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
   __shared__ int any_b;
   __shared__ double wdot[kSpConsumers][128];   // per consumer warp: running h^T v partials per column
@@ -385,7 +410,6 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   const bool lane_on = slot < R;
   const int q0 = ch, q1 = ch + L;
   const bool has1 = q1 < c4;
-  const int nst = so.count;
   const float4* Z4 = reinterpret_cast<const float4*>(Z);
   const float4* S4 = reinterpret_cast<const float4*>(S);
   const float4* V4 = reinterpret_cast<const float4*>(V);
@@ -394,7 +418,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   for (int x = tid; x < kSpConsumers * 128; x += kSpThreads) (&wdot[0][0])[x] = 0.0;
   if (tid == 0) {
     any_b = 0;
-    for (int s = 0; s < nst; ++s) {
+    for (int s = 0; s < kSpSlots; ++s) {
       sp_mbar_init(&full_bar[s], 1);
       sp_mbar_init(&empty_bar[s], kSpConsumers);
     }
@@ -415,13 +439,21 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     // ---------------- producer ----------------
     if (lane == 0) {
       int issued = 0;
-      for (int k = 0; k < nk; ++k) {
-        const int s = k % nst;
-        const uint32_t ph = (uint32_t)(k / nst) & 1u;
-        if (k >= nst && !sp_mbar_wait(&empty_bar[s], ph ^ 1u, q.err)) {
-          sp_flag(q.err);
-          break;
-        }
+      int head = 0;                    // next free byte of the ring
+      int released = -1;               // every tile <= released has been released
+      int ra[kSpSlots], rz[kSpSlots];  // byte range [ra, rz) of the tile in each slot (empty: ra = rz)
+      for (int s = 0; s < kSpSlots; ++s) ra[s] = rz[s] = 0;
+      bool ok = true;
+      // wait until tile j (and so every earlier tile) is released
+      auto release = [&](int j) {
+        if (j <= released) return true;
+        if (!sp_mbar_wait(&empty_bar[j % kSpSlots], (uint32_t)(j / kSpSlots) & 1u, q.err)) return false;
+        released = j;
+        return true;
+      };
+      for (int k = 0; k < nk && ok; ++k) {
+        const int s = k % kSpSlots;
+        if (k >= kSpSlots && !release(k - kSpSlots)) { ok = false; break; }
         const int64_t t = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
         const int32_t* rec = ptile + t * kTileWords;
         const int p0 = rec[0], nr = rec[1], r0b = rec[2], n0 = rec[3], r1b = rec[4], n1 = rec[5], r2b = rec[6],
@@ -429,13 +461,33 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
         const int64_t ea = e0 & ~(int64_t)1, eb = (e0 + ne + 1) & ~(int64_t)1;
         const int64_t pa = (int64_t)p0 & ~(int64_t)1, pb = ((int64_t)p0 + nr + 2) & ~(int64_t)1;
-        const bool staged = !tile_bad[t] && n0 + n1 + n2 <= cap_rows && nr <= cap_trows &&
-                            eb - ea <= cap_nnz + 2 && pb - pa <= cap_trows + 4;
+        const SpTileLayout lay = sp_tile_layout(n0 + n1 + n2, nr, eb - ea, pb - pa, ldc, use_b);
+        const bool staged = !tile_bad[t] && lay.bytes <= ring.bytes;
+        int base = 0;
+        ra[s] = rz[s] = 0;
+        if (staged) {
+          if (head + lay.bytes > ring.bytes) head = 0;
+          base = head;
+          // the newest earlier tile whose bytes overlap [base, base + bytes)
+          for (int j = k - 1; j > released && j > k - kSpSlots; --j) {
+            const int sj = j % kSpSlots;
+            if (ra[sj] < base + lay.bytes && base < rz[sj]) {
+              if (!release(j)) ok = false;
+              break;
+            }
+          }
+          if (!ok) break;
+          head = base + lay.bytes;
+          ra[s] = base;
+          rz[s] = head;
+        }
         int* mt = smeta[s];
         mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0;
         mt[5] = (int)(e0 - ea); mt[6] = (int)(p0 - pa);
+        mt[7] = base; mt[8] = base + lay.s; mt[9] = base + lay.v; mt[10] = base + lay.h;
+        mt[11] = base + lay.sp; mt[12] = base + lay.rp;
         if (staged) {
-          unsigned char* sb = smraw + (size_t)s * so.bytes;
+          unsigned char* sb = smraw + base;
           const uint32_t rb = (uint32_t)ldc * 4u;
           const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bo = (uint32_t)nr * rb,
                          bp = (uint32_t)(eb - ea) * 8u, br = (uint32_t)(pb - pa) * 8u;
@@ -444,23 +496,24 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
           if (n1 > 0) sp_bulk_load(sb + (size_t)n0 * rb, Z + (int64_t)r1b * ldc, (uint32_t)n1 * rb, &full_bar[s]);
           if (n2 > 0)
             sp_bulk_load(sb + (size_t)(n0 + n1) * rb, Z + (int64_t)r2b * ldc, (uint32_t)n2 * rb, &full_bar[s]);
-          sp_bulk_load(sb + so.s, S + (int64_t)p0 * ldc, bo, &full_bar[s]);
+          sp_bulk_load(sb + lay.s, S + (int64_t)p0 * ldc, bo, &full_bar[s]);
           if (use_b) {
-            sp_bulk_load(sb + so.v, V + (int64_t)p0 * ldc, bo, &full_bar[s]);
-            sp_bulk_load(sb + so.h, H + (int64_t)p0 * ldc, bo, &full_bar[s]);
+            sp_bulk_load(sb + lay.v, V + (int64_t)p0 * ldc, bo, &full_bar[s]);
+            sp_bulk_load(sb + lay.h, H + (int64_t)p0 * ldc, bo, &full_bar[s]);
           }
-          sp_bulk_load(sb + so.sp, pairs + ea, bp, &full_bar[s]);
-          sp_bulk_load(sb + so.rp, rowptr + pa, br, &full_bar[s]);
+          sp_bulk_load(sb + lay.sp, pairs + ea, bp, &full_bar[s]);
+          sp_bulk_load(sb + lay.rp, rowptr + pa, br, &full_bar[s]);
         } else {
           sp_mbar_arrive(&full_bar[s]);
         }
         issued = k + 1;
       }
+      if (!ok) sp_flag(q.err);
       // no copy may still be in flight when the block exits: wait (bounded)
-      // for the last fill of every stage
-      for (int s = 0; s < nst && s < issued; ++s) {
-        const int klast = s + ((issued - 1 - s) / nst) * nst;
-        if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / nst) & 1u, q.err)) sp_flag(q.err);
+      // for the last fill of every slot
+      for (int s = 0; s < kSpSlots && s < issued; ++s) {
+        const int klast = s + ((issued - 1 - s) / kSpSlots) * kSpSlots;
+        if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / kSpSlots) & 1u, q.err)) sp_flag(q.err);
       }
     }
   } else {
@@ -480,23 +533,21 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     };
     int cnt = 0;
     for (int k = 0; k < nk; ++k) {
-      const int s = k % nst;
+      const int s = k % kSpSlots;
       // warp-uniform outcome (the flush shuffles need every lane)
-      if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / nst) & 1u, q.err))) {
+      if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / kSpSlots) & 1u, q.err))) {
         if (lane == 0) sp_flag(q.err);
         break;
       }
       const int* mt = smeta[s];
       const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3];
       const bool staged = mt[4] != 0;
-      const int dsc = mt[5], drp = mt[6];
-      const unsigned char* sb = smraw + (size_t)s * so.bytes;
-      const float4* zs = reinterpret_cast<const float4*>(sb);
-      const float4* ss = reinterpret_cast<const float4*>(sb + so.s);
-      const float4* vs = reinterpret_cast<const float4*>(sb + so.v);
-      const float4* hs = reinterpret_cast<const float4*>(sb + so.h);
-      const int2* sp = reinterpret_cast<const int2*>(sb + so.sp) + dsc;
-      const int64_t* rp = reinterpret_cast<const int64_t*>(sb + so.rp) + drp;
+      const float4* zs = reinterpret_cast<const float4*>(smraw + mt[7]);
+      const float4* ss = reinterpret_cast<const float4*>(smraw + mt[8]);
+      const float4* vs = reinterpret_cast<const float4*>(smraw + mt[9]);
+      const float4* hs = reinterpret_cast<const float4*>(smraw + mt[10]);
+      const int2* sp = reinterpret_cast<const int2*>(smraw + mt[11]) + mt[5];
+      const int64_t* rp = reinterpret_cast<const int64_t*>(smraw + mt[12]) + mt[6];
       for (int rbase = wib * R; rbase < nr; rbase += kSpConsumers * R) {
         const int r = rbase + slot;
         const bool on = lane_on && r < nr;
@@ -595,13 +646,12 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   finish_scalars(step, part, ldc, c, 0, q, &wdot[0][0]);
 }
 
-// launch shape of kv_spmm_tma for a block width: per-stage capacities (the
-// largest tile's rows and nonzeros up to 48 rows and 40 nonzeros per row;
-// rows of Z within what is left of the budget), three stages when they fit
-// the budget, else two, one block per SM
+// launch shape of kv_spmm_tma: the byte ring takes the shared-memory budget;
+// one block per SM.  The cap_* fields describe which tiles fit the ring (for
+// the self-test's count): a tile is staged when its layout fits.
 struct StagedLaunch {
-  int blocks = 0, cap_rows = 0, cap_nnz = 0, cap_trows = 0;
-  SpStage so{};
+  int blocks = 0;
+  SpRing ring{};
   size_t smem = 0;
 };
 constexpr size_t kSpSmemMax = 204 * 1024;
@@ -610,37 +660,14 @@ static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
       cudaFuncSetAttribute(kv_spmm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmemMax) ==
       cudaSuccess;
   (void)attr;
-  auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
-  auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
   StagedLaunch L;
-  // a tile beyond these capacities (a dense cluster of points) runs from global
-  // memory; the tiles of evenly spread points stay within them
-  L.cap_trows = (int)std::min<int64_t>(48, std::max<int64_t>(Hd.max_tile_rows, 1));
-  L.cap_nnz = (int)std::min<int64_t>((int64_t)L.cap_trows * 40, std::max<int64_t>(Hd.max_tile_nnz, 1));
-  const size_t row_bytes = (size_t)ldc * sizeof(float);
-  const size_t fixed = 3 * (size_t)L.cap_trows * row_bytes + r16((size_t)(L.cap_nnz + 2) * 8) +
-                       r16((size_t)(L.cap_trows + 4) * 8) + 256;
-  const int64_t want = std::max<int64_t>(Hd.max_staged, 1);
-  for (int nst = kSpMaxStages; nst >= 2; --nst) {
-    const size_t budget = kSpSmemMax / nst / 128 * 128;
-    const int64_t fit = budget > fixed ? (int64_t)((budget - fixed) / row_bytes) - 1 : 0;
-    L.cap_rows = (int)std::max<int64_t>(0, std::min<int64_t>(fit, want));
-    L.so.count = nst;
-    if (L.cap_rows >= want) break;
-  }
-  size_t off = r128((size_t)(L.cap_rows + 1) * row_bytes);   // one spare row (see the kernel)
-  L.so.s = (int)off; off += (size_t)L.cap_trows * row_bytes;
-  L.so.v = (int)off; off += (size_t)L.cap_trows * row_bytes;
-  L.so.h = (int)off; off += (size_t)L.cap_trows * row_bytes;
-  L.so.sp = (int)r16(off); off = L.so.sp + r16((size_t)(L.cap_nnz + 2) * 8);
-  L.so.rp = (int)off; off += r16((size_t)(L.cap_trows + 4) * 8);
-  L.so.bytes = (int)r128(off);
-  L.smem = (size_t)L.so.bytes * L.so.count;
+  L.ring.bytes = (int)kSpSmemMax;
+  L.smem = kSpSmemMax;
   int dev = 0, sms = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_tma, kSpThreads, L.smem);
-  L.blocks = (L.cap_rows > 0 && L.smem <= kSpSmemMax && per > 0) ? std::min(Hd.ntiles, sms * per) : 0;
+  L.blocks = per > 0 ? std::min(Hd.ntiles, sms * per) : 0;
   return L;
 }
 
@@ -835,8 +862,8 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
       FSA_CUDA(cudaEventRecord(e0, s));
     }
     kv_spmm_tma<<<std::min(L.blocks, lay.nblk), kSpThreads, L.smem, s>>>(
-        Hd.ntiles, Hd.ptile.p, Hd.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, L.so, lay.c, lay.ldc, Hd.rowptr.p,
-        Hd.col.p, Hd.op.pairs32.p, vals, Z, S, V, Hv, beta, part, step, q);
+        Hd.ntiles, Hd.ptile.p, Hd.tile_bad.p, L.ring, lay.c, lay.ldc, Hd.rowptr.p, Hd.col.p, Hd.op.pairs32.p, vals,
+        Z, S, V, Hv, beta, part, step, q);
     FSA_CHECK_LAUNCH();
     if (prof) {
       FSA_CUDA(cudaEventRecord(e1, s));
