@@ -170,6 +170,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(elapsed_ms, steps, world, dist=None, device="cpu"):
+    """Whole-job timing of a replicas run: the timed region's length is the
+    maximum over the ranks (every rank evaluates its own problem, the job ends
+    with the slowest), and the throughput counts the evaluations of all ranks.
+    Returns (max elapsed ms, evaluations per second of the job)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, world * steps / (elapsed_ms / 1000.0)
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -238,14 +251,10 @@ def run_gpu(args):
     launches = int(lib.fsa_launch_count() - l0)
     lib.fsa_profile_enable(0)
     clk = clocks.stop()
-    elapsed_ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
+    elapsed_ms, value = combine_ranks(e0.elapsed_time(e1), args.steps, world, dist, "cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = world * args.steps / (elapsed_ms / 1000.0)
     # dominant kernel: the per-iteration tensor-core GEMMs
     prof = {}
     for tag in ("pcg_Aq", "pcg_AtX", "pcg_spmm", "pcg_ur", "pcg_z", "pcg_split", "build", "grad"):
