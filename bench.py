@@ -313,6 +313,19 @@ def run_gpu(args):
         e2e_s = (time.perf_counter() - t0) / args.steps
         result["e2e"] = {"value": round(world / e2e_s, 4), "unit": "evals/s", "h2d_bytes_per_step": 8 * w.n,
                          "d2h_bytes_per_step": 8 * 4, "timing": "host wall clock around the C-ABI call"}
+    # kmeans++ selection of the workload's inducing points on the GPU (paper
+    # §4.1's choice; theta-free preprocessing, not part of the metric)
+    if rank == 0:
+        try:
+            F.kmeanspp(locs[:2048], 16, 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sel = F.kmeanspp(locs, w.m, w.seed)
+            dt = time.perf_counter() - t0
+            result["kmeanspp"] = {"n": w.n, "m": w.m, "seconds": round(dt, 4), "distinct": len(set(sel.tolist())) == w.m,
+                                  "timing": "host wall clock around fsa_kmeanspp (copy of the locations included)"}
+        except Exception as exc:   # reported in the line, the measurement above stands
+            result["kmeanspp"] = {"error": str(exc)[:200]}
     # the faster single-BF16 operator form (lower accuracy) on the same workload and probes
     if args.precision != "bf16" and not args.no_fp64 and rank == 0:
         opts1 = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=F.FSA_MIXED_BF16, seed=w.seed,

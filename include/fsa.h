@@ -208,6 +208,31 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta,
 void fsa_free(fsa_handle* h);
 
 /*
+ * fsa_kmeanspp — kmeans++ selection of m inducing points among the n
+ * locations (paper §4.1, which chooses its inducing points this way; seeding
+ * of Arthur & Vassilvitskii 2007): the first point uniformly, each further
+ * point with probability proportional to its squared distance to the nearest
+ * point chosen so far.  The weights are the integers floor(d^2 2^e), d^2 =
+ * dx*dx + dy*dy with every operation rounded on its own, e = 62 -
+ * bitlength(n) - ex where the squared bounding-box diagonal is f 2^ex, f in
+ * [0.5, 1) (so n weights sum below 2^62): sums are exact and the result is
+ * reproducible bit for bit.  Draw k is h_k = (SplitMix64 output k of seed,
+ * stream 9) >> 11: the first index is floor(h_0 n / 2^53), and step k picks
+ * the first index whose inclusive prefix sum of the weights exceeds
+ * floor(h_k Q / 2^53), Q their total.
+ *   locs       n x 2 row-major HOST array, 1 <= n < 2^31
+ *   m          1 <= m <= n
+ *   seed       draw seed
+ *   idx_out    receives the m chosen indices (caller order), caller-owned host array
+ *   cuda_stream a cudaStream_t (NULL: the legacy default stream)
+ * Returns FSA_OK; FSA_ERR_ARG for bad arguments or fewer than m distinct
+ * locations; FSA_ERR_OOM / FSA_ERR_CUDA on device failures.  Allocates and
+ * frees its device memory; synchronises the stream before returning.
+ */
+fsa_status fsa_kmeanspp(const double* locs, int64_t n, int32_t m, uint64_t seed, int64_t* idx_out,
+                        void* cuda_stream);
+
+/*
  * fsa_csr_noalloc — the taper-support pattern of fsa_build + fsa_get_csr
  * (same rows, same ascending columns, caller's point order), computed without
  * allocating any memory.  The paper has no counterpart: this entry point exists

@@ -47,6 +47,7 @@ GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
 STREAM_EPS2 = 4   # probe part on the n data points
 STREAM_EPS1 = 5   # probe part on the m inducing points
 STREAM_PRED = 6   # prediction-variance probes
+STREAM_KMEANSPP = 9   # kmeans++ selection of the inducing points
 
 
 # ----------------------------------------------------------------------------
@@ -180,6 +181,62 @@ def splitmix64(seed: int, stream: int, counters: np.ndarray) -> np.ndarray:
         c = counters.astype(np.uint64) + np.uint64(1)
         state = key + c * GOLDEN_GAMMA
     return _mix64(state)
+
+
+# ----------------------------------------------------------------------------
+# kmeans++ selection of inducing points (§4.1; Arthur & Vassilvitskii 2007)
+# ----------------------------------------------------------------------------
+
+def kmeanspp_scale_exponent(locs: np.ndarray) -> int:
+    """Exponent e of the integer D^2 weights floor(d^2 * 2^e): the squared
+    bounding-box diagonal times 2^e stays <= 2^B with B = 62 - bitlength(n),
+    so that n weights sum to less than 2^62."""
+    n = locs.shape[0]
+    dx = float(locs[:, 0].max() - locs[:, 0].min())
+    dy = float(locs[:, 1].max() - locs[:, 1].min())
+    diag2 = dx * dx + dy * dy
+    B = 62 - int(n).bit_length()
+    if diag2 == 0.0:
+        return B
+    _, ex = math.frexp(diag2)          # diag2 = f * 2^ex, f in [0.5, 1)
+    return B - ex
+
+
+def kmeanspp(locs: np.ndarray, m: int, seed: int) -> np.ndarray:
+    """Indices of m inducing points chosen by kmeans++ seeding (D^2 sampling):
+    the first point uniformly, each further point i with probability
+    proportional to its squared distance to the nearest point chosen so far.
+    Weights are the integers q_i = floor(d_i^2 2^e) (d^2 = dx*dx + dy*dy, each
+    operation rounded on its own; e from ``kmeanspp_scale_exponent``), so
+    sums are exact.  Draw k uses h_k = SplitMix64(seed, stream 9, counter k)
+    >> 11 (53 bits): the first index is floor(h_0 n / 2^53); step k picks the
+    first i whose inclusive prefix sum of q exceeds floor(h_k Q / 2^53), Q the
+    total.  Raises ValueError when fewer than m distinct locations exist."""
+    n = locs.shape[0]
+    if not (1 <= m <= n):
+        raise ValueError("need 1 <= m <= n")
+    e = kmeanspp_scale_exponent(locs)
+    h = splitmix64(seed, STREAM_KMEANSPP, np.arange(m, dtype=np.uint64)) >> np.uint64(11)
+    first = (int(h[0]) * n) >> 53
+    idx = [first]
+
+    def weights(c):
+        dx = locs[:, 0] - locs[c, 0]
+        dy = locs[:, 1] - locs[c, 1]
+        d2 = dx * dx + dy * dy
+        return np.floor(np.ldexp(d2, e)).astype(np.uint64)
+
+    q = weights(first)
+    for k in range(1, m):
+        cum = np.cumsum(q, dtype=np.uint64)
+        total = int(cum[-1])
+        if total == 0:
+            raise ValueError("fewer than m distinct locations")
+        target = (int(h[k]) * total) >> 53
+        i = int(np.searchsorted(cum, np.uint64(target), side="right"))
+        idx.append(i)
+        q = np.minimum(q, weights(i))
+    return np.array(idx, dtype=np.int64)
 
 
 def rademacher(seed: int, stream: int, rows: np.ndarray, nrows: int, ncols: int) -> np.ndarray:

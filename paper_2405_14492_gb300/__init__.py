@@ -51,6 +51,16 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
+def kmeanspp(locs, m: int, seed: int = 14492, stream=None) -> np.ndarray:
+    """Indices of m inducing points chosen among the locations by kmeans++
+    seeding on the GPU (``fsa_kmeanspp``; paper §4.1)."""
+    locs = _f64(locs).reshape(-1, 2)
+    n = locs.shape[0]
+    out = np.empty(int(m), dtype=np.int64)
+    N.check(N.lib().fsa_kmeanspp(locs.ctypes.data, n, int(m), int(seed), out.ctypes.data, stream))
+    return out
+
+
 class FSAHandle:
     """A built FSA problem: locations, inducing points, taper range, covariance
     family (``fsa_build``).  Owns its device memory; ``close()`` frees it."""

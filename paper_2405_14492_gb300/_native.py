@@ -109,6 +109,7 @@ def _declare(lib):
         "fsa_server_get_stats": (C.c_int, [P, C.POINTER(FsaServerStats)]),
         "fsa_server_destroy": (None, [P]),
         "fsa_pool_used_high": (C.c_int64, [C.c_int]),
+        "fsa_kmeanspp": (C.c_int, [P, C.c_int64, C.c_int32, C.c_uint64, P, P]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(lib, name):

@@ -67,6 +67,10 @@ def test_argument_errors_need_no_gpu(libpath):
     st = N.lib().fsa_build(N.ptr(locs), 10, N.ptr(bad), 3, 0.1, 0, None, ctypes.byref(h))
     assert st == 5
     assert b"inducing" in N.lib().fsa_last_error()
+    out = np.zeros(11, dtype=np.int64)
+    assert N.lib().fsa_kmeanspp(N.ptr(locs), 10, 11, 1, N.ptr(out), None) == 1   # m > n
+    assert N.lib().fsa_kmeanspp(N.ptr(locs), 10, 0, 1, N.ptr(out), None) == 1    # m < 1
+    assert b"kmeanspp" in N.lib().fsa_last_error()
 
 
 def test_struct_layouts_match_the_header(tmp_path, libpath):

@@ -409,3 +409,48 @@ def test_control_variate_copt_is_the_least_squares_coefficient():
         assert abs(out["c"][p] - slope) <= 1e-8 * (1 + abs(slope))
     # the plain estimate is the c = 0 member of the family
     assert np.allclose(plain["Dl"], a.mean(1), atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# kmeans++ selection of inducing points (§4.1)
+# --------------------------------------------------------------------------
+
+def test_kmeanspp_distinct_and_first_uniform():
+    locs = fi.uniform_locations(500, 21)
+    idx = O.kmeanspp(locs, 60, 3)
+    assert len(set(idx.tolist())) == 60                 # a chosen point has weight 0 afterwards
+    h0 = int(O.splitmix64(3, O.STREAM_KMEANSPP, np.arange(1, dtype=np.uint64))[0]) >> 11
+    assert idx[0] == (h0 * 500) >> 53
+    with pytest.raises(ValueError):                     # three distinct points cannot give four
+        O.kmeanspp(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 0.0]]), 4, 1)
+
+
+def test_kmeanspp_second_point_follows_d2_distribution():
+    """Over many seeds the second point is drawn with probability proportional
+    to its squared distance from the first (chi-square test, brute-force
+    expected counts from the definition of D^2 sampling)."""
+    locs = np.array([[0.0, 0.0], [0.1, 0.0], [0.3, 0.0], [0.6, 0.0], [1.0, 0.0]])
+    counts = np.zeros((5, 5))
+    for seed in range(6000):
+        a, b = O.kmeanspp(locs, 2, seed)
+        counts[a, b] += 1
+    for a in range(5):
+        d2 = (locs[:, 0] - locs[a, 0]) ** 2
+        if counts[a].sum() < 200:
+            continue
+        exp = counts[a].sum() * d2 / d2.sum()
+        keep = exp > 0
+        chi2 = np.sum((counts[a, keep] - exp[keep]) ** 2 / exp[keep])
+        assert st.chi2.sf(chi2, keep.sum() - 1) > 1e-4, (a, counts[a], exp)
+        assert counts[a, a] == 0
+
+
+def test_kmeanspp_integer_weights_are_exact_scaled_distances():
+    """With a power-of-two scale the integer weights are floor(d^2 2^e) exactly;
+    e keeps n * (bounding-box diagonal)^2 * 2^e below 2^62."""
+    locs = fi.uniform_locations(1000, 22)
+    e = O.kmeanspp_scale_exponent(locs)
+    dx = locs[:, 0].max() - locs[:, 0].min()
+    dy = locs[:, 1].max() - locs[:, 1].min()
+    assert 1000 * (dx * dx + dy * dy) * 2.0 ** e <= 2.0 ** 62
+    assert 1000 * (dx * dx + dy * dy) * 2.0 ** (e + 2) > 2.0 ** 62   # and is not needlessly small
