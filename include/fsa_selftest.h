@@ -72,6 +72,20 @@ int fsa_selftest_spmm(fsa_handle* h, const fsa_theta* theta, int ncols, uint64_t
 int fsa_selftest_sddmm(fsa_handle* h, const fsa_theta* theta, int precision, int ncols, int cap_rows, uint64_t seed,
                        double* val_err, double* grad_tile, double* grad_row);
 
+/*
+ * fsa_selftest_wait_timeout — failure detection without a GPU fault: a kernel
+ * waits on an mbarrier that nothing completes, with the bounded wait the
+ * library's pipelines use (at most `polls` try_wait polls, 1..2^20), gives up,
+ * records the timeout in an error word and returns; a second kernel then runs
+ * to show that the context is still usable.  (A self-test; the paper has no
+ * counterpart.)
+ *   kernel_finished  receives 1 when the waiting kernel ran to its end
+ *   context_usable   receives 1 when the kernel launched after it ran
+ * Returns FSA_ERR_TIMEOUT when the wait ran out (the expected outcome), FSA_OK
+ * if it did not, another fsa_status on error.  Legacy stream, current device.
+ */
+int fsa_selftest_wait_timeout(uint32_t polls, int* kernel_finished, int* context_usable);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,3 +106,67 @@ extern "C" int fsa_selftest_tc_gemm(int M, int N, int K, int num_a, int num_b, u
     return e.code;
   }
 }
+
+namespace fsa {
+
+// A wait that nothing completes: thread 0 initialises an mbarrier expecting one
+// arrival, nobody arrives, and the bounded wait gives up after `polls`
+// try_wait polls and records kErrTimeout (the same bounded-wait pattern as the
+// tensor-core and SpMM pipelines).  `done` is written afterwards, so the host
+// sees that the kernel ran to its end.
+__global__ void k_wait_nothing(uint32_t polls, unsigned* __restrict__ err, int* __restrict__ done) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1u) : "memory");
+    bool ok = false;
+    for (uint32_t i = 0; i < polls && !ok; ++i) {
+      uint32_t r;
+      asm volatile(
+          "{\n.reg .pred p;\n"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          "selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(r)
+          : "r"(a), "r"(0u)
+          : "memory");
+      ok = r != 0;
+    }
+    if (!ok) atomicOr(err, kErrTimeout);
+    *done = 1;
+  }
+}
+
+__global__ void k_write_one(int* __restrict__ v) { *v = 1; }
+
+}  // namespace fsa
+
+extern "C" int fsa_selftest_wait_timeout(uint32_t polls, int* kernel_finished, int* context_usable) {
+  if (!kernel_finished || !context_usable || polls < 1 || polls > (1u << 20)) {
+    set_error("fsa_selftest_wait_timeout: bad argument");
+    return FSA_ERR_ARG;
+  }
+  try {
+    cudaStream_t s = nullptr;
+    DevPtr<unsigned> err(1);
+    DevPtr<int> done(2);
+    FSA_CUDA(cudaMemset(err.p, 0, sizeof(unsigned)));
+    FSA_CUDA(cudaMemset(done.p, 0, 2 * sizeof(int)));
+    k_wait_nothing<<<1, 32, 0, s>>>(polls, err.p, done.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaDeviceSynchronize());
+    // the context is still usable: a second kernel runs and its result comes back
+    k_write_one<<<1, 1, 0, s>>>(done.p + 1);
+    FSA_CHECK_LAUNCH();
+    int h[2] = {0, 0};
+    unsigned herr = 0;
+    FSA_CUDA(cudaMemcpy(h, done.p, sizeof(h), cudaMemcpyDeviceToHost));
+    FSA_CUDA(cudaMemcpy(&herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost));
+    *kernel_finished = h[0];
+    *context_usable = h[1];
+    return (herr & kErrTimeout) ? FSA_ERR_TIMEOUT : FSA_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    set_error(e.msg);
+    return e.code;
+  }
+}
