@@ -47,6 +47,7 @@ GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
 STREAM_EPS2 = 4   # probe part on the n data points
 STREAM_EPS1 = 5   # probe part on the m inducing points
 STREAM_PRED = 6   # prediction-variance probes
+STREAM_FISHER = 7   # Fisher-information probes
 STREAM_KMEANSPP = 9   # kmeans++ selection of the inducing points
 
 
@@ -331,6 +332,27 @@ class DenseFSA:
             g[k] = -0.5 * (np.sum(Sinv * dS.T) - u @ dS @ u)
         return g
 
+    def dPhat(self, which: int) -> np.ndarray:
+        """dP_hat/dtheta for P_hat = D_s + Sigma_l (Eq. eqfitcp): the low-rank
+        derivative dSigma_l off the diagonal, d(Sigma_ii) on it (the taper is 1
+        there, so dD_s,i = dSigma_ii - dSigma_l,ii); the identity for the nugget."""
+        s1, rho, nug = self.theta
+        n = self.locs.shape[0]
+        if which == 2:
+            return np.eye(n)
+        dK = dcov_matrix(self.inducing, self.locs, self.nu, s1, rho, which)
+        dSm = dcov_matrix(self.inducing, self.inducing, self.nu, s1, rho, which)
+        dSig_diag = np.diag(dcov_matrix(self.locs, self.locs, self.nu, s1, rho, which))
+        SmK = np.linalg.solve(self.Sm, self.K)
+        dSl = dK.T @ SmK + SmK.T @ dK - SmK.T @ dSm @ SmK
+        return dSl + np.diag(dSig_diag - np.diag(dSl))
+
+    def fisher(self) -> np.ndarray:
+        """Exact Fisher information (appendix "Fisher scoring"):
+        I_kl = 1/2 tr(Sdag^-1 dSdag_k Sdag^-1 dSdag_l)."""
+        X = [np.linalg.solve(self.Sdag, self.dSdag(k)) for k in range(3)]
+        return np.array([[0.5 * np.sum(X[k] * X[l].T) for l in range(3)] for k in range(3)])
+
     # -- exact FSA predictive distribution (§2.3, Eq. MuPredFSA) -------------
     def cross(self, pred):
         """Sigma^dag_{n,np} = Sigma^l_{n,np} + (Sigma_{n,np} - Sigma^l_{n,np}) o T_{n,np}."""
@@ -528,10 +550,73 @@ class IterativeFSA:
         dSs = sp.csr_matrix((dvals, self.col, self.rowptr), shape=(self.n, self.n))
         return dSs @ V + dSl_V
 
+    def _dlowrank(self, which):
+        """dSigma_mn, dSigma_m and C = Sigma_m^-1 Sigma_mn for theta[which] < 2."""
+        s1, rho, nug = self.theta
+        dK = dcov_matrix(self.inducing, self.locs, self.nu, s1, rho, which)
+        dSm = dcov_matrix(self.inducing, self.inducing, self.nu, s1, rho, which)
+        C = sla.cho_solve((self.Lm, True), self.K)
+        return dK, dSm, C
+
+    def dD(self, which):
+        """dD_s/dtheta: dSigma_ii - dSigma_l,ii per point (the taper is 1 on the
+        diagonal), 1 for the nugget; dSigma_l,ii = 2 dk_i.c_i - c_i.(dSigma_m c_i)."""
+        if which == 2:
+            return np.ones(self.n)
+        s1, rho, nug = self.theta
+        dK, dSm, C = self._dlowrank(which)
+        dsig0 = 1.0 if which == 0 else 0.0          # d(s1 r(0)) with r(0) = 1
+        dl = 2.0 * np.einsum("ij,ij->j", dK, C) - np.einsum("ij,ij->j", C, dSm @ C)
+        return dsig0 - dl
+
+    def dP_apply(self, which, V):
+        """dP_hat/dtheta V = dD_s V + dSigma_l V (Eq. eqfitcp differentiated),
+        dSigma_l = dK^T Sm^-1 K + K^T Sm^-1 dK - K^T Sm^-1 dSm Sm^-1 K."""
+        V = np.asarray(V, np.float64)
+        dD = self.dD(which)
+        out = dD[:, None] * V if V.ndim == 2 else dD * V
+        if which == 2:
+            return out
+        dK, dSm, C = self._dlowrank(which)
+        return out + dK.T @ (C @ V) + C.T @ (dK @ V) - C.T @ (dSm @ (C @ V))
+
+    def trace_Pinv_dP(self, which):
+        """Tr(P_hat^-1 dP_hat/dtheta) in O(n m^2) (appendix "Runtime of the FITC
+        preconditioner": like the log-determinant): Jacobi's formula applied to
+        the Sylvester identity logdet P_hat = logdet M_P - logdet Sigma_m + logdet D_s,
+            Tr(M_P^-1 dM_P) - Tr(Sigma_m^-1 dSigma_m) + sum_i dD_i / D_i,
+        dM_P = dSigma_m + dK D^-1 K^T + K D^-1 dK^T - K diag(dD / D^2) K^T."""
+        dD = self.dD(which)
+        K, D = self.K, self.D
+        dMp = -(K * (dD / D ** 2)) @ K.T
+        tr_m = 0.0
+        if which < 2:
+            dK, dSm, _ = self._dlowrank(which)
+            KdK = (K / D) @ dK.T
+            dMp += dSm + KdK + KdK.T
+            tr_m = float(np.trace(sla.cho_solve((self.Lm, True), dSm)))
+        return float(np.trace(sla.cho_solve((self.Lp, True), dMp))) - tr_m + float(np.sum(dD / D))
+
     def loglik_grad(self, y, num_probes, seed, tol, max_iter=1000, fixed_iters=0,
-                    probe="rademacher", exact_weight=False, want_grad=True, Z=None):
+                    probe="rademacher", exact_weight=False, want_grad=True, Z=None,
+                    control_variate=None):
         """Log-likelihood by preconditioned SLQ (§3.3) and gradient by STE (§3.3).
-        ``Z`` replaces the random probes (used by deterministic checks)."""
+        ``Z`` replaces the random probes (used by deterministic checks).
+
+        ``control_variate`` ("copt" or "c1") uses the preconditioner as control
+        variate in the trace estimate (appendix "Preconditioner as control
+        variate", Eq. Troptc): per parameter, with a_k = U_k^T dSdag W_k (the
+        plain STE term) and b_k = W_k^T dP_hat W_k (W = P_hat^-1 Z),
+            Tr(Sdag^-1 dSdag) ~ (1/l) sum_k (a_k - c b_k) + c Tr(P_hat^-1 dP_hat),
+        c = c_opt = sum_k (a_k - mean a) b_k / sum_k b_k^2 (as printed; 0 where
+        sum_k b_k^2 = 0), c = 1 ("c1"), or ("copt_centered") the variance-
+        minimising slope sum_k (a_k - mean a)(b_k - mean b) / sum_k (b_k - mean b)^2
+        (0 where the denominator vanishes).  The printed denominator is not
+        centred: where mean b dominates the spread of b, as it does here
+        (mean b estimates Tr(P_hat^-1 dP_hat)), the printed c_opt is near 0 and
+        the estimate is close to the plain one."""
+        if control_variate not in (None, "copt", "copt_centered", "c1"):
+            raise ValueError("control_variate must be None, 'copt', 'copt_centered' or 'c1'")
         n = self.n
         if Z is None:
             Z = self.probes(num_probes, seed, probe)
@@ -553,16 +638,61 @@ class IterativeFSA:
             W = res["Z0"][:, 1:]                # P^-1 z
             g = np.zeros(3)
             g_terms = np.zeros((3, num_probes))
+            cv_c, cv_terms, trace_P = np.zeros(3), np.zeros((3, num_probes)), np.zeros(3)
             for k in range(3):
                 dW = self.dS_apply(k, np.column_stack([W, u]))
                 per_probe = np.einsum("ij,ij->j", U, dW[:, :num_probes])
                 tr = float(np.mean(per_probe))
+                if control_variate is not None:
+                    b = np.einsum("ij,ij->j", W, self.dP_apply(k, W))
+                    trace_P[k] = self.trace_Pinv_dP(k)
+                    if control_variate == "c1":
+                        c = 1.0
+                    elif control_variate == "copt":
+                        den = float(np.sum(b * b))
+                        c = float(np.sum((per_probe - tr) * b)) / den if den > 0 else 0.0
+                    else:
+                        bc = b - np.mean(b)
+                        den = float(np.sum(bc * bc))
+                        c = float(np.sum((per_probe - tr) * bc)) / den if den > 0 else 0.0
+                    tr = float(np.mean(per_probe - c * b)) + c * trace_P[k]
+                    cv_c[k], cv_terms[k] = c, b
                 qf = float(u @ dW[:, num_probes])
                 g[k] = -0.5 * (tr - qf)
                 g_terms[k] = per_probe
             out["grad"] = g
             out["grad_terms"] = g_terms
+            if control_variate is not None:
+                out["cv_c"], out["cv_terms"], out["trace_P"] = cv_c, cv_terms, trace_P
         return out
+
+    # -- Fisher information by STE (appendix "Fisher scoring") ---------------
+    def fisher_ste(self, num_probes, seed, tol, max_iter=1000, probe="rademacher", Z=None):
+        """I_kl = 1/2 Tr(Sdag^-1 dSdag_k Sdag^-1 dSdag_l) estimated by STE:
+            1/2 (1/l) sum_i (z_i^T Sdag^-1 dSdag_k)(Sdag^-1 dSdag_l z_i),
+        z_i with E[z z^T] = I (Rademacher or Gaussian, stream 7; ``Z`` replaces
+        them).  The solves Sdag^-1 z_i and Sdag^-1 dSdag_l z_i run as one block of
+        FITC-preconditioned CG (Appendix A); z_i^T Sdag^-1 dSdag_k is
+        (dSdag_k Sdag^-1 z_i)^T.  Returns the estimate as printed ("fisher_raw",
+        not symmetric for finite l) and its symmetric part ("fisher")."""
+        n = self.n
+        if Z is None:
+            draw = rademacher if probe == "rademacher" else gaussian
+            Z = draw(seed, STREAM_FISHER, np.arange(n), n, num_probes)
+        l = Z.shape[1]
+        # right-hand sides z_i, dSdag_0 z_i, dSdag_1 z_i (dSdag_2 = I: no solve)
+        B = np.column_stack([Z, self.dS_apply(0, Z), self.dS_apply(1, Z)])
+        res = pcg_lanczos(self.apply, self.apply_Pinv, B, tol, max_iter)
+        V = res["U"][:, :l]
+        X = [res["U"][:, l:2 * l], res["U"][:, 2 * l:], V]
+        terms = np.empty((3, 3, l))
+        for k in range(3):
+            dV = self.dS_apply(k, V)
+            for j in range(3):
+                terms[k, j] = 0.5 * np.einsum("ij,ij->j", dV, X[j])
+        F = terms.mean(axis=2)
+        return dict(fisher=0.5 * (F + F.T), fisher_raw=F, terms=terms, iters=res["iters"],
+                    converged=res["converged"], Z=Z)
 
     # -- predictive distribution (§2.3 and Algorithm 1) ----------------------
     def cross_structures(self, pred):

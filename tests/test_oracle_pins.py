@@ -412,6 +412,160 @@ def test_control_variate_copt_is_the_least_squares_coefficient():
 
 
 # --------------------------------------------------------------------------
+# preconditioner derivative and the gradient control variate (appendix
+# "Preconditioner as control variate", Eq. Troptc)
+# --------------------------------------------------------------------------
+
+def test_fitc_derivative_and_trace_match_finite_differences():
+    """dP_hat from central differences of the dense P_hat(theta); the O(n m^2)
+    Tr(P_hat^-1 dP_hat) from Jacobi's formula d logdet P_hat (central
+    differences of a dense slogdet) and from a dense solve."""
+    locs, ind, g, nu, th = _problem(n=90, m=11, nu=1.5)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    V = np.random.default_rng(14).standard_normal((90, 3))
+    for k in range(3):
+        h = 1e-5 * th[k]
+        tp = list(th); tp[k] += h
+        tm = list(th); tm[k] -= h
+        Pp, Pm = O.DenseFSA(locs, ind, g, nu, tp).Phat, O.DenseFSA(locs, ind, g, nu, tm).Phat
+        dP = D.dPhat(k)
+        assert np.max(np.abs((Pp - Pm) / (2 * h) - dP)) < 1e-7 * max(1.0, np.max(np.abs(dP)))
+        assert np.allclose(It.dP_apply(k, V), dP @ V, rtol=1e-11, atol=1e-11)
+        tr = It.trace_Pinv_dP(k)
+        jac = (np.linalg.slogdet(Pp)[1] - np.linalg.slogdet(Pm)[1]) / (2 * h)
+        assert abs(tr - jac) < 1e-7 * max(1.0, abs(tr))
+        assert abs(tr - np.trace(np.linalg.solve(D.Phat, dP))) < 1e-10 * max(1.0, abs(tr))
+
+
+def test_gradient_control_variate_with_full_basis_probes_stays_exact():
+    """With probes z_i = sqrt(n) L e_i (P_hat = L L^T) the mean of
+    b_i = z_i^T P^-1 dP P^-1 z_i is exactly Tr(P_hat^-1 dP_hat), so every
+    control-variate coefficient leaves the STE gradient exact."""
+    locs, ind, g, nu, th = _problem(n=70, m=9, nu=1.5, theta=(0.9, 0.2, 0.15), gamma=0.15)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    y = np.random.default_rng(6).standard_normal(70)
+    Z = math.sqrt(70) * np.linalg.cholesky(D.Phat)
+    gd = D.grad(y)
+    for cv in ("c1", "copt", "copt_centered"):
+        out = It.loglik_grad(y, 70, 0, 1e-13, max_iter=400, Z=Z, control_variate=cv)
+        assert np.allclose(out["grad"], gd, rtol=1e-7, atol=1e-8)
+        assert np.allclose(out["trace_P"], [np.trace(np.linalg.solve(D.Phat, D.dPhat(k))) for k in range(3)],
+                           rtol=1e-9)
+
+
+def test_gradient_control_variate_c1_exact_when_fsa_equals_fitc():
+    """gamma below every pair distance: Sigma_dag = P_hat for every theta, so
+    a_i = b_i and the c = 1 estimate is Tr(P_hat^-1 dP_hat) = Tr(Sdag^-1 dSdag)
+    for any probes; the plain estimate is not."""
+    locs, ind, _, nu, th = _problem(n=80, m=10)
+    It = O.IterativeFSA(locs, ind, 1e-6, nu, th)
+    D = O.DenseFSA(locs, ind, 1e-6, nu, th)
+    y = np.random.default_rng(3).standard_normal(80)
+    gd = D.grad(y)
+    out = It.loglik_grad(y, 5, 1, 1e-12, control_variate="c1")
+    assert np.allclose(out["grad"], gd, rtol=1e-9, atol=1e-9)
+    plain = It.loglik_grad(y, 5, 1, 1e-12)
+    assert np.max(np.abs(plain["grad"] - gd)) > 1e-3
+
+
+def test_gradient_control_variate_coefficients_are_least_squares_slopes():
+    """Per parameter, with a_i = U_i^T dSdag W_i and b_i = W_i^T dP_hat W_i
+    built from dense solves: c_opt as printed is the slope of (a - mean a) on b
+    through the origin; the centred coefficient is the ordinary least-squares
+    slope of a on b (intercept free)."""
+    locs, ind, g, nu, th = _problem(n=150, m=20)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    y = np.random.default_rng(15).standard_normal(150)
+    l = 12
+    Z = It.probes(l, 21)
+    U = np.linalg.solve(D.Sdag, Z)
+    W = np.linalg.solve(D.Phat, Z)
+    o1 = It.loglik_grad(y, l, 21, 1e-12, Z=Z, control_variate="copt")
+    o2 = It.loglik_grad(y, l, 21, 1e-12, Z=Z, control_variate="copt_centered")
+    for k in range(3):
+        a = np.einsum("ij,ij->j", U, D.dSdag(k) @ W)
+        b = np.einsum("ij,ij->j", W, D.dPhat(k) @ W)
+        c1 = np.linalg.lstsq(b[:, None], a - a.mean(), rcond=None)[0][0]
+        c2 = np.polyfit(b, a, 1)[0]
+        assert abs(o1["cv_c"][k] - c1) <= 1e-6 * (1 + abs(c1))
+        assert abs(o2["cv_c"][k] - c2) <= 1e-6 * (1 + abs(c2))
+
+
+def test_gradient_control_variate_c1_unbiased_with_reduced_error():
+    """Over 40 probe seeds of 10 probes each, the c = 1 gradient stays within
+    4 standard errors of the exact gradient, and its error in the range
+    derivative is well below that of the plain STE (§4: the FITC control
+    variate reduces the variance of the gradient estimate)."""
+    locs, ind, g, nu, th = _problem(n=400, m=25, gamma=0.08)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    y = np.linalg.cholesky(D.Sdag) @ np.random.default_rng(9).standard_normal(400)
+    gd = D.grad(y)
+    cv = np.array([It.loglik_grad(y, 10, s, 1e-10, control_variate="c1")["grad"] for s in range(40)])
+    plain = np.array([It.loglik_grad(y, 10, s, 1e-10)["grad"] for s in range(40)])
+    se = cv.std(axis=0, ddof=1) / math.sqrt(40)
+    assert np.all(np.abs(cv.mean(axis=0) - gd) < 4 * se)
+    rmse = lambda a: np.sqrt(np.mean((a - gd) ** 2, axis=0))
+    assert rmse(cv)[1] < 0.5 * rmse(plain)[1]
+
+
+# --------------------------------------------------------------------------
+# Fisher information by STE (appendix "Fisher scoring")
+# --------------------------------------------------------------------------
+
+def test_dense_fisher_is_the_expected_negative_hessian():
+    """I = -Hessian of E_y[l(theta; y)] = -1/2 [logdet Sdag(theta) +
+    tr(Sdag(theta)^-1 Sdag(theta0))] + const at theta0 (y ~ N(0, Sdag(theta0))),
+    by central second differences of dense slogdet / solve; the nugget entry is
+    1/2 sum_i 1/lambda_i^2 over the eigenvalues of Sdag."""
+    locs, ind, g, nu, th = _problem(n=64, m=8, nu=1.5, theta=(0.9, 0.2, 0.15), gamma=0.15)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    F = D.fisher()
+    lam = np.linalg.eigvalsh(D.Sdag)
+    assert abs(F[2, 2] - 0.5 * np.sum(lam ** -2.0)) < 1e-10 * F[2, 2]
+
+    def f(t):
+        S = O.DenseFSA(locs, ind, g, nu, t).Sdag
+        return -0.5 * (np.linalg.slogdet(S)[1] + np.trace(np.linalg.solve(S, D.Sdag)))
+
+    for k in range(3):
+        for j in range(3):
+            hk, hj = 1e-3 * th[k], 1e-3 * th[j]
+
+            def at(a, b):
+                t = list(th); t[k] += a; t[j] += b
+                return f(t)
+
+            hess = (at(hk, hj) - at(hk, -hj) - at(-hk, hj) + at(-hk, -hj)) / (4 * hk * hj)
+            assert abs(-hess - F[k, j]) < 2e-5 * np.max(np.abs(F))
+
+
+def test_fisher_ste_with_hadamard_probes_is_exact():
+    """Sylvester-Hadamard probes (entries +-1, H H^T = n I) make the STE sum
+    the exact trace, so the estimate equals the dense Fisher information."""
+    locs, ind, g, nu, th = _problem(n=64, m=8, nu=1.5, theta=(0.9, 0.2, 0.15), gamma=0.15)
+    F = O.DenseFSA(locs, ind, g, nu, th).fisher()
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    out = It.fisher_ste(64, 0, 1e-12, Z=sla.hadamard(64).astype(np.float64))
+    assert np.allclose(out["fisher_raw"], F, rtol=1e-9, atol=1e-9)
+    assert np.allclose(out["fisher"], F, rtol=1e-9, atol=1e-9)
+
+
+def test_fisher_ste_random_probes_within_standard_error():
+    locs, ind, g, nu, th = _problem(n=400, m=25, gamma=0.08)
+    F = O.DenseFSA(locs, ind, g, nu, th).fisher()
+    out = O.IterativeFSA(locs, ind, g, nu, th).fisher_ste(100, 3, 1e-10)
+    assert set(np.unique(out["Z"])) == {-1.0, 1.0}
+    se = out["terms"].std(axis=2, ddof=1) / math.sqrt(100)
+    assert np.all(np.abs(out["fisher_raw"] - F) < 4 * se)
+    assert np.allclose(out["fisher"], out["fisher"].T)
+    assert np.all(np.linalg.eigvalsh(out["fisher"]) > 0)
+
+
+# --------------------------------------------------------------------------
 # kmeans++ selection of inducing points (§4.1)
 # --------------------------------------------------------------------------
 
