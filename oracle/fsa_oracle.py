@@ -33,6 +33,13 @@ design notes of the repository):
     with Sigma_m = L L^T, so that the sample has covariance P_hat.
   * SLQ weight: the paper's n / l (exact weight z^T P^-1 z as an option).
   * CG stop: absolute ||r||_2 < tol on the unpreconditioned residual, u0 = 0.
+  * Gradient control variate (appendix "Preconditioner as control variate"):
+    P = P_hat; the clamp of the residual diagonal is not differentiated.  The
+    printed c_opt (uncentred denominator) and the centred least-squares slope
+    are both available, as is c = 1.
+  * Fisher information by STE (appendix "Fisher scoring"): probes with
+    E[z z^T] = I, no preconditioner in the estimate, symmetric part returned
+    beside the raw estimate.
 """
 from __future__ import annotations
 
