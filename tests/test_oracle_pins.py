@@ -411,6 +411,24 @@ def test_control_variate_copt_is_the_least_squares_coefficient():
     assert np.allclose(plain["Dl"], a.mean(1), atol=1e-10)
 
 
+def test_iteration_trends_in_m_with_and_without_fitc():
+    """§4 (Table 1 and the iteration figure): with the FITC preconditioner CG
+    needs far fewer iterations than without, and the count falls as m grows,
+    while without a preconditioner it rises (effective range 0.2)."""
+    n = 2000
+    locs = fi.uniform_locations(n, 11)
+    b = np.random.default_rng(1).standard_normal((n, 1))
+    fitc, none = [], []
+    for m in (10, 40, 160):
+        ind = locs[fi.inducing_subset(n, m, 11)].copy()
+        It = O.IterativeFSA(locs, ind, 0.05, 0.5, (1.0, 0.2 / 3, 0.05))
+        fitc.append(int(O.pcg_lanczos(It.apply, It.apply_Pinv, b, 1e-6, 5000)["iters"][0]))
+        none.append(int(O.pcg_lanczos(It.apply, lambda V: V.copy(), b, 1e-6, 5000)["iters"][0]))
+    assert fitc[0] > fitc[1] > fitc[2]
+    assert none[0] < none[1] < none[2]
+    assert all(f < 0.75 * u for f, u in zip(fitc, none))
+
+
 # --------------------------------------------------------------------------
 # preconditioner derivative and the gradient control variate (appendix
 # "Preconditioner as control variate", Eq. Troptc)
@@ -468,6 +486,26 @@ def test_gradient_control_variate_c1_exact_when_fsa_equals_fitc():
     assert np.allclose(out["grad"], gd, rtol=1e-9, atol=1e-9)
     plain = It.loglik_grad(y, 5, 1, 1e-12)
     assert np.max(np.abs(plain["grad"] - gd)) > 1e-3
+
+
+def test_ste_gradient_euler_homogeneity_with_the_same_probes():
+    """Sdag and P_hat are homogeneous of degree 1 in (s1, nugget), so
+    s1 dSdag_0 + nug dSdag_2 = Sdag and s1 dP_0 + nug dP_2 = P_hat: the plain
+    STE gives s1 g_0 + nug g_2 = -1/2 (mean_k z_k^T P^-1 z_k - y^T u), the c = 1
+    control variate the exact -1/2 (n - y^T u), and
+    s1 Tr(P^-1 dP_0) + nug Tr(P^-1 dP_2) = n."""
+    locs, ind, g, nu, th = _problem(n=300, m=20, gamma=0.1)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    y = np.random.default_rng(4).standard_normal(300)
+    plain = It.loglik_grad(y, 8, 5, 1e-11)
+    cv = It.loglik_grad(y, 8, 5, 1e-11, control_variate="c1")
+    Z = plain["Z"]
+    zPz = float(np.mean(np.einsum("ij,ij->j", Z, np.linalg.solve(D.Phat, Z))))
+    lhs = lambda gr: th[0] * gr[0] + th[2] * gr[2]
+    assert abs(lhs(plain["grad"]) + 0.5 * (zPz - plain["quad"])) < 1e-8 * 300
+    assert abs(lhs(cv["grad"]) + 0.5 * (300 - cv["quad"])) < 1e-8 * 300
+    assert abs(lhs(cv["trace_P"]) - 300) < 1e-9 * 300
 
 
 def test_gradient_control_variate_coefficients_are_least_squares_slopes():
