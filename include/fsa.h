@@ -40,13 +40,13 @@ extern "C" {
 typedef enum {
   FSA_OK = 0,
   FSA_ERR_ARG = 1,             /* invalid argument (size, pointer, parameter) */
-  FSA_ERR_OOM = 2,             /* device memory could not be allocated / admitted */
+  FSA_ERR_OOM = 2,             /* device (or host) memory could not be allocated / admitted */
   FSA_ERR_NOT_PD = 3,          /* a Cholesky pivot <= 0 (Sigma_m or the Woodbury core) */
   FSA_ERR_NO_CONVERGENCE = 4,  /* CG hit its iteration limit; outputs still written */
   FSA_ERR_NAN = 5,             /* a non-finite input or intermediate */
   FSA_ERR_TIMEOUT = 6,         /* a bounded device or host wait ran out */
   FSA_ERR_BUSY = 7,            /* serving: result not ready yet */
-  FSA_ERR_CUDA = 8,            /* a CUDA runtime error */
+  FSA_ERR_CUDA = 8,            /* a CUDA runtime error, or another system error (a thread that could not start) */
   FSA_ERR_UNSUPPORTED = 9      /* option not available on this device / build */
 } fsa_status;
 

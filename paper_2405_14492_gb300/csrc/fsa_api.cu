@@ -12,6 +12,15 @@ namespace fsa {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+fsa_status fail_host_exception(const char* where, const std::exception& e) {
+  const bool oom = dynamic_cast<const std::bad_alloc*>(&e) != nullptr;
+  try {
+    set_error(std::string(where) + (oom ? ": host memory could not be allocated: " : ": ") + e.what());
+  } catch (...) {
+  }
+  return oom ? FSA_ERR_OOM : FSA_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // stream-ordered allocation: per-thread stream, pool configured once per device
 // ---------------------------------------------------------------------------
@@ -236,7 +245,7 @@ fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int3
     return fail(e);
   } catch (const std::exception& e) {
     fsa_free(hh);
-    return fail(Error{FSA_ERR_CUDA, e.what()});
+    return fail_host_exception("fsa_build", e);
   }
 }
 
@@ -250,6 +259,8 @@ fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col) {
     return FSA_OK;
   } catch (const Error& e) {
     return fail(e);
+  } catch (const std::exception& e) {
+    return fail_host_exception("fsa_get_csr", e);
   }
 }
 
@@ -310,6 +321,10 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
     cudaGetLastError();
     cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
     return fail(e);
+  } catch (const std::exception& e) {
+    cudaGetLastError();
+    cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
+    return fail_host_exception("fsa_loglik_grad", e);
   }
 }
 
@@ -335,6 +350,9 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
   } catch (const Error& e) {
     cudaGetLastError();
     return fail(e);
+  } catch (const std::exception& e) {
+    cudaGetLastError();
+    return fail_host_exception("fsa_matvec", e);
   }
 }
 
@@ -352,7 +370,11 @@ fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t pre
     *out = sc[2];
     return FSA_OK;
   } catch (const Error& e) {
+    cudaGetLastError();
     return fail(e);
+  } catch (const std::exception& e) {
+    cudaGetLastError();
+    return fail_host_exception("fsa_logdet_precond", e);
   }
 }
 
@@ -407,6 +429,10 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
     cudaGetLastError();
     cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
     return fail(e);
+  } catch (const std::exception& e) {
+    cudaGetLastError();
+    cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream);
+    return fail_host_exception("fsa_predict", e);
   }
 }
 

@@ -6,6 +6,8 @@
 
 #include <cmath>
 #include <cstdio>
+#include <exception>
+#include <new>
 #include <string>
 
 #include "../../include/fsa.h"
@@ -21,6 +23,11 @@ struct Error {
   fsa_status code;
   std::string msg;
 };
+
+// Status for a host-side exception other than Error (std::bad_alloc from a host
+// container -> FSA_ERR_OOM, anything else, e.g. a thread that could not be
+// started -> FSA_ERR_CUDA); records the message like set_error.
+fsa_status fail_host_exception(const char* where, const std::exception& e);
 
 #define FSA_CUDA(call)                                                            \
   do {                                                                            \

@@ -221,5 +221,8 @@ extern "C" fsa_status fsa_kmeanspp(const double* locs, int64_t n, int32_t m, uin
     cudaGetLastError();
     set_error(e.msg);
     return e.code;
+  } catch (const std::exception& e) {
+    cudaGetLastError();
+    return fail_host_exception("fsa_kmeanspp", e);
   }
 }

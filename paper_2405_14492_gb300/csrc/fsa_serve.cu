@@ -190,6 +190,39 @@ struct fsa_server {
   }
 };
 
+// the part of fsa_serve_submit that copies the request (host allocations)
+static fsa_status submit_job(fsa_server* S, const fsa_request* q, uint64_t* ticket) {
+  auto j = std::make_unique<Job>();
+  j->req = *q;
+  j->locs.assign(q->locs, q->locs + 2 * q->n);
+  j->inducing.assign(q->inducing, q->inducing + 2 * (int64_t)q->m);
+  j->y.assign(q->y, q->y + q->n);
+  const double nnz = 1.25 * expected_pairs(j->locs, q->n, nullptr, 0, q->taper_range);
+  if (q->kind == FSA_REQ_LOGLIK_GRAD) {
+    j->footprint = fsa_footprint_bytes(q->n, q->m, (int64_t)nnz, q->opts.num_probes, q->opts.precision);
+  } else {
+    j->pred.assign(q->pred_locs, q->pred_locs + 2 * q->n_p);
+    const double cross = 1.25 * expected_pairs(j->locs, q->n, &j->pred, q->n_p, q->taper_range);
+    j->footprint = predict_footprint(q->n, q->m, (int64_t)nnz, q->n_p, q->var ? q->num_var_samples : 0,
+                                     (int64_t)cross);
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (j->footprint > S->budget) {
+    set_error("request footprint " + std::to_string(j->footprint) + " bytes exceeds the server budget " +
+              std::to_string(S->budget));
+    return FSA_ERR_OOM;
+  }
+  if (S->stop) { set_error("server is shutting down"); return FSA_ERR_ARG; }
+  j->ticket = S->next_ticket++;
+  j->t_submit = S->now_ms();
+  if (S->first_submit < 0) S->first_submit = j->t_submit;
+  *ticket = j->ticket;
+  S->pending.push_back(std::move(j));
+  S->submitted++;
+  S->cv_work.notify_one();
+  return FSA_OK;
+}
+
 extern "C" {
 
 void fsa_default_server_cfg(fsa_server_cfg* c) {
@@ -232,7 +265,12 @@ fsa_status fsa_server_create(const fsa_server_cfg* cfg, fsa_server** out) {
       return FSA_ERR_CUDA;
     }
   }
-  for (int k = 0; k < c.max_slots; ++k) S->workers.emplace_back([S, k] { S->worker(k); });
+  try {
+    for (int k = 0; k < c.max_slots; ++k) S->workers.emplace_back([S, k] { S->worker(k); });
+  } catch (const std::exception& e) {
+    fsa_server_destroy(S);   // joins the workers that did start, destroys the streams
+    return fail_host_exception("fsa_server_create", e);
+  }
   *out = S;
   return FSA_OK;
 }
@@ -249,35 +287,11 @@ fsa_status fsa_serve_submit(fsa_server* S, const fsa_request* q, uint64_t* ticke
     set_error("prediction needs pred_locs, n_p >= 1 and mean");
     return FSA_ERR_ARG;
   }
-  auto j = std::make_unique<Job>();
-  j->req = *q;
-  j->locs.assign(q->locs, q->locs + 2 * q->n);
-  j->inducing.assign(q->inducing, q->inducing + 2 * (int64_t)q->m);
-  j->y.assign(q->y, q->y + q->n);
-  const double nnz = 1.25 * expected_pairs(j->locs, q->n, nullptr, 0, q->taper_range);
-  if (q->kind == FSA_REQ_LOGLIK_GRAD) {
-    j->footprint = fsa_footprint_bytes(q->n, q->m, (int64_t)nnz, q->opts.num_probes, q->opts.precision);
-  } else {
-    j->pred.assign(q->pred_locs, q->pred_locs + 2 * q->n_p);
-    const double cross = 1.25 * expected_pairs(j->locs, q->n, &j->pred, q->n_p, q->taper_range);
-    j->footprint = predict_footprint(q->n, q->m, (int64_t)nnz, q->n_p, q->var ? q->num_var_samples : 0,
-                                     (int64_t)cross);
+  try {
+    return submit_job(S, q, ticket);
+  } catch (const std::exception& e) {
+    return fail_host_exception("fsa_serve_submit", e);
   }
-  std::lock_guard<std::mutex> lk(S->mu);
-  if (j->footprint > S->budget) {
-    set_error("request footprint " + std::to_string(j->footprint) + " bytes exceeds the server budget " +
-              std::to_string(S->budget));
-    return FSA_ERR_OOM;
-  }
-  if (S->stop) { set_error("server is shutting down"); return FSA_ERR_ARG; }
-  j->ticket = S->next_ticket++;
-  j->t_submit = S->now_ms();
-  if (S->first_submit < 0) S->first_submit = j->t_submit;
-  *ticket = j->ticket;
-  S->pending.push_back(std::move(j));
-  S->submitted++;
-  S->cv_work.notify_one();
-  return FSA_OK;
 }
 
 static fsa_status take_result(fsa_server* S, uint64_t ticket, fsa_result* out) {
