@@ -264,6 +264,29 @@ def test_slq_and_ste_with_full_basis_probes_are_exact():
     assert np.allclose(out["grad"], D.grad(y), rtol=1e-7, atol=1e-8)
 
 
+def test_slq_exact_weight_with_an_unequal_norm_tight_frame_is_exact():
+    """Probes z_i = L v_i (P_hat = L L^T) whose v_i form a tight frame,
+    (1/l) sum v_i v_i^T = I, with unequal norms: at full convergence the
+    exact-weight SLQ sum (1/l) sum |v_i|^2 e_1^T log(T_i) e_1 is exactly
+    tr log(L^-1 Sdag L^-T), so the log-determinant is exact, while the paper's
+    weight n is not (the norms differ)."""
+    n, l = 60, 120
+    locs, ind, g, nu, th = _problem(n=n, m=8, nu=1.5, theta=(0.9, 0.2, 0.15), gamma=0.15)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    V0 = np.random.default_rng(3).standard_normal((n, l))
+    w, Q = np.linalg.eigh(V0 @ V0.T)
+    V = math.sqrt(l) * (Q / np.sqrt(w)) @ Q.T @ V0
+    assert np.allclose(V @ V.T / l, np.eye(n), atol=1e-12)
+    Z = np.linalg.cholesky(D.Phat) @ V
+    y = np.random.default_rng(6).standard_normal(n)
+    _, logdet, _ = D.loglik(y)
+    ew = It.loglik_grad(y, l, 0, 1e-13, max_iter=400, Z=Z, exact_weight=True, want_grad=False)
+    assert abs(ew["logdet"] - logdet) < 1e-9 * abs(logdet)
+    nw = It.loglik_grad(y, l, 0, 1e-13, max_iter=400, Z=Z, want_grad=False)
+    assert abs(nw["logdet"] - logdet) > 1e-3
+
+
 def test_dense_gradient_matches_central_differences():
     locs, ind, g, nu, th = _problem(n=80, m=10, nu=0.5)
     y = np.random.default_rng(7).standard_normal(80)
