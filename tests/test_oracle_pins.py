@@ -371,6 +371,27 @@ def test_algorithm1_random_probes_unbiased_within_tolerance():
     assert np.all(np.abs(out["var"] - var) <= 5 * sd + 1e-9)
 
 
+def test_algorithm1_gaussian_probes_unbiased_with_the_gaussian_variance():
+    """Gaussian probes: z_j (A z)_j has mean A_jj and variance
+    sum_k A_jk^2 + A_jj^2 (E z^4 = 3), so each point's D_l error stays within 5
+    of those standard deviations and their root mean square over the points is
+    near 1 (Algorithm 1 with N(0, I) probes)."""
+    locs, ind, g, nu, th = _problem(n=200, m=20)
+    pred = fi.uniform_locations(60, 4, stream=7)
+    y = np.random.default_rng(12).standard_normal(200)
+    D = O.DenseFSA(locs, ind, g, nu, th)
+    It = O.IterativeFSA(locs, ind, g, nu, th)
+    _, var = D.predict(y, pred)
+    s = 400
+    out = It.predict(y, pred, s, 78, 1e-12, probe="gaussian")
+    _, _, Ssnp, _ = D.cross(pred)
+    Amat = Ssnp.T @ np.linalg.solve(D.Ss, Ssnp)
+    sd = np.sqrt((np.sum(Amat ** 2, 1) + np.diag(Amat) ** 2) / s)
+    zsc = (out["var"] - var) / sd
+    assert np.all(np.abs(zsc) <= 5)
+    assert 0.6 < np.sqrt(np.mean(zsc ** 2)) < 1.5
+
+
 def test_control_variate_with_full_basis_probes_stays_exact():
     """With probes sqrt(s) e_j the sample mean of b_k = z_k o (S P_s^-1 S^T z_k)
     equals diag(S P_s^-1 S^T) exactly, so the control-variate estimator of D_l
