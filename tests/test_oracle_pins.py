@@ -35,6 +35,34 @@ def test_splitmix64_published_vectors():
     assert got == want
 
 
+def test_counter_based_splitmix64_equals_the_sequential_generator():
+    """Value k of the counter-based form is output k + 1 of the sequential
+    SplitMix64 generator (state += golden gamma, then mix) started at the
+    stream key, and a Rademacher entry is 1 - 2 * (top bit of that output),
+    at counter column * rows + row."""
+    M64 = (1 << 64) - 1
+    gam = int(O.GOLDEN_GAMMA)
+
+    def mix(z):
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        return z ^ (z >> 31)
+
+    for seed, stream in ((0, 0), (14492, 4), (2**63 + 5, 9)):
+        state = mix(seed ^ ((stream * gam) & M64))
+        seq = []
+        for _ in range(12):
+            state = (state + gam) & M64
+            seq.append(mix(state))
+        got = O.splitmix64(seed, stream, np.arange(12, dtype=np.uint64))
+        assert [int(v) for v in got] == seq
+    z = O.rademacher(14492, 4, np.arange(3), 3, 4)
+    h = O.splitmix64(14492, 4, np.arange(12, dtype=np.uint64))
+    for r in range(3):
+        for k in range(4):
+            assert z[r, k] == 1.0 - 2.0 * float(int(h[k * 3 + r]) >> 63)
+
+
 def test_rademacher_balance_and_independence():
     z = O.rademacher(3, O.STREAM_EPS2, np.arange(4000), 4000, 8)
     assert set(np.unique(z)) == {-1.0, 1.0}
