@@ -57,10 +57,19 @@ def test_counter_based_splitmix64_equals_the_sequential_generator():
         got = O.splitmix64(seed, stream, np.arange(12, dtype=np.uint64))
         assert [int(v) for v in got] == seq
     z = O.rademacher(14492, 4, np.arange(3), 3, 4)
-    h = O.splitmix64(14492, 4, np.arange(12, dtype=np.uint64))
+    h = O.splitmix64(14492, 4, np.arange(24, dtype=np.uint64))
     for r in range(3):
         for k in range(4):
             assert z[r, k] == 1.0 - 2.0 * float(int(h[k * 3 + r]) >> 63)
+    # Gaussian entry (r, k): Box-Muller of the outputs at counters 2c and 2c + 1,
+    # c = k * rows + r, with u = ((h >> 11) + 1) 2^-53
+    g = O.gaussian(14492, 4, np.arange(3), 3, 4)
+    for r in range(3):
+        for k in range(4):
+            c = k * 3 + r
+            u1 = ((int(h[2 * c]) >> 11) + 1) * 2.0 ** -53
+            u2 = ((int(h[2 * c + 1]) >> 11) + 1) * 2.0 ** -53
+            assert abs(g[r, k] - math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)) < 1e-14
 
 
 def test_rademacher_balance_and_independence():
@@ -131,6 +140,23 @@ def test_neighbour_csr_brute_force_vs_tree_bit_exact():
     assert all((j, i) in S for (i, j) in S)
     # nothing missed: count pairs inside the radius by brute force
     assert len(S) == int(np.sum(O.sqdist(pts, pts) < g * g))
+
+
+def test_neighbour_support_is_strict_at_exact_ties():
+    """§2.1: the taper is zero for d >= gamma, so pairs at distance exactly
+    gamma are not in the support.  On a lattice of spacing gamma = 1/8 (exact
+    binary fractions, so d^2 = gamma^2 holds exactly) each point has itself as
+    its only neighbour, in both the brute-force and the tree path; at
+    gamma * (1 + 2^-20) the four lattice neighbours join."""
+    g = 0.125
+    xs = np.arange(12) * g
+    pts = np.array([(x, y) for y in xs for x in xs])
+    for limit in (10 ** 8, 1):
+        rowptr, col = O.neighbour_csr(pts, pts, g, brute_force_limit=limit)
+        assert np.array_equal(col, np.arange(len(pts)))
+        rowptr, col = O.neighbour_csr(pts, pts, g * (1 + 2.0 ** -20), brute_force_limit=limit)
+        deg = np.diff(rowptr)
+        assert deg.max() == 5 and deg.min() == 3 and int(deg.sum()) == 144 + 2 * 2 * 11 * 12
 
 
 def test_neighbour_count_matches_paper_taper_choice():
