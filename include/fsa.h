@@ -146,7 +146,10 @@ int64_t fsa_nnz(const fsa_handle* h);
 
 /*
  * fsa_get_csr — the taper pattern in the caller's point order, columns
- * ascending: rowptr (n+1, int64) and col (nnz, int32) host arrays.
+ * ascending: rowptr (n+1, int64) and col (nnz, int32) host arrays, both
+ * caller-owned and sized by the caller (nnz from fsa_nnz).  Synchronises the
+ * handle's stream.
+ * Errors: FSA_ERR_ARG (NULL argument), FSA_ERR_OOM, FSA_ERR_CUDA.
  */
 fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col);
 
@@ -176,15 +179,22 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
  * (paper §3.1: Sigma_dag v = Sigma_s~ v + Sigma_mn^T Sigma_m^-1 Sigma_mn v;
  * appendix "Runtime of the FITC preconditioner": P_hat^-1 v by Woodbury).
  *   which   0: Sigma_dag v, 1: P_hat^-1 v, 2: Sigma_s~ v (sparse part only)
- *   v, out  n x k row-major host arrays, caller's point order
- * Uses the operator built for theta with the given precision.
+ *   v, out  n x k row-major host arrays (k >= 1), caller's point order,
+ *           caller-owned
+ * Uses the operator built for theta with the given precision (built on first
+ * use and cached in the handle for an unchanged theta and precision).
+ * Synchronises the handle's stream.
+ * Errors: FSA_ERR_ARG (NULL pointer, k < 1, which outside 0..2, bad theta or
+ * precision), FSA_ERR_NOT_PD, FSA_ERR_NAN, FSA_ERR_OOM, FSA_ERR_CUDA.
  */
 fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, int32_t which,
                       const double* v, int32_t k, double* out);
 
 /*
  * fsa_logdet_precond — log det P_hat by Sylvester's theorem (appendix
- * "Runtime of the FITC preconditioner") for theta at the given precision.
+ * "Runtime of the FITC preconditioner") for theta at the given precision;
+ * *out receives it.  Builds (or reuses) the operator like fsa_matvec.
+ * Errors: FSA_ERR_ARG, FSA_ERR_NOT_PD, FSA_ERR_NAN, FSA_ERR_OOM, FSA_ERR_CUDA.
  */
 fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t precision,
                               double* out);
@@ -199,6 +209,12 @@ fsa_status fsa_logdet_precond(fsa_handle* h, const fsa_theta* theta, int32_t pre
  * Linear solves: FITC-PCG for Sigma_dag^-1 y; D_s-preconditioned block CG
  * for Sigma_s~^-1 [Sigma_mn^T, S z_1..z_s]; Sigma_dag^-1 Sigma_mn^T by the exact
  * identity W2 M^-1 Sigma_m with M = Sigma_m + Sigma_mn W2 (Woodbury).
+ * Computed in the FP64 form (opts->precision must be FSA_FP64).
+ * Errors: FSA_ERR_ARG (NULL pointer, n_p < 1, num_var_samples outside
+ * [1, 4096] when var is given, bad theta or options), FSA_ERR_UNSUPPORTED
+ * (a mixed precision), FSA_ERR_NOT_PD, FSA_ERR_NO_CONVERGENCE (outputs
+ * written), FSA_ERR_NAN (non-finite prediction locations), FSA_ERR_OOM,
+ * FSA_ERR_CUDA.
  */
 fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta,
                        const fsa_opts* opts, const double* pred_locs, int64_t n_p,
