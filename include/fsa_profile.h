@@ -20,6 +20,19 @@
  *   "pcg_split" D^-1 R -> BF16 pieces, transposed   (block read, pieces written)
  * Timing adds one event pair per GEMM launch; it is meant for measurement
  * runs.  Not thread-safe across concurrent callers.
+ *
+ * Phase ranges (NVTX 3, always on, a few nanoseconds each without a tool):
+ *   "fsa_build", "fsa_loglik_grad", "fsa_predict", "fsa_matvec", "fsa_kmeanspp"
+ *                       one per C-ABI call
+ *   "operator_build"    the theta-dependent build (Sigma_m, A, residual values,
+ *                       D_s, Woodbury core), when theta or precision changed
+ *   "probes", "pcg", "slq_gradient"
+ *                       the phases of a mixed-precision log-likelihood
+ *   "loglik_grad_fp64"  the whole FP64-form solve
+ *   "serve_loglik_grad", "serve_predict"
+ *                       one request of the serving loop
+ * `ncu --nvtx --nvtx-include "pcg/"` captures only the CG loop's kernels.
+ * A toolkit without the NVTX 3 headers builds the library without ranges.
  */
 #ifndef FSA_PROFILE_H_
 #define FSA_PROFILE_H_

@@ -216,6 +216,7 @@ fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int3
   for (int32_t k = 0; k < 2 * m; ++k)
     if (!std::isfinite(inducing[k])) return fail(Error{FSA_ERR_NAN, "non-finite inducing point"});
   fsa_handle* hh = nullptr;
+  TraceRange trace("fsa_build");
   try {
     hh = new fsa_handle();
     Handle& H = hh->h;
@@ -278,6 +279,7 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
+  TraceRange trace("fsa_loglik_grad");
   try {
     FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
     H.y.ensure(H.n);
@@ -335,6 +337,7 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
   if (precision < FSA_FP64 || precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
+  TraceRange trace("fsa_matvec");
   try {
     ensure_operator(H, *theta, precision);
     size_t nk = (size_t)H.n * k;
@@ -393,6 +396,7 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
     return fail(Error{FSA_ERR_ARG, "pred_control_variate must be 0, 1 or 2"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
+  TraceRange trace("fsa_predict");
   try {
     FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
     H.y.ensure(H.n);

@@ -12,7 +12,35 @@
 
 #include "../../include/fsa.h"
 
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define FSA_HAVE_NVTX 1
+#endif
+#endif
+
 namespace fsa {
+
+// Named range around one phase of a call (an NVTX push/pop pair, header-only
+// NVTX 3): profilers that record NVTX show the phases on the timeline, and
+// `ncu --nvtx --nvtx-include "<name>/"` restricts a capture to the kernels
+// of one phase.  Without an attached tool a range costs a few nanoseconds.
+struct TraceRange {
+  explicit TraceRange(const char* name) {
+#ifdef FSA_HAVE_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~TraceRange() {
+#ifdef FSA_HAVE_NVTX
+    nvtxRangePop();
+#endif
+  }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // host-side error plumbing

@@ -187,6 +187,7 @@ extern "C" fsa_status fsa_kmeanspp(const double* locs, int64_t n, int32_t m, uin
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   AllocStreamScope scope(s);
+  TraceRange trace("fsa_kmeanspp");
   try {
     const int nb = (int)((n + kKppChunk - 1) / kKppChunk);
     DevPtr<double2> p(n), center(1);

@@ -13,6 +13,8 @@
 //   vector to ~2^-16 relative.  Vectors are FP32; CG scalars, dot-product
 //   accumulation, the m x m Cholesky factors / inverse and the Lanczos
 //   eigen-quadrature are FP64.
+#include <memory>
+
 #include "fsa_kernels.cuh"
 #include "fsa_solver.cuh"
 #include "fsa_tc.cuh"
@@ -749,6 +751,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   const Vec4Launch v4z = vec4_launch(lay, reinterpret_cast<const void*>(kv4_z_update));
   // probes: R = [y, A~ eps1 + D^1/2 eps2]
   {
+    TraceRange trace("probes");
     int l16 = round_up(l, 16);
     DevPtr<__nv_bfloat16> Ehi((size_t)l16 * C.m_pad), Elo((size_t)l16 * C.m_pad);
     DevPtr<float> Zp((size_t)n * l16);
@@ -770,6 +773,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
   }
+  auto pcg_trace = std::make_unique<TraceRange>("pcg");
   FSA_CUDA(cudaMemsetAsync(g.U32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
@@ -806,6 +810,8 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       if (*pin_active == 0) break;
     }
   }
+  pcg_trace.reset();
+  TraceRange slq_grad_trace("slq_gradient");
   // the Lanczos eigen-quadrature depends only on the tridiagonals: it runs on
   // the side stream (one thread per probe column) beside the gradient work
   if (!H.side) {

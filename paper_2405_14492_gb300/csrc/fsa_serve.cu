@@ -126,6 +126,7 @@ struct fsa_server {
     r.kind = j.req.kind;
     r.slot = slot;
     r.footprint_bytes = j.footprint;
+    TraceRange trace(j.req.kind == FSA_REQ_LOGLIK_GRAD ? "serve_loglik_grad" : "serve_predict");
     fsa_handle* h = nullptr;
     fsa_status st = fsa_build(j.locs.data(), j.req.n, j.inducing.data(), j.req.m, j.req.taper_range, j.req.cov, s, &h);
     if (st == FSA_OK) {

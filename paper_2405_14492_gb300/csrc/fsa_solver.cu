@@ -456,6 +456,7 @@ void ensure_operator(Handle& H, const fsa_theta& th, int precision) {
       op.theta.nugget == th.nugget)
     return;
   op.valid = false;
+  TraceRange trace("operator_build");
   if (precision == FSA_FP64) build_operator_fp64(H, th);
   else build_operator_mixed(H, th, precision);
   check_err(H);
@@ -620,7 +621,10 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
 
 LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o) {
   ensure_operator(H, th, o.precision);
-  if (o.precision == FSA_FP64) return run_loglik_grad_fp64(H, th, o);
+  if (o.precision == FSA_FP64) {
+    TraceRange trace("loglik_grad_fp64");
+    return run_loglik_grad_fp64(H, th, o);
+  }
   return run_loglik_grad_mixed(H, th, o);
 }
 
