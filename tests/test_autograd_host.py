@@ -1,0 +1,83 @@
+"""Host logic of the ``FSALogLik`` torch.autograd.Function, on the CPU.
+
+The Function only marshals: forward calls ``handle.loglik_grad`` and keeps the
+gradient, backward returns grad_output times it.  Here the handle is a stand-in
+whose log-likelihood and gradient are the dense oracle's exact ones (Eq.
+NEGLLDNEGLLFSA), so the checks below isolate the wrapper: the value and
+gradient it passes on, the chain rule through a reparameterisation, and
+agreement with central finite differences of step 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fsa_inputs as fi
+import paper_2405_14492_gb300 as F
+from oracle import fsa_oracle as O
+
+
+class DenseHandle:
+    """Duck-typed stand-in for FSAHandle backed by the dense oracle."""
+
+    def __init__(self, locs, inducing, gamma, nu):
+        self.args = (locs, inducing, gamma, nu)
+        self.calls = 0
+
+    def loglik_grad(self, y, theta, opts=None):
+        self.calls += 1
+        D = O.DenseFSA(*self.args, tuple(float(t) for t in theta))
+        return D.loglik(y)[0], D.grad(y), {"status": 0}
+
+
+@pytest.fixture(scope="module")
+def problem():
+    n, m = 120, 15
+    locs = fi.uniform_locations(n, 71)
+    ind = locs[fi.inducing_subset(n, m, 71)].copy()
+    y = np.random.default_rng(71).standard_normal(n)
+    return DenseHandle(locs, ind, 0.12, 1.5), y, (0.9, 0.15, 0.2)
+
+
+def test_forward_value_and_backward_gradient(problem):
+    h, y, th = problem
+    theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    ll = F.FSALogLik.apply(theta, h, y)
+    assert ll.dtype == torch.float64 and ll.dim() == 0
+    D = O.DenseFSA(*h.args, th)
+    assert ll.item() == D.loglik(y)[0]
+    (2.5 * ll).backward()
+    assert np.array_equal(theta.grad.numpy(), 2.5 * D.grad(y))
+
+
+def test_chain_rule_matches_central_differences_in_log_parameters(problem):
+    """An optimiser's view: phi = log theta, loss = -l(exp(phi)) / n; the
+    autograd gradient equals central differences of step 1e-4 in phi."""
+    h, y, th = problem
+    n = y.shape[0]
+    phi = torch.tensor(np.log(th), dtype=torch.float64, requires_grad=True)
+    loss = -F.FSALogLik.apply(torch.exp(phi), h, y) / n
+    loss.backward()
+
+    def f(p):
+        return -O.DenseFSA(*h.args, tuple(np.exp(p))).loglik(y)[0] / n
+
+    p0 = np.log(th)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1e-4
+        fd = (f(p0 + e) - f(p0 - e)) / 2e-4
+        assert abs(float(phi.grad[k]) - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_gradcheck_and_one_handle_call_per_forward(problem):
+    h, y, th = problem
+    theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    before = h.calls
+    assert torch.autograd.gradcheck(lambda t: F.FSALogLik.apply(t, h, y), (theta,), eps=1e-5, atol=1e-4,
+                                    rtol=1e-4)
+    # gradcheck's forward evaluations each call the handle exactly once
+    assert h.calls > before
+    before = h.calls
+    ll = F.FSALogLik.apply(theta, h, y)
+    ll.backward()
+    assert h.calls == before + 1

@@ -145,3 +145,23 @@ def test_error_paths(fsa):
         with pytest.raises(fsa.FsaError) as e:
             h.loglik_grad(y, (1.0, 0.1, 0.1))
         assert e.value.status == 3
+
+
+def test_autograd_function_passes_the_kernel_gradient(fsa):
+    """FSALogLik with a real handle: forward gives the C-ABI log-likelihood and
+    backward its STE gradient (same probes and fixed-order reductions, so the
+    same values), which match the oracle's under the same probes."""
+    import torch
+    locs, ind = _setup(2000, 50, 0.5, 0.05, 41)
+    th = (1.0, 0.1, 0.1)
+    y = fi.random_field(locs, 0.5, *th, 41)
+    opts = fsa.make_opts(num_probes=8, fixed_iters=15, seed=5)
+    with fsa.FSAHandle(locs, ind, 0.05, 0.5) as h:
+        ll0, g0, _ = h.loglik_grad(y, th, opts)
+        theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+        ll = fsa.FSALogLik.apply(theta, h, y, opts)
+        ll.backward()
+    assert abs(ll.item() - ll0) <= 1e-12 * abs(ll0)
+    assert np.allclose(theta.grad.numpy(), g0, rtol=1e-12, atol=0.0)
+    ref = O.IterativeFSA(locs, ind, 0.05, 0.5, th).loglik_grad(y, 8, 5, 0.0, fixed_iters=15)
+    assert _rel(theta.grad.numpy(), ref["grad"]) < 1e-6
