@@ -383,6 +383,13 @@ class DenseFSA:
         return mu, var
 
 
+def fisher_scoring_step(theta, grad, fisher):
+    """One Fisher-scoring update (appendix "Fisher scoring"):
+    theta + I^-1 dl/dtheta, with l the log-likelihood (so the step ascends l)."""
+    return np.asarray(theta, np.float64) + np.linalg.solve(np.asarray(fisher, np.float64),
+                                                          np.asarray(grad, np.float64))
+
+
 # ----------------------------------------------------------------------------
 # Iterative mode (the paper's algorithms, step by step)
 # ----------------------------------------------------------------------------

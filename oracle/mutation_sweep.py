@@ -147,6 +147,9 @@ MUTATIONS = [
     ("Fisher STE: solves of parameters 0 and 1 swapped",
      'X = [res["U"][:, l:2 * l], res["U"][:, 2 * l:], V]', 'X = [res["U"][:, 2 * l:], res["U"][:, l:2 * l], V]',
      None),
+    ("Fisher scoring descends instead of ascending",
+     "return np.asarray(theta, np.float64) + np.linalg.solve(", "return np.asarray(theta, np.float64) - np.linalg.solve(",
+     None),
     ("dense Fisher without the transpose", "        return np.array([[0.5 * np.sum(X[k] * X[l].T)",
      "        return np.array([[0.5 * np.sum(X[k] * X[l])", None),
 ]

@@ -701,6 +701,30 @@ def test_fisher_ste_random_probes_within_standard_error():
     assert np.all(np.linalg.eigvalsh(out["fisher"]) > 0)
 
 
+def test_fisher_scoring_converges_to_the_maximum_likelihood_estimate():
+    """Fisher scoring with the dense gradient and Fisher information reaches
+    the maximiser of the dense log-likelihood found independently by L-BFGS-B
+    (the optimiser of §4), from a start 20-30 % off in every parameter."""
+    n, m = 150, 20
+    locs = fi.uniform_locations(n, 81)
+    ind = locs[fi.inducing_subset(n, m, 81)].copy()
+    g, nu, th0 = 0.15, 1.5, (1.0, 0.1, 0.1)
+    y = np.linalg.cholesky(O.DenseFSA(locs, ind, g, nu, th0).Sdag) @ np.random.default_rng(81).standard_normal(n)
+
+    def negll(p):
+        D = O.DenseFSA(locs, ind, g, nu, tuple(np.exp(p)))
+        return -D.loglik(y)[0], -D.grad(y) * np.exp(p)
+
+    r = so.minimize(negll, np.log(th0), jac=True, method="L-BFGS-B",
+                    options=dict(ftol=1e-15, gtol=1e-10, maxiter=500))
+    mle = np.exp(r.x)
+    th = mle * np.array([1.3, 0.8, 1.2])
+    for _ in range(15):
+        D = O.DenseFSA(locs, ind, g, nu, tuple(th))
+        th = O.fisher_scoring_step(th, D.grad(y), D.fisher())
+    assert np.max(np.abs(th / mle - 1)) < 1e-6
+
+
 # --------------------------------------------------------------------------
 # kmeans++ selection of inducing points (§4.1)
 # --------------------------------------------------------------------------
