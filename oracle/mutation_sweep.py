@@ -12,6 +12,7 @@ The working tree is never modified: every run happens in its own temporary
 directory.
 
     python oracle/mutation_sweep.py            # all entries (several minutes)
+    python oracle/mutation_sweep.py -j 8       # eight copies at once
     python oracle/mutation_sweep.py -k taper   # entries whose label contains "taper"
 
 Exit status 0 when every non-equivalent mistake is caught and every
@@ -25,6 +26,7 @@ import shutil
 import subprocess
 import sys
 import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -166,8 +168,12 @@ def _copy_tree(dst):
         shutil.copy(os.path.join(ROOT, f), os.path.join(dst, f))
 
 
-def run_one(label, old, new):
+def run_one(label, old, new, threads=None):
     """'caught', 'passed' or 'not found' for one planted mistake."""
+    env = dict(os.environ)
+    if threads:
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
     with tempfile.TemporaryDirectory(prefix="oracle_mut_") as tmp:
         _copy_tree(tmp)
         path = os.path.join(tmp, "oracle", "fsa_oracle.py")
@@ -178,19 +184,21 @@ def run_one(label, old, new):
         with open(path, "w") as f:
             f.write(src.replace(old, new, 1))
         r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
-                            "-p", "no:cacheprovider"], cwd=tmp, capture_output=True, text=True)
+                            "-p", "no:cacheprovider"], cwd=tmp, capture_output=True, text=True, env=env)
         return "passed" if r.returncode == 0 else "caught"
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("-k", default="", help="run only entries whose label contains this text")
+    ap.add_argument("-j", type=int, default=1, help="copies run at once (BLAS threads are divided among them)")
     args = ap.parse_args()
+    todo = [e for e in MUTATIONS if not args.k or args.k in e[0]]
+    threads = max(1, (os.cpu_count() or 1) // args.j) if args.j > 1 else None
+    with ThreadPoolExecutor(max_workers=max(1, args.j)) as ex:
+        results = list(ex.map(lambda e: run_one(e[0], e[1], e[2], threads), todo))
     bad = 0
-    for label, old, new, equivalent in MUTATIONS:
-        if args.k and args.k not in label:
-            continue
-        got = run_one(label, old, new)
+    for (label, old, new, equivalent), got in zip(todo, results):
         want = "passed" if equivalent else "caught"
         ok = got == want
         bad += not ok
