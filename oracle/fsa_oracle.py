@@ -40,6 +40,10 @@ design notes of the repository):
   * Fisher information by STE (appendix "Fisher scoring"): probes with
     E[z z^T] = I, no preconditioner in the estimate, symmetric part returned
     beside the raw estimate.
+  * Vecchia with the FITC preconditioner (§5): conditioning on the nearest
+    earlier points in the given order; Eq. VL_v2 as printed is not an
+    identity, and the posterior solve uses
+    (Sigma_V^-1 + W)^-1 = Sigma_V (Sigma_V + W^-1)^-1 W^-1 with the same system.
 """
 from __future__ import annotations
 
@@ -48,6 +52,7 @@ import math
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401  (sp.linalg.spsolve_triangular)
 
 LOG2PI = math.log(2.0 * math.pi)
 GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -381,6 +386,109 @@ class DenseFSA:
         mu = C.T @ sla.cho_solve(c, y)
         var = s1 + nug - np.sum(C * sla.cho_solve(c, C), axis=0)
         return mu, var
+
+
+class VecchiaFITC:
+    """A Vecchia approximation of the latent GP with a Gaussian likelihood,
+    solved by CG under the FITC preconditioner (§5, "The FITC preconditioner
+    for Vecchia approximations").
+
+    Vecchia: in the given order, N(i) holds the min(m_v, i - 1) nearest of the
+    earlier points (squared distances as in ``sqdist``, ties to the lower
+    index), A_i = Sigma_{N(i),i}^T Sigma_{N(i)}^-1, D_i = Sigma_ii -
+    A_i Sigma_{N(i),i}; B is unit lower triangular with B_{i,N(i)} = -A_i, and
+    Sigma_V^-1 = B^T D^-1 B.  With the Gaussian likelihood W = I / nugget, the
+    response has covariance Sigma_V + W^-1.  FITC: P_hat = Sigma_mn^T
+    Sigma_m^-1 Sigma_mn + D_s with D_s = diag(Sigma - Sigma_mn^T Sigma_m^-1
+    Sigma_mn) + W^-1 (the residual diagonal clamped at 0), applied by Woodbury
+    with the core M_P = Sigma_m + Sigma_mn D_s^-1 Sigma_nm."""
+
+    def __init__(self, locs, inducing, m_v, nu, theta):
+        self.locs = np.asarray(locs, np.float64)
+        self.inducing = np.asarray(inducing, np.float64)
+        self.nu, self.m_v = float(nu), int(m_v)
+        self.theta = tuple(float(t) for t in theta)
+        s1, rho, nug = self.theta
+        n = self.n = self.locs.shape[0]
+        rows, cols, vals = list(range(n)), list(range(n)), [1.0] * n
+        self.D = np.empty(n)
+        self.N = []
+        for i in range(n):
+            k = min(self.m_v, i)
+            if k == 0:
+                Ni = np.zeros(0, dtype=np.int64)
+            else:
+                d2 = sqdist(self.locs[i:i + 1], self.locs[:i])[0]
+                Ni = np.sort(np.argsort(d2, kind="stable")[:k])
+            self.N.append(Ni)
+            if k == 0:
+                self.D[i] = s1
+                continue
+            SNN = cov_matrix(self.locs[Ni], self.locs[Ni], nu, s1, rho)
+            SNi = cov_matrix(self.locs[Ni], self.locs[i:i + 1], nu, s1, rho)[:, 0]
+            Ai = np.linalg.solve(SNN, SNi)
+            self.D[i] = s1 - float(Ai @ SNi)
+            rows += [i] * k
+            cols += Ni.tolist()
+            vals += (-Ai).tolist()
+        self.B = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+        self.BT = self.B.T.tocsr()
+        # FITC preconditioner (the same construction as Eq. eqfitcp, nugget as W^-1)
+        self.K = cov_matrix(self.inducing, self.locs, nu, s1, rho)
+        self.Lm = np.linalg.cholesky(cov_matrix(self.inducing, self.inducing, nu, s1, rho))
+        Al = sla.solve_triangular(self.Lm, self.K, lower=True)              # m x n
+        self.Ds = np.maximum(s1 - np.sum(Al * Al, axis=0), 0.0) + nug
+        self.Lp = np.linalg.cholesky(self.Lm @ self.Lm.T + (self.K / self.Ds) @ self.K.T)
+        self.logdet_P = (2.0 * np.sum(np.log(np.diag(self.Lp))) - 2.0 * np.sum(np.log(np.diag(self.Lm)))
+                         + float(np.sum(np.log(self.Ds))))
+
+    def apply_SigmaV(self, V):
+        """Sigma_V V = B^-1 D B^-T V (two sparse triangular solves)."""
+        X = sp.linalg.spsolve_triangular(self.BT, V, lower=False)
+        X = X * (self.D[:, None] if X.ndim == 2 else self.D)
+        return sp.linalg.spsolve_triangular(self.B, X, lower=True)
+
+    def apply(self, V):
+        """(Sigma_V + W^-1) V, the response covariance."""
+        return self.apply_SigmaV(V) + self.theta[2] * V
+
+    def apply_Pinv(self, V):
+        """P_hat^-1 V by Woodbury."""
+        V = np.asarray(V)
+        Ds = self.Ds[:, None] if V.ndim == 2 else self.Ds
+        DV = V / Ds
+        return DV - (self.K.T @ sla.cho_solve((self.Lp, True), self.K @ DV)) / Ds
+
+    def probes(self, num_probes, seed):
+        """z = Sigma_mn^T L_m^-T eps1 + D_s^1/2 eps2 ~ (0, P_hat), Rademacher eps
+        (streams 5 and 4)."""
+        e1 = rademacher(seed, STREAM_EPS1, np.arange(self.inducing.shape[0]), self.inducing.shape[0], num_probes)
+        e2 = rademacher(seed, STREAM_EPS2, np.arange(self.n), self.n, num_probes)
+        return self.K.T @ sla.solve_triangular(self.Lm.T, e1, lower=False) + np.sqrt(self.Ds)[:, None] * e2
+
+    def loglik(self, y, num_probes, seed, tol, max_iter=5000, Z=None):
+        """-1/2 [n log 2 pi + logdet(Sigma_V + W^-1) + y^T (Sigma_V + W^-1)^-1 y]
+        with the log-determinant by preconditioned SLQ (weight n / l, §3.3)."""
+        if Z is None:
+            Z = self.probes(num_probes, seed)
+        res = pcg_lanczos(self.apply, self.apply_Pinv, np.column_stack([y, Z]), tol, max_iter)
+        quads = np.array([lanczos_quadrature(res["diag"][k], res["off"][k]) for k in range(1, Z.shape[1] + 1)])
+        logdet = self.n * float(np.mean(quads)) + self.logdet_P
+        yu = float(y @ res["U"][:, 0])
+        return dict(loglik=-0.5 * (self.n * LOG2PI + logdet + yu), logdet=logdet, quad=yu, iters=res["iters"])
+
+    def posterior_solve(self, v, tol, max_iter=5000, precondition=True):
+        """(Sigma_V^-1 + W)^-1 v through the system of Eq. VL_v2, whose matrix
+        Sigma_V + W^-1 is solved by CG under the FITC preconditioner (or none).
+        As printed, W (Sigma_V + W^-1)^-1 Sigma_V^-1 v is not equal to
+        (Sigma_V^-1 + W)^-1 v (for scalars it is w^2 / s^2 times it); the
+        identity with the same system is
+            (Sigma_V^-1 + W)^-1 = Sigma_V (Sigma_V + W^-1)^-1 W^-1,
+        which is what is computed: solve with W^-1 v, then apply Sigma_V."""
+        rhs = self.theta[2] * np.asarray(v, np.float64).reshape(self.n, -1)      # W^-1 v
+        pinv = self.apply_Pinv if precondition else (lambda V: V.copy())
+        res = pcg_lanczos(self.apply, pinv, rhs, tol, max_iter)
+        return self.apply_SigmaV(res["U"]), res["iters"]
 
 
 def fisher_scoring_step(theta, grad, fisher):

@@ -152,6 +152,19 @@ MUTATIONS = [
     ("Fisher scoring descends instead of ascending",
      "return np.asarray(theta, np.float64) + np.linalg.solve(", "return np.asarray(theta, np.float64) - np.linalg.solve(",
      None),
+    ("Vecchia: B gets +A_i", "            vals += (-Ai).tolist()", "            vals += Ai.tolist()", None),
+    ("Vecchia: conditional variance without the correction", "            self.D[i] = s1 - float(Ai @ SNi)",
+     "            self.D[i] = s1", None),
+    ("Vecchia: farthest instead of nearest earlier points",
+     'Ni = np.sort(np.argsort(d2, kind="stable")[:k])', 'Ni = np.sort(np.argsort(-d2, kind="stable")[:k])', None),
+    ("Vecchia: FITC diagonal without the nugget", "        self.Ds = np.maximum(s1 - np.sum(Al * Al, axis=0), 0.0) + nug",
+     "        self.Ds = np.maximum(s1 - np.sum(Al * Al, axis=0), 0.0) + 0.5 * nug", None),
+    ("Vecchia: Sigma_V applied with B^-T and B^-1 swapped",
+     "        X = sp.linalg.spsolve_triangular(self.BT, V, lower=False)",
+     "        X = sp.linalg.spsolve_triangular(self.B, V, lower=True)", None),
+    ("Vecchia: posterior solve in the printed order",
+     "        return self.apply_SigmaV(res[\"U\"]), res[\"iters\"]",
+     "        return res[\"U\"], res[\"iters\"]", None),
     ("dense Fisher without the transpose", "        return np.array([[0.5 * np.sum(X[k] * X[l].T)",
      "        return np.array([[0.5 * np.sum(X[k] * X[l])", None),
 ]

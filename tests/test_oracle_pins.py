@@ -726,6 +726,108 @@ def test_fisher_scoring_converges_to_the_maximum_likelihood_estimate():
 
 
 # --------------------------------------------------------------------------
+# the FITC preconditioner for a Vecchia approximation (§5)
+# --------------------------------------------------------------------------
+
+def _vecchia(n=200, m=20, m_v=8, theta=(1.0, 0.1, 0.05), seed=3):
+    locs = fi.uniform_locations(n, seed)
+    ind = locs[fi.inducing_subset(n, m, seed)].copy()
+    return locs, ind, O.VecchiaFITC(locs, ind, m_v, 0.5, theta)
+
+
+def test_vecchia_factor_matches_its_definition():
+    """B unit lower triangular with B_{i,N(i)} = -A_i over the min(m_v, i-1)
+    nearest earlier points (brute force), Sigma_V = (B^T D^-1 B)^-1 applied by
+    the two triangular solves, and log det Sigma_V = sum log D_i (det B = 1)."""
+    locs, ind, V = _vecchia()
+    n = locs.shape[0]
+    B = V.B.toarray()
+    assert np.array_equal(np.diag(B), np.ones(n)) and np.all(np.triu(B, 1) == 0)
+    for i in (0, 1, 5, 8, 9, 57, 199):
+        d2 = np.array([np.sum((locs[i] - locs[j]) ** 2) for j in range(i)])
+        want = set(np.argsort(d2, kind="stable")[:min(8, i)].tolist())
+        assert set(np.nonzero(B[i, :i])[0].tolist()) <= want and len(V.N[i]) == min(8, i)
+        assert set(V.N[i].tolist()) == want
+    SV = np.linalg.inv(B.T @ np.diag(1.0 / V.D) @ B)
+    x = np.random.default_rng(1).standard_normal((n, 3))
+    assert np.allclose(V.apply_SigmaV(x), SV @ x, rtol=1e-10, atol=1e-10)
+    assert abs(np.linalg.slogdet(SV)[1] - np.sum(np.log(V.D))) < 1e-10 * n
+
+
+def test_vecchia_is_exact_where_the_conditioning_loses_nothing():
+    """m_v = n - 1 conditions on every earlier point: Sigma_V = Sigma.  The
+    exponential covariance on sorted points of a line is a Markov (Ornstein-
+    Uhlenbeck) process: m_v = 1 is already exact.  m_v = 0: Sigma_V = diag(Sigma)."""
+    th = (1.0, 0.1, 0.05)
+    locs = fi.uniform_locations(60, 3)
+    full = O.VecchiaFITC(locs, locs[:5], 59, 0.5, th)
+    Sig = O.cov_matrix(locs, locs, 0.5, 1.0, 0.1)
+    assert np.allclose(full.apply_SigmaV(np.eye(60)), Sig, atol=1e-12)
+    xs = np.sort(np.random.default_rng(2).random(80))
+    line = np.column_stack([xs, np.full(80, 0.3)])
+    ou = O.VecchiaFITC(line, line[:4], 1, 0.5, th)
+    assert np.allclose(ou.apply_SigmaV(np.eye(80)), O.cov_matrix(line, line, 0.5, 1.0, 0.1), atol=1e-12)
+    none = O.VecchiaFITC(locs, locs[:5], 0, 0.5, th)
+    assert np.allclose(none.apply_SigmaV(np.eye(60)), np.eye(60), atol=1e-15)
+
+
+def test_vecchia_fitc_preconditioner_and_posterior_solve():
+    """P_hat = Sigma_l + diag(Sigma - Sigma_l) + nugget I from dense
+    definitions; the posterior solve equals (Sigma_V^-1 + W)^-1 v, which the
+    printed form W (Sigma_V + W^-1)^-1 Sigma_V^-1 v of Eq. VL_v2 does not."""
+    locs, ind, V = _vecchia()
+    n, nug = locs.shape[0], 0.05
+    K = O.cov_matrix(ind, locs, 0.5, 1.0, 0.1)
+    Sl = K.T @ np.linalg.solve(O.cov_matrix(ind, ind, 0.5, 1.0, 0.1), K)
+    P = Sl + np.diag(np.diag(O.cov_matrix(locs, locs, 0.5, 1.0, 0.1) - Sl) + nug)
+    x = np.random.default_rng(4).standard_normal((n, 2))
+    assert np.allclose(V.apply_Pinv(x), np.linalg.solve(P, x), rtol=1e-10, atol=1e-10)
+    assert abs(V.logdet_P - np.linalg.slogdet(P)[1]) < 1e-10 * n
+    SV = V.apply_SigmaV(np.eye(n))
+    want = np.linalg.solve(np.linalg.inv(SV) + np.eye(n) / nug, x)
+    got, iters = V.posterior_solve(x, 1e-12)
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-10)
+    printed = (np.linalg.solve(SV + nug * np.eye(n), np.linalg.solve(SV, x))) / nug
+    assert np.max(np.abs(printed - want)) > 1e-2 * np.max(np.abs(want))
+
+
+def test_vecchia_loglik_by_slq_exact_with_full_basis_probes_and_within_se():
+    locs, ind, V = _vecchia()
+    n = locs.shape[0]
+    C = V.apply_SigmaV(np.eye(n)) + 0.05 * np.eye(n)
+    y = np.linalg.cholesky(C) @ np.random.default_rng(5).standard_normal(n)
+    ll = -0.5 * (n * O.LOG2PI + np.linalg.slogdet(C)[1] + y @ np.linalg.solve(C, y))
+    K = O.cov_matrix(ind, locs, 0.5, 1.0, 0.1)
+    Sl = K.T @ np.linalg.solve(O.cov_matrix(ind, ind, 0.5, 1.0, 0.1), K)
+    P = Sl + np.diag(np.diag(O.cov_matrix(locs, locs, 0.5, 1.0, 0.1) - Sl) + 0.05)
+    out = V.loglik(y, n, 0, 1e-12, Z=math.sqrt(n) * np.linalg.cholesky(P))
+    assert abs(out["loglik"] - ll) < 1e-9 * abs(ll)
+    Z = V.probes(60, 7)
+    r = V.loglik(y, 60, 7, 1e-10, Z=Z)
+    terms = []
+    for k in range(60):
+        rk = O.pcg_lanczos(V.apply, V.apply_Pinv, Z[:, k:k + 1], 1e-10, 5000)
+        terms.append(n * O.lanczos_quadrature(rk["diag"][0], rk["off"][0]))
+    se = np.std(terms, ddof=1) / math.sqrt(60)
+    assert abs(r["logdet"] - np.linalg.slogdet(C)[1]) < 4 * se
+
+
+def test_vecchia_fitc_iterations_fall_with_m():
+    """§5.2: the FITC preconditioner speeds up CG for the Vecchia system; with
+    more inducing points it needs fewer iterations (effective range 0.2)."""
+    n = 1500
+    locs = fi.uniform_locations(n, 13)
+    x = np.random.default_rng(2).standard_normal((n, 1))
+    fitc, none = [], []
+    for m in (10, 50, 200):
+        V = O.VecchiaFITC(locs, locs[fi.inducing_subset(n, m, 13)].copy(), 10, 0.5, (1.0, 0.2 / 3, 0.05))
+        fitc.append(int(V.posterior_solve(x, 1e-8)[1][0]))
+        none.append(int(V.posterior_solve(x, 1e-8, precondition=False)[1][0]))
+    assert fitc[0] > fitc[1] > fitc[2]
+    assert fitc[2] < 0.6 * none[2] and none[0] == none[1] == none[2]
+
+
+# --------------------------------------------------------------------------
 # kmeans++ selection of inducing points (§4.1)
 # --------------------------------------------------------------------------
 
