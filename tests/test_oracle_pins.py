@@ -870,3 +870,20 @@ def test_kmeanspp_integer_weights_are_exact_scaled_distances():
     dy = locs[:, 1].max() - locs[:, 1].min()
     assert 1000 * (dx * dx + dy * dy) * 2.0 ** e <= 2.0 ** 62
     assert 1000 * (dx * dx + dy * dy) * 2.0 ** (e + 2) > 2.0 ** 62   # and is not needlessly small
+
+
+def test_every_planted_mistake_of_the_sweep_still_applies():
+    """The planted-mistake sweep (oracle/mutation_sweep.py) stays in step with
+    the oracle: each entry's original text occurs in the source, and its
+    planted text differs from it."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("mutation_sweep", os.path.join(root, "oracle", "mutation_sweep.py"))
+    ms = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(ms)
+    src = open(os.path.join(root, "oracle", "fsa_oracle.py")).read()
+    assert len(ms.MUTATIONS) >= 60
+    for label, old, new, _ in ms.MUTATIONS:
+        assert old in src, label
+        assert old != new, label
