@@ -262,17 +262,24 @@ fsa_status fsa_kmeanspp(const double* locs, int64_t n, int32_t m, uint64_t seed,
  *   n             1 <= n <= 65536 (the size of the fixed array); larger n is
  *                 rejected with FSA_ERR_ARG (use fsa_build instead)
  *   taper_range   gamma > 0
- *   rowptr_dev    DEVICE int64[n + 1], written
- *   col_dev       DEVICE int32[col_capacity], written; NULL: only *nnz_out is set
+ *   rowptr_dev    DEVICE int64[n + 1]; all n + 1 entries are written by every
+ *                 call that gets past the argument checks, including the size
+ *                 query and the col_capacity error below, so a caller can keep
+ *                 them and skip a second count
+ *   col_dev       DEVICE int32[col_capacity], written; NULL: a size query that
+ *                 sets *nnz_out and rowptr_dev and writes no columns
  *   col_capacity  capacity of col_dev; if it is below the pattern's nonzeros the
- *                 call returns FSA_ERR_ARG with *nnz_out set to the size needed
+ *                 call returns FSA_ERR_ARG with *nnz_out and rowptr_dev set
  *   nnz_out       HOST int64, receives the number of nonzeros
  *   cuda_stream   stream to run on (NULL: legacy default stream); the call
  *                 synchronises this stream before returning
  * Errors: FSA_ERR_ARG, FSA_ERR_NAN (non-finite coordinates), FSA_ERR_CUDA.
  * The first call on a device looks up the device address of the fixed array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the same array and its
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * device's current CUDA context; make that first call before any stream
+ * capture.  After a device reset the next call looks the address up again.
+ * Each row is sorted in O(deg log deg) steps, so a taper range near the
+ * extent of the points (rows of up to n neighbours) stays bounded in time.  Every call shares the same array and its
  * contents persist between calls (the call clears what must start at zero), so
  * calls that overlap on the GPU (from two streams or threads at once) race.
  */

@@ -162,19 +162,12 @@ __global__ void cell_scatter_kernel(const int32_t* __restrict__ cell_of, int64_t
   }
 }
 
-// insertion sort of each cell's points by original index (cells are small
-// for spread-out data; order inside a cell is then independent of atomics)
+// sort each cell's points by original index, so that the order inside a cell
+// does not depend on the scatter's atomics
 __global__ void cell_sort_kernel(const int32_t* __restrict__ start, const int32_t* __restrict__ count,
                                  int ncells, int64_t* __restrict__ perm) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-    int b = start[c], e = b + count[c];
-    for (int k = b + 1; k < e; ++k) {
-      int64_t v = perm[k];
-      int j = k - 1;
-      while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
-      perm[j + 1] = v;
-    }
-  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+    heap_sort_thread(perm + start[c], (int64_t)count[c]);
 }
 
 __global__ void gather_points_kernel(const double* __restrict__ pts, const int64_t* __restrict__ perm,
@@ -246,12 +239,8 @@ __global__ void orig_fill_kernel(const int64_t* __restrict__ rowptr, const int32
        r += (int64_t)gridDim.x * blockDim.x) {
     int64_t k = iperm[r];
     int64_t b = rowptr[k], e = rowptr[k + 1], o = rowptr_o[r];
-    for (int64_t t = b; t < e; ++t) {
-      int32_t v = (int32_t)perm[col[t]];
-      int64_t j = o + (t - b) - 1;
-      while (j >= o && col_o[j] > v) { col_o[j + 1] = col_o[j]; --j; }
-      col_o[j + 1] = v;
-    }
+    for (int64_t t = b; t < e; ++t) col_o[o + (t - b)] = (int32_t)perm[col[t]];
+    heap_sort_thread(col_o + o, e - b);
   }
 }
 

@@ -178,4 +178,27 @@ enum : unsigned {
   kErrBounds = 8u,
 };
 
+// in-place ascending heap sort of a[0..len) by one thread: O(len log len)
+// steps whatever the input order, so a crowded cell or a long neighbour row
+// (a taper range close to the extent of the points) costs seconds at worst,
+// not the quadratic time of an insertion sort
+template <typename T>
+__device__ void heap_sort_thread(T* a, int64_t len) {
+  auto sift = [&](int64_t root, int64_t end) {
+    T v = a[root];
+    for (int64_t ch = 2 * root + 1; ch < end; ch = 2 * root + 1) {
+      if (ch + 1 < end && a[ch + 1] > a[ch]) ++ch;
+      if (!(a[ch] > v)) break;
+      a[root] = a[ch];
+      root = ch;
+    }
+    a[root] = v;
+  };
+  for (int64_t i = len / 2 - 1; i >= 0; --i) sift(i, len);
+  for (int64_t end = len - 1; end > 0; --end) {
+    T t = a[0]; a[0] = a[end]; a[end] = t;
+    sift(0, end);
+  }
+}
+
 }  // namespace fsa

@@ -10,6 +10,7 @@
 // cudaFree or an allocating library routine.  The array is part of the
 // library image: every GPU that loads libfsa holds it (about 6 MB) until the
 // process exits.
+#include <cuda.h>
 #include <mutex>
 
 #include "fsa_internal.cuh"
@@ -131,13 +132,7 @@ __global__ void k_scatter(const int32_t* __restrict__ cell_of, int64_t n, const 
 __global__ void k_cell_sort(const int32_t* __restrict__ start, const int32_t* __restrict__ count, int ncells,
                             int64_t* __restrict__ perm) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-    int b = start[c], e = b + count[c];
-    for (int k = b + 1; k < e; ++k) {
-      int64_t v = perm[k];
-      int j = k - 1;
-      while (j >= b && perm[j] > v) { perm[j + 1] = perm[j]; --j; }
-      perm[j + 1] = v;
-    }
+    heap_sort_thread(perm + start[c], (int64_t)count[c]);
   }
 }
 
@@ -174,10 +169,7 @@ __global__ void k_rows(int64_t n, const double* __restrict__ xs, const double* _
         for (int j = cstart[c], e = cstart[c] + ccount[c]; j < e; ++j) {
           if (sqdist_rn(xi, yi, xs[j], ys[j]) < g2) {
             if (kFill) {
-              int32_t v = (int32_t)perm[j];
-              int64_t t = w++ - 1;
-              while (t >= c0 && col[t] > v) { col[t + 1] = col[t]; --t; }
-              col[t + 1] = v;
+              col[w++] = (int32_t)perm[j];
             } else {
               ++num;
             }
@@ -185,29 +177,54 @@ __global__ void k_rows(int64_t n, const double* __restrict__ xs, const double* _
         }
       }
     }
-    if (!kFill) cnt[r] = num;
+    if (kFill) heap_sort_thread(col + c0, w - c0);
+    else cnt[r] = num;
   }
 }
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+static CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
 struct DeviceScratch {
+  CUcontext ctx = nullptr;
   unsigned char* base = nullptr;
 };
 
-// device address of the scratch array, looked up once per device (with that
-// device current); the host name of the array is not a device address
+// device address of the scratch array for the current device.  The host name
+// of the array is not a device address.  The address is looked up with the
+// device current on the first call in a CUDA context and kept for that
+// context; a reset of the device (cudaDeviceReset) makes a new context, where
+// the module is loaded again and the array may sit elsewhere, so the next
+// call looks it up again.
 static unsigned char* scratch_for_current_device() {
   static std::mutex mu;
   static DeviceScratch per_dev[64];
   int dev = 0;
   FSA_CUDA(cudaGetDevice(&dev));
   FSA_REQUIRE(dev >= 0 && dev < 64, FSA_ERR_UNSUPPORTED, "device index out of range");
+  FSA_CUDA(cudaFree(nullptr));   // makes the device's primary context current (frees nothing)
+  CUcontext ctx = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get || get(&ctx) != CUDA_SUCCESS) ctx = nullptr;   // context unknown: look up on every call
   std::lock_guard<std::mutex> lk(mu);
-  if (!per_dev[dev].base) {
+  if (!per_dev[dev].base || !ctx || per_dev[dev].ctx != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       throw Error{FSA_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e)};
     per_dev[dev].base = static_cast<unsigned char*>(p);
+    per_dev[dev].ctx = ctx;
   }
   return per_dev[dev].base;
 }

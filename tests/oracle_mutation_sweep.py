@@ -11,9 +11,9 @@ the sweep expects them to pass.
 The working tree is never modified: every run happens in its own temporary
 directory.
 
-    python oracle/mutation_sweep.py            # all entries (several minutes)
-    python oracle/mutation_sweep.py -j 8       # eight copies at once
-    python oracle/mutation_sweep.py -k taper   # entries whose label contains "taper"
+    python tests/oracle_mutation_sweep.py            # all entries (several minutes)
+    python tests/oracle_mutation_sweep.py -j 8       # eight copies at once
+    python tests/oracle_mutation_sweep.py -k taper   # entries whose label contains "taper"
 
 Exit status 0 when every non-equivalent mistake is caught and every
 equivalent one passes.
@@ -172,7 +172,7 @@ MUTATIONS = [
 
 def _copy_tree(dst):
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
-                    ignore=shutil.ignore_patterns("__pycache__", "mutation_sweep.py"))
+                    ignore=shutil.ignore_patterns("__pycache__"))
     os.makedirs(os.path.join(dst, "tests"))
     for f in ("conftest.py", "test_oracle_pins.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))

@@ -873,13 +873,13 @@ def test_kmeanspp_integer_weights_are_exact_scaled_distances():
 
 
 def test_every_planted_mistake_of_the_sweep_still_applies():
-    """The planted-mistake sweep (oracle/mutation_sweep.py) stays in step with
+    """The planted-mistake sweep (tests/oracle_mutation_sweep.py) stays in step with
     the oracle: each entry's original text occurs in the source, and its
     planted text differs from it."""
     import importlib.util
     import os
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    spec = importlib.util.spec_from_file_location("mutation_sweep", os.path.join(root, "oracle", "mutation_sweep.py"))
+    spec = importlib.util.spec_from_file_location("mutation_sweep", os.path.join(root, "tests", "oracle_mutation_sweep.py"))
     ms = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(ms)
     src = open(os.path.join(root, "oracle", "fsa_oracle.py")).read()

@@ -38,12 +38,15 @@ def _noalloc_csr(locs, gamma):
     # size query (no column buffer), then the real call
     st = lib.fsa_csr_noalloc(d_locs.data_ptr(), n, gamma, d_rowptr.data_ptr(), None, 0, ctypes.byref(nnz), None)
     assert st == 0, lib.fsa_last_error()
+    rowptr_query = d_rowptr.cpu().numpy().copy()   # the size query writes every row pointer
     d_col = torch.full((max(nnz.value, 1),), -7, dtype=torch.int32, device="cuda")
     st = lib.fsa_csr_noalloc(d_locs.data_ptr(), n, gamma, d_rowptr.data_ptr(), d_col.data_ptr(), nnz.value,
                              ctypes.byref(nnz), None)
     assert st == 0, lib.fsa_last_error()
     torch.cuda.synchronize()
-    return d_rowptr.cpu().numpy(), d_col[:nnz.value].cpu().numpy()
+    rowptr = d_rowptr.cpu().numpy()
+    assert np.array_equal(rowptr_query, rowptr)
+    return rowptr, d_col[:nnz.value].cpu().numpy()
 
 
 def _existing_csr(locs, gamma):
@@ -79,3 +82,14 @@ def test_noalloc_rejects_too_large_and_small_capacity():
     st = lib.fsa_csr_noalloc(d_locs.data_ptr(), 1000, 0.05, d_rowptr.data_ptr(), d_col.data_ptr(), 10,
                              ctypes.byref(nnz), None)
     assert st == 1 and nnz.value > 10
+
+
+def test_noalloc_long_rows_stay_bounded():
+    """A taper range wider than the points' extent puts every point in one
+    cell and every row at n neighbours; rows and cells are heap-sorted, so
+    the call ends quickly and gives the dense pattern."""
+    locs = fi.uniform_locations(3001, 34) * 0.01
+    rp, col = _noalloc_csr(locs, 0.5)
+    n = locs.shape[0]
+    assert np.array_equal(rp, np.arange(n + 1, dtype=np.int64) * n)
+    assert np.array_equal(col, np.tile(np.arange(n, dtype=np.int32), n))
