@@ -257,7 +257,8 @@ def run_gpu(args):
     ms_per_step = elapsed_ms / args.steps
     # dominant kernel: the per-iteration tensor-core GEMMs
     prof = {}
-    for tag in ("pcg_Aq", "pcg_AtX", "pcg_spmm", "pcg_ur", "pcg_z", "pcg_split", "build", "grad"):
+    for tag in ("pcg_Aq", "pcg_AtX", "pcg_spmm", "pcg_ur", "pcg_z", "pcg_split", "pcg_q", "pcg_reduce", "build",
+                "grad", "phase_build", "phase_probes", "phase_pcg", "phase_grad"):
         nl, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         if lib.fsa_profile_collect(tag.encode(), ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(by)) == 0:
             prof[tag] = {"launches": nl.value, "ms": ms.value, "bytes": by.value}
@@ -288,6 +289,18 @@ def run_gpu(args):
             roof["other_gemm"] = {"kernel": f"tc_gemm[{other}]",
                                   "achieved": round(o["bytes"] / o["launches"] / (o["ms"] / o["launches"] / 1000) / 1e9, 1),
                                   "share_of_step": round(o["ms"] / elapsed_ms, 4)}
+    # where a step's time goes: the four phases (CUDA events on the call's
+    # stream) and, inside the CG loop, its per-iteration kernels
+    per = lambda tag: prof.get(tag, {}).get("ms", 0.0) / args.steps
+    phases = {k: round(per("phase_" + k), 3) for k in ("build", "probes", "pcg", "grad")}
+    loop_tags = ("pcg_AtX", "pcg_reduce", "pcg_q", "pcg_Aq", "pcg_z", "pcg_spmm", "pcg_ur", "pcg_split")
+    loop_kernels = sum(per(t) for t in loop_tags)
+    breakdown = {"ms_per_step": round(ms_per_step, 3), "phases_ms": phases,
+                 "outside_phases_ms": round(ms_per_step - sum(phases.values()), 3),
+                 "pcg_kernels_ms": {t: round(per(t), 3) for t in loop_tags},
+                 "pcg_outside_kernels_ms": round(phases["pcg"] - loop_kernels, 3),
+                 "unattributed_frac": round((ms_per_step - sum(phases.values()) + phases["pcg"] - loop_kernels)
+                                            / ms_per_step, 4)}
     result = {"metric": METRIC, "value": round(value, 4), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
@@ -299,6 +312,7 @@ def run_gpu(args):
                          "build_s_theta_free": round(build_s, 3),
                          "theta_dependent_build": "in every timed evaluation (theta alternates by 1e-12)"},
               "gpu_launches": launches, "clocks": clk, "roofline": roof, "kernel_times": prof,
+              "step_breakdown": breakdown,
               "loglik": ll, "grad": list(map(float, g)), "logdet_se": infos[-1]["logdet_se"]}
     # end to end through the C ABI with a host (pinned) response
     if not args.no_e2e:

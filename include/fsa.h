@@ -96,6 +96,16 @@ typedef struct {
                                    diagonal preconditioner D_s as control variate and the
                                    per-point coefficient c_opt; 2 the same with c = 1
                                    (appendix "Preconditioner as control variate") */
+  int32_t grad_control_variate; /* fsa_loglik_grad: the FITC preconditioner as control variate
+                                   of the gradient's trace estimate (appendix "Preconditioner as
+                                   control variate", Eq. Troptc), per parameter
+                                     Tr(Sdag^-1 dSdag) ~ (1/l) sum_k (a_k - c b_k) + c Tr(P^-1 dP),
+                                   a_k = U_k^T dSdag W_k, b_k = W_k^T dP W_k, W = P^-1 Z:
+                                   0 none (the plain STE of §3.3); 1 c = c_opt as printed,
+                                   sum_k (a_k - mean a) b_k / sum_k b_k^2; 2 c = 1; 3 the centred
+                                   (variance-minimising) slope
+                                   sum_k (a_k - mean a)(b_k - mean b) / sum_k (b_k - mean b)^2.
+                                   Costs one n x m x m tensor-core product and row dots. */
 } fsa_opts;
 
 typedef struct {
@@ -110,6 +120,13 @@ typedef struct {
   int32_t num_probes;
   int64_t nnz;           /* nonzeros of the tapered residual (diagonal included) */
   double time_ms;        /* device time of the call */
+  /* fsa_loglik_grad with want_grad, per parameter (sigma1^2, rho, nugget):
+   * the gradient is -1/2 (grad_trace - grad_quad) */
+  double grad_trace[3];  /* estimate of Tr(Sigma_dag^-1 dSigma_dag/dtheta) (STE, §3.3; with the
+                            control variate when opts.grad_control_variate != 0) */
+  double grad_quad[3];   /* u^T dSigma_dag/dtheta u, u = Sigma_dag^-1 y (the CG solution) */
+  double trace_precond[3]; /* Tr(P_hat^-1 dP_hat/dtheta), exact (0 without the control variate) */
+  double cv_coef[3];     /* the control variate's coefficient c (0 without it) */
 } fsa_info;
 
 typedef struct fsa_handle fsa_handle;
@@ -173,6 +190,41 @@ fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col);
 fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* theta,
                            const fsa_opts* opts, double* loglik, double* grad,
                            fsa_info* info);
+
+/*
+ * fsa_grad_terms — the per-probe terms of the gradient's stochastic trace
+ * estimate (§3.3) from the last fsa_loglik_grad on this handle that computed
+ * the gradient: a[j][k] = U_k^T dSigma_dag/dtheta_j W_k and, with the control
+ * variate, b[j][k] = W_k^T dP_hat/dtheta_j W_k (appendix "Preconditioner as
+ * control variate"; zeros without it), j = (sigma1^2, rho, nugget),
+ * k = 0 .. l-1 (U = Sigma_dag^-1 Z, W = P_hat^-1 Z).
+ *   a, b        caller-owned HOST arrays of 3 * num_probes doubles, row-major [j][k]
+ *   num_probes  the l of that call
+ * Errors: FSA_ERR_ARG (NULL pointer, no gradient computed yet, or num_probes
+ * different from that call's l), FSA_ERR_CUDA.
+ */
+fsa_status fsa_grad_terms(fsa_handle* h, double* a, double* b, int32_t num_probes);
+
+/*
+ * fsa_fisher — Fisher information of theta = (sigma1^2, rho, nugget) by
+ * stochastic trace estimation (appendix "Fisher scoring"):
+ *   I_kj = 1/2 Tr(Sigma_dag^-1 dSigma_k Sigma_dag^-1 dSigma_j)
+ *        ~ 1/2 (1/l) sum_i (dSigma_k Sigma_dag^-1 z_i)^T (Sigma_dag^-1 dSigma_j z_i),
+ * z_i Rademacher or Gaussian (opts->probe) from SplitMix64 stream 7, counter
+ * i n + point index (caller order).  The 3 l solves (z_i, dSigma_sigma1^2 z_i,
+ * dSigma_rho z_i) run as one block of the FITC-preconditioned CG (Appendix A)
+ * with opts->cg_tol / fixed_iters; opts->precision selects the FP64 or the
+ * mixed form (mixed: l <= 42).
+ *   fisher      HOST double[9], row-major: the symmetric part of the estimate
+ *   fisher_raw  HOST double[9] or NULL: the estimate as it stands (not
+ *               symmetric for finite l)
+ *   info        optional: iters_max, converged, num_probes, nnz, time_ms
+ * Errors: FSA_ERR_ARG, FSA_ERR_UNSUPPORTED (too many probes for the mixed
+ * form), FSA_ERR_NO_CONVERGENCE (outputs written), FSA_ERR_NAN, FSA_ERR_NOT_PD,
+ * FSA_ERR_OOM, FSA_ERR_CUDA.  Synchronises the handle's stream.
+ */
+fsa_status fsa_fisher(fsa_handle* h, const fsa_theta* theta, const fsa_opts* opts, double* fisher,
+                      double* fisher_raw, fsa_info* info);
 
 /*
  * fsa_matvec — the FSA operator and its preconditioner on caller vectors

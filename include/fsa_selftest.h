@@ -54,23 +54,24 @@ int fsa_selftest_spmm(fsa_handle* h, const fsa_theta* theta, int ncols, uint64_t
 
 /*
  * fsa_selftest_sddmm — the two sampled dense products of the mixed form in
- * their tile form (A~ rows staged in shared memory per cell-grid tile) against
- * their row form (one warp per row, global gathers), on the handle's pattern:
+ * their tile form (m-long rows staged in shared memory per cell-grid tile)
+ * against their row form (one warp per row, global gathers), on the handle's
+ * pattern:
  *   - the tapered residual values val_ij = (c(s_i,s_j) - a_i.a_j) T(d_ij) and
  *     D_s (paper §2.1, Eq. eqfitcp) of the operator of theta in precision
  *     FSA_MIXED_BF16 or FSA_MIXED_BF16X2;
- *   - the sparse part of the gradient (paper §2.2) on seeded X, Y (ncols
- *     columns, 1..127) and seeded BF16 B, Q (n x m_pad).
+ *   - their range derivative (paper §2.2), (s1 r'(d) - b_i.a_j - a_i.q_j) T(d)
+ *     and its diagonal, with seeded BF16 pairs b and q (n x m_pad).
  *   cap_rows   0: automatic staging capacity; > 0: at most that many staged
  *              rows per tile (larger tiles take the global-memory path)
  *   val_err    receives [max |tile - row| / max |row| over the values,
  *              the same over D_s]
- *   grad_tile, grad_row  receive the three sums (sigma1^2, rho, nugget parts)
+ *   dval_err   the same two figures for the range derivative and its diagonal
  * The operator is rebuilt on the handle's next use.  Returns FSA_OK or an
  * fsa_status.  Runs on the handle's stream.
  */
-int fsa_selftest_sddmm(fsa_handle* h, const fsa_theta* theta, int precision, int ncols, int cap_rows, uint64_t seed,
-                       double* val_err, double* grad_tile, double* grad_row);
+int fsa_selftest_sddmm(fsa_handle* h, const fsa_theta* theta, int precision, int cap_rows, uint64_t seed,
+                       double* val_err, double* dval_err);
 
 /*
  * fsa_selftest_wait_timeout — failure detection without a GPU fault: a kernel

@@ -29,16 +29,19 @@ def cov_code(nu: float) -> int:
 
 
 FSA_PRED_CV_NONE, FSA_PRED_CV_COPT, FSA_PRED_CV_C1 = 0, 1, 2
+# control variate of the gradient's trace estimate: none, c_opt as printed, c = 1, centred c_opt
+FSA_GRAD_CV = {None: 0, "copt": 1, "c1": 2, "copt_centered": 3}
 
 
 def make_opts(num_probes=50, cg_tol=1e-3, cg_max_iter=1000, fixed_iters=0, precision=FSA_FP64,
               probe=FSA_PROBE_RADEMACHER, seed=14492, slq_exact_weight=False, want_grad=True,
-              y_on_device=False, pred_control_variate=FSA_PRED_CV_NONE) -> FsaOpts:
+              y_on_device=False, pred_control_variate=FSA_PRED_CV_NONE, grad_control_variate=None) -> FsaOpts:
     o = N.default_opts()
     o.num_probes, o.cg_tol, o.cg_max_iter, o.fixed_iters = num_probes, cg_tol, cg_max_iter, fixed_iters
     o.precision, o.probe, o.seed = precision, probe, seed
     o.slq_exact_weight, o.want_grad, o.y_on_device = int(slq_exact_weight), int(want_grad), int(y_on_device)
     o.pred_control_variate = int(pred_control_variate)
+    o.grad_control_variate = FSA_GRAD_CV[grad_control_variate]
     return o
 
 
@@ -105,7 +108,30 @@ class FSAHandle:
             N.check(st)
         d = info.as_dict()
         d["status"] = st
+        self.last_info = d
         return ll.value, g, d
+
+    def grad_terms(self, num_probes: int):
+        """Per-probe terms (a, b), each 3 x l, of the last gradient (``fsa_grad_terms``)."""
+        a = np.empty((3, num_probes))
+        b = np.empty((3, num_probes))
+        N.check(N.lib().fsa_grad_terms(self._h, N.ptr(a), N.ptr(b), int(num_probes)))
+        return a, b
+
+    def fisher(self, theta, opts: FsaOpts | None = None, raise_on_noconv: bool = False):
+        """(symmetric Fisher information 3 x 3, the raw estimate, info) by
+        stochastic trace estimation (``fsa_fisher``)."""
+        opts = opts or make_opts()
+        th = _theta(theta)
+        F = np.empty((3, 3))
+        Fr = np.empty((3, 3))
+        info = FsaInfo()
+        st = N.lib().fsa_fisher(self._h, C.byref(th), C.byref(opts), N.ptr(F), N.ptr(Fr), C.byref(info))
+        if st != N.FSA_OK and (st != 4 or raise_on_noconv):
+            N.check(st)
+        d = info.as_dict()
+        d["status"] = st
+        return F, Fr, d
 
     def matvec(self, theta, v, which=0, precision=FSA_FP64):
         """Sigma_dag v (0), P_hat^-1 v (1) or Sigma_s~ v (2) (``fsa_matvec``)."""

@@ -30,17 +30,23 @@ class FsaOpts(C.Structure):
     _fields_ = [("num_probes", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("fixed_iters", C.c_int32), ("precision", C.c_int32), ("probe", C.c_int32),
                 ("seed", C.c_uint64), ("slq_exact_weight", C.c_int32), ("want_grad", C.c_int32),
-                ("y_on_device", C.c_int32), ("pred_control_variate", C.c_int32)]
+                ("y_on_device", C.c_int32), ("pred_control_variate", C.c_int32),
+                ("grad_control_variate", C.c_int32)]
 
 
 class FsaInfo(C.Structure):
     _fields_ = [("iters_max", C.c_int32), ("iters_y", C.c_int32), ("resid_y", C.c_double),
                 ("logdet", C.c_double), ("logdet_precond", C.c_double), ("quad_form", C.c_double),
                 ("logdet_se", C.c_double), ("converged", C.c_int32), ("num_probes", C.c_int32),
-                ("nnz", C.c_int64), ("time_ms", C.c_double)]
+                ("nnz", C.c_int64), ("time_ms", C.c_double), ("grad_trace", C.c_double * 3),
+                ("grad_quad", C.c_double * 3), ("trace_precond", C.c_double * 3), ("cv_coef", C.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if isinstance(v, C.Array) else v
+        return d
 
 
 FSA_REQ_LOGLIK_GRAD, FSA_REQ_PREDICT = 0, 1
@@ -95,6 +101,8 @@ def _declare(lib):
         "fsa_get_csr": (C.c_int, [P, P, P]),
         "fsa_loglik_grad": (C.c_int, [P, P, C.POINTER(FsaTheta), C.POINTER(FsaOpts), DP, DP,
                                       C.POINTER(FsaInfo)]),
+        "fsa_grad_terms": (C.c_int, [P, P, P, C.c_int32]),
+        "fsa_fisher": (C.c_int, [P, C.POINTER(FsaTheta), C.POINTER(FsaOpts), P, P, C.POINTER(FsaInfo)]),
         "fsa_matvec": (C.c_int, [P, C.POINTER(FsaTheta), C.c_int32, C.c_int32, P, C.c_int32, P]),
         "fsa_logdet_precond": (C.c_int, [P, C.POINTER(FsaTheta), C.c_int32, DP]),
         "fsa_predict": (C.c_int, [P, P, C.POINTER(FsaTheta), C.POINTER(FsaOpts), P, C.c_int64, C.c_int32,

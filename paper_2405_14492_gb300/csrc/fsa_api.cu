@@ -252,6 +252,23 @@ fsa_status fsa_build(const double* locs, int64_t n, const double* inducing, int3
 
 int64_t fsa_nnz(const fsa_handle* h) { return h ? h->h.nnz : -1; }
 
+fsa_status fsa_grad_terms(fsa_handle* h, double* a, double* b, int32_t num_probes) {
+  if (!h || !a || !b) return fail(Error{FSA_ERR_ARG, "NULL argument"});
+  Handle& H = h->h;
+  if (H.gterms_l <= 0 || !H.gterms.p) return fail(Error{FSA_ERR_ARG, "no gradient has been computed on this handle"});
+  if (num_probes != H.gterms_l)
+    return fail(Error{FSA_ERR_ARG, "num_probes differs from the last call's (" + std::to_string(H.gterms_l) + ")"});
+  try {
+    const size_t k = (size_t)3 * num_probes;
+    FSA_CUDA(cudaMemcpyAsync(a, H.gterms.p, sizeof(double) * k, cudaMemcpyDeviceToHost, H.stream));
+    FSA_CUDA(cudaMemcpyAsync(b, H.gterms.p + k, sizeof(double) * k, cudaMemcpyDeviceToHost, H.stream));
+    FSA_CUDA(cudaStreamSynchronize(H.stream));
+    return FSA_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
 fsa_status fsa_get_csr(fsa_handle* h, int64_t* rowptr, int32_t* col) {
   if (!h || !rowptr || !col) return fail(Error{FSA_ERR_ARG, "NULL argument"});
   try {
@@ -277,6 +294,10 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   if (!(o.cg_tol >= 0.0)) return fail(Error{FSA_ERR_ARG, "cg_tol must be >= 0"});
   if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
+  if (o.grad_control_variate < 0 || o.grad_control_variate > 3)
+    return fail(Error{FSA_ERR_ARG, "grad_control_variate must be 0, 1, 2 or 3"});
+  if (o.grad_control_variate != 0 && o.num_probes < 2)
+    return fail(Error{FSA_ERR_ARG, "the gradient's control variate needs at least 2 probes"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
   TraceRange trace("fsa_loglik_grad");
@@ -315,6 +336,12 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
       info->num_probes = o.num_probes;
       info->nnz = H.nnz;
       info->time_ms = ms;
+      for (int q = 0; q < 3; ++q) {
+        info->grad_trace[q] = o.want_grad ? r.trace[q] : 0.0;
+        info->grad_quad[q] = o.want_grad ? r.quad[q] : 0.0;
+        info->trace_precond[q] = o.want_grad ? r.traceP[q] : 0.0;
+        info->cv_coef[q] = o.want_grad ? r.cv_c[q] : 0.0;
+      }
     }
     if (!std::isfinite(r.loglik)) return fail(Error{FSA_ERR_NAN, "non-finite log-likelihood"});
     if (!r.converged) return fail(Error{FSA_ERR_NO_CONVERGENCE, "CG iteration limit reached"});

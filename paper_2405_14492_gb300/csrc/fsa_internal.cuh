@@ -160,6 +160,8 @@ struct Handle {
   Workspace ws;
   DevPtr<double> y;                        // response in internal order
   DevPtr<double> outs;                     // device results [loglik, logdet, quad, g0, g1, g2, se, ...]
+  DevPtr<double> gterms;                   // per-probe gradient terms of the last call: a[3][l], b[3][l]
+  int gterms_l = 0;                        // l of gterms (0: none yet)
   double* host_pinned = nullptr;           // pinned mirror of small results
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // side stream for work that overlaps the main stream (SLQ beside the gradient)

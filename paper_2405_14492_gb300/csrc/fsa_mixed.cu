@@ -15,7 +15,9 @@
 //   eigen-quadrature are FP64.
 #include <memory>
 
+#include "fsa_grad.cuh"
 #include "fsa_kernels.cuh"
+#include "fsa_mixed.cuh"
 #include "fsa_solver.cuh"
 #include "fsa_tc.cuh"
 #include "fsa_vec.cuh"
@@ -360,11 +362,14 @@ __global__ void k_pack_pairs(int64_t nnz, const int32_t* __restrict__ scol, cons
 }
 
 // dst = bf16(a - b)
-__global__ void k_sub_to_bf16(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
-                              __nv_bfloat16* __restrict__ dst) {
+// hi + lo BF16 pair of a - b (FP32), in the blocked K-major layout with K = the column
+__global__ void k_sub_split(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
+                            __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t rows, int cols) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    dst[t] = __float2bfloat16_rn(a[t] - b[t]);
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = dst_index(t, rows, cols);
+    split_bf16(a[t] - b[t], hi[d], lo[d]);
+  }
 }
 
 __device__ __forceinline__ float dot8_bf16(const uint4& x, const uint4& y) {
@@ -378,119 +383,6 @@ __device__ __forceinline__ float dot8_bf16(const uint4& x, const uint4& y) {
     s = fmaf(u.y, v.y, s);
   }
   return s;
-}
-
-// Gradient, sparse part (Eq. NEGLLDNEGLLFSA with dSigma_dag of §2.2), one warp
-// per row i.  With G_ij = sum_k w_k X_ik Y_jk and the rho-derivative of the
-// low-rank entries dl_ij = b_i.a_j + a_i.(b_j - f_j)  (b = dK L^-T, f = A E):
-//   s0 += dval/ds1 G = (val_ij - nugget [i=j]) / s1 G
-//   sr += dval/drho G = (s1 r'(d) T(d) - dl_ij T(d)) G      (T(0) = 1, r'(0) = 0)
-//   s2 += [i = j] G
-// Rows a_i, b_i stay in registers (KC 16-byte chunks per lane); a_j and
-// q_j = b_j - f_j are gathered with 16-byte loads; X_i is in registers.
-template <int KC, int NS>
-__global__ void __launch_bounds__(256) k_grad_sparse_bf16(
-    int64_t n, int m_pad, int c, int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-    const double* __restrict__ vals, const double* __restrict__ xs, const double* __restrict__ ys,
-    const float* __restrict__ X, const float* __restrict__ Y, const __nv_bfloat16* __restrict__ A,
-    const __nv_bfloat16* __restrict__ B, const __nv_bfloat16* __restrict__ Q, int cov, double s1, double rho,
-    double nug, double gamma, double* __restrict__ part) {
-  __shared__ double red[3][8];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const int nch = m_pad / 8;   // 16-byte chunks per row
-  const float inv_l = c > 1 ? 1.0f / (float)(c - 1) : 0.f;
-  double s0 = 0.0, sr = 0.0, s2 = 0.0;
-  // A~ is in the blocked K-major layout: 16-byte chunk ch of row r is chunk
-  // (ch & 7) of 64-element block ch >> 3, at ((ch >> 3) n + r) 8 + (ch & 7)
-  const uint4* A4 = reinterpret_cast<const uint4*>(A);
-  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
-    const uint4* bi4 = reinterpret_cast<const uint4*>(B + i * m_pad);
-    uint4 ai[KC], bi[KC];
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      int ch = lane + 32 * k;
-      ai[k] = ch < nch ? A4[((int64_t)(ch >> 3) * n + i) * 8 + (ch & 7)] : make_uint4(0, 0, 0, 0);
-      bi[k] = ch < nch ? bi4[ch] : make_uint4(0, 0, 0, 0);
-    }
-    float xi[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      int col = lane + 32 * s;
-      xi[s] = col < c ? X[i * ldc + col] * (col == 0 ? -1.0f : inv_l) : 0.f;
-    }
-    const double xi0 = xs[i], yi0 = ys[i];
-    const int64_t rb = rowptr[i], re = rowptr[i + 1];
-    for (int64_t base = rb; base < re; base += 32) {
-      const int mcnt = (int)((re - base) < 32 ? (re - base) : 32);
-      const int myc = lane < mcnt ? colidx[base + lane] : 0;
-      for (int t = 0; t < mcnt; ++t) {
-        const int j = __shfl_sync(0xffffffffu, myc, t);
-        const uint4* qj4 = reinterpret_cast<const uint4*>(Q + (int64_t)j * m_pad);
-        float dl = 0.f;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          int ch = lane + 32 * k;
-          if (ch < nch) dl += dot8_bf16(bi[k], A4[((int64_t)(ch >> 3) * n + j) * 8 + (ch & 7)]) + dot8_bf16(ai[k], qj4[ch]);
-        }
-        float g = 0.f;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          int col = lane + 32 * s;
-          if (col < c) g = fmaf(xi[s], Y[(int64_t)j * ldc + col], g);
-        }
-        dl = warp_sum(dl);
-        g = warp_sum(g);
-        if (lane == 0) {
-          const double gd = (double)g;
-          const double v = vals[base + t];
-          if (j == i) {
-            s0 += (v - nug) / s1 * gd;
-            sr += -(double)dl * gd;
-            s2 += gd;
-          } else {
-            double d = sqrt(sqdist_rn(xi0, yi0, xs[j], ys[j]));
-            double tp = wendland(d, gamma);
-            s0 += v / s1 * gd;
-            sr += (s1 * matern_dr(cov, d, rho) - (double)dl) * tp * gd;
-          }
-        }
-      }
-    }
-  }
-  if (lane == 0) { red[0][wib] = s0; red[1][wib] = sr; red[2][wib] = s2; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-    part[(int64_t)blockIdx.x * 3 + threadIdx.x] = s;
-  }
-}
-
-static void launch_grad_sparse_bf16v(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
-                                     const float* X, const float* Y, const __nv_bfloat16* A,
-                                     const __nv_bfloat16* B, const __nv_bfloat16* Q, const fsa_theta& th,
-                                     double* part) {
-  const int kc = (m_pad / 8 + 31) / 32, ns = (ldc + 31) / 32;
-  FSA_REQUIRE(kc >= 1 && kc <= 8 && ns >= 1 && ns <= 4, FSA_ERR_UNSUPPORTED, "gradient kernel: m or l too large");
-#define GS_CASE(KC_, NS_)                                                                                        \
-  if (kc == KC_ && ns == NS_) {                                                                                  \
-    k_grad_sparse_bf16<KC_, NS_><<<nblocks, 256, 0, H.stream>>>(H.n, m_pad, c, ldc, H.rowptr.p, H.col.p, vals,    \
-                                                                H.xs.p, H.ys.p, X, Y, A, B, Q, H.cov,            \
-                                                                th.sigma1_sq, th.rho, th.nugget, H.gamma, part); \
-    FSA_CHECK_LAUNCH();                                                                                          \
-    return;                                                                                                      \
-  }
-#define GS_KC(KC_) GS_CASE(KC_, 1) GS_CASE(KC_, 2) GS_CASE(KC_, 3) GS_CASE(KC_, 4)
-  GS_KC(1) GS_KC(2) GS_KC(3) GS_KC(4) GS_KC(5) GS_KC(6) GS_KC(7) GS_KC(8)
-#undef GS_KC
-#undef GS_CASE
-}
-
-void grad_sparse_rows(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals, const float* X,
-                      const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q,
-                      const fsa_theta& th, double* part) {
-  launch_grad_sparse_bf16v(H, nblocks, m_pad, c, ldc, vals, X, Y, A, B, Q, th, part);
 }
 
 void csr_values_rows(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad) {
@@ -618,30 +510,20 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
 // ---------------------------------------------------------------------------
 // per-iteration products on the tensor cores
 // ---------------------------------------------------------------------------
-struct MixedCtx {
-  int ldc = 0, c = 0, m_pad = 0;
-  int64_t n = 0, n_pad = 0;
-  int splits_w = 1;
-  TmaMap mAt, mA, mX, mQ;
-  TmaMap mAt_lo, mA_lo;     // low halves of A (FSA_MIXED_BF16X2)
-  bool lo = false;
-  int nsplit = 2;           // BF16 pieces of the vector operands (3: FP32-exact)
-  float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
-};
 
 // vector-operand split: two BF16 pieces (~16 significant bits).  Three pieces
 // (the full FP32 24) are supported by the kernels (kVecSplit = 3) but changed
 // the n = 1e6 log-likelihood by < 1e-6 relative at a higher cost, so two are used.
 constexpr int kVecSplit = 2;
 static inline int pick_nsplit(int ldc) { return kVecSplit == 3 && 3 * ldc <= 256 ? 3 : 2; }
-static inline int mixed_ldc(int c) {
+int mixed_ldc(int c) {
   int l16 = (c + 15) / 16 * 16;
   return kVecSplit == 3 && 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
 }
 
 static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C);
 
-static void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc) {
+void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc) {
   Operator& op = H.op;
   CGState& g = H.cg;
   C.ldc = ldc; C.c = c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
@@ -667,7 +549,7 @@ static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C) {
 }
 
 // w (FP64, m x ldc) = A~^T X  where X = rows of `src` (scaled by rowscale), split hi/lo
-static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w,
+void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w,
                       const char* tag) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
@@ -675,7 +557,7 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   size_t smem = (size_t)(kSTRows * (ldc + 1) + kSTRows) * sizeof(float);
   {
     // FP32 block read once, nsplit BF16 pieces written
-    ProfScope ps("pcg_split", (double)C.n * ldc * (4.0 + 2.0 * C.nsplit), s, tag && tag[0] == 'p');
+    ProfScope ps("pcg_split", (double)C.n * C.c * (4.0 + 2.0 * C.nsplit), s, tag && tag[0] == 'p');
     k_split_transpose<<<(unsigned)((C.n_pad + kSTRows - 1) / kSTRows), 256, smem, s>>>(C.n, C.c, ldc, C.nsplit,
                                                                                       src, rowscale, C.n_pad, g.Xb.p);
     FSA_CHECK_LAUNCH();
@@ -693,13 +575,17 @@ static void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* row
   t.alg_bytes = t.num_a * (double)H.m * C.n * 2.0 + (double)C.nsplit * C.c * C.n * 2.0 +
                 (double)splits * H.m * C.c * 4.0;
   tc_gemm(t, H.err, s);
-  k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
-                                                                    t.split_stride, w, ldc, 0);
-  FSA_CHECK_LAUNCH();
+  {
+    // split-K partials read once (FP32), w written once (FP64)
+    ProfScope ps("pcg_reduce", (double)H.m * C.c * (4.0 * splits + 8.0), s, tag && tag[0] == 'p');
+    k_reduce_splits<<<grid_for((int64_t)H.m * ldc, 256), 256, 0, s>>>(splits, H.m, ldc, C.wpart, ldc,
+                                                                      t.split_stride, w, ldc, 0);
+    FSA_CHECK_LAUNCH();
+  }
 }
 
 // S (FP32 n x ldc) = A~ q, q FP64 m x ldc
-static void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag) {
+void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag) {
   cudaStream_t s = H.stream;
   CGState& g = H.cg;
   int ldc = C.ldc;
@@ -722,58 +608,29 @@ static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
   CGState& g = H.cg;
   Operator& op = H.op;
   mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
-  dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
+  {
+    // FP64 q = M^-1 w: m x m core read once, w read, q written
+    ProfScope ps("pcg_q", 8.0 * ((double)H.m * H.m + 2.0 * H.m * C.c), H.stream);
+    dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
+  }
   mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
 }
 
-LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
+// Block PCG of Appendix A on the right-hand sides in H.cg.R32 (n x ldc FP32,
+// columns >= c zero) with the mixed operator and the FITC preconditioner:
+// U receives Sigma_dag^-1 R, W0 the first preconditioner apply P_hat^-1 R, and
+// the per-column scalars the Lanczos tridiagonals, iteration counts and
+// residual norms.  Runs L iterations (opts.fixed_iters) or until every column
+// meets cg_tol.
+void pcg_mixed_run(Handle& H, MixedCtx& C, const CGLayout& lay, const fsa_opts& o, int L) {
   cudaStream_t s = H.stream;
   Operator& op = H.op;
   CGState& g = H.cg;
-  int64_t n = H.n;
-  int m = H.m;
-  int l = o.num_probes;
-  FSA_REQUIRE(l + 1 <= 128, FSA_ERR_UNSUPPORTED, "mixed precision supports at most 127 probes");
-  CGLayout lay;
-  int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
-  lay.setup(n, l + 1, L, mixed_ldc(l + 1));
-  ensure_cg(H, lay, false);
-  int ldc = lay.ldc;
-  size_t nc = (size_t)n * ldc;
-  g.U32.ensure(nc); g.R32.ensure(nc); g.Z32.ensure(nc); g.H32.ensure(nc); g.V32.ensure(nc);
-  g.S32.ensure(nc); g.W032.ensure(nc);
-  MixedCtx C;
-  mixed_ctx_setup(H, C, n, lay.c, ldc);
-  DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
-  C.wpart = wpart_buf.p;
-  FSA_REQUIRE(ldc % 4 == 0 && ldc <= 128, FSA_ERR_UNSUPPORTED, "mixed block width must be a multiple of 4, at most 128");
+  const int64_t n = H.n;
+  const int ldc = lay.ldc;
+  const size_t nc = (size_t)n * ldc;
   const Vec4Launch v4 = vec4_launch(lay, reinterpret_cast<const void*>(kv4_ur_update));
   const Vec4Launch v4z = vec4_launch(lay, reinterpret_cast<const void*>(kv4_z_update));
-  // probes: R = [y, A~ eps1 + D^1/2 eps2]
-  {
-    TraceRange trace("probes");
-    int l16 = round_up(l, 16);
-    DevPtr<__nv_bfloat16> Ehi((size_t)l16 * C.m_pad), Elo((size_t)l16 * C.m_pad);
-    DevPtr<float> Zp((size_t)n * l16);
-    k_eps1_split<<<grid_for((int64_t)l16 * C.m_pad, 256), 256, 0, s>>>(m, l, l16, C.m_pad, o.probe,
-                                                                       rng_key(o.seed, kStreamEps1), Ehi.p, Elo.p);
-    FSA_CHECK_LAUNCH();
-    TmaMap mEh = make_tma_bf16(Ehi.p, l16, C.m_pad, C.m_pad, l16), mEl = make_tma_bf16(Elo.p, l16, C.m_pad, C.m_pad, l16);
-    TcGemm t;
-    t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
-    t.b[0] = &mEh; t.b[1] = &mEl; t.num_b = 2;
-    t.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
-    t.M = (int)n; t.N = l16; t.K = C.m_pad; t.bn = l16;
-    t.out = Zp.p; t.ldo = l16;
-    t.tag = "build";
-    tc_gemm(t, H.err, s);
-    k_probe_finish_mixed<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, l16, o.probe,
-                                                                    rng_key(o.seed, kStreamEps2), H.perm.p, H.y.p,
-                                                                    op.D32.p, Zp.p, g.R32.p);
-    FSA_CHECK_LAUNCH();
-    FSA_CUDA(cudaStreamSynchronize(s));
-  }
-  auto pcg_trace = std::make_unique<TraceRange>("pcg");
   FSA_CUDA(cudaMemsetAsync(g.U32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
@@ -786,7 +643,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   const StagedLaunch sl = staged_launch(H, ldc);
   launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha, q);
   int32_t* pin_active = reinterpret_cast<int32_t*>(H.host_pinned);
-  const double blk_bytes = (double)n * ldc * sizeof(float);
+  const double blk_bytes = (double)n * lay.c * sizeof(float);   // algorithmic: the c columns, not the padding
   for (int it = 0; it < L; ++it) {
     {
       ProfScope ps("pcg_ur", 6.0 * blk_bytes, s);   // U, R read and written; H, V read
@@ -810,8 +667,208 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
       if (*pin_active == 0) break;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// range derivative of the mixed operator
+// ---------------------------------------------------------------------------
+void build_deriv_mixed(Handle& H, const MixedCtx& C, const fsa_theta& th, DerivMixed& Dv) {
+  cudaStream_t s = H.stream;
+  Operator& op = H.op;
+  const int64_t n = H.n;
+  const int m = H.m, m_pad = C.m_pad;
+  const size_t nm = (size_t)n * m_pad, mm_pad = (size_t)m_pad * m_pad;
+  Dv.Alo = op.Ab_lo.p;
+  if (!op.has_lo) {
+    Dv.zero_lo.alloc(nm);
+    FSA_CUDA(cudaMemsetAsync(Dv.zero_lo.p, 0, nm * sizeof(__nv_bfloat16), s));
+    Dv.Alo = Dv.zero_lo.p;
+  }
+  Dv.Bh.alloc(nm); Dv.Bl.alloc(nm); Dv.Qh.alloc(nm); Dv.Ql.alloc(nm);
+  Dv.E.alloc((size_t)m * m);
+  {
+    DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi(mm_pad), Llo(mm_pad);
+    DevPtr<float> B32(nm);
+    cov_nm_split(H, m_pad, th, 1, Khi.p, Klo.p);
+    k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p, Llo.p);
+    FSA_CHECK_LAUNCH();
+    TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+    TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128), mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
+    TcGemm t;
+    t.a[0] = &mKh; t.a[1] = &mKl; t.num_a = 2;
+    t.b[0] = &mLh; t.b[1] = &mLl; t.num_b = 2;
+    t.pairs = 1u | 2u | 4u;
+    t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
+    t.out = B32.p; t.ldo = m_pad;
+    t.tag = "grad";
+    tc_gemm(t, H.err, s);
+    k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Dv.Bh.p, Dv.Bl.p, n, m_pad);
+    FSA_CHECK_LAUNCH();
+    // E = L^-1 dSigma_m L^-T (FP64), F = A~ E (split products), q = b - F
+    DevPtr<double> dSm((size_t)m * m), T1((size_t)m * m);
+    cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
+    dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
+    dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, Dv.E.p, m, nullptr);
+    k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, Dv.E.p, m, m_pad, m_pad, Lhi.p, Llo.p);
+    FSA_CHECK_LAUNCH();
+    TcGemm f;
+    f.a[0] = &C.mA; f.a[1] = &C.mA_lo; f.num_a = C.lo ? 2 : 1;
+    f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
+    f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
+    f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
+    DevPtr<float> F32(nm);
+    f.out = F32.p; f.ldo = m_pad;
+    f.tag = "grad";
+    tc_gemm(f, H.err, s);
+    k_sub_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, F32.p, Dv.Qh.p, Dv.Ql.p, n, m_pad);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  }
+  // B^T as a BF16 pair (blocked, K = the point) for B^T X; B for B q
+  const size_t mn = (size_t)m_pad * C.n_pad;
+  Dv.Bth.alloc(mn); Dv.Btl.alloc(mn);
+  FSA_CUDA(cudaMemsetAsync(Dv.Bth.p, 0, sizeof(__nv_bfloat16) * mn, s));
+  FSA_CUDA(cudaMemsetAsync(Dv.Btl.p, 0, sizeof(__nv_bfloat16) * mn, s));
+  dim3 tgrid((unsigned)((n + 31) / 32), (m_pad + 31) / 32), tblk(32, 8);
+  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, Dv.Bh.p, m_pad, Dv.Bth.p, C.n_pad, 1, 1);
+  FSA_CHECK_LAUNCH();
+  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, Dv.Bl.p, m_pad, Dv.Btl.p, C.n_pad, 1, 1);
+  FSA_CHECK_LAUNCH();
+  Dv.CBt = C;
+  Dv.CBt.mAt = make_tma_bf16_blocked(Dv.Bth.p, m_pad, C.n_pad, 128);
+  Dv.CBt.mAt_lo = make_tma_bf16_blocked(Dv.Btl.p, m_pad, C.n_pad, 128);
+  Dv.CBt.lo = true;
+  Dv.CB = C;
+  Dv.CB.mA = make_tma_bf16_blocked(Dv.Bh.p, n, m_pad, 128);
+  Dv.CB.mA_lo = make_tma_bf16_blocked(Dv.Bl.p, n, m_pad, 128);
+  Dv.CB.lo = true;
+  // the range derivative of the residual values (per nonzero) and of D_s
+  Dv.dv.alloc(H.nnz + 4);
+  Dv.dD.alloc(n);
+  dvals_mixed(H, th, m_pad, op.Ab.p, Dv.Alo, Dv.Bh.p, Dv.Bl.p, Dv.Qh.p, Dv.Ql.p, Dv.dv.p, Dv.dD.p);
+}
+
+// out0 = Sigma_s~ X, out1 = dSigma_s~/drho X (FP32 blocks, lane L owns columns 4L .. 4L + 3)
+static __global__ void __launch_bounds__(256) kv_spmm2_f4(int64_t n, int ldc, const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ colidx,
+                                                          const float* __restrict__ vals,
+                                                          const float* __restrict__ dvals, const float* __restrict__ X,
+                                                          float* __restrict__ out0, float* __restrict__ out1) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const bool act = lane < (ldc >> 2);
+  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += nwarps) {
+    const int64_t rb = rowptr[i], re = rowptr[i + 1];
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    for (int64_t base = rb; base < re; base += 32) {
+      const int cnt = (int)((re - base) < 32 ? (re - base) : 32);
+      const int myc = lane < cnt ? colidx[base + lane] : 0;
+      const float myv = lane < cnt ? vals[base + lane] : 0.f;
+      const float myd = lane < cnt ? dvals[base + lane] : 0.f;
+      for (int t = 0; t < cnt; ++t) {
+        const int j = __shfl_sync(0xffffffffu, myc, t);
+        const float v = __shfl_sync(0xffffffffu, myv, t), d = __shfl_sync(0xffffffffu, myd, t);
+        if (act) {
+          const float4 x = *reinterpret_cast<const float4*>(X + (int64_t)j * ldc + 4 * lane);
+          a0.x = fmaf(v, x.x, a0.x); a0.y = fmaf(v, x.y, a0.y); a0.z = fmaf(v, x.z, a0.z); a0.w = fmaf(v, x.w, a0.w);
+          a1.x = fmaf(d, x.x, a1.x); a1.y = fmaf(d, x.y, a1.y); a1.z = fmaf(d, x.z, a1.z); a1.w = fmaf(d, x.w, a1.w);
+        }
+      }
+    }
+    if (act) {
+      *reinterpret_cast<float4*>(out0 + i * ldc + 4 * lane) = a0;
+      *reinterpret_cast<float4*>(out1 + i * ldc + 4 * lane) = a1;
+    }
+  }
+}
+
+// out0 = (out0 + T0 - nugget X) / sigma1^2; out1 += T1 + T2
+static __global__ void k_dsigma_combine(int64_t total, double s1, double nug, const float* __restrict__ X,
+                                        const float* __restrict__ T0, const float* __restrict__ T1,
+                                        const float* __restrict__ T2, float* __restrict__ out0,
+                                        float* __restrict__ out1) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    out0[t] = (float)(((double)out0[t] + (double)T0[t] - nug * (double)X[t]) / s1);
+    out1[t] = out1[t] + T1[t] + T2[t];
+  }
+}
+
+void apply_dsigma_mixed(Handle& H, MixedCtx& C, DerivMixed& Dv, const fsa_theta& th, const float* X, float* out0,
+                        float* out1) {
+  cudaStream_t s = H.stream;
+  const int64_t n = H.n;
+  const int m = H.m, ldc = C.ldc;
+  FSA_REQUIRE(ldc % 4 == 0 && ldc <= 128, FSA_ERR_UNSUPPORTED, "derivative apply needs ldc % 4 == 0, ldc <= 128");
+  kv_spmm2_f4<<<spmm_f4_blocks(), 256, 0, s>>>(n, ldc, H.rowptr.p, H.col.p, H.op.vals32.p, Dv.dv.p, X, out0, out1);
+  FSA_CHECK_LAUNCH();
+  const size_t mc = (size_t)m * ldc, nc = (size_t)n * ldc;
+  DevPtr<double> AX(mc), BX(mc);
+  mixed_AtX(H, C, X, nullptr, AX.p, "fisher");
+  mixed_AtX(H, Dv.CBt, X, nullptr, BX.p, "fisher");
+  // BX - E A~^T X (E symmetric)
+  dgemm(H.ws, s, false, false, m, ldc, m, -1.0, Dv.E.p, m, AX.p, ldc, 1.0, BX.p, ldc, nullptr);
+  DevPtr<float> T0(nc), T1(nc), T2(nc);
+  mixed_Aq(H, C, AX.p, T0.p, "fisher");
+  mixed_Aq(H, C, BX.p, T1.p, "fisher");
+  mixed_Aq(H, Dv.CB, AX.p, T2.p, "fisher");
+  k_dsigma_combine<<<grid_for((int64_t)nc, 256), 256, 0, s>>>((int64_t)nc, th.sigma1_sq, th.nugget, X, T0.p, T1.p,
+                                                              T2.p, out0, out1);
+  FSA_CHECK_LAUNCH();
+}
+
+LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o) {
+  cudaStream_t s = H.stream;
+  Operator& op = H.op;
+  CGState& g = H.cg;
+  int64_t n = H.n;
+  int m = H.m;
+  int l = o.num_probes;
+  FSA_REQUIRE(l + 1 <= 128, FSA_ERR_UNSUPPORTED, "mixed precision supports at most 127 probes");
+  CGLayout lay;
+  int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
+  lay.setup(n, l + 1, L, mixed_ldc(l + 1));
+  ensure_cg(H, lay, false);
+  int ldc = lay.ldc;
+  size_t nc = (size_t)n * ldc;
+  g.U32.ensure(nc); g.R32.ensure(nc); g.Z32.ensure(nc); g.H32.ensure(nc); g.V32.ensure(nc);
+  g.S32.ensure(nc); g.W032.ensure(nc);
+  MixedCtx C;
+  mixed_ctx_setup(H, C, n, lay.c, ldc);
+  DevPtr<float> wpart_buf((size_t)C.splits_w * C.m_pad * ldc);
+  C.wpart = wpart_buf.p;
+  FSA_REQUIRE(ldc % 4 == 0 && ldc <= 128, FSA_ERR_UNSUPPORTED, "mixed block width must be a multiple of 4, at most 128");
+  // probes: R = [y, A~ eps1 + D^1/2 eps2]
+  {
+    TraceRange trace("probes");
+    ProfScope phase("phase_probes", 0.0, s);
+    int l16 = round_up(l, 16);
+    DevPtr<__nv_bfloat16> Ehi((size_t)l16 * C.m_pad), Elo((size_t)l16 * C.m_pad);
+    DevPtr<float> Zp((size_t)n * l16);
+    k_eps1_split<<<grid_for((int64_t)l16 * C.m_pad, 256), 256, 0, s>>>(m, l, l16, C.m_pad, o.probe,
+                                                                       rng_key(o.seed, kStreamEps1), Ehi.p, Elo.p);
+    FSA_CHECK_LAUNCH();
+    TmaMap mEh = make_tma_bf16(Ehi.p, l16, C.m_pad, C.m_pad, l16), mEl = make_tma_bf16(Elo.p, l16, C.m_pad, C.m_pad, l16);
+    TcGemm t;
+    t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
+    t.b[0] = &mEh; t.b[1] = &mEl; t.num_b = 2;
+    t.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
+    t.M = (int)n; t.N = l16; t.K = C.m_pad; t.bn = l16;
+    t.out = Zp.p; t.ldo = l16;
+    t.tag = "build";
+    tc_gemm(t, H.err, s);
+    k_probe_finish_mixed<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, l16, o.probe,
+                                                                    rng_key(o.seed, kStreamEps2), H.perm.p, H.y.p,
+                                                                    op.D32.p, Zp.p, g.R32.p);
+    FSA_CHECK_LAUNCH();
+    FSA_CUDA(cudaStreamSynchronize(s));
+  }
+  auto pcg_trace = std::make_unique<TraceRange>("pcg");
+  auto pcg_phase = std::make_unique<ProfScope>("phase_pcg", 0.0, s);
+  pcg_mixed_run(H, C, lay, o, L);
+  pcg_phase.reset();
   pcg_trace.reset();
   TraceRange slq_grad_trace("slq_gradient");
+  auto grad_phase = std::make_unique<ProfScope>("phase_grad", 0.0, s);
   // the Lanczos eigen-quadrature depends only on the tridiagonals: it runs on
   // the side stream (one thread per probe column) beside the gradient work
   if (!H.side) {
@@ -826,102 +883,69 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   DevPtr<double> ypart((size_t)lay.nblk * ldc);
   k_dot_col0<float><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U32.p, ypart.p);
   FSA_CHECK_LAUNCH();
-  H.outs.ensure(16);
-  DevPtr<double> gbuf;
+  H.outs.ensure(kOutCount);
   if (o.want_grad) {
     // X = U (u in column 0), Y = W with u in column 0
     FSA_CUDA(cudaMemcpyAsync(g.Z32.p, g.W032.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
     k_copy_col0<float><<<grid_for(n, 256), 256, 0, s>>>(n, ldc, g.U32.p, g.Z32.p);
     FSA_CHECK_LAUNCH();
-    int c = lay.c;
-    int m_pad = C.m_pad;
-    size_t mc = (size_t)m * ldc;
-    size_t nm = (size_t)n * m_pad;
-    DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc), E((size_t)m * m), T1((size_t)m * m);
+    const int c = lay.c;
+    const int m_pad = C.m_pad;
+    const size_t mc = (size_t)m * ldc, nm = (size_t)n * m_pad, mm_pad = (size_t)m_pad * m_pad;
+    DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc);
     mixed_AtX(H, C, g.U32.p, nullptr, AX.p, "grad");
     mixed_AtX(H, C, g.Z32.p, nullptr, AY.p, "grad");
-    DevPtr<__nv_bfloat16> Bb(nm), Fb(nm);
-    {
-      // B = dK L^-T (split products), and B^T for the m-space projections
-      DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
-      DevPtr<float> B32(nm);
-      cov_nm_split(H, m_pad, th, 1, Khi.p, Klo.p);
-      k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
-                                                                         Llo.p);
+    DerivMixed Dv;
+    build_deriv_mixed(H, C, th, Dv);
+    mixed_AtX(H, Dv.CBt, g.U32.p, nullptr, BX.p, "grad");
+    mixed_AtX(H, Dv.CBt, g.Z32.p, nullptr, BY.p, "grad");
+    dgemm(H.ws, s, false, false, m, c, m, 1.0, Dv.E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
+    // sparse terms per column: one gather of Y's neighbour rows for the
+    // residual values and their range derivative
+    const int nb = coldots_blocks();
+    DevPtr<double> part((size_t)nb * kColTerms * ldc), lr((size_t)3 * ldc);
+    grad_coldots<float, float, float>(H, c, ldc, op.vals32.p, Dv.dv.p, g.U32.p, g.Z32.p, part.p, nb);
+    grad_lowrank_cols(H, m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, lr.p);
+    // control variate: A~ M^-1 on the tensor cores, row dots, m-space traces
+    DevPtr<double> cv, mtr;
+    int ncv = 0;
+    if (o.grad_control_variate != kCvNone) {
+      ncv = cv_blocks();
+      cv.alloc((size_t)ncv * kCvTerms);
+      mtr.alloc(2);
+      DevPtr<__nv_bfloat16> Mh(mm_pad), Ml(mm_pad);
+      k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, op.Minv.p, m, m_pad, m_pad, Mh.p, Ml.p);
       FSA_CHECK_LAUNCH();
-      TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
-      TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128),
-             mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
+      TmaMap mMh = make_tma_bf16(Mh.p, m_pad, m_pad, m_pad, 128), mMl = make_tma_bf16(Ml.p, m_pad, m_pad, m_pad, 128);
+      DevPtr<float> AM(nm);
       TcGemm t;
-      t.a[0] = &mKh; t.a[1] = &mKl; t.num_a = 2;
-      t.b[0] = &mLh; t.b[1] = &mLl; t.num_b = 2;
-      t.pairs = 1u | 2u | 4u;
+      t.a[0] = &C.mA; t.a[1] = &C.mA_lo; t.num_a = C.lo ? 2 : 1;
+      t.b[0] = &mMh; t.b[1] = &mMl; t.num_b = 2;
+      t.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
       t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
-      t.out = B32.p; t.ldo = m_pad;
+      t.out = AM.p; t.ldo = m_pad;
       t.tag = "grad";
       tc_gemm(t, H.err, s);
-      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Bb.p);
-      FSA_CHECK_LAUNCH();
-      // E = L^-1 dSigma_m L^-T (FP64), F = A~ E (split products)
-      DevPtr<double> dSm((size_t)m * m);
-      cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
-      dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
-      dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, E.p, m, nullptr);
-      k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, E.p, m, m_pad, m_pad, Lhi.p, Llo.p);
-      FSA_CHECK_LAUNCH();
-      TcGemm f;
-      f.a[0] = &C.mA; f.a[1] = &C.mA_lo; f.num_a = C.lo ? 2 : 1;
-      f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
-      f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
-      f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
-      DevPtr<float> F32(nm);
-      f.out = F32.p; f.ldo = m_pad;
-      f.tag = "grad";
-      tc_gemm(f, H.err, s);
-      // Q = B - F, the gathered operand of the sparse gradient term
-      k_sub_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, F32.p, Fb.p);
-      FSA_CHECK_LAUNCH();
-      FSA_CUDA(cudaStreamSynchronize(s));
+      cv_rowdots_mixed(H, m_pad, AM.p, op.Ab.p, Dv.Alo, Dv.Bh.p, Dv.Bl.p, op.D32.p, Dv.dD.p, cv.p, ncv);
+      mspace_traces(H, m, Dv.E.p, op.Minv.p, mtr.p);
     }
-    {
-      DevPtr<__nv_bfloat16> Bt((size_t)m_pad * C.n_pad);
-      FSA_CUDA(cudaMemsetAsync(Bt.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * C.n_pad, s));
-      k_transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (m_pad + 31) / 32), dim3(32, 8), 0, s>>>(n, m_pad, Bb.p,
-                                                                                              m_pad, Bt.p, C.n_pad, 1);
-      FSA_CHECK_LAUNCH();
-      MixedCtx CB = C;
-      CB.mAt = make_tma_bf16_blocked(Bt.p, m_pad, C.n_pad, 128);
-      CB.lo = false;
-      mixed_AtX(H, CB, g.U32.p, nullptr, BX.p, "grad");
-      mixed_AtX(H, CB, g.Z32.p, nullptr, BY.p, "grad");
-      FSA_CUDA(cudaStreamSynchronize(s));
-    }
-    dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
-    int ngpart = 152 * 8;
-    gbuf.alloc((size_t)ngpart * 3 + 2);
-    int nused = grad_sparse_tiles(H, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th, gbuf.p,
-                                  ngpart);
-    if (nused == 0) {
-      launch_grad_sparse_bf16v(H, ngpart, m_pad, c, ldc, op.vals.p, g.U32.p, g.Z32.p, op.Ab.p, Bb.p, Fb.p, th,
-                               gbuf.p);
-      nused = ngpart;
-    }
-    k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq,
-                                             gbuf.p + (size_t)ngpart * 3);
-    FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
-                                gbuf.p, nused, gbuf.p + (size_t)ngpart * 3, 1, H.outs.p);
+                                H.outs.p);
     FSA_CHECK_LAUNCH();
+    H.gterms.ensure((size_t)6 * l);
+    H.gterms_l = l;
+    grad_final(H, c, ldc, part.p, nb, lr.p, cv.p, ncv, mtr.p, th, o.grad_control_variate, H.gterms.p);
     FSA_CUDA(cudaStreamSynchronize(s));
   } else {
     FSA_CUDA(cudaStreamWaitEvent(s, H.ev_join, 0));
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, ypart.p, lay.nblk, ldc,
-                                nullptr, 0, nullptr, 0, H.outs.p);
+                                H.outs.p);
     FSA_CHECK_LAUNCH();
   }
+  grad_phase.reset();
   LoglikResult res;
-  double outs[8];
+  double outs[kOutCount];
   FSA_CUDA(cudaMemcpyAsync(outs, H.outs.p, sizeof(outs), cudaMemcpyDeviceToHost, s));
   std::vector<int32_t> iters(lay.c);
   std::vector<double> rn(lay.c);
@@ -934,7 +958,13 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   res.loglik = outs[0];
   res.logdet = outs[1];
   res.yu = outs[2];
-  for (int q = 0; q < 3; ++q) res.grad[q] = outs[3 + q];
+  for (int q = 0; q < 3; ++q) {
+    res.grad[q] = outs[kOutGrad + q];
+    res.trace[q] = outs[kOutTrace + q];
+    res.quad[q] = outs[kOutQuad + q];
+    res.traceP[q] = outs[kOutTraceP + q];
+    res.cv_c[q] = outs[kOutCvC + q];
+  }
   res.se = outs[6];
   res.logdetP = outs[7];
   res.iters_y = iters[0];

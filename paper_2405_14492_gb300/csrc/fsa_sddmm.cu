@@ -3,10 +3,8 @@
 //
 //   * the tapered residual values val_ij = (c(s_i, s_j) - a_i . a_j) T(d_ij)
 //     and D_s,i = sigma1^2 - |a_i|^2 + nugget (Eq. eqfitcp), and
-//   * the sparse part of the range derivative of the gradient (Eq.
-//     NEGLLDNEGLLFSA with the derivative of Sigma_dag), whose low-rank piece
-//     sum_ij w_ij (b_i . a_j + a_i . q_j) is evaluated row by row as
-//     b_i . (sum_j w_ij a_j) + a_i . (sum_j w_ij q_j).
+//   * the range derivative of those values (§2.2), with
+//     d(a_i . a_j)/drho = b_i . a_j + a_i . q_j (b = dK L^-T, q = b - A~ E).
 //
 // Both run over the cell-grid tiles of the SpMM: the taper neighbours of a
 // tile's rows lie in three contiguous row ranges, so the m-long rows a_j (and
@@ -266,65 +264,58 @@ bool csr_values_tiles(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, co
 }
 
 // ---------------------------------------------------------------------------
-// gradient, sparse part
+// range derivative of the tapered residual values (per nonzero)
 // ---------------------------------------------------------------------------
-// Per nonzero (i, j): G_ij = sum_k X_ik Y_jk w_k (w_0 = -1, w_k = 1/l), then
-//   s0 += dval/ds1 G = (val_ij - nugget [i = j]) / s1 G
-//   sr += s1 r'(d) T(d) G  (j != i)            (the covariance part)
-//   s2 += [i = j] G
-// and the weight w_ij = T(d_ij) G_ij (T(0) = 1) of the low-rank part
-//   sr -= sum_ij w_ij (b_i . a_j + a_i . q_j),  b = dK L^-T, q = b - A~ E.
-__device__ __forceinline__ float grad_weight(int64_t i, int64_t j, int c, int ldc, const float* __restrict__ X,
-                                             const float* __restrict__ Y, double val, const double* __restrict__ xs,
-                                             const double* __restrict__ ys, int cov, double s1, double rho,
-                                             double nug, double gamma, double& s0, double& sr, double& s2) {
-  const float inv_l = c > 1 ? 1.0f / (float)(c - 1) : 0.f;
-  const float4* x4 = reinterpret_cast<const float4*>(X + i * ldc);
-  const float4* y4 = reinterpret_cast<const float4*>(Y + j * ldc);
-  float gq[4] = {0.f, 0.f, 0.f, 0.f};   // four running sums (columns k mod 4), added pairwise
-  for (int k4 = 0; k4 < ldc / 4; ++k4) {
-    const float4 x = x4[k4], y = y4[k4];
-    const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = 4 * k4 + q;
-      if (k < c) gq[q] = fmaf(xv[q] * (k == 0 ? -1.0f : inv_l), yv[q], gq[q]);
-    }
-  }
-  const float g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
-  const double gd = (double)g;
+// dval_ij = (s1 r'(d_ij) - dl_ij) T(d_ij) for j != i and -dl_ii on the
+// diagonal (r(0) = 1 does not depend on rho, T(0) = 1), with
+//   dl_ij = b_i . a_j + a_i . q_j = d(a_i . a_j)/drho,  b = dK L^-T, q = b - A~ E,
+// every m-long row as a BF16 hi + lo pair (~2^-17).  The diagonal values are
+// dD_s/drho.  Staged like the values kernel: per stage the A~ and q rows of
+// the tile's three neighbour ranges and the b rows of its own rows.
+__device__ __forceinline__ void write_dvalue(int64_t t, int64_t i, int64_t j, double dl,
+                                             const double* __restrict__ xs, const double* __restrict__ ys, int cov,
+                                             double s1, double rho, double gamma, float* __restrict__ dvals,
+                                             float* __restrict__ dD) {
   if (j == i) {
-    s0 += (val - nug) / s1 * gd;
-    s2 += gd;
-    return g;
+    const float v = (float)(-dl);
+    dvals[t] = v;
+    dD[i] = v;
+  } else {
+    const double d = sqrt(sqdist_rn(xs[i], ys[i], xs[j], ys[j]));
+    dvals[t] = (float)((s1 * matern_dr(cov, d, rho) - dl) * wendland(d, gamma));
   }
-  const double d = sqrt(sqdist_rn(xs[i], ys[i], xs[j], ys[j]));
-  const double tp = wendland(d, gamma);
-  s0 += val / s1 * gd;
-  sr += s1 * matern_dr(cov, d, rho) * tp * gd;
-  return (float)(tp * gd);
 }
 
-__global__ void __launch_bounds__(kSdThreads, 1) k_grad_sparse_tiles(
+__device__ __forceinline__ double dl_rows_global(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Alo,
+                                                 const __nv_bfloat16* __restrict__ B, const __nv_bfloat16* __restrict__ Blo,
+                                                 const __nv_bfloat16* __restrict__ Q, const __nv_bfloat16* __restrict__ Qlo,
+                                                 int64_t n, int m_pad, int64_t i, int64_t j) {
+  double s = 0.0;
+  for (int kb = 0; kb < m_pad / 64; ++kb) {
+    const int64_t oi = ((int64_t)kb * n + i) * 64, oj = ((int64_t)kb * n + j) * 64;
+    s += (double)dot_block(reinterpret_cast<const uint4*>(B + oi), reinterpret_cast<const uint4*>(A + oj),
+                           reinterpret_cast<const uint4*>(Blo + oi), reinterpret_cast<const uint4*>(Alo + oj));
+    s += (double)dot_block(reinterpret_cast<const uint4*>(A + oi), reinterpret_cast<const uint4*>(Q + oj),
+                           reinterpret_cast<const uint4*>(Alo + oi), reinterpret_cast<const uint4*>(Qlo + oj));
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(kSdThreads, 1) k_dvals_tiles(
     int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, int cap_rows, int cap_nnz,
-    int cap_trows, int64_t n, int m_pad, int c, int ldc, const int64_t* __restrict__ rowptr,
-    const int32_t* __restrict__ col, const int32_t* __restrict__ scol, const double* __restrict__ vals,
-    const double* __restrict__ xs, const double* __restrict__ ys, const float* __restrict__ X,
-    const float* __restrict__ Y, const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-    const __nv_bfloat16* __restrict__ Q, int cov, double s1, double rho, double nug, double gamma,
-    double* __restrict__ part) {
+    int cap_trows, int64_t n, int m_pad, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ scol, const double* __restrict__ xs, const double* __restrict__ ys,
+    const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Alo, const __nv_bfloat16* __restrict__ B,
+    const __nv_bfloat16* __restrict__ Blo, const __nv_bfloat16* __restrict__ Q, const __nv_bfloat16* __restrict__ Qlo,
+    int cov, double s1, double rho, double gamma, float* __restrict__ dvals, float* __restrict__ dD) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double red[3][kSdThreads / 32];
-  // per stage: A~ rows of the ranges | q rows of the ranges | b rows of the tile (64 BF16 each)
-  const size_t sA = (size_t)cap_rows * 64, sB = (size_t)cap_trows * 64, sstage = 2 * sA + sB;
+  // per stage: A hi, A lo, q hi, q lo of the ranges (cap_rows rows each), then b hi, b lo of the tile rows
+  const size_t plane = (size_t)cap_rows * kSdRowV, tplane = (size_t)cap_trows * kSdRowV;
+  const size_t sstage = 4 * plane + 2 * tplane;
   __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smraw);
-  float* sw = reinterpret_cast<float*>(st + 2 * sstage);
-  int* ssc = reinterpret_cast<int*>(sw + cap_nnz);
-  int* srow = ssc + cap_nnz;
-  int* srp = srow + cap_nnz;   // cap_trows + 1 row offsets
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int* srow = reinterpret_cast<int*>(st + 2 * sstage);
+  int* ssc = srow + cap_nnz;
   const int nkb = m_pad / 64;
-  double s0 = 0.0, sr = 0.0, s2 = 0.0, sdl = 0.0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const TileRec T = load_tile(ptile, tile_bad, tile, cap_rows, cap_nnz, cap_trows);
     if (!T.staged) {
@@ -333,97 +324,105 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_grad_sparse_tiles(
         int64_t i = T.p0;
         while (rowptr[i + 1] <= e) ++i;
         const int64_t j = col[e];
-        const float w = grad_weight(i, j, c, ldc, X, Y, vals[e], xs, ys, cov, s1, rho, nug, gamma, s0, sr, s2);
-        float dl = 0.f;
-        for (int kb = 0; kb < nkb; ++kb) {
-          const uint32_t* aj = reinterpret_cast<const uint32_t*>(A + ((int64_t)kb * n + j) * 64);
-          const uint32_t* ai = reinterpret_cast<const uint32_t*>(A + ((int64_t)kb * n + i) * 64);
-          const uint32_t* bi = reinterpret_cast<const uint32_t*>(B + i * m_pad + kb * 64);
-          const uint32_t* qj = reinterpret_cast<const uint32_t*>(Q + j * m_pad + kb * 64);
-          for (int w2 = 0; w2 < 32; ++w2) {
-            const float2 a = bf2f(aj[w2]), b = bf2f(bi[w2]), a2 = bf2f(ai[w2]), q = bf2f(qj[w2]);
-            dl = fmaf(b.x, a.x, fmaf(b.y, a.y, dl));
-            dl = fmaf(a2.x, q.x, fmaf(a2.y, q.y, dl));
-          }
-        }
-        sdl += (double)(w * dl);
+        write_dvalue(e, i, j, dl_rows_global(A, Alo, B, Blo, Q, Qlo, n, m_pad, i, j), xs, ys, cov, s1, rho, gamma,
+                     dvals, dD);
       }
       continue;
     }
     tile_rows(T, rowptr, scol, srow, ssc);
-    for (int r = threadIdx.x; r <= T.nr; r += kSdThreads) srp[r] = (int)(rowptr[T.p0 + r] - T.e0);
     auto issue = [&](int kb) {
       __nv_bfloat16* sb = st + (size_t)(kb & 1) * sstage;
-      const __nv_bfloat16* Ak = A + (int64_t)kb * n * 64;
-      stage_rows(sb, 0, 64, Ak, 64, T.r0b, T.n0);
-      stage_rows(sb, T.n0, 64, Ak, 64, T.r1b, T.n1);
-      stage_rows(sb, T.n0 + T.n1, 64, Ak, 64, T.r2b, T.n2);
-      const __nv_bfloat16* Qk = Q + kb * 64;
-      stage_rows(sb + sA, 0, 64, Qk, m_pad, T.r0b, T.n0);
-      stage_rows(sb + sA, T.n0, 64, Qk, m_pad, T.r1b, T.n1);
-      stage_rows(sb + sA, T.n0 + T.n1, 64, Qk, m_pad, T.r2b, T.n2);
-      stage_rows(sb + 2 * sA, 0, 64, B + kb * 64, m_pad, T.p0, T.nr);
+      const __nv_bfloat16* srcs[4] = {A, Alo, Q, Qlo};
+      for (int p = 0; p < 4; ++p) {
+        const __nv_bfloat16* src = srcs[p] + (int64_t)kb * n * 64;
+        __nv_bfloat16* dst = sb + p * plane;
+        stage_rows(dst, 0, kSdRowV, src, 64, T.r0b, T.n0);
+        stage_rows(dst, T.n0, kSdRowV, src, 64, T.r1b, T.n1);
+        stage_rows(dst, T.n0 + T.n1, kSdRowV, src, 64, T.r2b, T.n2);
+      }
+      stage_rows(sb + 4 * plane, 0, kSdRowV, B + (int64_t)kb * n * 64, 64, T.p0, T.nr);
+      stage_rows(sb + 4 * plane + tplane, 0, kSdRowV, Blo + (int64_t)kb * n * 64, 64, T.p0, T.nr);
       cpa_commit();
     };
     issue(0);
-    __syncthreads();   // srow, ssc
-    for (int t = threadIdx.x; t < T.ne; t += kSdThreads)
-      sw[t] = grad_weight((int64_t)T.p0 + srow[t], col[T.e0 + t], c, ldc, X, Y, vals[T.e0 + t], xs, ys, cov, s1,
-                          rho, nug, gamma, s0, sr, s2);
+    double acc[kSdPer] = {0.0, 0.0, 0.0, 0.0};
     for (int kb = 0; kb < nkb; ++kb) {
       if (kb + 1 < nkb) issue(kb + 1);
       else cpa_commit();
       cpa_wait<1>();
-      __syncthreads();   // block kb staged by every thread; the weights written
-      const uint32_t* sa = reinterpret_cast<const uint32_t*>(st + (size_t)(kb & 1) * sstage);
-      const uint32_t* sq = sa + sA / 2;
-      const uint32_t* sbr = sa + sA;
-      for (int r = wib; r < T.nr; r += kSdWarps) {
-        const int tb = srp[r], te = srp[r + 1];
-        float px = 0.f, py = 0.f, qx = 0.f, qy = 0.f;
-#pragma unroll 4
-        for (int t = tb; t < te; ++t) {
-          const float w = sw[t];
-          const int rj = ssc[t];
-          const float2 a = bf2f(sa[rj * 32 + lane]), q = bf2f(sq[rj * 32 + lane]);
-          px = fmaf(w, a.x, px); py = fmaf(w, a.y, py);
-          qx = fmaf(w, q.x, qx); qy = fmaf(w, q.y, qy);
+      __syncthreads();
+      const __nv_bfloat16* sb = st + (size_t)(kb & 1) * sstage;
+#pragma unroll
+      for (int u = 0; u < kSdPer; ++u) {
+        const int t = threadIdx.x + u * kSdThreads;
+        if (t < T.ne) {
+          const int r = srow[t];
+          const int ri = T.n0 + (T.p0 + r - T.r1b), rj = ssc[t];
+          auto row = [&](int pl, int k) { return reinterpret_cast<const uint4*>(sb + pl * plane + (size_t)k * kSdRowV); };
+          const uint4* bh = reinterpret_cast<const uint4*>(sb + 4 * plane + (size_t)r * kSdRowV);
+          const uint4* bl = reinterpret_cast<const uint4*>(sb + 4 * plane + tplane + (size_t)r * kSdRowV);
+          acc[u] += (double)dot_block(bh, row(0, rj), bl, row(1, rj));
+          acc[u] += (double)dot_block(row(0, ri), row(2, rj), row(1, ri), row(3, rj));
         }
-        const int ri = T.n0 + (T.p0 + r - T.r1b);
-        const float2 ai = bf2f(sa[ri * 32 + lane]), bi = bf2f(sbr[r * 32 + lane]);
-        sdl += (double)(bi.x * px + bi.y * py + ai.x * qx + ai.y * qy);
       }
       __syncthreads();   // stage kb & 1 is free for block kb + 2
     }
+#pragma unroll
+    for (int u = 0; u < kSdPer; ++u) {
+      const int t = threadIdx.x + u * kSdThreads;
+      if (t < T.ne) {
+        const int64_t e = T.e0 + t;
+        write_dvalue(e, (int64_t)T.p0 + srow[t], col[e], acc[u], xs, ys, cov, s1, rho, gamma, dvals, dD);
+      }
+    }
+    __syncthreads();   // srow, ssc are rewritten by the next tile
   }
   cpa_wait<0>();
-  // fixed-order block reduction: warp sums, then the warps in order
-  s0 = warp_sum(s0);
-  s2 = warp_sum(s2);
-  const double srt = warp_sum(sr - sdl);
-  if (lane == 0) { red[0][wib] = s0; red[1][wib] = srt; red[2][wib] = s2; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < kSdThreads / 32; ++w) s += red[threadIdx.x][w];
-    part[(int64_t)blockIdx.x * 3 + threadIdx.x] = s;
-  }
 }
 
-int grad_sparse_tiles(Handle& H, int m_pad, int c, int ldc, const double* vals, const float* X, const float* Y,
-                      const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q, const fsa_theta& th,
-                      double* part, int max_blocks, int cap_rows_max) {
-  if (H.ntiles <= 0 || m_pad % 64 != 0 || ldc % 4 != 0) return 0;
-  const SdLaunch L = sd_launch(H, 2 * 64 * sizeof(__nv_bfloat16), 64 * sizeof(__nv_bfloat16),
-                               3 * sizeof(int) + sizeof(float), reinterpret_cast<const void*>(k_grad_sparse_tiles),
-                               cap_rows_max);
-  if (L.blocks <= 0) return 0;
-  const int blocks = std::min(L.blocks, max_blocks);
-  k_grad_sparse_tiles<<<blocks, kSdThreads, L.smem, H.stream>>>(
-      H.ntiles, H.ptile.p, H.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, H.n, m_pad, c, ldc, H.rowptr.p, H.col.p,
-      H.scol.p, vals, H.xs.p, H.ys.p, X, Y, A, B, Q, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma, part);
+// one warp per nonzero, from global memory (handles without tiles)
+__global__ void k_dvals_rows(int64_t n, int m_pad, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ xs, const double* __restrict__ ys,
+                             const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Alo,
+                             const __nv_bfloat16* __restrict__ B, const __nv_bfloat16* __restrict__ Blo,
+                             const __nv_bfloat16* __restrict__ Q, const __nv_bfloat16* __restrict__ Qlo, int cov,
+                             double s1, double rho, double gamma, float* __restrict__ dvals, float* __restrict__ dD) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      write_dvalue(e, i, col[e], dl_rows_global(A, Alo, B, Blo, Q, Qlo, n, m_pad, i, col[e]), xs, ys, cov, s1, rho,
+                   gamma, dvals, dD);
+}
+
+bool dvals_tiles(Handle& H, const fsa_theta& th, int m_pad, const __nv_bfloat16* A, const __nv_bfloat16* Alo,
+                 const __nv_bfloat16* B, const __nv_bfloat16* Blo, const __nv_bfloat16* Q, const __nv_bfloat16* Qlo,
+                 float* dvals, float* dD, int cap_rows_max) {
+  if (H.ntiles <= 0 || m_pad % 64 != 0) return false;
+  const SdLaunch L = sd_launch(H, 4 * kSdRowV * sizeof(__nv_bfloat16), 2 * kSdRowV * sizeof(__nv_bfloat16),
+                               2 * sizeof(int), reinterpret_cast<const void*>(k_dvals_tiles), cap_rows_max);
+  if (L.blocks <= 0) return false;
+  k_dvals_tiles<<<L.blocks, kSdThreads, L.smem, H.stream>>>(
+      H.ntiles, H.ptile.p, H.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, H.n, m_pad, H.rowptr.p, H.col.p,
+      H.scol.p, H.xs.p, H.ys.p, A, Alo, B, Blo, Q, Qlo, H.cov, th.sigma1_sq, th.rho, H.gamma, dvals, dD);
   FSA_CHECK_LAUNCH();
-  return blocks;
+  return true;
+}
+
+void dvals_rows(Handle& H, const fsa_theta& th, int m_pad, const __nv_bfloat16* A, const __nv_bfloat16* Alo,
+                const __nv_bfloat16* B, const __nv_bfloat16* Blo, const __nv_bfloat16* Q, const __nv_bfloat16* Qlo,
+                float* dvals, float* dD) {
+  k_dvals_rows<<<grid_for(H.n, 128), 128, 0, H.stream>>>(H.n, m_pad, H.rowptr.p, H.col.p, H.xs.p, H.ys.p, A, Alo,
+                                                          B, Blo, Q, Qlo, H.cov, th.sigma1_sq, th.rho, H.gamma,
+                                                          dvals, dD);
+  FSA_CHECK_LAUNCH();
+}
+
+void dvals_mixed(Handle& H, const fsa_theta& th, int m_pad, const __nv_bfloat16* A, const __nv_bfloat16* Alo,
+                 const __nv_bfloat16* B, const __nv_bfloat16* Blo, const __nv_bfloat16* Q, const __nv_bfloat16* Qlo,
+                 float* dvals, float* dD) {
+  FSA_REQUIRE(m_pad % 64 == 0 && A && Alo && B && Blo && Q && Qlo, FSA_ERR_UNSUPPORTED,
+              "range derivative values need BF16 pairs of A~, b and q with m_pad % 64 == 0");
+  if (!dvals_tiles(H, th, m_pad, A, Alo, B, Blo, Q, Qlo, dvals, dD, 0))
+    dvals_rows(H, th, m_pad, A, Alo, B, Blo, Q, Qlo, dvals, dD);
 }
 
 }  // namespace fsa

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fsa_grad.cuh"
 #include "fsa_vec.cuh"
 
 namespace fsa {
@@ -126,10 +127,10 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
 
 namespace fsa {
 
-static __global__ void k_fill_bf16(int64_t total, uint64_t key, __nv_bfloat16* __restrict__ out) {
+static __global__ void k_fill_bf16(int64_t total, uint64_t key, float scale, __nv_bfloat16* __restrict__ out) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x)
-    out[t] = __float2bfloat16_rn((float)(rng_at(key, (uint64_t)t) >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f);
+    out[t] = __float2bfloat16_rn(scale * ((float)(rng_at(key, (uint64_t)t) >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f));
 }
 
 // max |a - b| and max |b| over FP64 arrays (non-negative doubles as ordered bit patterns)
@@ -146,11 +147,25 @@ static __global__ void k_max_abs_diff_f64(int64_t total, const double* __restric
   atomicMax(out + 1, (unsigned long long)__double_as_longlong(mb));
 }
 
+// the same over FP32 arrays (stored as FP64 bit patterns)
+static __global__ void k_max_abs_diff_f32(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
+                                          unsigned long long* __restrict__ out) {
+  double mx = 0.0, mb = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double d = fabs((double)a[t] - (double)b[t]);
+    if (!(d <= mx)) mx = (d != d) ? INFINITY : d;
+    mb = fmax(mb, fabs((double)b[t]));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+  atomicMax(out + 1, (unsigned long long)__double_as_longlong(mb));
+}
+
 }  // namespace fsa
 
-extern "C" int fsa_selftest_sddmm(fsa_handle* hh, const fsa_theta* theta, int precision, int ncols, int cap_rows,
-                                  uint64_t seed, double* val_err, double* grad_tile, double* grad_row) {
-  if (!hh || !theta || !val_err || !grad_tile || !grad_row || ncols < 1 || ncols > 127 || cap_rows < 0 ||
+extern "C" int fsa_selftest_sddmm(fsa_handle* hh, const fsa_theta* theta, int precision, int cap_rows,
+                                  uint64_t seed, double* val_err, double* dval_err) {
+  if (!hh || !theta || !val_err || !dval_err || cap_rows < 0 ||
       (precision != FSA_MIXED_BF16 && precision != FSA_MIXED_BF16X2)) {
     set_error("fsa_selftest_sddmm: bad argument");
     return FSA_ERR_ARG;
@@ -172,46 +187,42 @@ extern "C" int fsa_selftest_sddmm(fsa_handle* hh, const fsa_theta* theta, int pr
     FSA_CUDA(cudaMemcpyAsync(Dt.p, op.D.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     csr_values_rows(H, *theta, op.Ab.p, Alo, m_pad);
     op.valid = false;   // the operator now holds the row form's values: rebuilt on next use
-    DevPtr<unsigned long long> mx(4);
-    FSA_CUDA(cudaMemsetAsync(mx.p, 0, 4 * sizeof(unsigned long long), s));
+    DevPtr<unsigned long long> mx(8);
+    FSA_CUDA(cudaMemsetAsync(mx.p, 0, 8 * sizeof(unsigned long long), s));
     k_max_abs_diff_f64<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, vt.p, op.vals.p, mx.p);
     k_max_abs_diff_f64<<<grid_for(n, 256), 256, 0, s>>>(n, Dt.p, op.D.p, mx.p + 2);
     FSA_CHECK_LAUNCH();
-    // gradient sparse part on seeded X, Y, B, Q
-    const int ldc = (ncols + 7) / 8 * 8;
-    const size_t nc = (size_t)n * ldc, nm = (size_t)n * m_pad;
-    DevPtr<float> X(nc), Y(nc);
-    DevPtr<__nv_bfloat16> B(nm), Q(nm);
-    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, ncols, ldc, rng_key(seed, 21), X.p);
-    k_fill_f32<<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, ncols, ldc, rng_key(seed, 22), Y.p);
-    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 23), B.p);
-    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 24), Q.p);
+    // range derivative of the values on seeded BF16 pairs a (zeros if single), b, q
+    const size_t nm = (size_t)n * m_pad;
+    DevPtr<__nv_bfloat16> zlo, Bh(nm), Bl(nm), Qh(nm), Ql(nm);
+    if (!Alo) {
+      zlo.alloc(nm);
+      FSA_CUDA(cudaMemsetAsync(zlo.p, 0, nm * sizeof(__nv_bfloat16), s));
+      Alo = zlo.p;
+    }
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 23), 1.0f, Bh.p);
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 24), 1.0f / 256, Bl.p);
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 25), 1.0f, Qh.p);
+    k_fill_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, rng_key(seed, 26), 1.0f / 256, Ql.p);
     FSA_CHECK_LAUNCH();
-    const int nb = 152 * 8;
-    DevPtr<double> pt((size_t)nb * 3), pr((size_t)nb * 3);
-    const int used = grad_sparse_tiles(H, m_pad, ncols, ldc, op.vals.p, X.p, Y.p, op.Ab.p, B.p, Q.p, *theta, pt.p, nb,
-                                       cap_rows);
-    FSA_REQUIRE(used > 0, FSA_ERR_UNSUPPORTED, "tile form unavailable for this handle");
-    grad_sparse_rows(H, nb, m_pad, ncols, ldc, op.vals.p, X.p, Y.p, op.Ab.p, B.p, Q.p, *theta, pr.p);
-    std::vector<double> ht((size_t)used * 3), hr((size_t)nb * 3);
-    unsigned long long bits[4];
-    FSA_CUDA(cudaMemcpyAsync(ht.data(), pt.p, sizeof(double) * ht.size(), cudaMemcpyDeviceToHost, s));
-    FSA_CUDA(cudaMemcpyAsync(hr.data(), pr.p, sizeof(double) * hr.size(), cudaMemcpyDeviceToHost, s));
+    DevPtr<float> dvt(nnz + 4), dDt(n), dvr(nnz + 4), dDr(n);
+    FSA_REQUIRE(dvals_tiles(H, *theta, m_pad, op.Ab.p, Alo, Bh.p, Bl.p, Qh.p, Ql.p, dvt.p, dDt.p, cap_rows),
+                FSA_ERR_UNSUPPORTED, "tile form unavailable for this handle");
+    dvals_rows(H, *theta, m_pad, op.Ab.p, Alo, Bh.p, Bl.p, Qh.p, Ql.p, dvr.p, dDr.p);
+    k_max_abs_diff_f32<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, dvt.p, dvr.p, mx.p + 4);
+    k_max_abs_diff_f32<<<grid_for(n, 256), 256, 0, s>>>(n, dDt.p, dDr.p, mx.p + 6);
+    FSA_CHECK_LAUNCH();
+    unsigned long long bits[8];
     FSA_CUDA(cudaMemcpyAsync(bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
     FSA_CUDA(cudaStreamSynchronize(s));
     check_err(H);
-    for (int k = 0; k < 3; ++k) {
-      double a = 0.0, b = 0.0;
-      for (int u = 0; u < used; ++u) a += ht[(size_t)u * 3 + k];
-      for (int u = 0; u < nb; ++u) b += hr[(size_t)u * 3 + k];
-      grad_tile[k] = a;
-      grad_row[k] = b;
-    }
-    double d[4];
+    double d[8];
     std::memcpy(d, bits, sizeof(d));
-    // max-norm relative differences of the values and of D
+    // max-norm relative differences
     val_err[0] = d[1] > 0 ? d[0] / d[1] : d[0];
     val_err[1] = d[3] > 0 ? d[2] / d[3] : d[2];
+    dval_err[0] = d[5] > 0 ? d[4] / d[5] : d[4];
+    dval_err[1] = d[7] > 0 ? d[6] / d[7] : d[6];
     return FSA_OK;
   } catch (const Error& e) {
     cudaGetLastError();

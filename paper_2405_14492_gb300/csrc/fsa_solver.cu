@@ -15,6 +15,7 @@
 // twice:  w = A^T (D^-1 r) ;  q = M^-1 w ;  s = A q = A A^T z ;
 // z = D^-1 (r - s) ;  Sigma_dag z = Sigma_s~ z + s ;  v_{l+1} = Sigma_dag z + beta v_l
 // (v = Sigma_dag h follows from h = z + beta h by linearity).
+#include "fsa_grad.cuh"
 #include "fsa_kernels.cuh"
 #include "fsa_solver.cuh"
 #include "fsa_vec.cuh"
@@ -230,113 +231,12 @@ __global__ void k_gather_y(int64_t n, const int64_t* __restrict__ perm, const do
 }
 
 // ---------------------------------------------------------------------------
-// gradient (Eq. NEGLLDNEGLLFSA with dSigma_dag of §2.2), sparse part:
-//   sum over the taper pattern of dval_ij G_ij,  G_ij = sum_k w_k X_ik Y_jk
-//   (w_0 = -1 with X_0 = Y_0 = u;  w_k = 1/l with X_k = U_k, Y_k = W_k)
-//   dval (s1)    = (val_ij - nugget [i=j]) / s1
-//   dval (rho)   = (s1 r'(d) - (b_i.a_j + a_i.b_j - a_i.f_j)) T(d),  b = dK L^-T, f = A E
-//   dval (nugget)= [i = j]
-// ---------------------------------------------------------------------------
-template <typename T, typename AT>
-__global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* __restrict__ rowptr,
-                              const int32_t* __restrict__ colidx, const double* __restrict__ vals,
-                              const double* __restrict__ xs, const double* __restrict__ ys, const T* __restrict__ X,
-                              const T* __restrict__ Y, const AT* __restrict__ A, const AT* __restrict__ B,
-                              const AT* __restrict__ F, int64_t lda, int cov, double s1, double rho, double nug,
-                              double gamma, double* __restrict__ part) {
-  __shared__ double red[3][32];
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double s0 = 0.0, sr = 0.0, s2 = 0.0;
-  double inv_l = c > 1 ? 1.0 / (c - 1) : 0.0;
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const T* xi = X + i * ldc;
-    const AT* ai = A + i * lda;
-    const AT* bi = B + i * lda;
-    double xi0 = xs[i], yi0 = ys[i];
-    for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
-      int j = colidx[t];
-      const T* yj = Y + (int64_t)j * ldc;
-      double g = 0.0;
-      for (int k = lane; k < c; k += 32) g += (k == 0 ? -1.0 : inv_l) * (double)xi[k] * (double)yj[k];
-      g = warp_sum(g);
-      const AT* aj = A + (int64_t)j * lda;
-      const AT* bj = B + (int64_t)j * lda;
-      const AT* fj = F + (int64_t)j * lda;
-      double dl = 0.0;
-      for (int k = lane; k < m; k += 32)
-        dl += (double)bi[k] * (double)aj[k] + (double)ai[k] * (double)bj[k] - (double)ai[k] * (double)fj[k];
-      dl = warp_sum(dl);
-      if (lane == 0) {
-        if (j == i) {
-          s0 += (vals[t] - nug) / s1 * g;
-          sr += -dl * g;
-          s2 += g;
-        } else {
-          double d = sqrt(sqdist_rn(xi0, yi0, xs[j], ys[j]));
-          double tp = wendland(d, gamma);
-          s0 += vals[t] / s1 * g;
-          sr += (s1 * matern_dr(cov, d, rho) - dl) * tp * g;
-        }
-      }
-    }
-  }
-  if (lane == 0) { red[0][wib] = s0; red[1][wib] = sr; red[2][wib] = s2; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-    part[(int64_t)blockIdx.x * 3 + threadIdx.x] = s;
-  }
-}
-
-void launch_grad_sparse_bf16(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
-                             const float* X, const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B,
-                             const __nv_bfloat16* F, const fsa_theta& th, double* part) {
-  k_grad_sparse<float, __nv_bfloat16><<<nblocks, 256, 0, H.stream>>>(
-      H.n, m_pad, c, ldc, H.rowptr.p, H.col.p, vals, H.xs.p, H.ys.p, X, Y, A, B, F, m_pad, H.cov, th.sigma1_sq,
-      th.rho, th.nugget, H.gamma, part);
-  FSA_CHECK_LAUNCH();
-}
-
-// low-rank part: sum_k w_k [ (A^T X_k).(A^T Y_k) / s1 ,
-//   (B^T X_k).(A^T Y_k) + (A^T X_k).(B^T Y_k) - (A^T X_k).(E A^T Y_k) ]
-__global__ void k_grad_lowrank(int m, int c, int ldc, const double* __restrict__ AX, const double* __restrict__ AY,
-                               const double* __restrict__ BX, const double* __restrict__ BY,
-                               const double* __restrict__ EAY, double s1, double* __restrict__ out2) {
-  __shared__ double sh[2][1024];
-  int k = threadIdx.x;
-  double a0 = 0.0, a1 = 0.0;
-  if (k < c) {
-    double w = k == 0 ? -1.0 : 1.0 / (c - 1);
-    double t0 = 0.0, t1 = 0.0;
-    for (int a = 0; a < m; ++a) {
-      int64_t idx = (int64_t)a * ldc + k;
-      t0 += AX[idx] * AY[idx];
-      t1 += BX[idx] * AY[idx] + AX[idx] * BY[idx] - AX[idx] * EAY[idx];
-    }
-    a0 = w * t0 / s1;
-    a1 = w * t1;
-  }
-  sh[0][threadIdx.x] = a0;
-  sh[1][threadIdx.x] = a1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0.0, s1_ = 0.0;
-    for (int t = 0; t < (int)blockDim.x; ++t) { s0 += sh[0][t]; s1_ += sh[1][t]; }
-    out2[0] = s0;
-    out2[1] = s1_;
-  }
-}
-
-// final assembly of log-likelihood, log det, gradient
-// outs: [0] loglik [1] logdet [2] yu [3..5] grad [6] logdet_se [7] logdetP
+// final assembly of the log-likelihood and log det (the gradient's slots are
+// written by grad_final)
+// outs: [0] loglik [1] logdet [2] yu [6] logdet_se [7] logdetP
 __global__ void k_assemble(int64_t n, int c, int exact_weight, const double* __restrict__ quads,
                            const double* __restrict__ rz0, const double* __restrict__ scal,
-                           const double* __restrict__ part_yu, int nblk_yu, int ldc,
-                           const double* __restrict__ gpart, int ngpart, const double* __restrict__ glow,
-                           int want_grad, double* __restrict__ outs) {
+                           const double* __restrict__ part_yu, int nblk_yu, int ldc, double* __restrict__ outs) {
   if (threadIdx.x != 0) return;
   int l = c - 1;
   double mean = 0.0;
@@ -356,14 +256,6 @@ __global__ void k_assemble(int64_t n, int c, int exact_weight, const double* __r
   outs[2] = yu;
   outs[6] = se;
   outs[7] = scal[2];
-  if (want_grad) {
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < ngpart; ++b)
-      for (int q = 0; q < 3; ++q) g[q] += gpart[(int64_t)b * 3 + q];
-    g[0] += glow[0];
-    g[1] += glow[1];
-    for (int q = 0; q < 3; ++q) outs[3 + q] = -0.5 * g[q];
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -457,6 +349,7 @@ void ensure_operator(Handle& H, const fsa_theta& th, int precision) {
     return;
   op.valid = false;
   TraceRange trace("operator_build");
+  ProfScope phase("phase_build", 0.0, H.stream);
   if (precision == FSA_FP64) build_operator_fp64(H, th);
   else build_operator_mixed(H, th, precision);
   check_err(H);
@@ -473,33 +366,19 @@ static void lowrank_fp64(Handle& H, const CGLayout& lay, const double* X, double
         nullptr);
 }
 
-LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o) {
+// Block PCG of Appendix A, FP64 form, on the right-hand sides in H.cg.R
+// (n x ldc, columns >= c zero): U receives Sigma_dag^-1 R, W0 the first
+// preconditioner apply P_hat^-1 R, the per-column scalars the Lanczos
+// tridiagonals, iteration counts and residual norms.
+void pcg_fp64_run(Handle& H, const CGLayout& lay, const fsa_opts& o, int L) {
   cudaStream_t s = H.stream;
   Operator& op = H.op;
   CGState& g = H.cg;
-  int64_t n = H.n;
-  int m = H.m;
-  int l = o.num_probes;
-  CGLayout lay;
-  int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
-  lay.setup(n, l + 1, L);
-  ensure_cg(H, lay, true);
-  int ldc = lay.ldc;
-  size_t nc = (size_t)n * ldc;
-  dim3 cgrid(lay.nblk), cblk(lay.threads), eblk(lay.ethreads);
+  const int64_t n = H.n;
+  const int ldc = lay.ldc;
+  const size_t nc = (size_t)n * ldc;
+  dim3 cgrid(lay.nblk), eblk(lay.ethreads);
   const size_t vsm = (size_t)lay.ethreads * sizeof(double);
-  // probes: R = [y, A eps1 + D^1/2 eps2]
-  {
-    DevPtr<double> E1((size_t)m * l);
-    k_eps1<<<grid_for((int64_t)m * l, 256), 256, 0, s>>>(m, l, o.probe, rng_key(o.seed, kStreamEps1), E1.p, l);
-    FSA_CHECK_LAUNCH();
-    dgemm(H.ws, s, false, false, (int)n, l, m, 1.0, op.A.p, m, E1.p, l, 0.0, g.R.p + 1, ldc, nullptr);
-    FSA_CUDA(cudaStreamSynchronize(s));
-    k_probe_finish<double><<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, o.probe,
-                                                                       rng_key(o.seed, kStreamEps2), H.perm.p,
-                                                                       H.y.p, op.D.p, g.R.p);
-    FSA_CHECK_LAUNCH();
-  }
   FSA_CUDA(cudaMemsetAsync(g.U.p, 0, nc * sizeof(double), s));
   FSA_CUDA(cudaMemsetAsync(g.V.p, 0, nc * sizeof(double), s));
   FSA_CUDA(cudaMemsetAsync(g.H.p, 0, nc * sizeof(double), s));
@@ -535,15 +414,40 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
       if (*pin_active == 0) break;
     }
   }
+}
+
+LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o) {
+  cudaStream_t s = H.stream;
+  Operator& op = H.op;
+  CGState& g = H.cg;
+  int64_t n = H.n;
+  int m = H.m;
+  int l = o.num_probes;
+  CGLayout lay;
+  int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
+  lay.setup(n, l + 1, L);
+  ensure_cg(H, lay, true);
+  int ldc = lay.ldc;
+  size_t nc = (size_t)n * ldc;
+  // probes: R = [y, A eps1 + D^1/2 eps2]
+  {
+    DevPtr<double> E1((size_t)m * l);
+    k_eps1<<<grid_for((int64_t)m * l, 256), 256, 0, s>>>(m, l, o.probe, rng_key(o.seed, kStreamEps1), E1.p, l);
+    FSA_CHECK_LAUNCH();
+    dgemm(H.ws, s, false, false, (int)n, l, m, 1.0, op.A.p, m, E1.p, l, 0.0, g.R.p + 1, ldc, nullptr);
+    FSA_CUDA(cudaStreamSynchronize(s));
+    k_probe_finish<double><<<grid_for((int64_t)nc, 256), 256, 0, s>>>(n, l, ldc, o.probe,
+                                                                       rng_key(o.seed, kStreamEps2), H.perm.p,
+                                                                       H.y.p, op.D.p, g.R.p);
+    FSA_CHECK_LAUNCH();
+  }
+  pcg_fp64_run(H, lay, o, L);
   // SLQ
   launch_slq(lay.c, L, g.iters.p, g.tdiag.p, g.toff.p, g.quads.p, H.err, s);
   // y^T u
   k_dot_col0<double><<<lay.nblk, 32, 0, s>>>(n, ldc, lay.chunk, H.y.p, g.U.p, g.part.p);
   FSA_CHECK_LAUNCH();
-  double* gpart = nullptr;
-  double* glow = nullptr;
-  int ngpart = 0;
-  DevPtr<double> gbuf;
+  H.outs.ensure(kOutCount);
   if (o.want_grad) {
     // X = U (u in column 0), Y = W with u in column 0 (stored in Z)
     FSA_CUDA(cudaMemcpyAsync(g.Z.p, g.W0.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -551,50 +455,44 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
     FSA_CHECK_LAUNCH();
     int c = lay.c;
     size_t mc = (size_t)m * ldc;
-    DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc), E((size_t)m * m), T1((size_t)m * m);
+    DevPtr<double> AX(mc), AY(mc), BX(mc), BY(mc), EAY(mc);
     dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, op.A.p, m, g.U.p, ldc, 0.0, AX.p, ldc, nullptr);
     dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, op.A.p, m, g.Z.p, ldc, 0.0, AY.p, ldc, nullptr);
-    DevPtr<double> Bm((size_t)n * m), F((size_t)n * m);
-    {
-      DevPtr<double> dK((size_t)n * m);
-      cov_cross(H, n, H.xs.p, H.ys.p, m, H.ind_x.p, H.ind_y.p, th, 1, dK.p, m);
-      dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, dK.p, m, op.Lmi.p, m, 0.0, Bm.p, m, nullptr);
-      FSA_CUDA(cudaStreamSynchronize(s));
+    DerivF64 Dv;
+    build_deriv_f64(H, th, Dv);
+    dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, Dv.B.p, m, g.U.p, ldc, 0.0, BX.p, ldc, nullptr);
+    dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, Dv.B.p, m, g.Z.p, ldc, 0.0, BY.p, ldc, nullptr);
+    dgemm(H.ws, s, false, false, m, c, m, 1.0, Dv.E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
+    // sparse terms per column (range derivative of the residual values, one gather)
+    const int nb = coldots_blocks();
+    DevPtr<double> part((size_t)nb * kColTerms * ldc), lr((size_t)3 * ldc);
+    grad_coldots<double, double, double>(H, c, ldc, op.vals.p, Dv.dv.p, g.U.p, g.Z.p, part.p, nb);
+    grad_lowrank_cols(H, m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, lr.p);
+    DevPtr<double> cv, mtr;
+    int ncv = 0;
+    if (o.grad_control_variate != kCvNone) {
+      ncv = cv_blocks();
+      cv.alloc((size_t)ncv * kCvTerms);
+      mtr.alloc(2);
+      DevPtr<double> AM((size_t)n * m);
+      dgemm(H.ws, s, false, false, (int)n, m, m, 1.0, op.A.p, m, op.Minv.p, m, 0.0, AM.p, m, nullptr);
+      cv_rowdots_f64(H, m, AM.p, op.A.p, Dv.B.p, op.D.p, Dv.dD.p, cv.p, ncv);
+      mspace_traces(H, m, Dv.E.p, op.Minv.p, mtr.p);
     }
-    dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, Bm.p, m, g.U.p, ldc, 0.0, BX.p, ldc, nullptr);
-    dgemm(H.ws, s, true, false, m, c, (int)n, 1.0, Bm.p, m, g.Z.p, ldc, 0.0, BY.p, ldc, nullptr);
-    {
-      DevPtr<double> dSm((size_t)m * m);
-      cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
-      dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
-      dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, E.p, m, nullptr);
-      FSA_CUDA(cudaStreamSynchronize(s));
-    }
-    dgemm(H.ws, s, false, false, m, c, m, 1.0, E.p, m, AY.p, ldc, 0.0, EAY.p, ldc, nullptr);
-    dgemm(H.ws, s, false, false, (int)n, m, m, 1.0, op.A.p, m, E.p, m, 0.0, F.p, m, nullptr);
-    ngpart = 152 * 8;
-    gbuf.alloc((size_t)ngpart * 3 + 2);
-    gpart = gbuf.p;
-    glow = gbuf.p + (size_t)ngpart * 3;
-    k_grad_sparse<double, double><<<ngpart, 256, 0, s>>>(n, m, c, ldc, H.rowptr.p, H.col.p, op.vals.p, H.xs.p,
-                                                         H.ys.p, g.U.p, g.Z.p, op.A.p, Bm.p, F.p, m, H.cov,
-                                                         th.sigma1_sq, th.rho, th.nugget, H.gamma, gpart);
-    FSA_CHECK_LAUNCH();
-    k_grad_lowrank<<<1, lay.threads, 0, s>>>(m, c, ldc, AX.p, AY.p, BX.p, BY.p, EAY.p, th.sigma1_sq, glow);
-    FSA_CHECK_LAUNCH();
-    H.outs.ensure(16);
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, g.part.p, lay.nblk,
-                                ldc, gpart, ngpart, glow, 1, H.outs.p);
+                                ldc, H.outs.p);
     FSA_CHECK_LAUNCH();
+    H.gterms.ensure((size_t)6 * l);
+    H.gterms_l = l;
+    grad_final(H, c, ldc, part.p, nb, lr.p, cv.p, ncv, mtr.p, th, o.grad_control_variate, H.gterms.p);
     FSA_CUDA(cudaStreamSynchronize(s));
   } else {
-    H.outs.ensure(16);
     k_assemble<<<1, 32, 0, s>>>(n, lay.c, o.slq_exact_weight, g.quads.p, g.rz0.p, op.scal.p, g.part.p, lay.nblk,
-                                ldc, nullptr, 0, nullptr, 0, H.outs.p);
+                                ldc, H.outs.p);
     FSA_CHECK_LAUNCH();
   }
   LoglikResult res;
-  double outs[8];
+  double outs[kOutCount];
   FSA_CUDA(cudaMemcpyAsync(outs, H.outs.p, sizeof(outs), cudaMemcpyDeviceToHost, s));
   std::vector<int32_t> iters(lay.c);
   std::vector<double> rn(lay.c);
@@ -607,7 +505,13 @@ LoglikResult run_loglik_grad_fp64(Handle& H, const fsa_theta& th, const fsa_opts
   res.loglik = outs[0];
   res.logdet = outs[1];
   res.yu = outs[2];
-  for (int q = 0; q < 3; ++q) res.grad[q] = outs[3 + q];
+  for (int q = 0; q < 3; ++q) {
+    res.grad[q] = outs[kOutGrad + q];
+    res.trace[q] = outs[kOutTrace + q];
+    res.quad[q] = outs[kOutQuad + q];
+    res.traceP[q] = outs[kOutTraceP + q];
+    res.cv_c[q] = outs[kOutCvC + q];
+  }
   res.se = outs[6];
   res.logdetP = outs[7];
   res.iters_y = iters[0];

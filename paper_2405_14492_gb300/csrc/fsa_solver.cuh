@@ -15,6 +15,9 @@ struct CGLayout {
 
 struct LoglikResult {
   double loglik = 0, logdet = 0, yu = 0, grad[3] = {0, 0, 0}, se = 0, logdetP = 0;
+  // gradient parts: trace estimate, quadratic term u^T dSigma u, Tr(P^-1 dP)
+  // and the control variate's coefficient, per parameter
+  double trace[3] = {0, 0, 0}, quad[3] = {0, 0, 0}, traceP[3] = {0, 0, 0}, cv_c[3] = {0, 0, 0};
   int iters_max = 0, iters_y = 0;
   double resid_y = 0;
   bool converged = true;
@@ -32,6 +35,8 @@ void ensure_cg(Handle& H, const CGLayout& lay, bool fp64);
 void sum_log_D(Handle& H, const double* D, double* scal);
 
 LoglikResult run_loglik_grad(Handle& H, const fsa_theta& th, const fsa_opts& o);
+// block PCG (Appendix A), FP64 form, on the right-hand sides in H.cg.R
+void pcg_fp64_run(Handle& H, const CGLayout& lay, const fsa_opts& o, int L);
 
 struct PredResult {
   int iters_u = 0, iters_sparse = 0;
@@ -48,38 +53,16 @@ __global__ void k_gather_y(int64_t n, const int64_t* __restrict__ perm, const do
 template <typename T>
 __global__ void k_probe_finish(int64_t n, int l, int ldc, int kind, uint64_t key, const int64_t* __restrict__ perm,
                                const double* __restrict__ y_int, const double* __restrict__ D, T* __restrict__ B);
-void launch_grad_sparse_bf16(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals,
-                             const float* X, const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B,
-                             const __nv_bfloat16* F, const fsa_theta& th, double* part);
-template <typename T, typename AT>
-__global__ void k_grad_sparse(int64_t n, int m, int c, int ldc, const int64_t* __restrict__ rowptr,
-                              const int32_t* __restrict__ colidx, const double* __restrict__ vals,
-                              const double* __restrict__ xs, const double* __restrict__ ys, const T* __restrict__ X,
-                              const T* __restrict__ Y, const AT* __restrict__ A, const AT* __restrict__ B,
-                              const AT* __restrict__ F, int64_t lda, int cov, double s1, double rho, double nug,
-                              double gamma, double* __restrict__ part);
-// tile forms of the mixed residual values and of the gradient's sparse part
-// (shared-memory staging of A~ over the cell-grid tiles); false / 0 when the
-// handle has no tiles or the shapes do not fit, and the caller runs the row
-// form.  cap_rows_max > 0 caps the staged rows per tile (tiles above it run
-// from global memory).  grad_sparse_tiles returns the blocks (partials) written.
+// tile form of the mixed residual values (shared-memory staging of A~ over
+// the cell-grid tiles); false when the handle has no tiles or the shapes do
+// not fit, and the caller runs the row form.  cap_rows_max > 0 caps the
+// staged rows per tile (tiles above it run from global memory).
 bool csr_values_tiles(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad,
                       int cap_rows_max = 0);
-int grad_sparse_tiles(Handle& H, int m_pad, int c, int ldc, const double* vals, const float* X, const float* Y,
-                      const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q, const fsa_theta& th,
-                      double* part, int max_blocks, int cap_rows_max = 0);
-// row forms (one warp per row, global gathers) of the same two products
+// row form (one warp per row, global gathers) of the same product
 void csr_values_rows(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, const __nv_bfloat16* Alo, int m_pad);
-void grad_sparse_rows(Handle& H, int nblocks, int m_pad, int c, int ldc, const double* vals, const float* X,
-                      const float* Y, const __nv_bfloat16* A, const __nv_bfloat16* B, const __nv_bfloat16* Q,
-                      const fsa_theta& th, double* part);
-__global__ void k_grad_lowrank(int m, int c, int ldc, const double* __restrict__ AX, const double* __restrict__ AY,
-                               const double* __restrict__ BX, const double* __restrict__ BY,
-                               const double* __restrict__ EAY, double s1, double* __restrict__ out2);
 __global__ void k_assemble(int64_t n, int c, int exact_weight, const double* __restrict__ quads,
                            const double* __restrict__ rz0, const double* __restrict__ scal,
-                           const double* __restrict__ part_yu, int nblk_yu, int ldc,
-                           const double* __restrict__ gpart, int ngpart, const double* __restrict__ glow,
-                           int want_grad, double* __restrict__ outs);
+                           const double* __restrict__ part_yu, int nblk_yu, int ldc, double* __restrict__ outs);
 
 }  // namespace fsa

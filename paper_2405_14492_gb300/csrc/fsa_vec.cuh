@@ -867,7 +867,7 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
     FSA_CHECK_LAUNCH();
     if (prof) {
       FSA_CUDA(cudaEventRecord(e1, s));
-      const double nb = (double)Hd.n * lay.ldc * sizeof(float);
+      const double nb = (double)Hd.n * lay.c * sizeof(float);   // the c columns; not the padding to ldc
       profile_record("pcg_spmm", e0, e1, (double)Hd.nnz * 8.0 + (double)(Hd.n + 1) * 8.0 + 6.0 * nb);
     }
     return;

@@ -198,33 +198,31 @@ def test_spmm_tile_kernel_equals_row_kernel(F, n, gamma, ncols):
     assert total > 0 and (staged > 0 or ncols > 100)
 
 
-def _sddmm_selftest(h, th, precision, ncols, cap_rows, seed=3):
+def _sddmm_selftest(h, th, precision, cap_rows, seed=3):
     from paper_2405_14492_gb300 import _native as N
     f = N.lib().fsa_selftest_sddmm
     f.restype = ctypes.c_int
-    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(N.FsaTheta), ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                  ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                  ctypes.POINTER(ctypes.c_double)]
-    ve, gt, gr = (ctypes.c_double * 2)(), (ctypes.c_double * 3)(), (ctypes.c_double * 3)()
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(N.FsaTheta), ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    ve, de = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
     t = N.FsaTheta(*th)
-    N.check(f(h._h, ctypes.byref(t), precision, ncols, cap_rows, seed, ve, gt, gr))
-    return np.array(ve[:]), np.array(gt[:]), np.array(gr[:])
+    N.check(f(h._h, ctypes.byref(t), precision, cap_rows, seed, ve, de))
+    return np.array(ve[:]), np.array(de[:])
 
 
-@pytest.mark.parametrize("n,gamma,m,ncols,cap_rows", [(30011, 0.012, 200, 65, 0), (30011, 0.012, 200, 17, 60),
-                                                       (8009, 0.03, 130, 33, 0)])
+@pytest.mark.parametrize("n,gamma,m,cap_rows", [(30011, 0.012, 200, 0), (30011, 0.012, 200, 60),
+                                                (8009, 0.03, 130, 0)])
 @pytest.mark.parametrize("x2", [False, True])
-def test_sddmm_tile_forms_match_row_forms(F, n, gamma, m, ncols, cap_rows, x2):
-    """The tile forms of the mixed residual values (and D_s) and of the
-    gradient's sparse part, with A~ rows staged in shared memory per cell-grid
-    tile, agree with the row forms (global gathers) up to FP32 summation order;
-    cap_rows = 60 sends most tiles down the global-memory path of the tile
-    kernels."""
+def test_sddmm_tile_forms_match_row_forms(F, n, gamma, m, cap_rows, x2):
+    """The tile forms of the mixed residual values (and D_s) and of their range
+    derivative, with the m-long rows staged in shared memory per cell-grid
+    tile, agree with the row forms (global gathers) up to FP32 summation
+    order; cap_rows = 60 sends most tiles down the global-memory path of the
+    tile kernels."""
     locs = fi.uniform_locations(n, 91)
     ind = locs[fi.inducing_subset(n, m, 91)]
     prec = F.FSA_MIXED_BF16X2 if x2 else F.FSA_MIXED_BF16
     with F.FSAHandle(locs, ind, gamma, 0.5) as h:
-        ve, gt, gr = _sddmm_selftest(h, (1.0, 0.05, 0.05), prec, ncols, cap_rows)
+        ve, de = _sddmm_selftest(h, (1.0, 0.05, 0.05), prec, cap_rows)
     assert ve[0] < 1e-4 and ve[1] < 1e-4, ve
-    assert np.all(np.abs(gt - gr) <= 1e-3 * np.abs(gr) + 1e-9), (gt, gr)
-    assert np.all(np.abs(gr) > 0)
+    assert de[0] < 1e-4 and de[1] < 1e-4, de
