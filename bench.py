@@ -228,7 +228,7 @@ def run_gpu(args):
     y_dev = torch.tensor(y, device="cuda", dtype=torch.float64)
     prec = {"bf16x2": F.FSA_MIXED_BF16X2, "bf16": F.FSA_MIXED_BF16, "fp64": F.FSA_FP64}[args.precision]
     opts = F.make_opts(num_probes=w.num_probes, cg_tol=w.cg_tol, precision=prec, seed=w.seed,
-                       y_on_device=True)
+                       y_on_device=True, vec_pieces=args.vec_pieces)
     infos = []
     for k in range(args.warmup):
         ll, g, info = h.loglik_grad(y_dev, next_theta(), opts)
@@ -367,18 +367,108 @@ def run_gpu(args):
         if "bf16_single_form" in result:
             result["bf16_single_form"]["loglik_rel_err_vs_fp64"] = abs(result["bf16_single_form"]["loglik"] - ll64) / abs(ll64)
     h.close()
+    if rank == 0 and args.predict_steps > 0:
+        result["predict"] = run_predict_leg(args, F, lib)
     if rank == 0 and args.serve_requests > 0:
         result["serving"] = run_serving(args, F)
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, ns, v, iters = oracle_sample_eval(w, locs, ind, y, args.cpu_sample)
+        # scaling check: a window twice as large should take about twice as long
+        dt2, ns2, v2, iters2 = oracle_sample_eval(w, locs, ind, y, 2 * args.cpu_sample)
         result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
                                   "sample": f"one oracle loglik+grad on a window of {ns} of the {w.n} points "
                                             f"(same density, taper, all {w.m} inducing points), {dt:.1f} s, "
-                                            f"scaled by n_s/n"}
+                                            f"scaled by n_s/n",
+                                  "window_cg_iters": iters, "full_cg_iters": int(infos[-1]["iters_max"]),
+                                  "double_window": {"n_s": ns2, "seconds": round(dt2, 2), "cg_iters": iters2,
+                                                    "evals_per_s_scaled": v2,
+                                                    "time_ratio_vs_window": round(dt2 / dt, 3)}}
+    if rank == 0 and args.cpu_full:
+        # the oracle on the whole workload, one evaluation (minutes, tens of GB of host memory)
+        from oracle import fsa_oracle as O
+        t0 = time.perf_counter()
+        it = O.IterativeFSA(locs, ind, w.taper_range(), w.nu, th)
+        out = it.loglik_grad(y, w.num_probes, w.seed, w.cg_tol, max_iter=1000)
+        dtf = time.perf_counter() - t0
+        result["cpu_full"] = {"seconds": round(dtf, 1), "evals_per_s": 1.0 / dtf, "cores": os.cpu_count(),
+                              "cg_iters": int(np.max(out["iters"])), "loglik": out["loglik"],
+                              "kind": "oracle", "sample": f"the whole workload, n = {w.n}, one evaluation"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# prediction leg: n = 2e5 training, n_p = 1e5 prediction points, m = 800, s = 100
+# ----------------------------------------------------------------------------
+def run_predict_leg(args, F, lib):
+    """Algorithm 1 at the predictive-distribution workload: the mixed form timed
+    (CUDA events on the handle's stream), the plain FP64 form once with the
+    same probes, and both against the exact FSA predictive variances of the
+    first 2000 prediction points (D_l by sparse solves, pred_exact_var)."""
+    import ctypes
+
+    import torch
+    w = fi.WORKLOADS["pred-n2e5-np1e5-m800"]
+    locs = fi.uniform_locations(w.n, w.seed)
+    ind = locs[fi.inducing_subset(w.n, w.m, w.seed)]
+    y = fi.random_field(locs, w.nu, w.sigma1_sq, w.rho, w.nugget, w.seed, features=256)
+    pred = fi.uniform_locations(w.n_pred, w.seed, stream=fi.STREAM_PRED_LOCATIONS)
+    th = (w.sigma1_sq, w.rho, w.nugget)
+    th_alt = (w.sigma1_sq * (1.0 + 1e-12), w.rho, w.nugget)
+    s = w.num_var_samples
+    stream = torch.cuda.Stream()
+    out = {"workload": w.name, "n": w.n, "n_pred": w.n_pred, "m": w.m, "num_var_samples": s, "probe": "gaussian",
+           "cg_tol": w.cg_tol}
+    with F.FSAHandle(locs, ind, w.taper_range(), w.nu, stream=stream.cuda_stream) as h:
+        mk = lambda prec, **kw: F.make_opts(cg_tol=w.cg_tol, seed=w.seed, precision=prec,
+                                            probe=F.FSA_PROBE_GAUSSIAN, **kw)
+        h.predict(y, th_alt, pred, s, mk(F.FSA_MIXED_BF16X2))   # warm-up
+        torch.cuda.synchronize()
+        lib.fsa_profile_reset()
+        lib.fsa_profile_enable(1)
+        times = []
+        for k in range(args.predict_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mean_x, var_x, info_x = h.predict(y, th if k % 2 == 0 else th_alt, pred, s, mk(F.FSA_MIXED_BF16X2))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        lib.fsa_profile_enable(0)
+        nl, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        gemm_ms = ms.value if lib.fsa_profile_collect(b"predict", ctypes.byref(nl), ctypes.byref(ms),
+                                                      ctypes.byref(by)) == 0 else 0.0
+        t_mixed = statistics.median(times) / 1000.0
+        out["mixed"] = {"seconds_per_eval": round(t_mixed, 4), "evals_per_s": round(1.0 / t_mixed, 4),
+                        "iters_u": int(info_x["iters_y"]), "iters_sparse": int(info_x["iters_max"]),
+                        "tensor_gemm_share": round(gemm_ms / args.predict_steps / (t_mixed * 1000.0), 4),
+                        "tensor_gemm_launches_per_eval": int(nl.value) // max(1, args.predict_steps)}
+        if not args.no_predict_fp64:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mean_64, var_64, info_64 = h.predict(y, th, pred, s, mk(F.FSA_FP64))
+            t64 = time.perf_counter() - t0
+            out["fp64"] = {"seconds_per_eval": round(t64, 3), "iters_u": int(info_64["iters_y"]),
+                           "iters_sparse": int(info_64["iters_max"])}
+            out["mixed_speedup_vs_fp64"] = round(t64 / t_mixed, 2)
+            # the same point set, probes and theta: the mixed form's rounding alone
+            if k % 2 == 1:   # the last timed evaluation ran at theta_alt
+                mean_x, var_x, _ = h.predict(y, th, pred, s, mk(F.FSA_MIXED_BF16X2))
+            out["mixed_vs_fp64"] = {"mean_max_abs": float(np.max(np.abs(mean_x - mean_64))),
+                                    "var_max_abs": float(np.max(np.abs(var_x - var_64))),
+                                    "var_rms": float(np.sqrt(np.mean((var_x - var_64) ** 2)))}
+            # exact FSA predictive variances of the first 2000 prediction points
+            ns = min(2000, w.n_pred)
+            t0 = time.perf_counter()
+            _, var_ex, _ = h.predict(y, th, pred[:ns], s, mk(F.FSA_FP64, pred_exact_var=True))
+            out["exact_subset"] = {"points": ns, "seconds": round(time.perf_counter() - t0, 3),
+                                   "rmse_mixed": float(np.sqrt(np.mean((var_x[:ns] - var_ex) ** 2))),
+                                   "rmse_fp64": float(np.sqrt(np.mean((var_64[:ns] - var_ex) ** 2))),
+                                   "paper_context": "RMSE 5.0e-4 at l = 50 and 1.2e-4 at l = 500, n = n_p = 1e5, "
+                                                    "64-core EPYC (Table 2)"}
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -390,9 +480,7 @@ def _make_request_inputs(args):
 
 
 def _serving_opts(F, req, precision):
-    if req.kind == "loglik":
-        return F.make_opts(num_probes=req.num_probes, cg_tol=1e-3, precision=precision, seed=req.seed)
-    return F.make_opts(num_probes=req.num_probes, cg_tol=1e-3, precision=F.FSA_FP64, seed=req.seed)
+    return F.make_opts(num_probes=req.num_probes, cg_tol=1e-3, precision=precision, seed=req.seed)
 
 
 def _submit_request(F, srv, req, data, precision):
@@ -405,27 +493,37 @@ def _submit_request(F, srv, req, data, precision):
 
 
 def _run_alone(F, req, data, precision):
+    """One request on its own (build + solve), as the one-at-a-time path runs
+    it; returns (seconds, loglik or None, (mean, var) or None)."""
+    import torch
     locs, ind, y, pred = data
     th = (req.sigma1_sq, req.rho, req.nugget)
     opts = _serving_opts(F, req, precision)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     with F.FSAHandle(locs, ind, req.taper_range(), req.nu) as h:
         if req.kind == "loglik":
-            return h.loglik_grad(y, th, opts)[0]
-        h.predict(y, th, pred, req.num_var_samples, opts)
-        return None
+            ll = h.loglik_grad(y, th, opts)[0]
+            out = (ll, None)
+        else:
+            mean, var, _ = h.predict(y, th, pred, req.num_var_samples, opts)
+            out = (None, (mean, var))
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out[0], out[1]
 
 
 def run_serving(args, F):
-    """Replays the request stream (Poisson arrivals) against one server and
-    reports latency percentiles and completed evaluations per second, beside
-    the plain FP64 one-request-at-a-time GPU form on an evenly spaced sample of
-    the same requests."""
+    """Replays the request stream (Poisson arrivals) against one server in the
+    mixed form; reports latency (arrival to completion) and service time
+    percentiles and completed evaluations per second.  On the same requests it
+    times the one-request-at-a-time paths, FP64 and mixed, and compares every
+    result with the FP64 one."""
     import multiprocessing as mp
 
-    reqs = fi.serving_stream(args.serve_requests)
+    reqs = fi.serving_stream(512)[: args.serve_requests]
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
-        data = pool.map(_make_request_inputs, [(args.serve_requests, k) for k in range(len(reqs))], chunksize=4)
+        data = pool.map(_make_request_inputs, [(512, k) for k in range(len(reqs))], chunksize=4)
     prec = F.FSA_MIXED_BF16X2
     with F.FSAServer(max_slots=args.serve_slots) as srv:
         # warm-up: one request of each kind, not counted
@@ -444,32 +542,39 @@ def run_serving(args, F):
         wall = time.perf_counter() - t0
         st = srv.stats()
     lat = np.array([r["latency_ms"] for r in res])
+    run = np.array([r["run_ms"] for r in res])
     ok = [r for r in res if r["status"] in (0, 4)]
+    pct = lambda a, q: float(np.percentile(a, q, method="inverted_cdf"))
     served = {"requests": len(reqs), "arrival_rate_per_s": 200.0, "slots": args.serve_slots,
               "completed": len(ok), "failed": len(res) - len(ok),
-              "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")),
-              "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")),
-              "mean_run_ms": float(np.mean([r["run_ms"] for r in res])),
-              "evals_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 2),
-              "loglik_precision": "bf16x2", "predict_precision": "fp64",
+              "latency_p50_ms": pct(lat, 50), "latency_p99_ms": pct(lat, 99),
+              "service_p50_ms": pct(run, 50), "service_p99_ms": pct(run, 99),
+              "evals_per_s": round(len(ok) / wall, 3), "wall_s": round(wall, 2), "precision": "bf16x2",
               "peak_running": st["peak_running"], "peak_footprint_gb": round(st["peak_in_use_bytes"] / 1e9, 2),
               "budget_gb": round(st["budget_bytes"] / 1e9, 1), "warmup_requests": base["completed"]}
-    # one-request-at-a-time FP64 GPU form on an evenly spaced sample
-    sample = reqs[:: max(1, len(reqs) // args.serve_fp64_sample)][: args.serve_fp64_sample]
-    t0 = time.perf_counter()
-    ll64 = {}
-    for r in sample:
-        ll64[r.index] = _run_alone(F, r, data[r.index], F.FSA_FP64)
-    t64 = time.perf_counter() - t0
-    errs = [abs(res[r.index]["loglik"] - ll64[r.index]) / abs(ll64[r.index])
-            for r in sample if r.kind == "loglik" and ll64[r.index]]
-    served["fp64_one_at_a_time"] = {"requests": len(sample), "evals_per_s": round(len(sample) / t64, 3),
-                                    "sample": f"every {max(1, len(reqs) // args.serve_fp64_sample)}th request"}
-    served["speedup_vs_fp64_one_at_a_time"] = round(served["evals_per_s"] / (len(sample) / t64), 2)
-    served["loglik_rel_err_vs_fp64_max"] = float(max(errs)) if errs else None
-    served["loglik_rel_err_vs_fp64_each"] = {str(r.index): float(abs(res[r.index]["loglik"] - ll64[r.index]) /
-                                                                 abs(ll64[r.index]))
-                                             for r in sample if r.kind == "loglik" and ll64[r.index]}
+    # the same requests one at a time: FP64 and mixed
+    t64, tmx = 0.0, 0.0
+    lerr, merr, verr = [], [], []
+    for r, sr in zip(reqs, res):
+        d64, ll64, mv64 = _run_alone(F, r, data[r.index], F.FSA_FP64)
+        dmx, _, _ = _run_alone(F, r, data[r.index], prec)
+        t64 += d64
+        tmx += dmx
+        if r.kind == "loglik" and ll64:
+            lerr.append(abs(sr["loglik"] - ll64) / abs(ll64))
+        elif mv64 is not None and "mean" in sr:
+            merr.append(float(np.max(np.abs(sr["mean"] - mv64[0])) / max(1e-300, np.max(np.abs(mv64[0])))))
+            verr.append(float(np.max(np.abs(sr["var"] - mv64[1]))))
+    served["fp64_one_at_a_time"] = {"requests": len(reqs), "evals_per_s": round(len(reqs) / t64, 3),
+                                    "seconds": round(t64, 2), "same_requests": True}
+    served["mixed_one_at_a_time"] = {"requests": len(reqs), "evals_per_s": round(len(reqs) / tmx, 3),
+                                     "seconds": round(tmx, 2)}
+    served["speedup_vs_fp64_one_at_a_time"] = round(served["evals_per_s"] / (len(reqs) / t64), 2)
+    served["overlap_gain_vs_mixed_one_at_a_time"] = round(served["evals_per_s"] / (len(reqs) / tmx), 2)
+    served["loglik_rel_err_vs_fp64_max"] = float(max(lerr)) if lerr else None
+    served["loglik_requests_over_1e-4"] = int(sum(e > 1e-4 for e in lerr))
+    served["predict_mean_rel_err_vs_fp64_max"] = float(max(merr)) if merr else None
+    served["predict_var_abs_err_vs_fp64_max"] = float(max(verr)) if verr else None
     return served
 
 
@@ -485,10 +590,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--cpu-full", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2500)
-    ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--predict-steps", type=int, default=3)
+    ap.add_argument("--no-predict-fp64", action="store_true")
+    ap.add_argument("--vec-pieces", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-fp64-sample", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

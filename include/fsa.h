@@ -106,6 +106,17 @@ typedef struct {
                                    (variance-minimising) slope
                                    sum_k (a_k - mean a)(b_k - mean b) / sum_k (b_k - mean b)^2.
                                    Costs one n x m x m tensor-core product and row dots. */
+  int32_t pred_exact_var;       /* fsa_predict, FP64 form: 1 computes D_l = diag(S Sigma_s~^-1 S^T)
+                                   exactly, by n_p sparse solves (one per prediction point), in
+                                   place of Algorithm 1's simulation: the exact FSA predictive
+                                   variances (§2.3), a reference for the simulated ones; cost and
+                                   memory grow with n_p (n x n_p right-hand sides). */
+  int32_t vec_pieces;           /* mixed forms: BF16 pieces of the vector operands of the
+                                   tensor-core products (D^-1 r and q in the CG iteration):
+                                   0 or 2: two (about 16 significant bits); 3: three (FP32's 24;
+                                   needs 3 x (columns rounded to 16) <= 256, else two are used).
+                                   Three cost one more piece of the blocks (not of A~) and
+                                   help problems with a long range and a small nugget. */
 } fsa_opts;
 
 typedef struct {
@@ -127,6 +138,19 @@ typedef struct {
   double grad_quad[3];   /* u^T dSigma_dag/dtheta u, u = Sigma_dag^-1 y (the CG solution) */
   double trace_precond[3]; /* Tr(P_hat^-1 dP_hat/dtheta), exact (0 without the control variate) */
   double cv_coef[3];     /* the control variate's coefficient c (0 without it) */
+  /* mixed forms: 2^-24 |M - I|_inf of the Woodbury core M = I + A~^T D^-1 A~
+   * summed on the tensor cores, and whether M was therefore formed in FP64
+   * (core_fp64 = 1 when that figure exceeds 1e-3: long ranges with small
+   * nuggets, where FP32 sums would lose M's identity part) */
+  double core_scale;
+  int32_t core_fp64;
+  /* mixed forms: 2^-16 sigma1 |L_m^-1|_inf, the relative rounding of A~ =
+   * Sigma_nm L_m^-T formed from BF16 pairs on the tensor cores, and whether A~
+   * was therefore formed in FP64 before its rounding to the pair (a_fp64 = 1
+   * above 1e-4: a badly conditioned Sigma_m, i.e. a long range against the
+   * spacing of the inducing points) */
+  double a_scale;
+  int32_t a_fp64;
 } fsa_info;
 
 typedef struct fsa_handle fsa_handle;

@@ -35,13 +35,16 @@ FSA_GRAD_CV = {None: 0, "copt": 1, "c1": 2, "copt_centered": 3}
 
 def make_opts(num_probes=50, cg_tol=1e-3, cg_max_iter=1000, fixed_iters=0, precision=FSA_FP64,
               probe=FSA_PROBE_RADEMACHER, seed=14492, slq_exact_weight=False, want_grad=True,
-              y_on_device=False, pred_control_variate=FSA_PRED_CV_NONE, grad_control_variate=None) -> FsaOpts:
+              y_on_device=False, pred_control_variate=FSA_PRED_CV_NONE, grad_control_variate=None,
+              pred_exact_var=False, vec_pieces=2) -> FsaOpts:
     o = N.default_opts()
     o.num_probes, o.cg_tol, o.cg_max_iter, o.fixed_iters = num_probes, cg_tol, cg_max_iter, fixed_iters
     o.precision, o.probe, o.seed = precision, probe, seed
     o.slq_exact_weight, o.want_grad, o.y_on_device = int(slq_exact_weight), int(want_grad), int(y_on_device)
     o.pred_control_variate = int(pred_control_variate)
     o.grad_control_variate = FSA_GRAD_CV[grad_control_variate]
+    o.pred_exact_var = int(pred_exact_var)
+    o.vec_pieces = int(vec_pieces)
     return o
 
 

@@ -31,7 +31,8 @@ class FsaOpts(C.Structure):
                 ("fixed_iters", C.c_int32), ("precision", C.c_int32), ("probe", C.c_int32),
                 ("seed", C.c_uint64), ("slq_exact_weight", C.c_int32), ("want_grad", C.c_int32),
                 ("y_on_device", C.c_int32), ("pred_control_variate", C.c_int32),
-                ("grad_control_variate", C.c_int32)]
+                ("grad_control_variate", C.c_int32), ("pred_exact_var", C.c_int32),
+                ("vec_pieces", C.c_int32)]
 
 
 class FsaInfo(C.Structure):
@@ -39,7 +40,9 @@ class FsaInfo(C.Structure):
                 ("logdet", C.c_double), ("logdet_precond", C.c_double), ("quad_form", C.c_double),
                 ("logdet_se", C.c_double), ("converged", C.c_int32), ("num_probes", C.c_int32),
                 ("nnz", C.c_int64), ("time_ms", C.c_double), ("grad_trace", C.c_double * 3),
-                ("grad_quad", C.c_double * 3), ("trace_precond", C.c_double * 3), ("cv_coef", C.c_double * 3)]
+                ("grad_quad", C.c_double * 3), ("trace_precond", C.c_double * 3), ("cv_coef", C.c_double * 3),
+                ("core_scale", C.c_double), ("core_fp64", C.c_int32), ("a_scale", C.c_double),
+                ("a_fp64", C.c_int32)]
 
     def as_dict(self):
         d = {}

@@ -294,6 +294,8 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
   if (!(o.cg_tol >= 0.0)) return fail(Error{FSA_ERR_ARG, "cg_tol must be >= 0"});
   if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.probe != FSA_PROBE_RADEMACHER && o.probe != FSA_PROBE_GAUSSIAN) return fail(Error{FSA_ERR_ARG, "bad probe"});
+  if (o.vec_pieces != 0 && o.vec_pieces != 2 && o.vec_pieces != 3)
+    return fail(Error{FSA_ERR_ARG, "vec_pieces must be 0, 2 or 3"});
   if (o.grad_control_variate < 0 || o.grad_control_variate > 3)
     return fail(Error{FSA_ERR_ARG, "grad_control_variate must be 0, 1, 2 or 3"});
   if (o.grad_control_variate != 0 && o.num_probes < 2)
@@ -316,6 +318,7 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
       FSA_CHECK_LAUNCH();
       check_err(H);
     }
+    H.vec_pieces = o.vec_pieces == 3 ? 3 : 2;
     LoglikResult r = run_loglik_grad(H, *theta, o);
     FSA_CUDA(cudaEventRecord(H.ev1, H.stream));
     FSA_CUDA(cudaEventSynchronize(H.ev1));
@@ -342,6 +345,10 @@ fsa_status fsa_loglik_grad(fsa_handle* h, const double* y, const fsa_theta* thet
         info->trace_precond[q] = o.want_grad ? r.traceP[q] : 0.0;
         info->cv_coef[q] = o.want_grad ? r.cv_c[q] : 0.0;
       }
+      info->core_scale = H.op.core_scale;
+      info->core_fp64 = H.op.core_fp64 ? 1 : 0;
+      info->a_scale = H.op.a_scale;
+      info->a_fp64 = H.op.a_fp64 ? 1 : 0;
     }
     if (!std::isfinite(r.loglik)) return fail(Error{FSA_ERR_NAN, "non-finite log-likelihood"});
     if (!r.converged) return fail(Error{FSA_ERR_NO_CONVERGENCE, "CG iteration limit reached"});
@@ -365,6 +372,7 @@ fsa_status fsa_matvec(fsa_handle* h, const fsa_theta* theta, int32_t precision, 
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
   TraceRange trace("fsa_matvec");
+  H.vec_pieces = 2;
   try {
     ensure_operator(H, *theta, precision);
     size_t nk = (size_t)H.n * k;
@@ -417,10 +425,11 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
     return fail(Error{FSA_ERR_ARG, "num_var_samples must be in [1, 4096]"});
   fsa_opts o = resolve_opts(opts);
   if (o.cg_max_iter > 8000) return fail(Error{FSA_ERR_ARG, "cg_max_iter must be <= 8000"});
-  if (o.precision != FSA_FP64)
-    return fail(Error{FSA_ERR_UNSUPPORTED, "prediction is implemented in the FP64 form"});
+  if (o.precision < FSA_FP64 || o.precision > FSA_MIXED_BF16X2) return fail(Error{FSA_ERR_ARG, "bad precision"});
   if (o.pred_control_variate < 0 || o.pred_control_variate > 2)
     return fail(Error{FSA_ERR_ARG, "pred_control_variate must be 0, 1 or 2"});
+  if (o.pred_exact_var && (o.precision != FSA_FP64 || !var))
+    return fail(Error{FSA_ERR_ARG, "pred_exact_var needs the FP64 form and a variance output"});
   Handle& H = h->h;
   AllocStreamScope scope(H.stream);
   TraceRange trace("fsa_predict");
@@ -439,8 +448,11 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
       FSA_CHECK_LAUNCH();
       check_err(H);
     }
-    ensure_operator(H, *theta, FSA_FP64);
-    PredResult r = run_predict_fp64(H, *theta, o, pred_locs, n_p, num_var_samples, mean, var);
+    H.vec_pieces = o.vec_pieces == 3 ? 3 : 2;
+    ensure_operator(H, *theta, o.precision);
+    PredResult r = o.precision == FSA_FP64
+                       ? run_predict_fp64(H, *theta, o, pred_locs, n_p, num_var_samples, mean, var)
+                       : run_predict_mixed(H, *theta, o, pred_locs, n_p, num_var_samples, mean, var);
     FSA_CUDA(cudaEventRecord(H.ev1, H.stream));
     FSA_CUDA(cudaEventSynchronize(H.ev1));
     float ms = 0;
@@ -453,6 +465,10 @@ fsa_status fsa_predict(fsa_handle* h, const double* y, const fsa_theta* theta, c
       info->num_probes = num_var_samples;
       info->nnz = H.nnz;
       info->time_ms = ms;
+      info->core_scale = H.op.core_scale;
+      info->core_fp64 = H.op.core_fp64 ? 1 : 0;
+      info->a_scale = H.op.a_scale;
+      info->a_fp64 = H.op.a_fp64 ? 1 : 0;
     }
     if (!r.converged) return fail(Error{FSA_ERR_NO_CONVERGENCE, "CG iteration limit reached"});
     return FSA_OK;

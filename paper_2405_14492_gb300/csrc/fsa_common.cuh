@@ -201,4 +201,10 @@ __device__ void heap_sort_thread(T* a, int64_t len) {
   }
 }
 
+// an FP32 value as a BF16 hi + lo pair (about 16 significant bits)
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 }  // namespace fsa

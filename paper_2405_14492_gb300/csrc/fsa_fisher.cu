@@ -129,7 +129,7 @@ static FisherRun run_fisher_mixed(Handle& H, const fsa_theta& th, const fsa_opts
   FSA_REQUIRE(c <= 127, FSA_ERR_UNSUPPORTED, "mixed-precision Fisher information supports at most 42 probes");
   const int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
   CGLayout lay;
-  lay.setup(n, c, L, mixed_ldc(c));
+  lay.setup(n, c, L, mixed_ldc(c, H.vec_pieces));
   ensure_cg(H, lay, false);
   const int ldc = lay.ldc;
   const size_t nc = (size_t)n * ldc;
@@ -220,6 +220,7 @@ extern "C" fsa_status fsa_fisher(fsa_handle* h, const fsa_theta* theta, const fs
   TraceRange trace("fsa_fisher");
   try {
     FSA_CUDA(cudaEventRecord(H.ev0, H.stream));
+    H.vec_pieces = o.vec_pieces == 3 ? 3 : 2;
     ensure_operator(H, *theta, o.precision);
     DevPtr<double> raw(9);
     FisherRun r = o.precision == FSA_FP64 ? run_fisher_fp64(H, *theta, o, raw.p) : run_fisher_mixed(H, *theta, o, raw.p);

@@ -44,7 +44,9 @@ constexpr int kCdWarps = 8, kCdThreads = 32 * kCdWarps, kCdPerLane = 4, kCdCols 
 // [cb, cb + 128) of this launch:
 //   q = 0: X_k^T Sigma_s~ Y_k     q = 1: X_k^T dSigma_s~/drho Y_k
 //   q = 2: X_k^T Y_k              q = 3: Y_k^T Y_k        q = 4: sum_i dD_i Y_ik^2
-// one warp per row; lane L owns columns cb + L + 32 r
+// one warp per row; lane L owns columns cb + L + 32 r.  A row's gathers are
+// summed in the vectors' precision (FP32 in the mixed form, as the CG's own
+// SpMM), the per-row products and the sums over rows in FP64.
 template <typename T, typename VT, typename DT>
 __global__ void __launch_bounds__(kCdThreads) k_grad_coldots(int64_t n, int c, int ldc, int cb,
                                                               const int64_t* __restrict__ rowptr,
@@ -64,24 +66,25 @@ __global__ void __launch_bounds__(kCdThreads) k_grad_coldots(int64_t n, int c, i
   for (int r = 0; r < kCdPerLane; ++r) on[r] = cb + lane + 32 * r < c;
   const int64_t nwarps = (int64_t)gridDim.x * kCdWarps;
   for (int64_t i = (int64_t)blockIdx.x * kCdWarps + wib; i < n; i += nwarps) {
-    double ts[kCdPerLane] = {0.0, 0.0, 0.0, 0.0}, td[kCdPerLane] = {0.0, 0.0, 0.0, 0.0};
+    using Acc = typename AccOf<T>::type;
+    Acc ts[kCdPerLane] = {0, 0, 0, 0}, td[kCdPerLane] = {0, 0, 0, 0};
     double dDi = 0.0;
     const int64_t rb = rowptr[i], re = rowptr[i + 1];
     for (int64_t base = rb; base < re; base += 32) {
       const int cnt = (int)((re - base) < 32 ? (re - base) : 32);
       const int myj = lane < cnt ? col[base + lane] : 0;
-      const double myv = lane < cnt ? (double)vals[base + lane] : 0.0;
-      const double myd = lane < cnt ? (double)dvals[base + lane] : 0.0;
+      const Acc myv = lane < cnt ? (Acc)vals[base + lane] : (Acc)0;
+      const Acc myd = lane < cnt ? (Acc)dvals[base + lane] : (Acc)0;
       for (int t = 0; t < cnt; ++t) {
         const int j = __shfl_sync(0xffffffffu, myj, t);
-        const double v = __shfl_sync(0xffffffffu, myv, t);
-        const double dv = __shfl_sync(0xffffffffu, myd, t);
-        if (j == i) dDi = dv;
+        const Acc v = __shfl_sync(0xffffffffu, myv, t);
+        const Acc dv = __shfl_sync(0xffffffffu, myd, t);
+        if (j == i) dDi = (double)dv;
         const T* yj = Y + (int64_t)j * ldc + cb + lane;
 #pragma unroll
         for (int r = 0; r < kCdPerLane; ++r)
           if (on[r]) {
-            const double y = (double)yj[32 * r];
+            const Acc y = (Acc)yj[32 * r];
             ts[r] = fma(v, y, ts[r]);
             td[r] = fma(dv, y, td[r]);
           }
@@ -93,8 +96,8 @@ __global__ void __launch_bounds__(kCdThreads) k_grad_coldots(int64_t n, int c, i
     for (int r = 0; r < kCdPerLane; ++r)
       if (on[r]) {
         const double x = (double)xi[32 * r], y = (double)yi[32 * r];
-        acc[0][r] = fma(x, ts[r], acc[0][r]);
-        acc[1][r] = fma(x, td[r], acc[1][r]);
+        acc[0][r] = fma(x, (double)ts[r], acc[0][r]);
+        acc[1][r] = fma(x, (double)td[r], acc[1][r]);
         acc[2][r] = fma(x, y, acc[2][r]);
         acc[3][r] = fma(y, y, acc[3][r]);
         acc[4][r] = fma(dDi * y, y, acc[4][r]);

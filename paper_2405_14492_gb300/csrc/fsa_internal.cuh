@@ -101,6 +101,10 @@ struct Operator {
   DevPtr<float> vals32;
   DevPtr<int2> pairs32;   // per nonzero (staged column in its SpMM tile, FP32 value bits)
   DevPtr<float> D32, Dinv32;
+  double core_scale = 0.0;   // 2^-24 |M - I|_inf of the tensor-core Woodbury core
+  bool core_fp64 = false;    // the core was formed in FP64 (core_scale too large)
+  double a_scale = 0.0;      // 2^-16 sigma1 |L_m^-1|_inf: the tensor-core A's rounding, relative
+  bool a_fp64 = false;       // A = Sigma_nm L_m^-T was formed in FP64 (a_scale too large)
   int m_pad = 0;
   int64_t n_pad = 0;
 };
@@ -162,6 +166,7 @@ struct Handle {
   DevPtr<double> outs;                     // device results [loglik, logdet, quad, g0, g1, g2, se, ...]
   DevPtr<double> gterms;                   // per-probe gradient terms of the last call: a[3][l], b[3][l]
   int gterms_l = 0;                        // l of gterms (0: none yet)
+  int vec_pieces = 2;                      // BF16 pieces of the vector operands (mixed forms; per call)
   double* host_pinned = nullptr;           // pinned mirror of small results
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // side stream for work that overlaps the main stream (SLQ beside the gradient)

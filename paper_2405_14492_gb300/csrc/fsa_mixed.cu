@@ -28,12 +28,16 @@ namespace fsa {
 // on the tensor cores (512 rows; the spans are reduced in FP64)
 constexpr int kCoreSpanBlocks = 8;
 constexpr int kCoreSpans = 64;      // spans per launch
+// 2^-24 |M - I|_inf above which the core is formed in FP64 (M's identity part
+// would be resolved to worse than about 1e-5 by the FP32 span sums)
+constexpr double kCoreFp64Above = 1e-3;
+// 2^-16 sigma1 |L_m^-1|_inf above which A = Sigma_nm L_m^-T is formed in FP64:
+// the split products of the tensor cores round each term of the sum to about
+// 2^-16 of |k| |L_m^-1|, and a badly conditioned Sigma_m (long range, close
+// inducing points) makes those terms far larger than the entries of A
+constexpr double kAFp64Above = 1e-4;
 
 
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(v);
-  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
 
 // coordinates as FP32 hi/lo pairs: x = x_hi + x_lo to ~2^-48 relative
 __global__ void k_coord_split(int64_t n, const double* __restrict__ xs, const double* __restrict__ ys,
@@ -228,6 +232,69 @@ __global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __
   }
 }
 
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// out[0] = max_r sum_c |L_rc| (the infinity norm of an m x m matrix), one block
+__global__ void k_inf_norm(int m, const double* __restrict__ L, double* __restrict__ out) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < m; ++c) s += fabs(L[(int64_t)r * m + c]);
+    mx = fmax(mx, s);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) v = fmax(v, red[t]);
+    out[0] = v;
+  }
+}
+
+__global__ void k_set_identity(int m, double* __restrict__ M) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)m * m;
+       t += (int64_t)gridDim.x * blockDim.x)
+    M[t] = (t / m == t % m) ? 1.0 : 0.0;
+}
+
+// out[0] = max_r sum_c |M_rc - [r == c]|  (the infinity norm of M - I), one block
+__global__ void k_core_norm(int m, const double* __restrict__ M, double* __restrict__ out) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < m; ++c) s += fabs(M[(int64_t)r * m + c] - (r == c ? 1.0 : 0.0));
+    mx = fmax(mx, s);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) v = fmax(v, red[t]);
+    out[0] = v;
+  }
+}
+
+// A (FP64, n x m row-major) = the BF16 pair (hi + lo, blocked K-major, m_pad columns)
+__global__ void k_pair_to_f64(int64_t n, int m, const __nv_bfloat16* __restrict__ hi,
+                              const __nv_bfloat16* __restrict__ lo, double* __restrict__ A) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / m;
+    const int k = (int)(t - i * m);
+    const int64_t b = blocked_index(i, k, n);
+    A[t] = (double)__bfloat162float(hi[b]) + (lo ? (double)__bfloat162float(lo[b]) : 0.0);
+  }
+}
+
 // out[r][c] = sum_s part[s][r][c] (+1 on the diagonal), FP64
 __global__ void k_reduce_splits(int splits, int rows, int cols, const float* __restrict__ part, int64_t ldp,
                                 int64_t split_stride, double* __restrict__ out, int64_t ldo, int add_identity,
@@ -398,6 +465,8 @@ void csr_values_rows(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, con
 // ---------------------------------------------------------------------------
 static inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
+__global__ void k_f64_to_f32_pad(int64_t n, int k, int ldk, const double* __restrict__ src, float* __restrict__ dst);
+
 void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   Operator& op = H.op;
   cudaStream_t s = H.stream;
@@ -415,20 +484,41 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   {
     DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi((size_t)m_pad * m_pad), Llo((size_t)m_pad * m_pad);
     DevPtr<float> A32(nm);
-    cov_nm_split(H, m_pad, th, 0, Khi.p, Klo.p);
-    k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
-                                                                       Llo.p);
-    FSA_CHECK_LAUNCH();
-    TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
-    TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128), mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
-    TcGemm g;
-    g.a[0] = &mKh; g.a[1] = &mKl; g.num_a = 2;
-    g.b[0] = &mLh; g.b[1] = &mLl; g.num_b = 2;
-    g.pairs = 1u | 2u | 4u;   // hi.hi + hi.lo + lo.hi
-    g.M = (int)n; g.N = m_pad; g.K = m_pad; g.bn = 128;
-    g.out = A32.p; g.ldo = m_pad;
-    g.tag = "build";
-    tc_gemm(g, H.err, s);
+    {
+      DevPtr<double> nrm(1);
+      k_inf_norm<<<1, 256, 0, s>>>(m, op.Lmi.p, nrm.p);
+      FSA_CHECK_LAUNCH();
+      double h = 0.0;
+      FSA_CUDA(cudaMemcpyAsync(&h, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      FSA_CUDA(cudaStreamSynchronize(s));
+      op.a_scale = 0x1p-16 * sqrt(th.sigma1_sq) * h;
+      op.a_fp64 = op.a_scale > kAFp64Above;
+    }
+    if (op.a_fp64) {
+      // A = Sigma_nm L_m^-T in FP64, then rounded like the tensor-core result
+      DevPtr<double> K64((size_t)n * m), A64((size_t)n * m);
+      cov_cross(H, n, H.xs.p, H.ys.p, m, H.ind_x.p, H.ind_y.p, th, 0, K64.p, m);
+      dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, K64.p, m, op.Lmi.p, m, 0.0, A64.p, m, nullptr);
+      k_f64_to_f32_pad<<<grid_for((int64_t)n * m_pad, 256), 256, 0, s>>>(n, m, m_pad, A64.p, A32.p);
+      FSA_CHECK_LAUNCH();
+      FSA_CUDA(cudaStreamSynchronize(s));
+    } else {
+      cov_nm_split(H, m_pad, th, 0, Khi.p, Klo.p);
+      k_split_f64<<<grid_for((int64_t)m_pad * m_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p,
+                                                                         Llo.p);
+      FSA_CHECK_LAUNCH();
+      TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+      TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128),
+             mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
+      TcGemm g;
+      g.a[0] = &mKh; g.a[1] = &mKl; g.num_a = 2;
+      g.b[0] = &mLh; g.b[1] = &mLl; g.num_b = 2;
+      g.pairs = 1u | 2u | 4u;   // hi.hi + hi.lo + lo.hi
+      g.M = (int)n; g.N = m_pad; g.K = m_pad; g.bn = 128;
+      g.out = A32.p; g.ldo = m_pad;
+      g.tag = "build";
+      tc_gemm(g, H.err, s);
+    }
     op.Ab.ensure(nm);
     if (lo) {
       op.Ab_lo.ensure(nm);
@@ -500,6 +590,34 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
     }
     FSA_CUDA(cudaStreamSynchronize(s));
   }
+  // The FP32 sums above round each span at about 2^-24 of its size, which is
+  // bounded by |M - I|.  Where that is not small against the identity (a long
+  // range with a small nugget puts entries of order n / nugget beside it), the
+  // small eigenvalues of M, and with them log det P and the identity
+  // A~^T z = q of the two-pass CG iteration, would be lost: M - I is then
+  // formed in FP64 from the same A~ and D.
+  {
+    DevPtr<double> nrm(1);
+    k_core_norm<<<1, 256, 0, s>>>(m, op.Mp.p, nrm.p);
+    FSA_CHECK_LAUNCH();
+    double h = 0.0;
+    FSA_CUDA(cudaMemcpyAsync(&h, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaStreamSynchronize(s));
+    op.core_scale = h * 0x1p-24;
+    op.core_fp64 = op.core_scale > kCoreFp64Above;
+    if (op.core_fp64) {
+      DevPtr<double> A64((size_t)n * m), Dinv64(n);
+      k_pair_to_f64<<<grid_for((int64_t)n * m, 256), 256, 0, s>>>(n, m, op.Ab.p, lo ? op.Ab_lo.p : nullptr, A64.p);
+      FSA_CHECK_LAUNCH();
+      // the D^-1 the CG applies (FP32), so that A~^T z = q holds for its iterates
+      k_f32_to_f64<<<grid_for(n, 256), 256, 0, s>>>(n, op.Dinv32.p, Dinv64.p);
+      FSA_CHECK_LAUNCH();
+      k_set_identity<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(m, op.Mp.p);
+      FSA_CHECK_LAUNCH();
+      dgemm(H.ws, s, true, false, m, m, (int)n, 1.0, A64.p, m, A64.p, m, 1.0, op.Mp.p, m, Dinv64.p);
+      FSA_CUDA(cudaStreamSynchronize(s));
+    }
+  }
   check_err(H);
   finish_core(H);
   op.theta = th;
@@ -511,14 +629,14 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
 // per-iteration products on the tensor cores
 // ---------------------------------------------------------------------------
 
-// vector-operand split: two BF16 pieces (~16 significant bits).  Three pieces
-// (the full FP32 24) are supported by the kernels (kVecSplit = 3) but changed
-// the n = 1e6 log-likelihood by < 1e-6 relative at a higher cost, so two are used.
-constexpr int kVecSplit = 2;
-static inline int pick_nsplit(int ldc) { return kVecSplit == 3 && 3 * ldc <= 256 ? 3 : 2; }
-int mixed_ldc(int c) {
+// vector-operand split: two BF16 pieces (~16 significant bits) by default;
+// three (the full FP32 24) when the call asks for them (fsa_opts.vec_pieces)
+// and the stacked block fits one N tile (3 ldc <= 256, ldc a multiple of 16
+// so that 3 ldc is a multiple of the MMA's N granule)
+static inline int pick_nsplit(int ldc, int pieces) { return pieces == 3 && 3 * ldc <= 256 && ldc % 16 == 0 ? 3 : 2; }
+int mixed_ldc(int c, int pieces) {
   int l16 = (c + 15) / 16 * 16;
-  return kVecSplit == 3 && 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
+  return pieces == 3 && 3 * l16 <= 256 ? l16 : (c + 7) / 8 * 8;
 }
 
 static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C);
@@ -527,7 +645,7 @@ void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc) {
   Operator& op = H.op;
   CGState& g = H.cg;
   C.ldc = ldc; C.c = c; C.m_pad = op.m_pad; C.n = n; C.n_pad = op.n_pad;
-  C.nsplit = pick_nsplit(ldc);
+  C.nsplit = pick_nsplit(ldc, H.vec_pieces);
   const int ns = C.nsplit * ldc;
   FSA_REQUIRE(ns <= 256, FSA_ERR_UNSUPPORTED, "block too wide for the tensor-core products");
   g.Xb.ensure((size_t)ns * C.n_pad);
@@ -826,7 +944,7 @@ LoglikResult run_loglik_grad_mixed(Handle& H, const fsa_theta& th, const fsa_opt
   FSA_REQUIRE(l + 1 <= 128, FSA_ERR_UNSUPPORTED, "mixed precision supports at most 127 probes");
   CGLayout lay;
   int L = o.fixed_iters > 0 ? o.fixed_iters : (o.cg_max_iter > 0 ? o.cg_max_iter : 1000);
-  lay.setup(n, l + 1, L, mixed_ldc(l + 1));
+  lay.setup(n, l + 1, L, mixed_ldc(l + 1, H.vec_pieces));
   ensure_cg(H, lay, false);
   int ldc = lay.ldc;
   size_t nc = (size_t)n * ldc;
@@ -1004,7 +1122,7 @@ void apply_operator_mixed(Handle& H, int which, const double* v, int k, double* 
   int m = H.m;
   FSA_REQUIRE(k <= 128, FSA_ERR_UNSUPPORTED, "mixed matvec supports at most 128 columns");
   CGLayout lay;
-  lay.setup(n, k, 1, mixed_ldc(k));
+  lay.setup(n, k, 1, mixed_ldc(k, H.vec_pieces));
   int ldc = lay.ldc;
   size_t nc = (size_t)n * ldc;
   DevPtr<float> V32(nc), S32(nc), O32(nc);

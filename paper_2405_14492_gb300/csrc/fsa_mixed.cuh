@@ -18,7 +18,8 @@ struct MixedCtx {
   float* wpart = nullptr;   // split-K partials of A^T X (splits_w x m_pad x ldc)
 };
 
-int mixed_ldc(int c);
+// CG block width for c columns with `pieces` BF16 pieces of the vector operands
+int mixed_ldc(int c, int pieces);
 void mixed_ctx_setup(Handle& H, MixedCtx& C, int64_t n, int c, int ldc);
 // w (FP64, m x ldc) = A~^T X, X = rows of src (scaled by rowscale when not NULL)
 void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w, const char* tag);

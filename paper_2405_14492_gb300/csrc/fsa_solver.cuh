@@ -44,6 +44,8 @@ struct PredResult {
 };
 PredResult run_predict_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o, const double* pred_host, int64_t np,
                             int s, double* mean_host, double* var_host);
+PredResult run_predict_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o, const double* pred_host, int64_t np,
+                            int s, double* mean_host, double* var_host);
 void apply_operator(Handle& H, int which, const double* v_dev_internal, int k, double* out_dev_internal);
 
 // kernels used across units

@@ -688,7 +688,8 @@ __device__ __forceinline__ void vec4_block_partials(const double (&acc)[4], int 
   }
 }
 
-// U += a H ; R -= a V ; part = ||R||^2
+// U += a H ; R -= a V ; part = ||R||^2.  Two rows per thread per step, their
+// loads issued before the arithmetic (as in kv4_z_update).
 static __global__ void kv4_ur_update(int64_t n, int c, int ldc, int rpb, float* __restrict__ U, float* __restrict__ R,
                                      const float* __restrict__ H, const float* __restrict__ V,
                                      const double* __restrict__ alpha, const int32_t* __restrict__ active,
@@ -704,23 +705,32 @@ static __global__ void kv4_ur_update(int64_t n, int c, int ldc, int rpb, float* 
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   float sub[4] = {0.f, 0.f, 0.f, 0.f};
   int cnt = 0;
-#pragma unroll 4
-  for (int64_t i = row0; i < n; i += rstride) {
-    const int64_t idx = i * ldc + col0;
-    float4 r = *reinterpret_cast<const float4*>(R + idx);
-    const float4 h = *reinterpret_cast<const float4*>(H + idx);
-    const float4 v = *reinterpret_cast<const float4*>(V + idx);
-    float4 u = *reinterpret_cast<const float4*>(U + idx);
+  auto urow = [&](float4 r, const float4 h, const float4 v, float4 u, const int64_t idx) {
     u.x = fmaf(a[0], h.x, u.x); u.y = fmaf(a[1], h.y, u.y); u.z = fmaf(a[2], h.z, u.z); u.w = fmaf(a[3], h.w, u.w);
     r.x = fmaf(-a[0], v.x, r.x); r.y = fmaf(-a[1], v.y, r.y); r.z = fmaf(-a[2], v.z, r.z); r.w = fmaf(-a[3], v.w, r.w);
     *reinterpret_cast<float4*>(U + idx) = u;
     *reinterpret_cast<float4*>(R + idx) = r;
     sub[0] += r.x * r.x; sub[1] += r.y * r.y; sub[2] += r.z * r.z; sub[3] += r.w * r.w;
-    if (++cnt == 32) {
+  };
+  int64_t i = row0;
+  for (; i + rstride < n; i += 2 * rstride) {
+    const int64_t ia = i * ldc + col0, ib = (i + rstride) * ldc + col0;
+    const float4 ra = *reinterpret_cast<const float4*>(R + ia), rb = *reinterpret_cast<const float4*>(R + ib);
+    const float4 ha = *reinterpret_cast<const float4*>(H + ia), hb = *reinterpret_cast<const float4*>(H + ib);
+    const float4 va = *reinterpret_cast<const float4*>(V + ia), vb = *reinterpret_cast<const float4*>(V + ib);
+    const float4 ua = *reinterpret_cast<const float4*>(U + ia), ub = *reinterpret_cast<const float4*>(U + ib);
+    urow(ra, ha, va, ua, ia);
+    urow(rb, hb, vb, ub, ib);
+    if (++cnt == 16) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) { acc[k] += (double)sub[k]; sub[k] = 0.f; }
       cnt = 0;
     }
+  }
+  if (i < n) {
+    const int64_t ia = i * ldc + col0;
+    urow(*reinterpret_cast<const float4*>(R + ia), *reinterpret_cast<const float4*>(H + ia),
+         *reinterpret_cast<const float4*>(V + ia), *reinterpret_cast<const float4*>(U + ia), ia);
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) acc[k] += (double)sub[k];
@@ -728,7 +738,9 @@ static __global__ void kv4_ur_update(int64_t n, int c, int ldc, int rpb, float* 
   finish_scalars(step, part, ldc, c, l, q, red4);
 }
 
-// Z = (R - S) Dinv ; part = r^T z
+// Z = (R - S) Dinv ; part = r^T z.  A thread takes two rows per step and
+// issues all their loads before the arithmetic: the kernel streams two arrays
+// in and one out, and one row in flight per thread left the DRAM half idle.
 static __global__ void kv4_z_update(int64_t n, int c, int ldc, int rpb, const float* __restrict__ R,
                                     const float* __restrict__ S, const float* __restrict__ Dinv,
                                     float* __restrict__ Z, double* __restrict__ part, int step, int l, CGScalars q) {
@@ -740,21 +752,32 @@ static __global__ void kv4_z_update(int64_t n, int c, int ldc, int rpb, const fl
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   float sub[4] = {0.f, 0.f, 0.f, 0.f};
   int cnt = 0;
-#pragma unroll 4
-  for (int64_t i = row0; i < n; i += rstride) {
-    const int64_t idx = i * ldc + col0;
-    const float4 r = *reinterpret_cast<const float4*>(R + idx);
-    const float4 sv = *reinterpret_cast<const float4*>(S + idx);
-    const float d = Dinv[i];
+  auto zrow = [&](const float4 r, const float4 sv, const float d, const int64_t idx) {
     // columns >= c hold zeros in R and S, so Z is zero there
-    float4 z = make_float4((r.x - sv.x) * d, (r.y - sv.y) * d, (r.z - sv.z) * d, (r.w - sv.w) * d);
+    const float4 z = make_float4((r.x - sv.x) * d, (r.y - sv.y) * d, (r.z - sv.z) * d, (r.w - sv.w) * d);
     *reinterpret_cast<float4*>(Z + idx) = z;
     sub[0] += r.x * z.x; sub[1] += r.y * z.y; sub[2] += r.z * z.z; sub[3] += r.w * z.w;
-    if (++cnt == 32) {
+  };
+  int64_t i = row0;
+#pragma unroll 2
+  for (; i + rstride < n; i += 2 * rstride) {
+    const int64_t ia = i * ldc + col0, ib = (i + rstride) * ldc + col0;
+    const float4 ra = *reinterpret_cast<const float4*>(R + ia);
+    const float4 sa = *reinterpret_cast<const float4*>(S + ia);
+    const float4 rb = *reinterpret_cast<const float4*>(R + ib);
+    const float4 sb = *reinterpret_cast<const float4*>(S + ib);
+    const float da = Dinv[i], db = Dinv[i + rstride];
+    zrow(ra, sa, da, ia);
+    zrow(rb, sb, db, ib);
+    if (++cnt == 16) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) { acc[k] += (double)sub[k]; sub[k] = 0.f; }
       cnt = 0;
     }
+  }
+  if (i < n) {
+    const int64_t ia = i * ldc + col0;
+    zrow(*reinterpret_cast<const float4*>(R + ia), *reinterpret_cast<const float4*>(S + ia), Dinv[i], ia);
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) acc[k] += (double)sub[k];

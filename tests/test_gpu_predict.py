@@ -114,3 +114,54 @@ def test_predict_control_variate_reduces_error_to_exact(F):
     sd = np.sqrt((np.sum(E ** 2, 1) - np.diag(E) ** 2) / s)
     assert np.all(np.abs(var_cv - var_exact) <= 5 * sd + 1e-9)
     assert np.sqrt(np.mean((var_co - var_exact) ** 2)) < 0.8 * np.sqrt(np.mean((var_pl - var_exact) ** 2))
+
+
+@pytest.mark.parametrize("x2", [True, False])
+def test_mixed_predict_parity_same_probes(F, x2):
+    """The mixed form of Algorithm 1 (its m-column products on the tensor
+    cores with BF16 pairs, the sparse solves in FP32, the cores in FP64)
+    against the FP64 oracle with the same probes.
+    Variances: each of D1, 2 D2, D3 and D_l is a sum of products rounded to
+    about 2^-16 (a BF16 pair), so the variance of point p is held to
+    3e-4 (|D1| + 2 |D2| + |D3| + |D_l|)_p, a tenth of which is measured.
+    Mean: a linear functional of u = Sigma_dag^-1 y, where the mixed operator
+    (A~ as a pair, FP32 vectors) differs from the FP64 one by about 2^-16 of
+    its norm; the solve amplifies that by up to the conditioning of Sigma_dag,
+    lambda_max / nugget, about 1e3 here.  It is held to 2e-3 of max |mean|
+    (4e-4 measured).  The single-BF16 operator (A~ rounded to 8 bits, 2^-9)
+    is held to ten times both bounds."""
+    n, m, n_p, s, gamma = 20011, 200, 3001, 24, fi.taper_range_for(25, 20011)
+    locs, ind, pred = _case(n, m, n_p, 94, gamma)
+    th = (1.0, 0.05, 0.05)
+    y = fi.random_field(locs, 0.5, *th, 94)
+    tol_cg = 1e-6 * np.linalg.norm(y)
+    ref = O.IterativeFSA(locs, ind, gamma, 0.5, th).predict(y, pred, s, 17, tol_cg)
+    prec = F.FSA_MIXED_BF16X2 if x2 else F.FSA_MIXED_BF16
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        mean, var, info = h.predict(y, th, pred, s, F.make_opts(cg_tol=tol_cg, seed=17, precision=prec))
+    assert info["converged"] == 1
+    k = 1.0 if x2 else 10.0
+    scale_v = np.abs(ref["D1"]) + 2 * np.abs(ref["D2"]) + np.abs(ref["D3"]) + np.abs(ref["Dl"])
+    err_m = np.max(np.abs(mean - ref["mean"])) / np.max(np.abs(ref["mean"]))
+    err_v = np.max(np.abs(var - ref["var"]) / scale_v)
+    print(f"mixed predict ({'bf16x2' if x2 else 'bf16'}): mean err {err_m:.2e} of max|mean|, "
+          f"var err {err_v:.2e} of its parts; iterations {info['iters_y']} / {info['iters_max']}")
+    assert err_m < k * 2e-3
+    assert err_v < k * 3e-4
+
+
+def test_exact_variances_match_the_dense_definition(F):
+    """pred_exact_var: D_l = diag(S Sigma_s~^-1 S^T) by n_p sparse solves makes
+    the predictive variance exact (§2.3); it equals the dense FSA predictive
+    variance sigma1^2 + nugget - diag(Sigma_dag_np^T Sigma_dag^-1 Sigma_dag_np)."""
+    n, m, n_p, gamma = 1500, 40, 300, 0.06
+    locs, ind, pred = _case(n, m, n_p, 95, gamma)
+    th = (1.0, 0.1, 0.1)
+    y = fi.random_field(locs, 0.5, *th, 95)
+    D = O.DenseFSA(locs, ind, gamma, 0.5, th)
+    mu, var_exact = D.predict(y, pred)
+    with F.FSAHandle(locs, ind, gamma, 0.5) as h:
+        mean, var, info = h.predict(y, th, pred, 8, F.make_opts(cg_tol=1e-11, seed=3, pred_exact_var=True))
+    assert info["converged"] == 1
+    assert np.max(np.abs(mean - mu)) < 1e-7
+    assert np.max(np.abs(var - var_exact)) < 1e-8, np.max(np.abs(var - var_exact))
