@@ -295,16 +295,19 @@ __global__ void k_pair_to_f64(int64_t n, int m, const __nv_bfloat16* __restrict_
   }
 }
 
-// out[r][c] = sum_s part[s][r][c] (+1 on the diagonal), FP64
+// out[r][c] = sum_s part[s][r][c] (+1 on the diagonal), FP64; with mirror,
+// the entries above the diagonal are read from below it (symmetric products
+// whose upper tiles were not computed)
 __global__ void k_reduce_splits(int splits, int rows, int cols, const float* __restrict__ part, int64_t ldp,
                                 int64_t split_stride, double* __restrict__ out, int64_t ldo, int add_identity,
-                                int accumulate = 0) {
+                                int accumulate = 0, int mirror = 0) {
   int64_t total = (int64_t)rows * cols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(t / cols), c = (int)(t % cols);
     double s = accumulate ? out[(int64_t)r * ldo + c] : ((add_identity && r == c) ? 1.0 : 0.0);
-    for (int z = 0; z < splits; ++z) s += (double)part[(int64_t)z * split_stride + (int64_t)r * ldp + c];
+    const int pr = mirror && c > r ? c : r, pc = mirror && c > r ? r : c;
+    for (int z = 0; z < splits; ++z) s += (double)part[(int64_t)z * split_stride + (int64_t)pr * ldp + pc];
     out[(int64_t)r * ldo + c] = s;
   }
 }
@@ -568,6 +571,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
     g.b[0] = &mYh; g.b[1] = &mYl; g.num_b = 2;
     g.pairs = lo ? (1u | 2u | 4u) : (1u | 2u);
     g.M = m_pad; g.N = m_pad; g.bn = 128;
+    g.lower = true;   // symmetric: the tiles on and below the diagonal, mirrored in the reduction
     // M - I = A~^T D^-1 A~ has entries up to n / min(D) while the identity is
     // what the small eigenvalues of M keep: FP32 accumulation runs over spans
     // of kCoreSpanBlocks k-blocks only and the spans are summed in FP64, in
@@ -585,7 +589,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
       g.splits = (nb + kCoreSpanBlocks - 1) / kCoreSpanBlocks;
       tc_gemm(g, H.err, s);
       k_reduce_splits<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(g.splits, m, m, part.p, m_pad, g.split_stride,
-                                                                    op.Mp.p, m, 1, first ? 0 : 1);
+                                                                    op.Mp.p, m, 1, first ? 0 : 1, 1);
       FSA_CHECK_LAUNCH();
     }
     FSA_CUDA(cudaStreamSynchronize(s));

@@ -37,6 +37,9 @@ struct Params {
   uint32_t blk;                                         // bit a: A_a blocked; bit 2 + b: B_b blocked
   uint32_t a_bytes, b_bytes, stage_bytes, tmem_cols, idesc;
   int stack, n_valid;
+  int lower;                                            // 1: only tiles on or below the diagonal
+  int vec_store;                                        // 1: rows 16-byte aligned (two 16-byte stores per 8 columns)
+  int ntn;                                              // persistent form: N tiles (tile t: M tile t % mtiles, N tile t / mtiles)
   float* out;
   int64_t ldo, split_stride;
   unsigned* err;
@@ -141,6 +144,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 consecutive output columns of one row from col: two 16-byte stores when
+// the row is 16-byte aligned and all 8 columns are valid, else one by one
+__device__ __forceinline__ void store8(float* orow, int col, const float (&v)[8], int n_valid, bool vec) {
+  if (vec && col + 8 <= n_valid) {
+    *reinterpret_cast<float4*>(orow + col) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(orow + col + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (col + j < n_valid) orow[col + j] = v[j];
+  }
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -152,6 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
 
+  // a symmetric product needs the tiles on and below the diagonal only (the
+  // whole CTA leaves before any barrier or TMEM allocation)
+  if (p.lower && (int)blockIdx.y * p.bn >= ((int)blockIdx.x + 1) * BM) return;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
@@ -260,11 +279,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           tmem_ld8(taddr + c0, r);
           tmem_wait_ld();
           if (in) {
+            float v[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              int col = n0 + c0 + j;
-              if (col < p.n_valid) orow[col] = __uint_as_float(r[j]);
-            }
+            for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+            store8(orow, n0 + c0, v, p.n_valid, p.vec_store != 0);
           }
         }
       } else {
@@ -277,13 +295,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           if (p.stack == 3) tmem_ld8(taddr + 2 * h + c0, u);
           tmem_wait_ld();
           if (in) {
+            float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              int col = c0 + j;
-              float v = __uint_as_float(r[j]) + __uint_as_float(t[j]);
-              if (p.stack == 3) v += __uint_as_float(u[j]);
-              if (col < p.n_valid) orow[col] = v;
+              v[j] = __uint_as_float(r[j]) + __uint_as_float(t[j]);
+              if (p.stack == 3) v[j] += __uint_as_float(u[j]);
             }
+            store8(orow, c0, v, p.n_valid, p.vec_store != 0);
           }
         }
       }
@@ -299,8 +317,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   }
 }
 
-// Persistent form for problems of many M tiles (one N tile, no split-K): one
-// CTA per SM loops over the M tiles blockIdx.x, + gridDim.x, ...  The TMA
+// Persistent form for problems of many output tiles (no split-K): one CTA per
+// SM loops over the tiles blockIdx.x, + gridDim.x, ..., tile t being M tile
+// t % mtiles of N tile t / mtiles (consecutive CTAs share a B box).  The TMA
 // producer runs ahead through the stage ring across tile boundaries; the
 // accumulator is double-buffered in TMEM (two column ranges of tmem_cols / 2),
 // so the epilogue of tile j (tcgen05.ld + stores) overlaps the MMAs of tile
@@ -318,7 +337,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = p.kblocks - p.kb_base;
   const int S = p.stages;
-  const int ntiles = (p.M + BM - 1) / BM;
+  const int mtiles = (p.M + BM - 1) / BM;
+  const int ntiles = mtiles * p.ntn;
   const int nt = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   const uint32_t half = p.tmem_cols / 2;   // columns of one accumulator buffer
 
@@ -352,7 +372,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
       // ------------------------------------------------------------ producer
       int it = 0;
       for (int j = 0; j < nt && !abort_sh; ++j) {
-        const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * BM;
+        const int t = (int)blockIdx.x + j * (int)gridDim.x;
+        const int m0 = (t % mtiles) * BM, n0 = (t / mtiles) * p.bn;
         for (int i = 0; i < nk && !abort_sh; ++i, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -368,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
             load_operand(st + a * p.a_bytes, &p.ma[a], (p.blk >> a) & 1u, &full_bar[s], kb, m0);
           for (int b = 0; b < p.num_b; ++b)
             load_operand(st + p.num_a * p.a_bytes + b * p.b_bytes, &p.mb[b], (p.blk >> (2 + b)) & 1u, &full_bar[s],
-                         kb, 0);
+                         kb, n0);
         }
       }
       // drain: every copy issued by this thread has landed before the CTA exits
@@ -432,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
         break;
       }
       fence_after();
-      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * BM;
+      const int t = (int)blockIdx.x + j * (int)gridDim.x;
+      const int m0 = (t % mtiles) * BM, n0 = (t / mtiles) * p.bn;
       const int row = m0 + q * 32 + lane;
       const uint32_t taddr = tmem + (uint32_t)b * half + ((uint32_t)(q * 32) << 16);
       float* orow = p.out + (int64_t)row * p.ldo;
@@ -443,11 +465,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
           tmem_ld8(taddr + c0, r);
           tmem_wait_ld();
           if (in) {
+            float v[8];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int col = c0 + jj;
-              if (col < p.n_valid) orow[col] = __uint_as_float(r[jj]);
-            }
+            for (int jj = 0; jj < 8; ++jj) v[jj] = __uint_as_float(r[jj]);
+            store8(orow, n0 + c0, v, p.n_valid, p.vec_store != 0);
           }
         }
       } else {
@@ -459,13 +480,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_persistent(const __grid_cons
           if (p.stack == 3) tmem_ld8(taddr + 2 * h + c0, u);
           tmem_wait_ld();
           if (in) {
+            float v[8];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
-              const int col = c0 + jj;
-              float v = __uint_as_float(r[jj]) + __uint_as_float(t[jj]);
-              if (p.stack == 3) v += __uint_as_float(u[jj]);
-              if (col < p.n_valid) orow[col] = v;
+              v[jj] = __uint_as_float(r[jj]) + __uint_as_float(t[jj]);
+              if (p.stack == 3) v[jj] += __uint_as_float(u[jj]);
             }
+            store8(orow, c0, v, p.n_valid, p.vec_store != 0);
           }
         }
       }
@@ -590,6 +611,8 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   // instruction descriptor: D FP32, A BF16, B BF16, both K-major, N >> 3, M >> 4
   p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
   p.stack = stack;
+  p.lower = g.lower ? 1 : 0;
+  p.vec_store = ((uintptr_t)g.out % 16 == 0 && g.ldo % 4 == 0 && g.split_stride % 4 == 0) ? 1 : 0;
   p.n_valid = g.n_valid > 0 ? g.n_valid : (stack > 1 ? bn / stack : g.N);
   p.out = g.out;
   p.ldo = g.ldo;
@@ -609,7 +632,9 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   dim3 grid((g.M + tc::BM - 1) / tc::BM, (g.N + bn - 1) / bn, splits);
   // many M tiles of one N tile: the persistent form (one CTA per SM, a deeper
   // stage ring, double-buffered accumulators)
-  const bool persistent = splits == 1 && grid.y == 1 && sms > 0 && (int)grid.x >= 2 * sms && 2 * cols <= 512;
+  const bool persistent = splits == 1 && (grid.y == 1 || stack == 1) && !g.lower && sms > 0 &&
+                          (int)(grid.x * grid.y) >= 2 * sms && 2 * cols <= 512;
+  p.ntn = (int)grid.y;
   if (persistent) {
     p.tmem_cols = 2 * cols;
     p.stages = std::max(2, std::min(tc::kMaxStages, (199 * 1024) / (int)p.stage_bytes));

@@ -54,6 +54,8 @@ struct TcGemm {
   int64_t ldo = 0;
   int64_t split_stride = 0;
   int n_valid = 0;          // columns of out written (<= N or N/2)
+  bool lower = false;       // symmetric result: only the tiles on or below the diagonal are computed
+                            // (output tiles strictly above it are left unwritten)
   const char* tag = nullptr;  // profiling tag (fsa_profile.h)
   double alg_bytes = 0;       // algorithmic bytes of this launch (0: from the shapes)
 };

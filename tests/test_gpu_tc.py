@@ -47,6 +47,8 @@ def _selftest(M, N, K, na, nb, pairs, halves, splits, seed=1):
     (50000, 144, 1024, 2, 1, 5, 2, 1),     # persistent form (>= 2 tiles per SM): A q with A hi/lo, ragged M
     (40000, 256, 128, 1, 1, 1, 0, 1),      # persistent form, full 256-column tile, two K blocks
     (39001, 48, 64, 1, 1, 1, 1, 1),        # persistent form, one K block per tile
+    (40000, 512, 128, 1, 1, 1, 0, 1),      # persistent form over two N tiles
+    (20011, 1024, 256, 2, 2, 7, 0, 1),     # persistent form over four N tiles, split products (the A~ build shape)
 ])
 def test_tc_gemm_selftest(F, M, N, K, na, nb, pairs, halves, splits):
     st, err, act = _selftest(M, N, K, na, nb, pairs, halves, splits)
