@@ -492,13 +492,15 @@ int64_t fsa_footprint_bytes(int64_t n, int32_t m, int64_t nnz, int32_t num_probe
   // peak of one fsa_build + fsa_loglik_grad: pattern and coordinates, m x m
   // matrices, the n x m operator with its build or gradient temporaries
   // (whichever is larger), and the n x ldc CG block; plus 25 % and a fixed
-  // allowance for split-K partials and scratch
+  // allowance for split-K partials and scratch.  The SpMM row groups' union
+  // entries (32 bytes of sources, and in the mixed forms 32 bytes of values)
+  // number at most nnz.
   const int64_t c = (int64_t)num_probes + 1, ldc = (c + 7) / 8 * 8, mp = ((int64_t)m + 63) / 64 * 64;
-  int64_t b = 64 * n + 16 * nnz + 128 * (int64_t)m * m + ((int64_t)64 << 20);
+  int64_t b = 64 * n + 52 * nnz + 128 * (int64_t)m * m + ((int64_t)64 << 20);
   if (precision == FSA_FP64)
     b += 32 * n * (int64_t)m + 72 * n * ldc;
   else
-    b += (precision == FSA_MIXED_BF16X2 ? 20 : 16) * n * mp + 40 * n * ldc;
+    b += (precision == FSA_MIXED_BF16X2 ? 20 : 16) * n * mp + 40 * n * ldc + 32 * nnz;
   return b + b / 4;
 }
 

@@ -291,6 +291,118 @@ __global__ void k_tile_scol(const int64_t* __restrict__ tiles, const int64_t* __
   }
 }
 
+// Row groups of the SpMM tiles.  A tile's rows p0 .. p1 - 1 are cut into
+// groups of kGrpRows consecutive rows; the union list of a group holds every
+// staged row that is a taper neighbour of one of its rows, in ascending order.
+// The staged index grows with the column index (the ranges lie in ascending
+// order), so each row's nonzeros appear in its list in CSR order.  Both passes
+// mark the group's staged rows in a bitmap of the tile's staged rows in shared
+// memory; tiles with more than kGrpMaxStaged staged rows are marked bad (the
+// SpMM then gathers their rows from global memory).
+constexpr int kGrpMaxStaged = 16384;
+
+__device__ __forceinline__ void grp_mark(uint32_t* bits, int nw, int64_t eb, int64_t ee,
+                                         const int32_t* __restrict__ scol) {
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) bits[w] = 0u;
+  __syncthreads();
+  for (int64_t e = eb + threadIdx.x; e < ee; e += blockDim.x) {
+    const int sr = scol[e];
+    atomicOr(&bits[sr >> 5], 1u << (sr & 31));
+  }
+  __syncthreads();
+}
+
+// pass 1: cnt[gbase[t] + j] = entries of group j of tile t
+__global__ void k_grp_count(const int64_t* __restrict__ tiles, const int64_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ scol, int32_t* __restrict__ bad,
+                            const int32_t* __restrict__ gbase, int32_t* __restrict__ cnt) {
+  extern __shared__ uint32_t bits[];
+  __shared__ int tot;
+  const int t = blockIdx.x;
+  const int64_t* d = tiles + (int64_t)t * 8;
+  const int64_t p0 = d[0], p1 = d[1];
+  const int64_t ns = (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]);
+  const int ng = (int)((p1 - p0 + kGrpRows - 1) / kGrpRows);
+  const int32_t g0 = gbase[t];
+  if (bad[t] || ns > kGrpMaxStaged) {
+    __syncthreads();   // every thread has read bad[t] before it changes
+    if (threadIdx.x == 0) bad[t] = 1;
+    for (int j = threadIdx.x; j < ng; j += blockDim.x) cnt[g0 + j] = 0;
+    return;
+  }
+  const int nw = (int)((ns + 31) / 32);
+  for (int j = 0; j < ng; ++j) {
+    const int64_t ra = p0 + (int64_t)j * kGrpRows, rz = min(p1, ra + kGrpRows);
+    if (threadIdx.x == 0) tot = 0;
+    grp_mark(bits, nw, rowptr[ra], rowptr[rz], scol);
+    int c = 0;
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) c += __popc(bits[w]);
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&tot, c);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[g0 + j] = tot;
+    __syncthreads();
+  }
+}
+
+// pass 2: the entries (src, kEntWords int32 each, preset to -1): word 0 the staged
+// row, word 1 + g the nonzero of the group's row g in that column, relative
+// to the tile's first nonzero
+__global__ void k_grp_fill(const int64_t* __restrict__ tiles, const int32_t* __restrict__ ptile,
+                           const int64_t* __restrict__ rowptr, const int32_t* __restrict__ scol,
+                           const int32_t* __restrict__ bad, const int32_t* __restrict__ gofs,
+                           int32_t* __restrict__ src) {
+  extern __shared__ uint32_t sm[];
+  const int t = blockIdx.x;
+  if (bad[t]) return;
+  const int64_t* d = tiles + (int64_t)t * 8;
+  const int32_t* rec = ptile + (int64_t)t * kTileWords;
+  const int64_t p0 = d[0], p1 = d[1];
+  const int64_t ns = (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]);
+  const int ng = (int)((p1 - p0 + kGrpRows - 1) / kGrpRows);
+  const int nw = (int)((ns + 31) / 32);
+  uint32_t* bits = sm;
+  uint32_t* pre = sm + nw;
+  const int64_t e0 = rowptr[p0];
+  const int32_t* go = gofs + rec[11];
+  const int64_t ent0 = (int64_t)(uint32_t)rec[12] | ((int64_t)rec[13] << 32);
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < ng; ++j) {
+    const int64_t ra = p0 + (int64_t)j * kGrpRows, rz = min(p1, ra + kGrpRows);
+    grp_mark(bits, nw, rowptr[ra], rowptr[rz], scol);
+    // exclusive prefix of the words' popcounts (first warp)
+    if (threadIdx.x < 32) {
+      uint32_t run = 0;
+      for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t own = w < nw ? (uint32_t)__popc(bits[w]) : 0u;
+        uint32_t v = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += y;
+        }
+        if (w < nw) pre[w] = run + v - own;
+        run += __shfl_sync(0xffffffffu, v, 31);
+      }
+    }
+    __syncthreads();
+    const int64_t base = ent0 + go[j];
+    auto rank = [&](int sr) {
+      const uint32_t w = bits[sr >> 5];
+      return (int64_t)pre[sr >> 5] + __popc(w & ((1u << (sr & 31)) - 1u));
+    };
+    for (int sr = threadIdx.x; sr < (int)ns; sr += blockDim.x)
+      if ((bits[sr >> 5] >> (sr & 31)) & 1u) src[(base + rank(sr)) * kEntWords] = sr;
+    for (int64_t r = ra; r < rz; ++r) {
+      const int g = (int)(r - ra);
+      for (int64_t e = rowptr[r] + threadIdx.x; e < rowptr[r + 1]; e += blockDim.x)
+        src[(base + rank(scol[e])) * kEntWords + 1 + g] = (int32_t)(e - e0);
+    }
+    __syncthreads();
+  }
+}
+
 void build_structure(Handle& H, const double* locs_host) {
   cudaStream_t s = H.stream;
   int64_t n = H.n;
@@ -354,18 +466,14 @@ void build_structure(Handle& H, const double* locs_host) {
   FSA_CUDA(cudaStreamSynchronize(s));
 }
 
-// SpMM tiles (host): each grid row of cells is cut into runs of cells holding
-// about kTileRows points; the taper neighbours of a run's points lie in the
-// run's cells widened by one on each side, in the rows above, at and below
-// (cell side >= gamma), i.e. in three contiguous ranges of the internal order.
-void build_tiles(Handle& H) {
-  constexpr int64_t kTileRows = 24;
-  const int ncx = H.grid.ncx, ncy = H.grid.ncy;
-  const int64_t ncells = (int64_t)ncx * ncy;
-  std::vector<int32_t> start(ncells), count(ncells);
-  FSA_CUDA(cudaMemcpyAsync(start.data(), H.cell_start.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
-  FSA_CUDA(cudaMemcpyAsync(count.data(), H.cell_count.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
-  FSA_CUDA(cudaStreamSynchronize(H.stream));
+// Tiles of about `rows` points: each grid row of cells is cut into runs of
+// cells holding at least that many points; the taper neighbours of a run's
+// points lie in the run's cells widened by one on each side, in the rows
+// above, at and below (cell side >= gamma), i.e. in three contiguous ranges of
+// the internal order.  Per tile 8 int64: p0, p1, then [begin, end) of the
+// three ranges.
+static std::vector<int64_t> cut_tiles(const std::vector<int32_t>& start, const std::vector<int32_t>& count, int ncx,
+                                      int ncy, int64_t rows, int64_t* max_staged) {
   auto range = [&](int cy, int cxa, int cxb, int64_t* out) {
     if (cy < 0 || cy >= ncy) { out[0] = out[1] = 0; return; }
     const int a = std::max(cxa - 1, 0), b = std::min(cxb + 1, ncx - 1);
@@ -374,13 +482,13 @@ void build_tiles(Handle& H) {
     out[1] = (int64_t)start[c1] + count[c1];
   };
   std::vector<int64_t> t;
-  int64_t max_staged = 0;
+  int64_t ms = 0;
   for (int cy = 0; cy < ncy; ++cy) {
     int cxa = 0;
     int64_t acc = 0;
     for (int cx = 0; cx < ncx; ++cx) {
       acc += count[(int64_t)cy * ncx + cx];
-      if (acc >= kTileRows || cx == ncx - 1) {
+      if (acc >= rows || cx == ncx - 1) {
         if (acc > 0) {
           int64_t d[8];
           d[0] = start[(int64_t)cy * ncx + cxa];
@@ -388,7 +496,7 @@ void build_tiles(Handle& H) {
           range(cy - 1, cxa, cx, d + 2);
           range(cy, cxa, cx, d + 4);
           range(cy + 1, cxa, cx, d + 6);
-          max_staged = std::max(max_staged, (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]));
+          ms = std::max(ms, (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]));
           t.insert(t.end(), d, d + 8);
         }
         cxa = cx + 1;
@@ -396,29 +504,18 @@ void build_tiles(Handle& H) {
       }
     }
   }
-  H.ntiles = (int)(t.size() / 8);
-  H.max_staged = max_staged;
-  H.tiles.alloc(std::max<size_t>(t.size(), 8));
-  if (!t.empty())
-    FSA_CUDA(cudaMemcpyAsync(H.tiles.p, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, H.stream));
-  // largest tile (rows, nonzeros) from the row pointers
-  std::vector<int64_t> rp(H.n + 1);
-  FSA_CUDA(cudaMemcpyAsync(rp.data(), H.rowptr.p, sizeof(int64_t) * (H.n + 1), cudaMemcpyDeviceToHost, H.stream));
-  FSA_CUDA(cudaStreamSynchronize(H.stream));
-  int64_t mr = 0, me = 0;
-  for (int k = 0; k < H.ntiles; ++k) {
-    mr = std::max(mr, t[8 * k + 1] - t[8 * k]);
-    me = std::max(me, rp[t[8 * k + 1]] - rp[t[8 * k]]);
-  }
-  H.max_tile_rows = mr;
-  H.max_tile_nnz = me;
-  // the pipelined SpMM's record: p0, rows, (begin, length) of the three
-  // ranges, first nonzero (low, high 32 bits), nonzeros, unused
-  FSA_REQUIRE(H.n < ((int64_t)1 << 31), FSA_ERR_ARG, "more than 2^31 - 1 points");
-  std::vector<int32_t> pt((size_t)std::max(H.ntiles, 1) * 12, 0);
-  for (int k = 0; k < H.ntiles; ++k) {
+  if (max_staged) *max_staged = ms;
+  return t;
+}
+
+// tile records (kTileWords int32; words 11-15 zero): p0, rows, (begin,
+// length) of the three ranges, first nonzero (low, high 32 bits), nonzeros
+static std::vector<int32_t> tile_records(const std::vector<int64_t>& t, const std::vector<int64_t>& rp) {
+  const int nt = (int)(t.size() / 8);
+  std::vector<int32_t> pt((size_t)std::max(nt, 1) * kTileWords, 0);
+  for (int k = 0; k < nt; ++k) {
     const int64_t* d = &t[8 * (size_t)k];
-    int32_t* o = &pt[12 * (size_t)k];
+    int32_t* o = &pt[kTileWords * (size_t)k];
     const int64_t e0 = rp[d[0]];
     o[0] = (int32_t)d[0];
     o[1] = (int32_t)(d[1] - d[0]);
@@ -430,15 +527,122 @@ void build_tiles(Handle& H) {
     o[9] = (int32_t)(e0 >> 32);
     o[10] = (int32_t)(rp[d[1]] - e0);
   }
+  return pt;
+}
+
+// The SpMM's own tiling (kSpTileRows) and the row groups of its tiles: the
+// records (words 11-15: offset of the tile's group offsets in gofs, first
+// union entry, union entries, bad flag), the group offsets and the union
+// entries' sources.  Its staged columns and bad flags are needed only here.
+static void build_spmm_groups(Handle& H, const std::vector<int64_t>& t, const std::vector<int64_t>& rp) {
+  cudaStream_t s = H.stream;
+  const int nt = (int)(t.size() / 8);
+  H.sp_ntiles = nt;
+  std::vector<int32_t> pt = tile_records(t, rp);
+  std::vector<int32_t> gbase(std::max(nt, 1), 0);
+  int64_t ngroups = 0;
+  for (int k = 0; k < nt; ++k) {
+    gbase[k] = (int32_t)ngroups;
+    ngroups += (pt[kTileWords * (size_t)k + 1] + kGrpRows - 1) / kGrpRows;
+  }
+  FSA_REQUIRE(ngroups + nt + 4 < ((int64_t)1 << 31), FSA_ERR_ARG, "too many SpMM row groups");
+  H.grp_entries = 0;
+  std::vector<int32_t> go((size_t)(ngroups + nt + 4), 0);
+  DevPtr<int64_t> tiles(std::max<size_t>(t.size(), 8));
+  DevPtr<int32_t> scol(H.nnz + 4), bad(std::max(nt, 1));
+  if (nt > 0) {
+    FSA_CUDA(cudaMemcpyAsync(tiles.p, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, s));
+    FSA_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int32_t) * nt, s));
+    k_tile_scol<<<nt, 256, 0, s>>>(tiles.p, H.rowptr.p, H.col.p, scol.p, bad.p);
+    FSA_CHECK_LAUNCH();
+    // union-list sizes of the row groups
+    DevPtr<int32_t> gb(nt), cnt(std::max<int64_t>(ngroups, 1));
+    FSA_CUDA(cudaMemcpyAsync(gb.p, gbase.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    const size_t bits_bytes = (size_t)(kGrpMaxStaged / 32) * sizeof(uint32_t);
+    k_grp_count<<<nt, 256, bits_bytes, s>>>(tiles.p, H.rowptr.p, scol.p, bad.p, gb.p, cnt.p);
+    FSA_CHECK_LAUNCH();
+    std::vector<int32_t> gc((size_t)std::max<int64_t>(ngroups, 1)), hb(nt);
+    FSA_CUDA(cudaMemcpyAsync(gc.data(), cnt.p, sizeof(int32_t) * gc.size(), cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaMemcpyAsync(hb.data(), bad.p, sizeof(int32_t) * nt, cudaMemcpyDeviceToHost, s));
+    FSA_CUDA(cudaStreamSynchronize(s));
+    int64_t ent = 0;
+    for (int k = 0; k < nt; ++k) {
+      int32_t* o = &pt[kTileWords * (size_t)k];
+      const int ng = (o[1] + kGrpRows - 1) / kGrpRows;
+      const int64_t gob = (int64_t)gbase[k] + k;   // ng + 1 offsets from here
+      int64_t rel = 0;
+      for (int j = 0; j < ng; ++j) {
+        go[(size_t)(gob + j)] = (int32_t)rel;
+        rel += gc[(size_t)gbase[k] + j];
+      }
+      go[(size_t)(gob + ng)] = (int32_t)rel;
+      FSA_REQUIRE(rel < ((int64_t)1 << 30), FSA_ERR_ARG, "SpMM tile with too many union entries");
+      o[11] = (int32_t)gob;
+      o[12] = (int32_t)(uint32_t)((uint64_t)ent & 0xffffffffu);
+      o[13] = (int32_t)(ent >> 32);
+      o[14] = (int32_t)rel;
+      o[15] = hb[k] ? 1 : 0;
+      ent += rel;
+    }
+    H.grp_entries = ent;
+  }
+  H.sp_ptile.alloc(pt.size());
+  FSA_CUDA(cudaMemcpyAsync(H.sp_ptile.p, pt.data(), sizeof(int32_t) * pt.size(), cudaMemcpyHostToDevice, s));
+  H.gofs.alloc(go.size());   // spare entries: the SpMM copies in 16-byte units
+  FSA_CUDA(cudaMemcpyAsync(H.gofs.p, go.data(), sizeof(int32_t) * go.size(), cudaMemcpyHostToDevice, s));
+  const size_t nv = (size_t)std::max<int64_t>(H.grp_entries, 1) * kEntVec;
+  H.grp_src.alloc(nv);
+  FSA_CUDA(cudaMemsetAsync(H.grp_src.p, 0xff, sizeof(int4) * nv, s));
+  if (nt > 0 && H.grp_entries > 0) {
+    const size_t sm_bytes = 2 * (size_t)(kGrpMaxStaged / 32) * sizeof(uint32_t);
+    k_grp_fill<<<nt, 256, sm_bytes, s>>>(tiles.p, H.sp_ptile.p, H.rowptr.p, scol.p, bad.p, H.gofs.p,
+                                         reinterpret_cast<int32_t*>(H.grp_src.p));
+    FSA_CHECK_LAUNCH();
+  }
+  FSA_CUDA(cudaStreamSynchronize(s));   // the temporaries are freed on return
+}
+
+// Tiles of the tile-staged kernels: the SDDMM forms of the residual values and
+// their range derivative (kTileRows points per tile) and the SpMM
+// (kSpTileRows, its own tiling: its staged rows are Z rows of at most 512
+// bytes, the SDDMM's are BF16 pairs of A~ blocks).
+void build_tiles(Handle& H) {
+  constexpr int64_t kTileRows = 24, kSpTileRows = 48;
+  const int ncx = H.grid.ncx, ncy = H.grid.ncy;
+  const int64_t ncells = (int64_t)ncx * ncy;
+  std::vector<int32_t> start(ncells), count(ncells);
+  std::vector<int64_t> rp(H.n + 1);
+  FSA_CUDA(cudaMemcpyAsync(start.data(), H.cell_start.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaMemcpyAsync(count.data(), H.cell_count.p, sizeof(int32_t) * ncells, cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaMemcpyAsync(rp.data(), H.rowptr.p, sizeof(int64_t) * (H.n + 1), cudaMemcpyDeviceToHost, H.stream));
+  FSA_CUDA(cudaStreamSynchronize(H.stream));
+  FSA_REQUIRE(H.n < ((int64_t)1 << 31), FSA_ERR_ARG, "more than 2^31 - 1 points");
+  int64_t max_staged = 0;
+  const std::vector<int64_t> t = cut_tiles(start, count, ncx, ncy, kTileRows, &max_staged);
+  H.ntiles = (int)(t.size() / 8);
+  H.max_staged = max_staged;
+  H.tiles.alloc(std::max<size_t>(t.size(), 8));
+  if (!t.empty())
+    FSA_CUDA(cudaMemcpyAsync(H.tiles.p, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, H.stream));
+  // largest tile (rows, nonzeros) from the row pointers
+  int64_t mr = 0, me = 0;
+  for (int k = 0; k < H.ntiles; ++k) {
+    mr = std::max(mr, t[8 * k + 1] - t[8 * k]);
+    me = std::max(me, rp[t[8 * k + 1]] - rp[t[8 * k]]);
+  }
+  H.max_tile_rows = mr;
+  H.max_tile_nnz = me;
+  const std::vector<int32_t> pt = tile_records(t, rp);
   H.ptile.alloc(pt.size());
   FSA_CUDA(cudaMemcpyAsync(H.ptile.p, pt.data(), sizeof(int32_t) * pt.size(), cudaMemcpyHostToDevice, H.stream));
-  H.scol.alloc(H.nnz + 4);   // spare entries: the SpMM copies in 16-byte units
+  H.scol.alloc(H.nnz + 4);   // spare entries: copies in 16-byte units
   H.tile_bad.alloc(std::max(H.ntiles, 1));
   FSA_CUDA(cudaMemsetAsync(H.tile_bad.p, 0, sizeof(int32_t) * std::max(H.ntiles, 1), H.stream));
   if (H.ntiles > 0) {
     k_tile_scol<<<H.ntiles, 256, 0, H.stream>>>(H.tiles.p, H.rowptr.p, H.col.p, H.scol.p, H.tile_bad.p);
     FSA_CHECK_LAUNCH();
   }
+  build_spmm_groups(H, cut_tiles(start, count, ncx, ncy, kSpTileRows, nullptr), rp);
 }
 
 void build_cross_structure(Handle& H, const double* qx, const double* qy, int64_t nq,

@@ -78,6 +78,17 @@ struct Grid {
 // ---------------------------------------------------------------------------
 // theta-dependent operator (paper §2.1, §3.1, Eq. eqfitcp)
 // ---------------------------------------------------------------------------
+// SpMM tile record (int32 words): p0, rows, (begin, length) of the three
+// staged ranges, first nonzero (low, high words), nonzeros, offset of the
+// tile's group offsets in gofs, first union entry (low, high words), union
+// entries, bad flag (a copy of tile_bad)
+constexpr int kTileWords = 16;
+constexpr int kGrpRows = 3;   // rows per SpMM row group
+static_assert(kGrpRows >= 1 && kGrpRows <= 7, "a union entry holds at most 7 values");
+// int32 words of a union entry (staged column + kGrpRows values, padded to 16 or 32 bytes)
+constexpr int kEntWords = kGrpRows <= 3 ? 4 : 8;
+constexpr int kEntVec = kEntWords / 4;   // int4 per entry
+
 struct Operator {
   bool valid = false;
   fsa_theta theta{};
@@ -99,7 +110,10 @@ struct Operator {
   DevPtr<__nv_bfloat16> Ab_lo, Atb_lo;   // low halves (FSA_MIXED_BF16X2): A = Ab + Ab_lo
   bool has_lo = false;
   DevPtr<float> vals32;
-  DevPtr<int2> pairs32;   // per nonzero (staged column in its SpMM tile, FP32 value bits)
+  // per union entry of an SpMM row group (kEntWords words): its staged
+  // column, then the FP32 values of the group's kGrpRows rows in that column
+  // (0 where the column is not a neighbour of the row, and in the padding)
+  DevPtr<int4> grp_ent;
   DevPtr<float> D32, Dinv32;
   double core_scale = 0.0;   // 2^-24 |M - I|_inf of the tensor-core Woodbury core
   bool core_fp64 = false;    // the core was formed in FP64 (core_scale too large)
@@ -146,14 +160,23 @@ struct Handle {
   DevPtr<int64_t> perm, iperm, rowptr;     // perm[internal] = original
   DevPtr<int32_t> col, cell_start, cell_count;
   int64_t nnz = 0;
-  // SpMM tiles: runs of cells of one grid row (about kTileRows points) whose
-  // taper neighbours all lie in three contiguous index ranges (the same cells
-  // +-1 in the rows above, at and below).  Per tile 8 int64: p0, p1 (its
-  // rows), then [begin, end) of the three ranges.
+  // Tiles of the SDDMM kernels: runs of cells of one grid row (about 24
+  // points) whose taper neighbours all lie in three contiguous index ranges
+  // (the same cells +-1 in the rows above, at and below).  Per tile 8 int64:
+  // p0, p1 (its rows), then [begin, end) of the three ranges.
   DevPtr<int64_t> tiles;
-  DevPtr<int32_t> ptile;                   // per tile 12 int32 for the pipelined SpMM (see build_tiles)
+  DevPtr<int32_t> ptile;                   // per tile kTileWords int32 (words 0-10; see tile_records)
   DevPtr<int32_t> scol;                    // per nonzero: row of its column in the tile's staged ranges
   DevPtr<int32_t> tile_bad;                // 1: a column of the tile lies outside its ranges
+  // The SpMM's own tiling (larger tiles) and the row groups of its tiles
+  // (kGrpRows consecutive rows; the last one of a tile may be shorter).  A
+  // group's union list holds, in ascending order, every staged row that is a
+  // neighbour of at least one of its rows.
+  DevPtr<int32_t> sp_ptile;                // per tile kTileWords int32 (see build_spmm_groups)
+  int sp_ntiles = 0;
+  DevPtr<int32_t> gofs;                    // per tile, at sp_ptile word 11: its groups' list offsets (ng + 1, tile-relative)
+  DevPtr<int4> grp_src;                    // per entry (kEntWords): staged column, then per row the tile-relative nonzero or -1
+  int64_t grp_entries = 0;
   int ntiles = 0;
   int64_t max_staged = 0;                  // largest sum of the three range lengths
   int64_t max_tile_rows = 0, max_tile_nnz = 0;

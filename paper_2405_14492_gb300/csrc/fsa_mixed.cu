@@ -424,11 +424,27 @@ __global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kin
   }
 }
 
-// pairs[t] = (scol[t], bits of vals32[t])
-__global__ void k_pack_pairs(int64_t nnz, const int32_t* __restrict__ scol, const float* __restrict__ vals32,
-                             int2* __restrict__ pairs) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
-    pairs[t] = make_int2(scol[t], __float_as_int(vals32[t]));
+// values of the SpMM row groups' union entries (one block per tile): entry
+// word 0 the staged column, word 1 + g the FP32 value of the group's row g in
+// that column (bits), or 0 where the column is not one of its neighbours
+__global__ void k_grp_values(const int32_t* __restrict__ ptile, const int4* __restrict__ src,
+                             const float* __restrict__ vals32, int4* __restrict__ ent) {
+  const int t = blockIdx.x;
+  const int32_t* rec = ptile + (int64_t)t * kTileWords;
+  if (rec[15]) return;   // bad tile: no union entries
+  const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
+  const int64_t eb = (int64_t)(uint32_t)rec[12] | ((int64_t)rec[13] << 32);
+  const int ne = rec[14];
+  auto val = [&](int r) { return r >= 0 ? __float_as_int(vals32[e0 + r]) : 0; };
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const int64_t x = kEntVec * (eb + i);
+    const int4 a = src[x];
+    ent[x] = make_int4(a.x, val(a.y), val(a.z), val(a.w));
+    if (kEntVec == 2) {
+      const int4 b = src[x + 1];
+      ent[x + 1] = make_int4(val(b.x), val(b.y), val(b.z), val(b.w));
+    }
+  }
 }
 
 // dst = bf16(a - b)
@@ -552,10 +568,12 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   op.D32.ensure(n);
   op.Dinv32.ensure(n);
   if (!csr_values_tiles(H, th, op.Ab.p, Alo, m_pad)) csr_values_rows(H, th, op.Ab.p, Alo, m_pad);
-  // the SpMM's (staged column, value) pairs, read by one bulk copy per tile
-  op.pairs32.ensure(H.nnz + 2);   // spare entries: the SpMM copies in 16-byte units
-  k_pack_pairs<<<grid_for(H.nnz, 256), 256, 0, s>>>(H.nnz, H.scol.p, op.vals32.p, op.pairs32.p);
-  FSA_CHECK_LAUNCH();
+  // the values of the SpMM row groups' union entries, read by one bulk copy per tile
+  op.grp_ent.ensure((size_t)std::max<int64_t>(H.grp_entries, 1) * kEntVec);
+  if (H.sp_ntiles > 0 && H.grp_entries > 0) {
+    k_grp_values<<<H.sp_ntiles, 128, 0, s>>>(H.sp_ptile.p, H.grp_src.p, op.vals32.p, op.grp_ent.p);
+    FSA_CHECK_LAUNCH();
+  }
   // Woodbury core M = I + A^T D^-1 A on the tensor cores (split-K, FP64 reduction)
   {
     size_t mn = (size_t)m_pad * n_pad;

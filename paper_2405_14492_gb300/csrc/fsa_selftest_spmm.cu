@@ -92,31 +92,27 @@ extern "C" int fsa_selftest_spmm(fsa_handle* hh, const fsa_theta* theta, int nco
     unsigned long long bits = 0;
     FSA_CUDA(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, s));
     // which tiles fit the staging capacity (the kernel's own test)
-    std::vector<int64_t> td((size_t)H.ntiles * 8), rp(H.n + 1);
-    std::vector<int32_t> bad(std::max(H.ntiles, 1));
-    if (H.ntiles > 0) {
-      FSA_CUDA(cudaMemcpyAsync(td.data(), H.tiles.p, sizeof(int64_t) * td.size(), cudaMemcpyDeviceToHost, s));
-      FSA_CUDA(cudaMemcpyAsync(bad.data(), H.tile_bad.p, sizeof(int32_t) * H.ntiles, cudaMemcpyDeviceToHost, s));
-    }
-    FSA_CUDA(cudaMemcpyAsync(rp.data(), H.rowptr.p, sizeof(int64_t) * (H.n + 1), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> pt((size_t)std::max(H.sp_ntiles, 1) * kTileWords);
+    if (H.sp_ntiles > 0)
+      FSA_CUDA(cudaMemcpyAsync(pt.data(), H.sp_ptile.p, sizeof(int32_t) * (size_t)H.sp_ntiles * kTileWords,
+                               cudaMemcpyDeviceToHost, s));
     FSA_CUDA(cudaStreamSynchronize(s));
     check_err(H);
     int staged = 0;
-    for (int k = 0; k < H.ntiles; ++k) {
-      const int64_t* d = &td[(size_t)k * 8];
-      const int64_t rows = (d[3] - d[2]) + (d[5] - d[4]) + (d[7] - d[6]);
-      const int64_t e0 = rp[d[0]], ne = rp[d[1]] - e0, p0 = d[0], nr = d[1] - d[0];
-      const int64_t npairs = ((e0 + ne + 1) & ~(int64_t)1) - (e0 & ~(int64_t)1);
-      const int64_t nrp = ((p0 + nr + 2) & ~(int64_t)1) - (p0 & ~(int64_t)1);
+    for (int k = 0; k < H.sp_ntiles; ++k) {
+      const int32_t* o = &pt[(size_t)k * kTileWords];
+      const int nr = o[1], ng = (nr + kGrpRows - 1) / kGrpRows;
+      int ga, gz;
+      sp_gofs_range(o[11], ng, ga, gz);
       // with V and H staged (the nonzero-beta pass; the larger layout)
-      const SpTileLayout lay = sp_tile_layout((int)rows, (int)nr, npairs, nrp, ldc, true);
-      if (!bad[k] && lay.bytes <= sl.ring.bytes) ++staged;
+      const SpTileLayout lay = sp_tile_layout(o[3] + o[5] + o[7], nr, o[14], gz - ga, ldc, true);
+      if (!o[15] && lay.bytes <= sl.ring.bytes) ++staged;
     }
     double d;
     std::memcpy(&d, &bits, sizeof(d));
     *max_abs_diff = d;
     if (staged_tiles) *staged_tiles = staged;
-    if (total_tiles) *total_tiles = H.ntiles;
+    if (total_tiles) *total_tiles = H.sp_ntiles;
     return FSA_OK;
   } catch (const Error& e) {
     cudaGetLastError();

@@ -343,47 +343,64 @@ __device__ __forceinline__ void sp_bulk_load(void* dst, const void* src, uint32_
 // FP32 form over the cell-grid tiles, warp-specialised: one persistent block
 // per SM runs its tiles (blockIdx.x, + gridDim.x, ...) through a byte ring of
 // shared memory in which consecutive tiles are placed back to back (each at
-// its own size, so that about three average tiles are in flight).  The
-// producer lane (last warp) places a tile and fills it with bulk copies (TMA,
-// completion counted in bytes on the tile slot's full barrier): its three
-// neighbour ranges of Z (contiguous runs of rows), its own rows of S, V and H
-// (contiguous; V and H only when some beta is nonzero), its (staged column,
-// value) pairs and its row pointers (the last two rounded out to 16-byte
-// boundaries; the arrays are padded for it).  Before placing a tile the
-// producer waits for the release (empty barrier) of the newest earlier tile
-// whose bytes it would overwrite, and of the tile that last used the slot.
-// The consumer warps wait on the full barrier, compute the tile entirely from
+// its own size).  The producer lane (last warp) gathers the tile records 16
+// at a time (cp.async into one of two buffers, completion on an mbarrier),
+// places a tile and fills it
+// with bulk copies (TMA, completion counted in bytes on the tile slot's full
+// barrier): its three neighbour ranges of Z (contiguous runs of rows), its own
+// rows of S, V and H (V and H only when some beta is nonzero), the union
+// entries of its row groups and the groups' entry offsets (rounded out to
+// 16-byte boundaries; the arrays are padded for it).  Before placing a tile
+// the producer waits for the release (empty barrier) of the newest earlier
+// tile whose bytes it would overwrite, and of the tile that last used the
+// slot.  The consumer warps wait on the full barrier, compute the tile from
 // shared memory, store V and H, and release the slot on its empty barrier;
-// there is no block-wide barrier per tile.  Each consumer warp runs R rows at
-// once, L lanes per row (lane owns float4 chunks ch and ch + L), per nonzero
-// one broadcast 8-byte load of the pair and one 16-byte shared load per chunk;
-// every row sums its products in CSR order, exactly as the row kernel.  A tile
-// larger than the ring, or holding a column outside its ranges (the cell-grid
-// pattern produces none), gathers from global memory.
-// Tile record (int32 x 12): p0, rows, then (begin, length) of the three
-// ranges, first nonzero (lo, hi words), nonzeros, unused.
-constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpSlots = 4, kTileWords = 12;
-constexpr int kSpMeta = 16;   // per slot: p0, nr, n0, r1b, staged, pair and row-pointer offsets, byte offsets
+// there is no block-wide barrier per tile.
+//
+// Work unit: a row group (kGrpRows consecutive rows of the tile), taken by the
+// consumer warps in turn across tiles.  Lane ch owns the float4 chunk ch of
+// every row (ldc <= 128).  Per union entry: one (kGrpRows <= 3) or two
+// broadcast 16-byte loads of the entry (staged column, the group's values)
+// and one 16-byte load of the staged Z row per lane, then kGrpRows x 4 FMAs;
+// each staged Z row is read once per group instead of once per (row, nonzero).  Every row sums its products in
+// CSR order (a zero value leaves the sum unchanged), exactly as the row
+// kernel.  A tile larger than the ring, or holding a column outside its
+// ranges (the cell-grid pattern produces none), gathers from global memory.
+constexpr int kSpConsumers = 15, kSpThreads = (kSpConsumers + 1) * 32, kSpSlots = 4;
+// true: a tile's own rows of S, V and H are staged in the ring with its Z
+// ranges; false: each consumer warp loads its group's rows from global memory
+// when it starts the group (the loads complete behind the group's products)
+constexpr bool kSpStageOwn = false;
+constexpr int kSpRecBatch = 16;   // tile records per bulk copy
+constexpr int kSpMeta = 16;   // per slot: p0, nr, n0, r1b, staged, groups and the byte offsets of the parts
 
 // shared-memory bytes of a staged tile and the offsets of its parts from the
-// tile's start: Z rows (+ one spare row), S, V, H rows, pairs, row pointers
+// tile's start: Z rows, S, V, H rows, union entries (kEntWords int32 each),
+// group offsets (ngo int32, a multiple of 4)
 struct SpTileLayout {
-  int s, v, h, sp, rp, bytes;
+  int s, v, h, en, go, bytes;
 };
-__host__ __device__ __forceinline__ SpTileLayout sp_tile_layout(int zrows, int nr, int64_t npairs, int64_t nrp,
+__host__ __device__ __forceinline__ SpTileLayout sp_tile_layout(int zrows, int nr, int64_t nent, int64_t ngo,
                                                                  int ldc, bool use_b) {
   const int64_t rb = (int64_t)ldc * 4;
   SpTileLayout l;
-  int64_t off = (int64_t)(zrows + 1) * rb;
-  l.s = (int)off; off += (int64_t)nr * rb;
-  l.v = (int)off; if (use_b) off += (int64_t)nr * rb;
-  l.h = (int)off; if (use_b) off += (int64_t)nr * rb;
-  off = (off + 15) / 16 * 16;
-  l.sp = (int)off; off += npairs * 8;
-  l.rp = (int)off; off += nrp * 8;
+  int64_t off = (int64_t)zrows * rb;
+  const int64_t own = kSpStageOwn ? (int64_t)nr * rb : 0;
+  l.s = (int)off; off += own;
+  l.v = (int)off; if (use_b) off += own;
+  l.h = (int)off; if (use_b) off += own;
+  l.en = (int)off; off += nent * (kEntWords * 4);
+  l.go = (int)off; off += ngo * 4;
   const int64_t bytes = (off + 127) / 128 * 128;
   l.bytes = bytes > (int64_t)1 << 30 ? 1 << 30 : (int)bytes;
   return l;
+}
+
+// the int32 range [ga, gz) of gofs holding a tile's ng + 1 group offsets from
+// gb, rounded out to 16-byte boundaries
+__host__ __device__ __forceinline__ void sp_gofs_range(int gb, int ng, int& ga, int& gz) {
+  ga = gb & ~3;
+  gz = (gb + ng + 1 + 3) & ~3;
 }
 
 struct SpRing {   // the ring's size in bytes
@@ -391,30 +408,25 @@ struct SpRing {   // the ring's size in bytes
 };
 
 static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
-    int ntiles, const int32_t* __restrict__ ptile, const int32_t* __restrict__ tile_bad, SpRing ring, int c,
-    int ldc, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-    const int2* __restrict__ pairs, const float* __restrict__ vals, const float* __restrict__ Z,
-    const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H, const double* __restrict__ beta,
-    double* __restrict__ part, int step, CGScalars q) {
+    int ntiles, const int32_t* __restrict__ ptile, SpRing ring, int c, int ldc,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, const int4* __restrict__ gent, const int32_t* __restrict__ gofs, const float* __restrict__ vals,
+    const float* __restrict__ Z, const float* __restrict__ S, float* __restrict__ V, float* __restrict__ H,
+    const double* __restrict__ beta, double* __restrict__ part, int step, CGScalars q) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t full_bar[kSpSlots], empty_bar[kSpSlots];
   __shared__ int smeta[kSpSlots][kSpMeta];
-  __shared__ float bsh[136];   // beta per column (0 beyond c), 8 spare for the odd-c4 chunk
+  __shared__ __align__(16) float bsh[128];   // beta per column (0 beyond c)
   __shared__ int any_b;
   __shared__ double wdot[kSpConsumers][128];   // per consumer warp: running h^T v partials per column
+  __shared__ __align__(16) int recs[2][kSpRecBatch][kTileWords];   // tile records, two batches
+  __shared__ __align__(8) uint64_t rec_bar[2];
   const int tid = threadIdx.x;
   const int c4 = ldc >> 2;
   const int lane = tid & 31, wib = tid >> 5;
-  const int L = (c4 + 1) >> 1, R = 32 / L;
-  const int slot = lane / L, ch = lane - (lane / L) * L;
-  const bool lane_on = slot < R;
-  const int q0 = ch, q1 = ch + L;
-  const bool has1 = q1 < c4;
   const float4* Z4 = reinterpret_cast<const float4*>(Z);
   const float4* S4 = reinterpret_cast<const float4*>(S);
   const float4* V4 = reinterpret_cast<const float4*>(V);
   const float4* H4 = reinterpret_cast<const float4*>(H);
-  float sub[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int x = tid; x < kSpConsumers * 128; x += kSpThreads) (&wdot[0][0])[x] = 0.0;
   if (tid == 0) {
     any_b = 0;
@@ -422,18 +434,22 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
       sp_mbar_init(&full_bar[s], 1);
       sp_mbar_init(&empty_bar[s], kSpConsumers);
     }
+    sp_mbar_init(&rec_bar[0], 1);
+    sp_mbar_init(&rec_bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  for (int col = tid; col < 136; col += kSpThreads) {
+  for (int col = tid; col < 128; col += kSpThreads) {
     const float bv = col < c ? (float)beta[col] : 0.f;
     bsh[col] = bv;
     if (bv != 0.f) any_b = 1;
   }
   __syncthreads();
   const bool use_b = any_b != 0;
-  // this block's tiles: k -> blockIdx.x + k * gridDim.x (gridDim.x <= ntiles)
+  // this block's tiles: k -> blockIdx.x + k * gridDim.x (gridDim.x <= ntiles):
+  // the blocks sweep the cell rows together, so the neighbour ranges one block
+  // stages are in L2 for the blocks on the adjacent cell rows
   const int nk = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (wib == kSpConsumers) {
     // ---------------- producer ----------------
@@ -451,18 +467,50 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         released = j;
         return true;
       };
+      // tile records, kSpRecBatch per bulk copy into two alternating buffers:
+      // batch bt holds tiles [bt kSpRecBatch, (bt + 1) kSpRecBatch) and uses
+      // buffer bt & 1 with barrier phase (bt >> 1) & 1
+      int rec_issued = 0, rec_ready = 0;   // batches issued, batches waited for
+      auto rec_issue = [&]() {
+        const int k0 = rec_issued * kSpRecBatch;
+        if (k0 >= nk) return;
+        const int cnt = min(kSpRecBatch, nk - k0);
+        for (int r = 0; r < cnt; ++r) {
+          const int4* src = reinterpret_cast<const int4*>(ptile + ((int64_t)blockIdx.x + (int64_t)(k0 + r) * gridDim.x) *
+                                                                      kTileWords);
+          int4* dst = reinterpret_cast<int4*>(recs[rec_issued & 1][r]);
+#pragma unroll
+          for (int w = 0; w < kTileWords / 4; ++w) cpa16(dst + w, src + w);
+        }
+        // the barrier's one arrival comes when these copies have landed
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sp_smem(&rec_bar[rec_issued & 1]))
+                     : "memory");
+        ++rec_issued;
+      };
+      // the record of this block's tile kk (nullptr if a wait ran out)
+      auto rec_of = [&](int kk) -> const int* {
+        const int bt = kk / kSpRecBatch;
+        while (rec_ready <= bt) {
+          if (!sp_mbar_wait(&rec_bar[rec_ready & 1], (uint32_t)(rec_ready >> 1) & 1u, q.err)) return nullptr;
+          ++rec_ready;
+        }
+        return recs[bt & 1][kk % kSpRecBatch];
+      };
+      rec_issue();
+      rec_issue();
       for (int k = 0; k < nk && ok; ++k) {
         const int s = k % kSpSlots;
         if (k >= kSpSlots && !release(k - kSpSlots)) { ok = false; break; }
-        const int64_t t = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
-        const int32_t* rec = ptile + t * kTileWords;
+        const int* rec = rec_of(k);
+        if (!rec) { ok = false; break; }
         const int p0 = rec[0], nr = rec[1], r0b = rec[2], n0 = rec[3], r1b = rec[4], n1 = rec[5], r2b = rec[6],
-                  n2 = rec[7], ne = rec[10];
-        const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
-        const int64_t ea = e0 & ~(int64_t)1, eb = (e0 + ne + 1) & ~(int64_t)1;
-        const int64_t pa = (int64_t)p0 & ~(int64_t)1, pb = ((int64_t)p0 + nr + 2) & ~(int64_t)1;
-        const SpTileLayout lay = sp_tile_layout(n0 + n1 + n2, nr, eb - ea, pb - pa, ldc, use_b);
-        const bool staged = !tile_bad[t] && lay.bytes <= ring.bytes;
+                  n2 = rec[7], gb = rec[11], ne = rec[14];
+        const int64_t eb = (int64_t)(uint32_t)rec[12] | ((int64_t)rec[13] << 32);
+        const int ng = (nr + kGrpRows - 1) / kGrpRows;
+        int ga, gz;
+        sp_gofs_range(gb, ng, ga, gz);
+        const SpTileLayout lay = sp_tile_layout(n0 + n1 + n2, nr, ne, gz - ga, ldc, use_b);
+        const bool staged = !rec[15] && lay.bytes <= ring.bytes;
         int base = 0;
         ra[s] = rz[s] = 0;
         if (staged) {
@@ -482,154 +530,167 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
           rz[s] = head;
         }
         int* mt = smeta[s];
-        mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0;
-        mt[5] = (int)(e0 - ea); mt[6] = (int)(p0 - pa);
-        mt[7] = base; mt[8] = base + lay.s; mt[9] = base + lay.v; mt[10] = base + lay.h;
-        mt[11] = base + lay.sp; mt[12] = base + lay.rp;
+        mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0; mt[5] = ng;
+        mt[6] = base + lay.go + (gb - ga) * 4;
+        mt[7] = base; mt[8] = base + lay.s; mt[9] = base + lay.v; mt[10] = base + lay.h; mt[11] = base + lay.en;
         if (staged) {
           unsigned char* sb = smraw + base;
           const uint32_t rb = (uint32_t)ldc * 4u;
           const uint32_t bz = (uint32_t)(n0 + n1 + n2) * rb, bo = (uint32_t)nr * rb,
-                         bp = (uint32_t)(eb - ea) * 8u, br = (uint32_t)(pb - pa) * 8u;
-          sp_mbar_expect_tx(&full_bar[s], bz + (use_b ? 3u : 1u) * bo + bp + br);
+                         be = (uint32_t)ne * (uint32_t)(kEntWords * 4),
+                         bg = (uint32_t)(gz - ga) * 4u;
+          sp_mbar_expect_tx(&full_bar[s], bz + (kSpStageOwn ? (use_b ? 3u : 1u) * bo : 0u) + be + bg);
           if (n0 > 0) sp_bulk_load(sb, Z + (int64_t)r0b * ldc, (uint32_t)n0 * rb, &full_bar[s]);
           if (n1 > 0) sp_bulk_load(sb + (size_t)n0 * rb, Z + (int64_t)r1b * ldc, (uint32_t)n1 * rb, &full_bar[s]);
           if (n2 > 0)
             sp_bulk_load(sb + (size_t)(n0 + n1) * rb, Z + (int64_t)r2b * ldc, (uint32_t)n2 * rb, &full_bar[s]);
-          sp_bulk_load(sb + lay.s, S + (int64_t)p0 * ldc, bo, &full_bar[s]);
-          if (use_b) {
+          if (kSpStageOwn) sp_bulk_load(sb + lay.s, S + (int64_t)p0 * ldc, bo, &full_bar[s]);
+          if (kSpStageOwn && use_b) {
             sp_bulk_load(sb + lay.v, V + (int64_t)p0 * ldc, bo, &full_bar[s]);
             sp_bulk_load(sb + lay.h, H + (int64_t)p0 * ldc, bo, &full_bar[s]);
           }
-          sp_bulk_load(sb + lay.sp, pairs + ea, bp, &full_bar[s]);
-          sp_bulk_load(sb + lay.rp, rowptr + pa, br, &full_bar[s]);
+          if (ne > 0) sp_bulk_load(sb + lay.en, gent + kEntVec * eb, be, &full_bar[s]);
+          sp_bulk_load(sb + lay.go, gofs + ga, bg, &full_bar[s]);
         } else {
           sp_mbar_arrive(&full_bar[s]);
         }
         issued = k + 1;
+        // the last record of a batch has been read: its buffer takes the
+        // batch after next
+        if (k % kSpRecBatch == kSpRecBatch - 1) rec_issue();
       }
       if (!ok) sp_flag(q.err);
       // no copy may still be in flight when the block exits: wait (bounded)
-      // for the last fill of every slot
+      // for the last fill of every slot and for the record batches not yet waited for
       for (int s = 0; s < kSpSlots && s < issued; ++s) {
         const int klast = s + ((issued - 1 - s) / kSpSlots) * kSpSlots;
         if (!sp_mbar_wait(&full_bar[s], (uint32_t)(klast / kSpSlots) & 1u, q.err)) sp_flag(q.err);
       }
+      for (; rec_ready < rec_issued; ++rec_ready)
+        if (!sp_mbar_wait(&rec_bar[rec_ready & 1], (uint32_t)(rec_ready >> 1) & 1u, q.err)) sp_flag(q.err);
     }
   } else {
     // ---------------- consumers ----------------
+    // lanes >= c4 own no columns and only take part in the barrier waits
+    const bool lane_on = lane < c4;
+    const float4 b4 = lane_on ? make_float4(bsh[4 * lane], bsh[4 * lane + 1], bsh[4 * lane + 2], bsh[4 * lane + 3])
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    float sub[4] = {0.f, 0.f, 0.f, 0.f};
+    int rows_since = 0;
     auto flush = [&]() {
+      if (lane_on) {
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        double v = (double)sub[kk];
-        for (int sl = 1; sl < R; ++sl) {
-          const double o = __shfl_sync(0xffffffffu, v, (ch + sl * L) & 31);
-          if (slot == 0) v += o;
+        for (int kk = 0; kk < 4; ++kk) {
+          wdot[wib][4 * lane + kk] += (double)sub[kk];
+          sub[kk] = 0.f;
         }
-        const int col = kk < 4 ? 4 * q0 + kk : 4 * q1 + (kk - 4);
-        if (slot == 0 && col < ldc && col < 128) wdot[wib][col] += v;
-        sub[kk] = 0.f;
       }
+      rows_since = 0;
     };
-    int cnt = 0;
+    // V, H of row i from its product acc, S, Z_i (and V, H for beta != 0)
+    auto finish_row = [&](int64_t i, const float4& acc, const float4& sv, const float4& zi, const float4& vv,
+                          const float4& hh) {
+      float4 vo = make_float4(acc.x + sv.x, acc.y + sv.y, acc.z + sv.z, acc.w + sv.w);
+      float4 ho = zi;
+      if (use_b) {
+        vo.x += b4.x * vv.x; vo.y += b4.y * vv.y; vo.z += b4.z * vv.z; vo.w += b4.w * vv.w;
+        ho.x += b4.x * hh.x; ho.y += b4.y * hh.y; ho.z += b4.z * hh.z; ho.w += b4.w * hh.w;
+      }
+      reinterpret_cast<float4*>(V)[i * c4 + lane] = vo;
+      reinterpret_cast<float4*>(H)[i * c4 + lane] = ho;
+      sub[0] += ho.x * vo.x; sub[1] += ho.y * vo.y; sub[2] += ho.z * vo.z; sub[3] += ho.w * vo.w;
+    };
+    int gseq = 0;   // row groups of this block's earlier tiles (the groups are dealt to the warps in turn)
     for (int k = 0; k < nk; ++k) {
       const int s = k % kSpSlots;
-      // warp-uniform outcome (the flush shuffles need every lane)
       if (!__all_sync(0xffffffffu, sp_mbar_wait(&full_bar[s], (uint32_t)(k / kSpSlots) & 1u, q.err))) {
         if (lane == 0) sp_flag(q.err);
         break;
       }
       const int* mt = smeta[s];
-      const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3];
+      const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3], ng = mt[5];
       const bool staged = mt[4] != 0;
+      const int* gos = reinterpret_cast<const int*>(smraw + mt[6]);
       const float4* zs = reinterpret_cast<const float4*>(smraw + mt[7]);
       const float4* ss = reinterpret_cast<const float4*>(smraw + mt[8]);
       const float4* vs = reinterpret_cast<const float4*>(smraw + mt[9]);
       const float4* hs = reinterpret_cast<const float4*>(smraw + mt[10]);
-      const int2* sp = reinterpret_cast<const int2*>(smraw + mt[11]) + mt[5];
-      const int64_t* rp = reinterpret_cast<const int64_t*>(smraw + mt[12]) + mt[6];
-      for (int rbase = wib * R; rbase < nr; rbase += kSpConsumers * R) {
-        const int r = rbase + slot;
-        const bool on = lane_on && r < nr;
-        const int64_t i = (int64_t)p0 + r;
-        const int64_t i0 = i * c4;
-        if (on) {
-          float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, zi0 = a0, zi1 = a0;
-          float4 s0 = a0, s1 = a0, v0 = a0, v1 = a0, h0 = a0, h1 = a0;
+      const int4* en = reinterpret_cast<const int4*>(smraw + mt[11]);
+      int j = (wib - gseq % kSpConsumers + kSpConsumers) % kSpConsumers;
+      gseq += ng;
+      if (lane_on) {
+        for (; j < ng; j += kSpConsumers) {
+          const int r0 = j * kGrpRows;
+          const int gr = min(kGrpRows, nr - r0);
+          float4 acc[kGrpRows];
+#pragma unroll
+          for (int g = 0; g < kGrpRows; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (staged) {
-            const int64_t eb = rp[0];
-            const int tb = (int)(rp[r] - eb), te = (int)(rp[r + 1] - eb);
-            // q1 may run one chunk past the row for odd c4: it reads the next
-            // staged row (in bounds: one spare row is allocated; kept off the output)
-#pragma unroll 4
-            for (int t = tb; t < te; ++t) {
-              const int2 pv = sp[t];
-              const float v = __int_as_float(pv.y);
-              const int zr = pv.x * c4;
-              const float4 z0 = zs[zr + q0];
-              const float4 z1 = zs[zr + q1];
-              a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
-              a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
-              a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
-              a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
+            const int eb = gos[j], ee = gos[j + 1];
+            float4 gs[kGrpRows], gv[kGrpRows], gh[kGrpRows];   // own rows from global memory
+            if (!kSpStageOwn) {
+#pragma unroll
+              for (int g = 0; g < kGrpRows; ++g) {
+                gs[g] = gv[g] = gh[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < gr) {
+                  const int64_t x = ((int64_t)p0 + r0 + g) * c4 + lane;
+                  gs[g] = S4[x];
+                  if (use_b) { gv[g] = V4[x]; gh[g] = H4[x]; }
+                }
+              }
             }
-            const int zr = (n0 + (int)(i - r1b)) * c4;
-            zi0 = zs[zr + q0];
-            s0 = ss[r * c4 + q0];
-            if (use_b) { v0 = vs[r * c4 + q0]; h0 = hs[r * c4 + q0]; }
-            if (has1) {
-              zi1 = zs[zr + q1];
-              s1 = ss[r * c4 + q1];
-              if (use_b) { v1 = vs[r * c4 + q1]; h1 = hs[r * c4 + q1]; }
+#pragma unroll 8
+            for (int e = eb; e < ee; ++e) {
+              const int4 m0 = en[kEntVec * e];
+              const int4 m1 = kEntVec == 2 ? en[kEntVec * e + 1] : make_int4(0, 0, 0, 0);
+              const float4 z = zs[m0.x * c4 + lane];
+              const float w[7] = {__int_as_float(m0.y), __int_as_float(m0.z), __int_as_float(m0.w),
+                                  __int_as_float(m1.x), __int_as_float(m1.y), __int_as_float(m1.z),
+                                  __int_as_float(m1.w)};
+#pragma unroll
+              for (int g = 0; g < kGrpRows; ++g) {
+                acc[g].x = fmaf(w[g], z.x, acc[g].x); acc[g].y = fmaf(w[g], z.y, acc[g].y);
+                acc[g].z = fmaf(w[g], z.z, acc[g].z); acc[g].w = fmaf(w[g], z.w, acc[g].w);
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < kGrpRows; ++g) {
+              if (g < gr) {
+                const int r = r0 + g;
+                const int64_t i = (int64_t)p0 + r;
+                const float4 zi = zs[(n0 + (int)(i - r1b)) * c4 + lane];
+                float4 sv, vv = make_float4(0.f, 0.f, 0.f, 0.f), hh = vv;
+                if (kSpStageOwn) {
+                  sv = ss[r * c4 + lane];
+                  if (use_b) { vv = vs[r * c4 + lane]; hh = hs[r * c4 + lane]; }
+                } else {
+                  sv = gs[g]; vv = gv[g]; hh = gh[g];
+                }
+                finish_row(i, acc[g], sv, zi, vv, hh);
+              }
             }
           } else {
-            zi0 = Z4[i0 + q0];
-            s0 = S4[i0 + q0];
-            if (use_b) { v0 = V4[i0 + q0]; h0 = H4[i0 + q0]; }
-            if (has1) {
-              zi1 = Z4[i0 + q1];
-              s1 = S4[i0 + q1];
-              if (use_b) { v1 = V4[i0 + q1]; h1 = H4[i0 + q1]; }
-            }
-            const int64_t rb = rowptr[i], re = rowptr[i + 1];
-            for (int64_t t = rb; t < re; ++t) {
-              const int64_t j = colidx[t];
-              const float v = vals[t];
-              const float4 z0 = Z4[j * c4 + q0];
-              const float4 z1 = has1 ? Z4[j * c4 + q1] : make_float4(0.f, 0.f, 0.f, 0.f);
-              a0.x = fmaf(v, z0.x, a0.x); a0.y = fmaf(v, z0.y, a0.y);
-              a0.z = fmaf(v, z0.z, a0.z); a0.w = fmaf(v, z0.w, a0.w);
-              a1.x = fmaf(v, z1.x, a1.x); a1.y = fmaf(v, z1.y, a1.y);
-              a1.z = fmaf(v, z1.z, a1.z); a1.w = fmaf(v, z1.w, a1.w);
-            }
-          }
-          float4 vo0 = make_float4(a0.x + s0.x, a0.y + s0.y, a0.z + s0.z, a0.w + s0.w);
-          float4 vo1 = make_float4(a1.x + s1.x, a1.y + s1.y, a1.z + s1.z, a1.w + s1.w);
-          float4 ho0 = zi0, ho1 = zi1;
-          if (use_b) {
-            const float* b = bsh + 4 * q0;
-            vo0.x += b[0] * v0.x; vo0.y += b[1] * v0.y; vo0.z += b[2] * v0.z; vo0.w += b[3] * v0.w;
-            ho0.x += b[0] * h0.x; ho0.y += b[1] * h0.y; ho0.z += b[2] * h0.z; ho0.w += b[3] * h0.w;
-            if (has1) {
-              const float* b1 = bsh + 4 * q1;
-              vo1.x += b1[0] * v1.x; vo1.y += b1[1] * v1.y; vo1.z += b1[2] * v1.z; vo1.w += b1[3] * v1.w;
-              ho1.x += b1[0] * h1.x; ho1.y += b1[1] * h1.y; ho1.z += b1[2] * h1.z; ho1.w += b1[3] * h1.w;
+            // rows gathered from global memory in CSR order
+#pragma unroll
+            for (int g = 0; g < kGrpRows; ++g) {
+              if (g < gr) {
+                const int64_t i = (int64_t)p0 + r0 + g;
+                const int64_t rb = rowptr[i], re = rowptr[i + 1];
+                for (int64_t t = rb; t < re; ++t) {
+                  const float v = vals[t];
+                  const float4 z = Z4[(int64_t)colidx[t] * c4 + lane];
+                  acc[g].x = fmaf(v, z.x, acc[g].x); acc[g].y = fmaf(v, z.y, acc[g].y);
+                  acc[g].z = fmaf(v, z.z, acc[g].z); acc[g].w = fmaf(v, z.w, acc[g].w);
+                }
+                const float4 zi = Z4[i * c4 + lane], sv = S4[i * c4 + lane];
+                float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), hh = vv;
+                if (use_b) { vv = V4[i * c4 + lane]; hh = H4[i * c4 + lane]; }
+                finish_row(i, acc[g], sv, zi, vv, hh);
+              }
             }
           }
-          float4* Vw = reinterpret_cast<float4*>(V);
-          float4* Hw = reinterpret_cast<float4*>(H);
-          Vw[i0 + q0] = vo0;
-          Hw[i0 + q0] = ho0;
-          sub[0] += ho0.x * vo0.x; sub[1] += ho0.y * vo0.y; sub[2] += ho0.z * vo0.z; sub[3] += ho0.w * vo0.w;
-          if (has1) {
-            Vw[i0 + q1] = vo1;
-            Hw[i0 + q1] = ho1;
-            sub[4] += ho1.x * vo1.x; sub[5] += ho1.y * vo1.y; sub[6] += ho1.z * vo1.z; sub[7] += ho1.w * vo1.w;
-          }
-        }
-        if (++cnt == 32) {
-          flush();
-          cnt = 0;
+          rows_since += gr;
+          if (rows_since >= 28) flush();
         }
       }
       __syncwarp();
@@ -655,19 +716,32 @@ struct StagedLaunch {
   size_t smem = 0;
 };
 constexpr size_t kSpSmemMax = 204 * 1024;
+// the ring's dynamic shared memory for this translation unit's copy of the
+// kernel (every launcher below is static, so it launches the copy whose
+// attribute it set); false if the device refuses it (the error is cleared)
+static inline bool sp_ring_enabled() {
+  static const bool ok = [] {
+    const bool r = cudaFuncSetAttribute(kv_spmm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSpSmemMax) == cudaSuccess;
+    if (!r) cudaGetLastError();
+    return r;
+  }();
+  return ok;
+}
 static inline StagedLaunch staged_launch(const Handle& Hd, int ldc) {
-  static const bool attr =
-      cudaFuncSetAttribute(kv_spmm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmemMax) ==
-      cudaSuccess;
-  (void)attr;
+  (void)ldc;
   StagedLaunch L;
   L.ring.bytes = (int)kSpSmemMax;
   L.smem = kSpSmemMax;
+  if (!sp_ring_enabled()) return L;   // blocks = 0: the row kernel runs
   int dev = 0, sms = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_tma, kSpThreads, L.smem);
-  L.blocks = per > 0 ? std::min(Hd.ntiles, sms * per) : 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kv_spmm_tma, kSpThreads, L.smem) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  L.blocks = per > 0 ? std::min(Hd.sp_ntiles, sms * per) : 0;
   return L;
 }
 
@@ -845,7 +919,7 @@ CGScalars make_scalars(Handle& H, const fsa_opts& o, int L);
 inline bool should_poll(int /*it*/) { return true; }
 
 template <typename T, typename VT>
-inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t* rowptr, const int32_t* col,
+static inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t* rowptr, const int32_t* col,
                               const VT* vals, const T* Z, const T* S, T* V, T* H, const double* beta,
                               double* part, int step, const CGScalars& q) {
   if constexpr (std::is_same<T, float>::value && std::is_same<VT, float>::value) {
@@ -869,14 +943,15 @@ inline void launch_spmm_fused(const CGLayout& lay, cudaStream_t s, const int64_t
 
 // FP32 SpMM of the CG loop: the staged tile kernel when the handle has tiles,
 // the row kernel otherwise
-inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedLaunch& L, cudaStream_t s,
+static inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedLaunch& L, cudaStream_t s,
                             const float* vals, const float* Z, const float* S, float* V, float* Hv,
                             const double* beta, double* part, int step, const CGScalars& q) {
-  if (Hd.ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0 && vals == Hd.op.vals32.p &&
-      Hd.op.pairs32.p) {
+  if (Hd.sp_ntiles > 0 && lay.ldc % 4 == 0 && lay.ldc <= 128 && L.blocks > 0 && vals == Hd.op.vals32.p &&
+      Hd.op.grp_ent.p && sp_ring_enabled()) {
     // timed under the profiling hooks (tag pcg_spmm); algorithmic bytes: the
-    // pattern (staged column + value per nonzero, row pointers), Z and S read
-    // once, V and H read and written once
+    // CSR pattern (column + value per nonzero, row pointers), Z and S read
+    // once, V and H read and written once (the union entries the kernel reads
+    // instead of the pattern are not counted)
     const bool prof = profile_on() && step != kStepNone;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) {
@@ -885,8 +960,8 @@ inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const StagedL
       FSA_CUDA(cudaEventRecord(e0, s));
     }
     kv_spmm_tma<<<std::min(L.blocks, lay.nblk), kSpThreads, L.smem, s>>>(
-        Hd.ntiles, Hd.ptile.p, Hd.tile_bad.p, L.ring, lay.c, lay.ldc, Hd.rowptr.p, Hd.col.p, Hd.op.pairs32.p, vals,
-        Z, S, V, Hv, beta, part, step, q);
+        Hd.sp_ntiles, Hd.sp_ptile.p, L.ring, lay.c, lay.ldc, Hd.rowptr.p, Hd.col.p, Hd.op.grp_ent.p, Hd.gofs.p, vals, Z,
+        S, V, Hv, beta, part, step, q);
     FSA_CHECK_LAUNCH();
     if (prof) {
       FSA_CUDA(cudaEventRecord(e1, s));

@@ -187,10 +187,13 @@ def _spmm_selftest(h, th, ncols, seed=1):
     return d.value, st.value, tot.value
 
 
-@pytest.mark.parametrize("n,gamma,ncols", [(20011, 0.015, 65), (50021, 0.0071, 17), (3001, 0.05, 127)])
+@pytest.mark.parametrize("n,gamma,ncols", [(20011, 0.015, 65), (50021, 0.0071, 17), (3001, 0.05, 127),
+                                           (200003, fi.taper_range_for(20, 200003), 65), (4001, 0.05, 1)])
 def test_spmm_tile_kernel_equals_row_kernel(F, n, gamma, ncols):
-    """The shared-memory tile SpMM gives the row kernel's result bit for bit
-    (same per-row summation order), for block widths from 17 to 127 columns."""
+    """The shared-memory tile SpMM (row groups over the union of their
+    neighbour lists) gives the row kernel's result bit for bit (same per-row
+    summation order), for block widths from 1 to 127 columns, at the headline's
+    density (20 nonzeros per row) among them."""
     locs = fi.uniform_locations(n, 84)
     ind = locs[fi.inducing_subset(n, 60, 84)]
     with F.FSAHandle(locs, ind, gamma, 0.5) as h:
