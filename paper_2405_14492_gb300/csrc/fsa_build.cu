@@ -607,7 +607,7 @@ static void build_spmm_groups(Handle& H, const std::vector<int64_t>& t, const st
 // (kSpTileRows, its own tiling: its staged rows are Z rows of at most 512
 // bytes, the SDDMM's are BF16 pairs of A~ blocks).
 void build_tiles(Handle& H) {
-  constexpr int64_t kTileRows = 24, kSpTileRows = 48;
+  constexpr int64_t kTileRows = 24, kSpTileRows = 40;
   const int ncx = H.grid.ncx, ncy = H.grid.ncy;
   const int64_t ncells = (int64_t)ncx * ncy;
   std::vector<int32_t> start(ncells), count(ncells);

@@ -417,7 +417,6 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   __shared__ int smeta[kSpSlots][kSpMeta];
   __shared__ __align__(16) float bsh[128];   // beta per column (0 beyond c)
   __shared__ int any_b;
-  __shared__ double wdot[kSpConsumers][128];   // per consumer warp: running h^T v partials per column
   __shared__ __align__(16) int recs[2][kSpRecBatch][kTileWords];   // tile records, two batches
   __shared__ __align__(8) uint64_t rec_bar[2];
   const int tid = threadIdx.x;
@@ -427,7 +426,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
   const float4* S4 = reinterpret_cast<const float4*>(S);
   const float4* V4 = reinterpret_cast<const float4*>(V);
   const float4* H4 = reinterpret_cast<const float4*>(H);
-  for (int x = tid; x < kSpConsumers * 128; x += kSpThreads) (&wdot[0][0])[x] = 0.0;
+  double dacc[4] = {0.0, 0.0, 0.0, 0.0};
   if (tid == 0) {
     any_b = 0;
     for (int s = 0; s < kSpSlots; ++s) {
@@ -571,6 +570,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     }
   } else {
     // ---------------- consumers ----------------
+    // (dacc: this lane's running h^T v partials of its 4 columns)
     // lanes >= c4 own no columns and only take part in the barrier waits
     const bool lane_on = lane < c4;
     const float4 b4 = lane_on ? make_float4(bsh[4 * lane], bsh[4 * lane + 1], bsh[4 * lane + 2], bsh[4 * lane + 3])
@@ -578,12 +578,10 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     float sub[4] = {0.f, 0.f, 0.f, 0.f};
     int rows_since = 0;
     auto flush = [&]() {
-      if (lane_on) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          wdot[wib][4 * lane + kk] += (double)sub[kk];
-          sub[kk] = 0.f;
-        }
+      for (int kk = 0; kk < 4; ++kk) {
+        dacc[kk] += (double)sub[kk];
+        sub[kk] = 0.f;
       }
       rows_since = 0;
     };
@@ -698,13 +696,22 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
     }
     flush();
   }
+  // every copy into the ring has landed (the producer waited for them): the
+  // ring holds the consumer warps' column partials now
+  __syncthreads();
+  double* wdot = reinterpret_cast<double*>(smraw);   // [kSpConsumers][128]
+  if (wib < kSpConsumers && lane < c4) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) wdot[wib * 128 + 4 * lane + kk] = dacc[kk];
+  }
   __syncthreads();
   for (int col = tid; col < ldc; col += kSpThreads) {
     double t = 0.0;
-    for (int w = 0; w < kSpConsumers; ++w) t += wdot[w][col];
+    for (int w = 0; w < kSpConsumers; ++w) t += wdot[w * 128 + col];
     part[(int64_t)blockIdx.x * ldc + col] = t;
   }
-  finish_scalars(step, part, ldc, c, 0, q, &wdot[0][0]);
+  __syncthreads();
+  finish_scalars(step, part, ldc, c, 0, q, wdot);
 }
 
 // launch shape of kv_spmm_tma: the byte ring takes the shared-memory budget;
@@ -715,7 +722,7 @@ struct StagedLaunch {
   SpRing ring{};
   size_t smem = 0;
 };
-constexpr size_t kSpSmemMax = 204 * 1024;
+constexpr size_t kSpSmemMax = 219 * 1024;
 // the ring's dynamic shared memory for this translation unit's copy of the
 // kernel (every launcher below is static, so it launches the copy whose
 // attribute it set); false if the device refuses it (the error is cleared)
