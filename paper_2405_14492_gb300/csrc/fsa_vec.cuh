@@ -822,7 +822,11 @@ static __global__ void kv4_ur_update(int64_t n, int c, int ldc, int rpb, float* 
 // Z = (R - S) Dinv ; part = r^T z.  A thread takes two rows per step and
 // issues all their loads before the arithmetic: the kernel streams two arrays
 // in and one out, and one row in flight per thread left the DRAM half idle.
-static __global__ void kv4_z_update(int64_t n, int c, int ldc, int rpb, const float* __restrict__ R,
+// at most 51 registers: five blocks of up to 256 threads per SM (the loop is
+// latency-bound; more resident warps keep more rows' loads in flight; at six
+// blocks the registers spill and it is slower)
+static __global__ void __launch_bounds__(256, 5) kv4_z_update(int64_t n, int c, int ldc, int rpb,
+                                                            const float* __restrict__ R,
                                     const float* __restrict__ S, const float* __restrict__ Dinv,
                                     float* __restrict__ Z, double* __restrict__ part, int step, int l, CGScalars q) {
   extern __shared__ double red4[];
