@@ -531,6 +531,7 @@ TmaMap make_tma_bf16_blocked(const __nv_bfloat16* ptr, int64_t rows, int64_t kpa
   FSA_REQUIRE(box_rows >= 8 && box_rows <= 256, FSA_ERR_ARG, "TMA box rows out of range");
   TmaMap t;
   t.blocked = 1;
+  t.box_rows = box_rows;
   cuuint64_t gdim[3] = {64, (cuuint64_t)rows, (cuuint64_t)(kpad / 64)};
   cuuint64_t gstride[2] = {128, (cuuint64_t)rows * 128};
   cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
@@ -547,6 +548,7 @@ TmaMap make_tma_bf16(const __nv_bfloat16* ptr, int64_t rows, int64_t cols, int64
   FSA_REQUIRE((ld * 2) % 16 == 0, FSA_ERR_ARG, "TMA row stride not a multiple of 16 bytes");
   FSA_REQUIRE(box_rows >= 8 && box_rows <= 256, FSA_ERR_ARG, "TMA box rows out of range");
   TmaMap t;
+  t.box_rows = box_rows;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
   cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
@@ -580,11 +582,16 @@ int tc_gemm(const TcGemm& g, unsigned* err, cudaStream_t s) {
   FSA_REQUIRE(g.M > 0 && g.N > 0 && g.K > 0, FSA_ERR_ARG, "tc_gemm empty problem");
   tc::Params p;
   std::memset(&p, 0, sizeof(p));
+  // a box fills exactly one operand slot of a stage: BM rows of A, bn rows of
+  // B (a larger box would write past its slot and deliver more bytes than the
+  // stage's barrier expects)
   for (int a = 0; a < g.num_a; ++a) {
+    FSA_REQUIRE(g.a[a]->box_rows == tc::BM, FSA_ERR_ARG, "tc_gemm: A box rows must equal the M tile");
     p.ma[a] = g.a[a]->map;
     if (g.a[a]->blocked) p.blk |= 1u << a;
   }
   for (int b = 0; b < g.num_b; ++b) {
+    FSA_REQUIRE(g.b[b]->box_rows == bn, FSA_ERR_ARG, "tc_gemm: B box rows must equal the N tile");
     p.mb[b] = g.b[b]->map;
     if (g.b[b]->blocked) p.blk |= 4u << b;
   }

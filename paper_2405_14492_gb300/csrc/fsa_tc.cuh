@@ -18,7 +18,8 @@ namespace fsa {
 
 struct TmaMap {
   CUtensorMap map;
-  int blocked = 0;   // 1: the blocked K-major layout below (3-D map)
+  int blocked = 0;     // 1: the blocked K-major layout below (3-D map)
+  int box_rows = 0;    // rows of one box (one TMA copy fills exactly this many rows)
 };
 
 // 2-D K-major BF16 tensor map: rows x cols (cols contiguous, leading dimension

@@ -111,13 +111,14 @@ void tc_dgemm(Handle& H, bool ta, bool tb, int M, int N, int K, const TA* A, int
   DevPtr<__nv_bfloat16> Ah(na), Al(na), Bh(nb), Bl(nb);
   split_operand<TA>(M, K, kpad, A, lda, ta, Ah.p, Al.p, s);
   split_operand<TB>(N, K, kpad, B, ldb, !tb, Bh.p, Bl.p, s);
+  const int bn = std::min(128, (N + 15) / 16 * 16);   // the N tile; B's box has exactly its rows
   TmaMap mAh = make_tma_bf16_blocked(Ah.p, M, kpad, 128), mAl = make_tma_bf16_blocked(Al.p, M, kpad, 128);
-  TmaMap mBh = make_tma_bf16_blocked(Bh.p, N, kpad, 128), mBl = make_tma_bf16_blocked(Bl.p, N, kpad, 128);
+  TmaMap mBh = make_tma_bf16_blocked(Bh.p, N, kpad, bn), mBl = make_tma_bf16_blocked(Bl.p, N, kpad, bn);
   TcGemm g;
   g.a[0] = &mAh; g.a[1] = &mAl; g.num_a = 2;
   g.b[0] = &mBh; g.b[1] = &mBl; g.num_b = 2;
   g.pairs = 1u | 2u | 4u;   // hi.hi + hi.lo + lo.hi
-  g.M = M; g.N = N; g.bn = std::min(128, (N + 15) / 16 * 16);
+  g.M = M; g.N = N; g.bn = bn;
   g.tag = tag;
   const int kb = (int)(kpad / 64);
   if (C32 && kb <= kTcdSpanBlocks) {

@@ -116,8 +116,8 @@ def test_predict_control_variate_reduces_error_to_exact(F):
     assert np.sqrt(np.mean((var_co - var_exact) ** 2)) < 0.8 * np.sqrt(np.mean((var_pl - var_exact) ** 2))
 
 
-@pytest.mark.parametrize("x2", [True, False])
-def test_mixed_predict_parity_same_probes(F, x2):
+@pytest.mark.parametrize("m,x2", [(200, True), (200, False), (100, True)])
+def test_mixed_predict_parity_same_probes(F, m, x2):
     """The mixed form of Algorithm 1 (its m-column products on the tensor
     cores with BF16 pairs, the sparse solves in FP32, the cores in FP64)
     against the FP64 oracle with the same probes.
@@ -129,8 +129,9 @@ def test_mixed_predict_parity_same_probes(F, x2):
     its norm; the solve amplifies that by up to the conditioning of Sigma_dag,
     lambda_max / nugget, about 1e3 here.  It is held to 2e-3 of max |mean|
     (4e-4 measured).  The single-BF16 operator (A~ rounded to 8 bits, 2^-9)
-    is held to ten times both bounds."""
-    n, m, n_p, s, gamma = 20011, 200, 3001, 24, fi.taper_range_for(25, 20011)
+    is held to ten times both bounds.  m = 100 gives the tensor-core products
+    an N tile of 112 rows (N < 128), m = 200 a ragged second N tile."""
+    n, n_p, s, gamma = 20011, 3001, 24, fi.taper_range_for(25, 20011)
     locs, ind, pred = _case(n, m, n_p, 94, gamma)
     th = (1.0, 0.05, 0.05)
     y = fi.random_field(locs, 0.5, *th, 94)
