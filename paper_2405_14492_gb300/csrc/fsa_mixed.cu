@@ -379,6 +379,112 @@ __global__ void __launch_bounds__(256) k_split_transpose(int64_t n, int c, int l
   }
 }
 
+// One CG step's U += a H, R -= a V and ||R||^2 (as kv4_ur_update, with the
+// kStepResid scalar step) fused with the split of D^-1 R into the blocked
+// K-major BF16 pieces of the next A~^T X (as k_split_transpose, bit for bit):
+// the block keeps its tile of updated R rows in shared memory for the
+// transpose, so R is read once per iteration instead of twice.  Persistent:
+// the blocks take the kSTRows-point tiles in turn.  rpb x c4 threads (c4 =
+// ldc / 4); a thread keeps one float4 column chunk and takes the tile rows
+// tid / c4 + k rpb, two at a time with both rows' loads issued first.
+__global__ void __launch_bounds__(256, 4) k_ur_split(int64_t n, int c, int ldc, int rpb, int nsplit, int64_t n_pad,
+                                                  float* __restrict__ U, float* __restrict__ R,
+                                                  const float* __restrict__ Hm, const float* __restrict__ V,
+                                                  const float* __restrict__ rowscale,
+                                                  const double* __restrict__ alpha, const int32_t* __restrict__ active,
+                                                  __nv_bfloat16* __restrict__ dst, double* __restrict__ part,
+                                                  int step, int l, CGScalars q) {
+  extern __shared__ __align__(16) unsigned char ursm[];
+  float* tf = reinterpret_cast<float*>(ursm);   // [kSTRows][ldc + 1] then rowscale[kSTRows]
+  const int ls = ldc + 1;
+  float* rs = tf + kSTRows * ls;
+  const int c4 = ldc >> 2;
+  const int cq = threadIdx.x % c4, col0 = 4 * cq, rr0 = threadIdx.x / c4;
+  float a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = (col0 + k < c && active[col0 + k]) ? (float)alpha[col0 + k] : 0.f;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float sub[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // updated row -> U, R in global memory, R into the tile, its squares into sub
+  auto urow = [&](float4 r, const float4 h, const float4 v, float4 u, const int64_t idx, float* trow) {
+    u.x = fmaf(a[0], h.x, u.x); u.y = fmaf(a[1], h.y, u.y); u.z = fmaf(a[2], h.z, u.z); u.w = fmaf(a[3], h.w, u.w);
+    r.x = fmaf(-a[0], v.x, r.x); r.y = fmaf(-a[1], v.y, r.y); r.z = fmaf(-a[2], v.z, r.z); r.w = fmaf(-a[3], v.w, r.w);
+    *reinterpret_cast<float4*>(U + idx) = u;
+    *reinterpret_cast<float4*>(R + idx) = r;
+    sub[0] += r.x * r.x; sub[1] += r.y * r.y; sub[2] += r.z * r.z; sub[3] += r.w * r.w;
+    trow[0] = r.x; trow[1] = r.y; trow[2] = r.z; trow[3] = r.w;
+  };
+  auto zrow = [&](float* trow) { trow[0] = 0.f; trow[1] = 0.f; trow[2] = 0.f; trow[3] = 0.f; };
+  const int64_t ntiles = (n_pad + kSTRows - 1) / kSTRows;
+  const int64_t ns = (int64_t)nsplit * ldc;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kSTRows;
+    for (int rr = rr0; rr < kSTRows; rr += 2 * rpb) {
+      const int rb = rr + rpb;
+      const int64_t ra_i = r0 + rr, rb_i = r0 + rb;
+      const bool va = ra_i < n, vb = rb < kSTRows && rb_i < n;
+      const int64_t ia = ra_i * ldc + col0, ib = rb_i * ldc + col0;
+      float4 ra = zero4, ha = zero4, vva = zero4, ua = zero4, rbv = zero4, hb = zero4, vvb = zero4, ub = zero4;
+      if (va) {
+        ra = *reinterpret_cast<const float4*>(R + ia);
+        ha = *reinterpret_cast<const float4*>(Hm + ia);
+        vva = *reinterpret_cast<const float4*>(V + ia);
+        ua = *reinterpret_cast<const float4*>(U + ia);
+      }
+      if (vb) {
+        rbv = *reinterpret_cast<const float4*>(R + ib);
+        hb = *reinterpret_cast<const float4*>(Hm + ib);
+        vvb = *reinterpret_cast<const float4*>(V + ib);
+        ub = *reinterpret_cast<const float4*>(U + ib);
+      }
+      if (va) urow(ra, ha, vva, ua, ia, tf + rr * ls + col0);
+      else zrow(tf + rr * ls + col0);
+      if (vb) urow(rbv, hb, vvb, ub, ib, tf + rb * ls + col0);
+      else if (rb < kSTRows) zrow(tf + rb * ls + col0);
+      if (++cnt == 16) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { acc[k] += (double)sub[k]; sub[k] = 0.f; }
+        cnt = 0;
+      }
+    }
+    for (int k = threadIdx.x; k < kSTRows; k += blockDim.x) {
+      const int64_t r = r0 + k;
+      rs[k] = (r < n) ? (rowscale ? rowscale[r] : 1.f) : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ldc * (kSTRows / 8); k += blockDim.x) {
+      const int g = k & 7, cc = k >> 3;
+      if (r0 + 8 * g >= n_pad) continue;
+      uint32_t w[3][4];   // 8 BF16 per piece, packed in pairs
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        __nv_bfloat16 e[3], o[3];
+        const float ve = cc < c ? tf[(8 * g + j) * ls + cc] * rs[8 * g + j] : 0.f;
+        const float vo = cc < c ? tf[(8 * g + j + 1) * ls + cc] * rs[8 * g + j + 1] : 0.f;
+        split_n(ve, nsplit, e);
+        split_n(vo, nsplit, o);
+        if (nsplit != 3) { e[2] = e[1]; o[2] = o[1]; }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          w[p][j / 2] = (uint32_t)__bfloat16_as_ushort(e[p]) | ((uint32_t)__bfloat16_as_ushort(o[p]) << 16);
+      }
+      const int64_t base = (t * ns + cc) * 64 + 8 * g;
+      *reinterpret_cast<uint4*>(dst + base) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+      *reinterpret_cast<uint4*>(dst + base + (int64_t)ldc * 64) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+      if (nsplit == 3)
+        *reinterpret_cast<uint4*>(dst + base + (int64_t)2 * ldc * 64) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+    }
+    __syncthreads();   // the tile buffer is rewritten by the next tile
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] += (double)sub[k];
+  double* red4 = reinterpret_cast<double*>(ursm);   // the tile buffer is free now
+  vec4_block_partials(acc, ldc, c4, rpb, red4, part);
+  finish_scalars(step, part, ldc, c, l, q, red4);
+}
+
 // q (m x ldc FP64) -> (nsplit ldc x m_pad) BF16 pieces, K-major (q transposed)
 __global__ void k_split_q(int m, int c, int ldc, int nsplit, int m_pad, const double* __restrict__ q,
                           __nv_bfloat16* __restrict__ dst) {
@@ -688,6 +794,8 @@ static void set_operator_maps(const Operator& op, int64_t n, MixedCtx& C) {
   }
 }
 
+static void mixed_AtX_pieces(Handle& H, MixedCtx& C, double* w, const char* tag);
+
 // w (FP64, m x ldc) = A~^T X  where X = rows of `src` (scaled by rowscale), split hi/lo
 void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, double* w,
                       const char* tag) {
@@ -702,6 +810,13 @@ void mixed_AtX(Handle& H, MixedCtx& C, const float* src, const float* rowscale, 
                                                                                       src, rowscale, C.n_pad, g.Xb.p);
     FSA_CHECK_LAUNCH();
   }
+  mixed_AtX_pieces(H, C, w, tag);
+}
+
+// w (FP64, m x ldc) = A~^T X with X already split into the blocked pieces (H.cg.Xb)
+static void mixed_AtX_pieces(Handle& H, MixedCtx& C, double* w, const char* tag) {
+  cudaStream_t s = H.stream;
+  const int ldc = C.ldc;
   TcGemm t;
   t.a[0] = &C.mAt; t.a[1] = &C.mAt_lo; t.num_a = C.lo ? 2 : 1;
   t.b[0] = &C.mX; t.num_b = 1;
@@ -743,17 +858,47 @@ void mixed_Aq(Handle& H, MixedCtx& C, const double* q, float* S, const char* tag
   tc_gemm(t, H.err, s);
 }
 
-// S = A~ M^-1 A~^T (D^-1 R)
-static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
+// S = A~ M^-1 w  (w = A~^T (D^-1 R) in H.cg.w)
+static void lowrank_mixed_tail(Handle& H, MixedCtx& C, float* S) {
   CGState& g = H.cg;
   Operator& op = H.op;
-  mixed_AtX(H, C, R, op.Dinv32.p, g.w.p, "pcg_AtX");
   {
     // FP64 q = M^-1 w: m x m core read once, w read, q written
     ProfScope ps("pcg_q", 8.0 * ((double)H.m * H.m + 2.0 * H.m * C.c), H.stream);
     dgemm_tall(H.ws, H.stream, H.m, C.ldc, H.m, op.Minv.p, H.m, g.w.p, C.ldc, g.q.p, C.ldc);
   }
   mixed_Aq(H, C, g.q.p, S, "pcg_Aq");
+}
+
+// S = A~ M^-1 A~^T (D^-1 R)
+static void lowrank_mixed(Handle& H, MixedCtx& C, const float* R, float* S) {
+  mixed_AtX(H, C, R, H.op.Dinv32.p, H.cg.w.p, "pcg_AtX");
+  lowrank_mixed_tail(H, C, S);
+}
+
+// launch shape of k_ur_split: one full wave (SM count x resident blocks, at
+// most the layout's partial rows and the tile count)
+struct URSplitLaunch {
+  int blocks = 1, threads = 32, rpb = 1;
+  size_t smem = 0;
+};
+static URSplitLaunch ur_split_launch(const CGLayout& lay, int64_t n_pad) {
+  URSplitLaunch u;
+  const int ldc = lay.ldc, c4 = ldc / 4;
+  u.rpb = std::max(1, 256 / c4);
+  u.threads = u.rpb * c4;
+  u.smem = std::max((size_t)(kSTRows * (ldc + 1) + kSTRows) * sizeof(float), (size_t)u.threads * 4 * sizeof(double));
+  int dev = 0, sms = 152, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ur_split, u.threads, u.smem) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  const int64_t ntiles = std::max<int64_t>((n_pad + kSTRows - 1) / kSTRows, 1);
+  int64_t b = std::min<int64_t>(ntiles, (int64_t)sms * std::max(per, 1));
+  u.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(b, lay.nblk));
+  return u;
 }
 
 // Block PCG of Appendix A on the right-hand sides in H.cg.R32 (n x ldc FP32,
@@ -769,7 +914,8 @@ void pcg_mixed_run(Handle& H, MixedCtx& C, const CGLayout& lay, const fsa_opts& 
   const int64_t n = H.n;
   const int ldc = lay.ldc;
   const size_t nc = (size_t)n * ldc;
-  const Vec4Launch v4 = vec4_launch(lay, reinterpret_cast<const void*>(kv4_ur_update));
+  FSA_REQUIRE(ldc % 4 == 0 && ldc == C.ldc, FSA_ERR_ARG, "block layout and tensor-core context disagree");
+  const URSplitLaunch us = ur_split_launch(lay, C.n_pad);
   const Vec4Launch v4z = vec4_launch(lay, reinterpret_cast<const void*>(kv4_z_update));
   FSA_CUDA(cudaMemsetAsync(g.U32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
@@ -786,13 +932,15 @@ void pcg_mixed_run(Handle& H, MixedCtx& C, const CGLayout& lay, const fsa_opts& 
   const double blk_bytes = (double)n * lay.c * sizeof(float);   // algorithmic: the c columns, not the padding
   for (int it = 0; it < L; ++it) {
     {
-      ProfScope ps("pcg_ur", 6.0 * blk_bytes, s);   // U, R read and written; H, V read
-      kv4_ur_update<<<v4.blocks, v4.threads, v4.smem, s>>>(n, lay.c, ldc, v4.rpb, g.U32.p, g.R32.p, g.H32.p,
-                                                           g.V32.p, g.alpha.p, g.active.p, g.part.p, kStepResid, it,
-                                                           q);
+      // U, R read and written; H, V read; the nsplit BF16 pieces of D^-1 R written; D^-1
+      ProfScope ps("pcg_ur", (6.0 + 0.5 * C.nsplit) * blk_bytes + 4.0 * n, s);
+      k_ur_split<<<us.blocks, us.threads, us.smem, s>>>(n, lay.c, ldc, us.rpb, C.nsplit, C.n_pad, g.U32.p, g.R32.p,
+                                                        g.H32.p, g.V32.p, op.Dinv32.p, g.alpha.p, g.active.p, g.Xb.p,
+                                                        g.part.p, kStepResid, it, q);
       FSA_CHECK_LAUNCH();
     }
-    lowrank_mixed(H, C, g.R32.p, g.S32.p);
+    mixed_AtX_pieces(H, C, g.w.p, "pcg_AtX");
+    lowrank_mixed_tail(H, C, g.S32.p);
     {
       ProfScope ps("pcg_z", 3.0 * blk_bytes + 4.0 * n, s);   // R, S read, Z written; D^-1
       kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
