@@ -20,13 +20,20 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, const double
                                                     const double* __restrict__ B, int64_t ldb,
                                                     const double* __restrict__ scale, double* __restrict__ C,
                                                     int64_t ldc, double alpha, double beta, int kchunk,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ partial, int tri) {
   __shared__ double As[GBK][GBM + 1];
   __shared__ double Bs[GBK][GBN + 1];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int i0 = blockIdx.x * GBM, j0 = blockIdx.y * GBN;
   int kbeg = blockIdx.z * kchunk;
   int kend = min(K, kbeg + kchunk);
+  // the K range where neither operand tile is known to be zero (an empty range
+  // leaves acc = 0, which the epilogue writes as usual)
+  if (tri & kTriA_KgeI) kbeg = max(kbeg, i0);
+  if (tri & kTriA_KleI) kend = min(kend, i0 + GBM);
+  if (tri & kTriB_KgeJ) kbeg = max(kbeg, j0);
+  if (tri & kTriB_KleJ) kend = min(kend, j0 + GBN);
+  if ((tri & kTriSymLower) && j0 >= i0 + GBM) kend = kbeg;   // above the diagonal: mirrored afterwards
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -97,10 +104,21 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const double* __r
   }
 }
 
+// C[i][j] = C[j][i] for j > i (the strictly upper part from the lower)
+__global__ void k_mirror_lower(double* __restrict__ C, int64_t ldc, int M) {
+  const int64_t total = (int64_t)M * M;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M), j = (int)(t % M);
+    if (j > i) C[(int64_t)i * ldc + j] = C[(int64_t)j * ldc + i];
+  }
+}
+
 void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
-           int64_t ldc, const double* scale) {
+           int64_t ldc, const double* scale, int tri) {
   if (M <= 0 || N <= 0) return;
+  FSA_REQUIRE(!(tri & kTriSymLower) || M == N, FSA_ERR_ARG, "symmetric dgemm result must be square");
   if (K <= 0) {
     // C = beta * C
     dgemm(ws, s, false, false, M, N, 1, 0.0, C, ldc, C, ldc, beta, C, ldc, nullptr);
@@ -123,7 +141,7 @@ void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
   if (splits > 1) part = ws.scratch_f64((size_t)splits * M * N);
 #define LAUNCH_DG(a, b)                                                                               \
   k_dgemm<a, b><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, scale, C, ldc, alpha, beta, kchunk, \
-                                          part)
+                                          part, tri)
   if (!ta && !tb) LAUNCH_DG(0, 0);
   else if (!ta && tb) LAUNCH_DG(0, 1);
   else if (ta && !tb) LAUNCH_DG(1, 0);
@@ -132,6 +150,10 @@ void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
   FSA_CHECK_LAUNCH();
   if (splits > 1) {
     splitk_reduce_kernel<<<grid_for((int64_t)M * N, 256), 256, 0, s>>>(M, N, splits, part, C, ldc, alpha, beta);
+    FSA_CHECK_LAUNCH();
+  }
+  if (tri & kTriSymLower) {
+    k_mirror_lower<<<grid_for((int64_t)M * M, 256), 256, 0, s>>>(C, ldc, M);
     FSA_CHECK_LAUNCH();
   }
 }
@@ -224,24 +246,38 @@ void dgemm_tall(Workspace& ws, cudaStream_t s, int M, int N, int K, const double
 // ---------------------------------------------------------------------------
 constexpr int CNB = 32;
 
-__global__ void potrf_diag_kernel(double* __restrict__ A, int64_t lda, int kb, int nb, unsigned* __restrict__ err) {
-  __shared__ double S[CNB][CNB + 1];
-  int r = threadIdx.y, c = threadIdx.x;
-  if (r < nb && c < nb) S[r][c] = A[(int64_t)(kb + r) * lda + kb + c];
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (r == 0 && c == 0) {
-      double p = S[j][j];
-      if (!(p > 0.0)) { atomicOr(err, kErrNotPD); p = 1.0; }
-      S[j][j] = sqrt(p);
+// the diagonal block, by one warp: lane r holds row r of the block in
+// registers (every index is a compile-time constant, so nothing goes to local
+// memory); the pivot and the column below it move between lanes by shuffles.
+// Rows and columns past nb are the identity and leave the factor unchanged.
+__global__ void __launch_bounds__(32) potrf_diag_kernel(double* __restrict__ A, int64_t lda, int kb, int nb,
+                                                        unsigned* __restrict__ err) {
+  const int r = threadIdx.x;
+  double a[CNB];
+#pragma unroll
+  for (int c = 0; c < CNB; ++c)
+    a[c] = (r < nb && c < nb) ? A[(int64_t)(kb + r) * lda + kb + c] : (r == c ? 1.0 : 0.0);
+#pragma unroll
+  for (int j = 0; j < CNB; ++j) {
+    double p = __shfl_sync(0xffffffffu, a[j], j);
+    if (!(p > 0.0)) {
+      if (r == 0) atomicOr(err, kErrNotPD);
+      p = 1.0;
     }
-    __syncthreads();
-    if (c == j && r > j && r < nb) S[r][j] /= S[j][j];
-    __syncthreads();
-    if (r > j && c > j && c <= r && r < nb) S[r][c] -= S[r][j] * S[c][j];
-    __syncthreads();
+    const double d = sqrt(p);
+    if (r == j) a[j] = d;
+    else if (r > j) a[j] = a[j] / d;
+#pragma unroll
+    for (int c = j + 1; c < CNB; ++c) {
+      const double lcj = __shfl_sync(0xffffffffu, a[j], c);
+      if (r >= c) a[c] -= a[j] * lcj;
+    }
   }
-  if (r < nb && c < nb) A[(int64_t)(kb + r) * lda + kb + c] = (c <= r) ? S[r][c] : 0.0;
+  if (r < nb) {
+#pragma unroll
+    for (int c = 0; c < CNB; ++c)
+      if (c < nb) A[(int64_t)(kb + r) * lda + kb + c] = (c <= r) ? a[c] : 0.0;
+  }
 }
 
 // rows below the diagonal block: L[i, kb:kb+nb] = A[i, kb:kb+nb] L_kk^-T
@@ -254,14 +290,23 @@ __global__ void potrf_panel_kernel(double* __restrict__ A, int64_t lda, int m, i
   __syncthreads();
   int i = kb + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
+  // the row in registers: loops over the compile-time block size, guarded by nb
   double x[CNB];
   double* row = A + (int64_t)i * lda + kb;
-  for (int j = 0; j < nb; ++j) {
-    double v = row[j];
-    for (int t = 0; t < j; ++t) v -= x[t] * Lkk[j][t];
-    x[j] = v / Lkk[j][j];
+#pragma unroll
+  for (int j = 0; j < CNB; ++j) x[j] = j < nb ? row[j] : 0.0;
+#pragma unroll
+  for (int j = 0; j < CNB; ++j) {
+    if (j < nb) {
+      double v = x[j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) v -= x[t] * Lkk[j][t];
+      x[j] = v / Lkk[j][j];
+    }
   }
-  for (int j = 0; j < nb; ++j) row[j] = x[j];
+#pragma unroll
+  for (int j = 0; j < CNB; ++j)
+    if (j < nb) row[j] = x[j];
 }
 
 // trailing update of the lower triangle: A[i][j] -= sum_t L[i][kb+t] L[j][kb+t]
@@ -296,7 +341,7 @@ __global__ void zero_upper_kernel(double* __restrict__ A, int64_t lda, int m) {
 void cholesky(double* A, int64_t lda, int m, unsigned* err, cudaStream_t s) {
   for (int kb = 0; kb < m; kb += CNB) {
     int nb = min(CNB, m - kb);
-    potrf_diag_kernel<<<1, dim3(CNB, CNB), 0, s>>>(A, lda, kb, nb, err);
+    potrf_diag_kernel<<<1, 32, 0, s>>>(A, lda, kb, nb, err);
     FSA_CHECK_LAUNCH();
     int rest = m - kb - nb;
     if (rest > 0) {
@@ -324,13 +369,22 @@ __global__ void trsm_block_kernel(const double* __restrict__ L, int64_t ldl, int
   __syncthreads();
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= r) return;
+  // the column's block rows in registers (compile-time indices, guarded by nb)
   double x[CNB];
-  for (int a = 0; a < nb; ++a) {
-    double v = B[(int64_t)(rb + a) * ldb + j];
-    for (int t = 0; t < a; ++t) v -= Lbb[a][t] * x[t];
-    x[a] = v / Lbb[a][a];
+#pragma unroll
+  for (int a = 0; a < CNB; ++a) x[a] = a < nb ? B[(int64_t)(rb + a) * ldb + j] : 0.0;
+#pragma unroll
+  for (int a = 0; a < CNB; ++a) {
+    if (a < nb) {
+      double v = x[a];
+#pragma unroll
+      for (int t = 0; t < a; ++t) v -= Lbb[a][t] * x[t];
+      x[a] = v / Lbb[a][a];
+    }
   }
-  for (int a = 0; a < nb; ++a) B[(int64_t)(rb + a) * ldb + j] = x[a];
+#pragma unroll
+  for (int a = 0; a < CNB; ++a)
+    if (a < nb) B[(int64_t)(rb + a) * ldb + j] = x[a];
 }
 
 void trsm_lower(Workspace& ws, const double* L, int64_t ldl, int m, double* B, int64_t ldb, int r,
@@ -354,10 +408,22 @@ __global__ void set_identity_kernel(double* __restrict__ A, int64_t lda, int m) 
   }
 }
 
+// L^-1 by right-looking block substitution on X = I: block row kb is solved
+// with L_kk (its nonzeros lie in the columns < kb + nb), then subtracted from
+// every later block row, X[w:, :w] -= L[w:, kb:w] X[kb:w, :w] (w = kb + nb).
+// Each update is a wide product of depth nb, so the GPU is filled from the
+// first block on; the columns >= w of those rows are still zero and skipped.
 void lower_inverse(Workspace& ws, const double* L, int m, double* Li, cudaStream_t s) {
   set_identity_kernel<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(Li, m, m);
   FSA_CHECK_LAUNCH();
-  trsm_lower(ws, L, m, m, Li, m, m, s);
+  for (int kb = 0; kb < m; kb += CNB) {
+    const int nb = min(CNB, m - kb), w = kb + nb;
+    trsm_block_kernel<<<(w + 127) / 128, 128, 0, s>>>(L, m, kb, nb, Li, m, w);
+    FSA_CHECK_LAUNCH();
+    if (w < m)
+      dgemm(ws, s, false, false, m - w, w, nb, -1.0, L + (int64_t)w * m + kb, m, Li + (int64_t)kb * m, m, 1.0,
+            Li + (int64_t)w * m, m, nullptr);
+  }
 }
 
 __global__ void logdiag_sum_kernel(const double* __restrict__ L, int64_t lda, int m, double* __restrict__ out) {

@@ -435,14 +435,15 @@ void build_deriv_f64(Handle& H, const fsa_theta& th, DerivF64& Dv) {
   {
     DevPtr<double> dK((size_t)n * m);
     cov_cross(H, n, H.xs.p, H.ys.p, m, H.ind_x.p, H.ind_y.p, th, 1, dK.p, m);
-    dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, dK.p, m, op.Lmi.p, m, 0.0, Dv.B.p, m, nullptr);
+    dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, dK.p, m, op.Lmi.p, m, 0.0, Dv.B.p, m, nullptr, kTriB_KleJ);
     FSA_CUDA(cudaStreamSynchronize(s));
   }
   {
     DevPtr<double> dSm((size_t)m * m), T1((size_t)m * m);
     cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
-    dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
-    dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, Dv.E.p, m, nullptr);
+    dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr, kTriA_KleI);
+    dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, Dv.E.p, m, nullptr,
+          kTriB_KleJ | kTriSymLower);
     FSA_CUDA(cudaStreamSynchronize(s));
   }
   dgemm(H.ws, s, false, false, (int)n, m, m, 1.0, op.A.p, m, Dv.E.p, m, 0.0, Dv.F.p, m, nullptr);

@@ -208,9 +208,19 @@ void build_cross_structure(Handle& H, const double* qx, const double* qy, int64_
                            DevPtr<int64_t>& rowptr, DevPtr<int32_t>& col, int64_t& nnz);
 void export_csr(Handle& H, int64_t* rowptr_host, int32_t* col_host);
 
+// known zero triangles of the operands of dgemm (the products skip them; the
+// operand must hold exact zeros there) and a symmetric result (only the tiles
+// on and below the diagonal are computed, then mirrored; M == N)
+enum DgemmTri : int {
+  kTriA_KgeI = 1,     // op(A)(i, k) = 0 for k < i  (op(A) upper triangular, e.g. L^T)
+  kTriA_KleI = 2,     // op(A)(i, k) = 0 for k > i  (op(A) lower triangular)
+  kTriB_KgeJ = 4,     // op(B)(k, j) = 0 for k < j  (op(B) lower triangular)
+  kTriB_KleJ = 8,     // op(B)(k, j) = 0 for k > j  (op(B) upper triangular, e.g. L^T)
+  kTriSymLower = 16,  // C symmetric
+};
 void dgemm(Workspace& ws, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
-           int64_t ldc, const double* scale);
+           int64_t ldc, const double* scale, int tri = 0);
 // C = A B for a narrow B (N <= 128 columns, a multiple of 8; else the general
 // form): every column in one block, K split across the GPU
 void dgemm_tall(Workspace& ws, cudaStream_t s, int M, int N, int K, const double* A, int64_t lda, const double* B,

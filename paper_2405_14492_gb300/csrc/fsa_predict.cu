@@ -357,8 +357,8 @@ PredResult run_predict_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o, c
   {
     DevPtr<double> Kp((size_t)np * m);
     cov_cross(H, np, px.p, py.p, m, H.ind_x.p, H.ind_y.p, th, 0, Kp.p, m);
-    dgemm(H.ws, st, false, true, (int)np, m, m, 1.0, Kp.p, m, op.Lmi.p, m, 0.0, Ap.p, m, nullptr);
-    dgemm(H.ws, st, false, false, (int)np, m, m, 1.0, Ap.p, m, op.Lmi.p, m, 0.0, Gt.p, m, nullptr);
+    dgemm(H.ws, st, false, true, (int)np, m, m, 1.0, Kp.p, m, op.Lmi.p, m, 0.0, Ap.p, m, nullptr, kTriB_KleJ);
+    dgemm(H.ws, st, false, false, (int)np, m, m, 1.0, Ap.p, m, op.Lmi.p, m, 0.0, Gt.p, m, nullptr, kTriB_KgeJ);
     FSA_CUDA(cudaStreamSynchronize(st));
   }
   DevPtr<double> svals(snnz > 0 ? snnz : 1);
@@ -426,7 +426,8 @@ PredResult run_predict_fp64(Handle& H, const fsa_theta& th, const fsa_opts& o, c
     {
       DevPtr<double> Li((size_t)m * m);
       lower_inverse(H.ws, Mm.p, m, Li.p, st);
-      dgemm(H.ws, st, true, false, m, m, m, 1.0, Li.p, m, Li.p, m, 0.0, Minv.p, m, nullptr);
+      dgemm(H.ws, st, true, false, m, m, m, 1.0, Li.p, m, Li.p, m, 0.0, Minv.p, m, nullptr,
+            kTriA_KgeI | kTriB_KgeJ | kTriSymLower);
       FSA_CUDA(cudaStreamSynchronize(st));
     }
     check_err(H);
@@ -751,7 +752,8 @@ PredResult run_predict_mixed(Handle& H, const fsa_theta& th, const fsa_opts& o, 
     {
       DevPtr<double> Li((size_t)m * m);
       lower_inverse(H.ws, Mm.p, m, Li.p, st);
-      dgemm(H.ws, st, true, false, m, m, m, 1.0, Li.p, m, Li.p, m, 0.0, Minv.p, m, nullptr);
+      dgemm(H.ws, st, true, false, m, m, m, 1.0, Li.p, m, Li.p, m, 0.0, Minv.p, m, nullptr,
+            kTriA_KgeI | kTriB_KgeJ | kTriSymLower);
       FSA_CUDA(cudaStreamSynchronize(st));
     }
     check_err(H);

@@ -156,7 +156,8 @@ void finish_core(Handle& H) {
   DevPtr<double> Lpi((size_t)m * m);
   lower_inverse(H.ws, op.Mp.p, m, Lpi.p, H.stream);
   op.Minv.ensure((size_t)m * m);
-  dgemm(H.ws, H.stream, true, false, m, m, m, 1.0, Lpi.p, m, Lpi.p, m, 0.0, op.Minv.p, m, nullptr);
+  dgemm(H.ws, H.stream, true, false, m, m, m, 1.0, Lpi.p, m, Lpi.p, m, 0.0, op.Minv.p, m, nullptr,
+        kTriA_KgeI | kTriB_KgeJ | kTriSymLower);   // M^-1 = L^-T L^-1
   FSA_CUDA(cudaStreamSynchronize(H.stream));
 }
 
@@ -170,7 +171,8 @@ void build_operator_fp64(Handle& H, const fsa_theta& th) {
     DevPtr<double> Knm((size_t)n * m);
     cov_cross(H, n, H.xs.p, H.ys.p, m, H.ind_x.p, H.ind_y.p, th, 0, Knm.p, m);
     op.A.ensure((size_t)n * m);
-    dgemm(H.ws, H.stream, false, true, (int)n, m, m, 1.0, Knm.p, m, op.Lmi.p, m, 0.0, op.A.p, m, nullptr);
+    dgemm(H.ws, H.stream, false, true, (int)n, m, m, 1.0, Knm.p, m, op.Lmi.p, m, 0.0, op.A.p, m, nullptr,
+          kTriB_KleJ);
     FSA_CUDA(cudaStreamSynchronize(H.stream));
   }
   op.vals.ensure(H.nnz);
