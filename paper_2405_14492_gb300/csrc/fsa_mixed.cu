@@ -48,34 +48,61 @@ __global__ void k_coord_split(int64_t n, const double* __restrict__ xs, const do
   }
 }
 
-// Sigma_nm (or its rho-derivative) in FP32, split hi/lo BF16, n x m_pad (zero
-// padded).  Thread = one inducing point k (its coordinates in registers),
-// looping over rows; the coordinate differences come from the FP32 hi/lo
-// pairs, (x_hi,i - x_hi,k) + (x_lo,i - x_lo,k), each within a rounding of
-// the exact difference, so no FP64 arithmetic is needed per element.
+// 8 FP32 values -> their BF16 hi (and lo) pieces, packed for one 16-byte store each
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& h, uint4& l) {
+  uint32_t wh[4], wl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(v[2 * k], h0, l0);
+    split_bf16(v[2 * k + 1], h1, l1);
+    wh[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    wl[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  h = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  l = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+}
+
+// Sigma_nm (deriv = 0) or its rho-derivative in FP32, split hi/lo BF16,
+// row-major n x m_pad (columns m .. m_pad - 1 zero).  The coordinate
+// differences come from the FP32 hi/lo pairs, (x_hi,i - x_hi,k) + (x_lo,i -
+// x_lo,k), each within a rounding of the exact difference, so no FP64
+// arithmetic is needed per element.  A thread keeps the coordinates of 8
+// consecutive inducing points in registers and takes the rows blockIdx.x,
+// blockIdx.x + gridDim.x, ...: one 16-byte store per piece and row.
 __global__ void k_cov_nm_split(int64_t n, int m, int m_pad, const float4* __restrict__ pxy,
                                const float4* __restrict__ ixy, int cov, float s1, float rho, int deriv,
                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  const int k = blockIdx.y * blockDim.x + threadIdx.x;
-  if (k >= m_pad) return;
-  const float4 q = k < m ? ixy[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int k0 = 8 * (blockIdx.y * blockDim.x + threadIdx.x);
+  if (k0 >= m_pad) return;
+  float4 q[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) q[j] = k0 + j < m ? ixy[k0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float irho = 1.0f / rho;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    float v = 0.f;
-    if (k < m) {
-      const float4 p = pxy[i];
-      const float dx = (p.x - q.x) + (p.y - q.y), dy = (p.z - q.z) + (p.w - q.w);
-      const float d = sqrtf(dx * dx + dy * dy);
-      if (cov == 0) {
-        const float e = expf(-d * irho);
-        v = deriv ? s1 * (d * irho * irho) * e : s1 * e;
-      } else {
-        const float x = 1.7320508f * d * irho;
-        const float e = expf(-x);
-        v = deriv ? s1 * (x * x * irho) * e : s1 * (1.f + x) * e;
+    const float4 p = pxy[i];
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float x = 0.f;
+      if (k0 + j < m) {
+        const float dx = (p.x - q[j].x) + (p.y - q[j].y), dy = (p.z - q[j].z) + (p.w - q[j].w);
+        const float d = sqrtf(dx * dx + dy * dy);
+        if (cov == 0) {
+          const float e = expf(-d * irho);
+          x = deriv ? s1 * (d * irho * irho) * e : s1 * e;
+        } else {
+          const float t = 1.7320508f * d * irho;
+          const float e = expf(-t);
+          x = deriv ? s1 * (t * t * irho) * e : s1 * (1.f + t) * e;
+        }
       }
+      v[j] = x;
     }
-    split_bf16(v, hi[i * m_pad + k], lo[i * m_pad + k]);
+    uint4 h, l;
+    split8(v, h, l);
+    *reinterpret_cast<uint4*>(hi + i * m_pad + k0) = h;
+    *reinterpret_cast<uint4*>(lo + i * m_pad + k0) = l;
   }
 }
 
@@ -89,9 +116,12 @@ static void cov_nm_split(Handle& H, int m_pad, const fsa_theta& th, int deriv, _
     k_coord_split<<<grid_for(H.m, 256), 256, 0, s>>>(H.m, H.ind_x.p, H.ind_y.p, H.ixy32.p);
     FSA_CHECK_LAUNCH();
   }
-  dim3 grid((unsigned)std::min<int64_t>(H.n, 152 * 16), (unsigned)((m_pad + 255) / 256));
-  k_cov_nm_split<<<grid, 256, 0, s>>>(H.n, H.m, m_pad, H.xy32.p, H.ixy32.p, H.cov, (float)th.sigma1_sq,
-                                      (float)th.rho, deriv, hi, lo);
+  FSA_REQUIRE(m_pad % 8 == 0, FSA_ERR_ARG, "inducing-point padding must be a multiple of 8");
+  const int chunks = m_pad / 8, threads = std::min(256, (chunks + 31) / 32 * 32);
+  const unsigned gy = (unsigned)((chunks + threads - 1) / threads);
+  dim3 grid((unsigned)std::min<int64_t>(H.n, (int64_t)152 * 16 * 256 / threads), gy);
+  k_cov_nm_split<<<grid, threads, 0, s>>>(H.n, H.m, m_pad, H.xy32.p, H.ixy32.p, H.cov, (float)th.sigma1_sq,
+                                          (float)th.rho, deriv, hi, lo);
   FSA_CHECK_LAUNCH();
 }
 
@@ -109,30 +139,7 @@ __global__ void k_split_f64(int rows, int cols, const double* __restrict__ src, 
   }
 }
 
-// destination index of element t of a row-major rows x cols source: the same
-// (cols == 0) or the blocked K-major layout with K = the column
-__device__ __forceinline__ int64_t dst_index(int64_t t, int64_t rows, int cols) {
-  if (cols == 0) return t;
-  const int64_t r = t / cols;
-  return blocked_index(r, t - r * cols, rows);
-}
-
-__global__ void k_f32_to_bf16(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                              int64_t rows = 0, int cols = 0) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    dst[dst_index(t, rows, cols)] = __float2bfloat16_rn(src[t]);
-}
-
-__global__ void k_f32_split(int64_t total, const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
-                            __nv_bfloat16* __restrict__ lo, int64_t rows = 0, int cols = 0) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = dst_index(t, rows, cols);
-    split_bf16(src[t], hi[d], lo[d]);
-  }
-}
-
+// a BF16 pair (hi + lo, lo optional) of element pair k as two FP32 values
 __device__ __forceinline__ float2 ld_pair(const __nv_bfloat162* hi, const __nv_bfloat162* lo, int k) {
   float2 a = __bfloat1622float2(hi[k]);
   if (lo) {
@@ -143,27 +150,91 @@ __device__ __forceinline__ float2 ld_pair(const __nv_bfloat162* hi, const __nv_b
   return a;
 }
 
-// dst (cols x ld_dst) = src^T, src rows x cols (ld_src); 32 x 32 tiles through shared memory
-// dst = src^T; blocked != 0: dst in the blocked K-major layout (K = the src
-// row index, cols rows), else row-major with leading dimension ld_dst
-__global__ void k_transpose_bf16(int64_t rows, int cols, const __nv_bfloat16* __restrict__ src, int64_t ld_src,
-                                 __nv_bfloat16* __restrict__ dst, int64_t ld_dst, int blocked, int src_blocked = 0) {
-  __shared__ __nv_bfloat16 tile[32][34];
-  int64_t r0 = (int64_t)blockIdx.x * 32;
-  int c0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    int64_t r = r0 + k;
-    int c = c0 + threadIdx.x;
-    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[src_blocked ? blocked_index(r, c, rows) : r * ld_src + c]
-                                                  : __float2bfloat16(0.f);
+// src (n x m_pad FP32, row-major) -> its BF16 pieces in the blocked K-major
+// layout of both orientations: hi/lo with rows n and K = m_pad (the A operand
+// of A~ q) and hiT/loT with rows m_pad and K = n_pad (the A operand of A~^T X),
+// the points n .. n_pad - 1 of the latter written as zeros; lo = loT = nullptr
+// writes the single rounded piece.  Persistent: a block takes 64 x 64 tiles in
+// turn.  16-byte loads of the rows; the row-major pieces are written from
+// registers, the tile goes through shared memory (row stride 65 words) for the
+// transposed ones (a thread: 8 consecutive points of one column, one 16-byte
+// store per piece).
+constexpr int kSBT = 64;
+__global__ void __launch_bounds__(256) k_split_both(int64_t n, int m_pad, int64_t n_pad, const float* __restrict__ src,
+                                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                    __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
+  __shared__ float tf[kSBT][kSBT + 1];
+  const int ktiles = m_pad / kSBT;
+  const int64_t ntiles = (n_pad / kSBT) * ktiles;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t rt = t / ktiles;
+    const int kt = (int)(t - rt * ktiles);
+    const int64_t r0 = rt * kSBT;
+    const int k0 = kt * kSBT;
+    for (int f = threadIdx.x; f < kSBT * 8; f += blockDim.x) {
+      const int rr = f >> 3, q = f & 7;   // row rr, columns 8q .. 8q + 7 of the tile
+      const int64_t r = r0 + rr;
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (r < n) {
+        const float4 a = *reinterpret_cast<const float4*>(src + r * m_pad + k0 + 8 * q);
+        const float4 b = *reinterpret_cast<const float4*>(src + r * m_pad + k0 + 8 * q + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        uint4 h, l;
+        split8(v, h, l);
+        const int64_t d = blocked_index(r, k0 + 8 * q, n);
+        if (lo) {
+          *reinterpret_cast<uint4*>(hi + d) = h;
+          *reinterpret_cast<uint4*>(lo + d) = l;
+        } else {
+          uint32_t w[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k + 1])) << 16);
+          *reinterpret_cast<uint4*>(hi + d) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tf[rr][8 * q + k] = v[k];
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < kSBT * 8; f += blockDim.x) {
+      const int g = f & 7, kk = f >> 3;   // column kk, points 8g .. 8g + 7 of the tile
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = tf[8 * g + k][kk];
+      const int64_t d = blocked_index(k0 + kk, r0 + 8 * g, m_pad);
+      if (loT) {
+        uint4 h, l;
+        split8(v, h, l);
+        *reinterpret_cast<uint4*>(hiT + d) = h;
+        *reinterpret_cast<uint4*>(loT + d) = l;
+      } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k])) |
+                 ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k + 1])) << 16);
+        *reinterpret_cast<uint4*>(hiT + d) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    __syncthreads();   // the tile is rewritten by the next one
   }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    int c = c0 + k;
-    int64_t r = r0 + threadIdx.x;
-    if (c < cols && r < rows)
-      dst[blocked ? blocked_index(c, r, cols) : (int64_t)c * ld_dst + r] = tile[threadIdx.x][k];
-  }
+}
+
+// one full wave of k_split_both (SM count x resident blocks)
+static int split_both_blocks(int64_t ntiles) {
+  static const int wave = [] {
+    int dev = 0, sms = 152, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_split_both, 256, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    return sms * std::max(per, 1);
+  }();
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, wave));
 }
 
 // residual values from the BF16 A~ (FP32 products of BF16 values are exact;
@@ -218,17 +289,32 @@ __global__ void k_csr_values_mixed(int64_t n, int m_pad, const int64_t* __restri
 }
 
 // Y^T = (D^-1 A~)^T split hi/lo, from A~^T (m_pad x n_pad)
-// (all four in the blocked K-major layout: element t holds point (t / (64 m_pad)) 64 + t % 64)
+// (all four in the blocked K-major layout: element t holds point (t / (64 m_pad)) 64 + t % 64);
+// a thread takes 8 consecutive elements (8 consecutive points of one row)
 __global__ void k_scale_cols_split(int m_pad, int64_t n, int64_t n_pad, const __nv_bfloat16* __restrict__ At,
                                    const __nv_bfloat16* __restrict__ At_lo, const float* __restrict__ Dinv,
                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  int64_t total = (int64_t)m_pad * n_pad;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = (t / (64 * (int64_t)m_pad)) * 64 + (t & 63);
-    float a = __bfloat162float(At[t]) + (At_lo ? __bfloat162float(At_lo[t]) : 0.f);
-    float v = i < n ? a * Dinv[i] : 0.f;
-    split_bf16(v, hi[t], lo[t]);
+  const int64_t total8 = (int64_t)m_pad * n_pad / 8;
+  for (int64_t t8 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t8 < total8;
+       t8 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = 8 * t8;
+    const int64_t i = (t / (64 * (int64_t)m_pad)) * 64 + (t & 63);
+    const uint4 ah = *reinterpret_cast<const uint4*>(At + t);
+    uint4 al = make_uint4(0u, 0u, 0u, 0u);
+    if (At_lo) al = *reinterpret_cast<const uint4*>(At_lo + t);
+    const uint32_t wh[4] = {ah.x, ah.y, ah.z, ah.w}, wl[4] = {al.x, al.y, al.z, al.w};
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float a0 = __uint_as_float(wh[k] << 16) + (At_lo ? __uint_as_float(wl[k] << 16) : 0.f);
+      const float a1 = __uint_as_float(wh[k] & 0xffff0000u) + (At_lo ? __uint_as_float(wl[k] & 0xffff0000u) : 0.f);
+      v[2 * k] = i + 2 * k < n ? a0 * Dinv[i + 2 * k] : 0.f;
+      v[2 * k + 1] = i + 2 * k + 1 < n ? a1 * Dinv[i + 2 * k + 1] : 0.f;
+    }
+    uint4 h, l;
+    split8(v, h, l);
+    *reinterpret_cast<uint4*>(hi + t) = h;
+    *reinterpret_cast<uint4*>(lo + t) = l;
   }
 }
 
@@ -553,14 +639,26 @@ __global__ void k_grp_values(const int32_t* __restrict__ ptile, const int4* __re
   }
 }
 
-// dst = bf16(a - b)
-// hi + lo BF16 pair of a - b (FP32), in the blocked K-major layout with K = the column
-__global__ void k_sub_split(int64_t total, const float* __restrict__ a, const float* __restrict__ b,
-                            __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t rows, int cols) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = dst_index(t, rows, cols);
-    split_bf16(a[t] - b[t], hi[d], lo[d]);
+// hi + lo BF16 pair of a - b (FP32 rows x cols, row-major), in the blocked
+// K-major layout with K = the column; a thread takes 8 consecutive columns
+// (cols a multiple of 8)
+__global__ void k_sub_split(int64_t rows, int cols, const float* __restrict__ a, const float* __restrict__ b,
+                            __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t total8 = rows * cols / 8;
+  for (int64_t t8 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t8 < total8;
+       t8 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = 8 * t8;
+    const int64_t r = t / cols;
+    const int k = (int)(t - r * cols);
+    const float4 a0 = *reinterpret_cast<const float4*>(a + t), a1 = *reinterpret_cast<const float4*>(a + t + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(b + t), b1 = *reinterpret_cast<const float4*>(b + t + 4);
+    const float v[8] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z, a0.w - b0.w,
+                        a1.x - b1.x, a1.y - b1.y, a1.z - b1.z, a1.w - b1.w};
+    uint4 h, l;
+    split8(v, h, l);
+    const int64_t d = blocked_index(r, k, rows);
+    *reinterpret_cast<uint4*>(hi + d) = h;
+    *reinterpret_cast<uint4*>(lo + d) = l;
   }
 }
 
@@ -623,7 +721,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
       // A = Sigma_nm L_m^-T in FP64, then rounded like the tensor-core result
       DevPtr<double> K64((size_t)n * m), A64((size_t)n * m);
       cov_cross(H, n, H.xs.p, H.ys.p, m, H.ind_x.p, H.ind_y.p, th, 0, K64.p, m);
-      dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, K64.p, m, op.Lmi.p, m, 0.0, A64.p, m, nullptr);
+      dgemm(H.ws, s, false, true, (int)n, m, m, 1.0, K64.p, m, op.Lmi.p, m, 0.0, A64.p, m, nullptr, kTriB_KleJ);
       k_f64_to_f32_pad<<<grid_for((int64_t)n * m_pad, 256), 256, 0, s>>>(n, m, m_pad, A64.p, A32.p);
       FSA_CHECK_LAUNCH();
       FSA_CUDA(cudaStreamSynchronize(s));
@@ -644,26 +742,24 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
       g.tag = "build";
       tc_gemm(g, H.err, s);
     }
+    // the GEMM's operands are freed (stream-ordered) before the pieces are allocated
+    Khi.release(); Klo.release(); Lhi.release(); Llo.release();
+    // A~ as BF16 pieces in both orientations: A~ (rows n, K = m_pad) for A~ q and
+    // A~^T (rows m_pad, K = n_pad, zero past n) for A~^T X, from one pass over A32
     op.Ab.ensure(nm);
+    op.Atb.ensure((size_t)m_pad * n_pad);
     if (lo) {
       op.Ab_lo.ensure(nm);
-      k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, op.Ab_lo.p, n, m_pad);
-    } else {
-      k_f32_to_bf16<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, A32.p, op.Ab.p, n, m_pad);
+      op.Atb_lo.ensure((size_t)m_pad * n_pad);
     }
-    FSA_CHECK_LAUNCH();
+    {
+      ProfScope ps("build_split", 4.0 * n * m_pad + (lo ? 8.0 : 4.0) * n * m_pad, s);   // A32 read; pieces twice
+      const int64_t nt = (n_pad / kSBT) * (m_pad / kSBT);
+      k_split_both<<<split_both_blocks(nt), 256, 0, s>>>(n, m_pad, n_pad, A32.p, op.Ab.p, lo ? op.Ab_lo.p : nullptr,
+                                                          op.Atb.p, lo ? op.Atb_lo.p : nullptr);
+      FSA_CHECK_LAUNCH();
+    }
     FSA_CUDA(cudaStreamSynchronize(s));
-  }
-  dim3 tgrid((unsigned)((n + 31) / 32), (m_pad + 31) / 32), tblk(32, 8);
-  op.Atb.ensure((size_t)m_pad * n_pad);
-  FSA_CUDA(cudaMemsetAsync(op.Atb.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
-  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab.p, m_pad, op.Atb.p, n_pad, 1, 1);
-  FSA_CHECK_LAUNCH();
-  if (lo) {
-    op.Atb_lo.ensure((size_t)m_pad * n_pad);
-    FSA_CUDA(cudaMemsetAsync(op.Atb_lo.p, 0, sizeof(__nv_bfloat16) * (size_t)m_pad * n_pad, s));
-    k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, op.Ab_lo.p, m_pad, op.Atb_lo.p, n_pad, 1, 1);
-    FSA_CHECK_LAUNCH();
   }
   const __nv_bfloat16* Alo = lo ? op.Ab_lo.p : nullptr;
   const __nv_bfloat16* Atlo = lo ? op.Atb_lo.p : nullptr;
@@ -684,8 +780,8 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   {
     size_t mn = (size_t)m_pad * n_pad;
     DevPtr<__nv_bfloat16> Yhi(mn), Ylo(mn);
-    k_scale_cols_split<<<grid_for((int64_t)mn, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, Atlo, op.Dinv32.p,
-                                                                    Yhi.p, Ylo.p);
+    k_scale_cols_split<<<grid_for((int64_t)mn / 8, 256), 256, 0, s>>>(m_pad, n, n_pad, op.Atb.p, Atlo, op.Dinv32.p,
+                                                                        Yhi.p, Ylo.p);
     FSA_CHECK_LAUNCH();
     TmaMap mAt = make_tma_bf16_blocked(op.Atb.p, m_pad, n_pad, 128);
     TmaMap mAtl = lo ? make_tma_bf16_blocked(op.Atb_lo.p, m_pad, n_pad, 128) : mAt;
@@ -972,56 +1068,64 @@ void build_deriv_mixed(Handle& H, const MixedCtx& C, const fsa_theta& th, DerivM
     FSA_CUDA(cudaMemsetAsync(Dv.zero_lo.p, 0, nm * sizeof(__nv_bfloat16), s));
     Dv.Alo = Dv.zero_lo.p;
   }
-  Dv.Bh.alloc(nm); Dv.Bl.alloc(nm); Dv.Qh.alloc(nm); Dv.Ql.alloc(nm);
   Dv.E.alloc((size_t)m * m);
   {
-    DevPtr<__nv_bfloat16> Khi(nm), Klo(nm), Lhi(mm_pad), Llo(mm_pad);
-    DevPtr<float> B32(nm);
-    cov_nm_split(H, m_pad, th, 1, Khi.p, Klo.p);
-    k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p, Llo.p);
-    FSA_CHECK_LAUNCH();
-    TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+    // order: F = A~ E, then B = dK L^-T, so that the n x m temporaries peak at
+    // four of them (B32, the pieces of q, of B and of B^T)
+    DevPtr<__nv_bfloat16> Lhi(mm_pad), Llo(mm_pad);
     TmaMap mLh = make_tma_bf16(Lhi.p, m_pad, m_pad, m_pad, 128), mLl = make_tma_bf16(Llo.p, m_pad, m_pad, m_pad, 128);
-    TcGemm t;
-    t.a[0] = &mKh; t.a[1] = &mKl; t.num_a = 2;
-    t.b[0] = &mLh; t.b[1] = &mLl; t.num_b = 2;
-    t.pairs = 1u | 2u | 4u;
-    t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
-    t.out = B32.p; t.ldo = m_pad;
-    t.tag = "grad";
-    tc_gemm(t, H.err, s);
-    k_f32_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, Dv.Bh.p, Dv.Bl.p, n, m_pad);
-    FSA_CHECK_LAUNCH();
-    // E = L^-1 dSigma_m L^-T (FP64), F = A~ E (split products), q = b - F
-    DevPtr<double> dSm((size_t)m * m), T1((size_t)m * m);
-    cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
-    dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr);
-    dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, Dv.E.p, m, nullptr);
+    // E = L^-1 dSigma_m L^-T (FP64), F = A~ E (split products)
+    {
+      DevPtr<double> dSm((size_t)m * m), T1((size_t)m * m);
+      cov_cross(H, m, H.ind_x.p, H.ind_y.p, m, H.ind_x.p, H.ind_y.p, th, 1, dSm.p, m);
+      dgemm(H.ws, s, false, false, m, m, m, 1.0, op.Lmi.p, m, dSm.p, m, 0.0, T1.p, m, nullptr, kTriA_KleI);
+      dgemm(H.ws, s, false, true, m, m, m, 1.0, T1.p, m, op.Lmi.p, m, 0.0, Dv.E.p, m, nullptr,
+            kTriB_KleJ | kTriSymLower);
+    }
     k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, Dv.E.p, m, m_pad, m_pad, Lhi.p, Llo.p);
     FSA_CHECK_LAUNCH();
-    TcGemm f;
-    f.a[0] = &C.mA; f.a[1] = &C.mA_lo; f.num_a = C.lo ? 2 : 1;
-    f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
-    f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
-    f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
     DevPtr<float> F32(nm);
-    f.out = F32.p; f.ldo = m_pad;
-    f.tag = "grad";
-    tc_gemm(f, H.err, s);
-    k_sub_split<<<grid_for((int64_t)nm, 256), 256, 0, s>>>((int64_t)nm, B32.p, F32.p, Dv.Qh.p, Dv.Ql.p, n, m_pad);
+    {
+      TcGemm f;
+      f.a[0] = &C.mA; f.a[1] = &C.mA_lo; f.num_a = C.lo ? 2 : 1;
+      f.b[0] = &mLh; f.b[1] = &mLl; f.num_b = 2;
+      f.pairs = C.lo ? (1u | 2u | 4u) : (1u | 2u);
+      f.M = (int)n; f.N = m_pad; f.K = m_pad; f.bn = 128;
+      f.out = F32.p; f.ldo = m_pad;
+      f.tag = "grad";
+      tc_gemm(f, H.err, s);
+    }
+    // B = dK L^-T (the pieces of L^-1 replace those of E once F is done: same stream)
+    DevPtr<float> B32(nm);
+    {
+      DevPtr<__nv_bfloat16> Khi(nm), Klo(nm);
+      cov_nm_split(H, m_pad, th, 1, Khi.p, Klo.p);
+      k_split_f64<<<grid_for((int64_t)mm_pad, 256), 256, 0, s>>>(m, m, op.Lmi.p, m, m_pad, m_pad, Lhi.p, Llo.p);
+      FSA_CHECK_LAUNCH();
+      TmaMap mKh = make_tma_bf16(Khi.p, n, m_pad, m_pad, 128), mKl = make_tma_bf16(Klo.p, n, m_pad, m_pad, 128);
+      TcGemm t;
+      t.a[0] = &mKh; t.a[1] = &mKl; t.num_a = 2;
+      t.b[0] = &mLh; t.b[1] = &mLl; t.num_b = 2;
+      t.pairs = 1u | 2u | 4u;
+      t.M = (int)n; t.N = m_pad; t.K = m_pad; t.bn = 128;
+      t.out = B32.p; t.ldo = m_pad;
+      t.tag = "grad";
+      tc_gemm(t, H.err, s);
+    }
+    // q = b - F as a BF16 pair
+    Dv.Qh.alloc(nm); Dv.Ql.alloc(nm);
+    k_sub_split<<<grid_for((int64_t)nm / 8, 256), 256, 0, s>>>(n, m_pad, B32.p, F32.p, Dv.Qh.p, Dv.Ql.p);
+    FSA_CHECK_LAUNCH();
+    F32.release();
+    // B as a BF16 pair in both orientations: B (rows n) for B q, B^T (blocked,
+    // K = the point, zero past n) for B^T X
+    const size_t mn = (size_t)m_pad * C.n_pad;
+    Dv.Bh.alloc(nm); Dv.Bl.alloc(nm); Dv.Bth.alloc(mn); Dv.Btl.alloc(mn);
+    const int64_t nt = (C.n_pad / kSBT) * (m_pad / kSBT);
+    k_split_both<<<split_both_blocks(nt), 256, 0, s>>>(n, m_pad, C.n_pad, B32.p, Dv.Bh.p, Dv.Bl.p, Dv.Bth.p, Dv.Btl.p);
     FSA_CHECK_LAUNCH();
     FSA_CUDA(cudaStreamSynchronize(s));
   }
-  // B^T as a BF16 pair (blocked, K = the point) for B^T X; B for B q
-  const size_t mn = (size_t)m_pad * C.n_pad;
-  Dv.Bth.alloc(mn); Dv.Btl.alloc(mn);
-  FSA_CUDA(cudaMemsetAsync(Dv.Bth.p, 0, sizeof(__nv_bfloat16) * mn, s));
-  FSA_CUDA(cudaMemsetAsync(Dv.Btl.p, 0, sizeof(__nv_bfloat16) * mn, s));
-  dim3 tgrid((unsigned)((n + 31) / 32), (m_pad + 31) / 32), tblk(32, 8);
-  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, Dv.Bh.p, m_pad, Dv.Bth.p, C.n_pad, 1, 1);
-  FSA_CHECK_LAUNCH();
-  k_transpose_bf16<<<tgrid, tblk, 0, s>>>(n, m_pad, Dv.Bl.p, m_pad, Dv.Btl.p, C.n_pad, 1, 1);
-  FSA_CHECK_LAUNCH();
   Dv.CBt = C;
   Dv.CBt.mAt = make_tma_bf16_blocked(Dv.Bth.p, m_pad, C.n_pad, 128);
   Dv.CBt.mAt_lo = make_tma_bf16_blocked(Dv.Btl.p, m_pad, C.n_pad, 128);
