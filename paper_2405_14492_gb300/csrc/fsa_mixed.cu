@@ -1017,10 +1017,20 @@ void pcg_mixed_run(Handle& H, MixedCtx& C, const CGLayout& lay, const fsa_opts& 
   FSA_CUDA(cudaMemsetAsync(g.V32.p, 0, nc * sizeof(float), s));
   FSA_CUDA(cudaMemsetAsync(g.H32.p, 0, nc * sizeof(float), s));
   CGScalars q = make_scalars(H, o, L);
+  const ZBulkLaunch zb = zbulk_launch(lay);
+  // Z = D^-1 (R - S) with its r^T z step: the bulk-copy stream where its
+  // shared memory is granted, else the register form
+  auto z_update = [&](int step, int l) {
+    if (zb.blocks > 0)
+      kz_bulk<<<zb.blocks, zb.threads, zb.smem, s>>>(n, lay.c, ldc, zb.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
+                                                     g.part.p, step, l, q);
+    else
+      kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
+                                                            g.Z32.p, g.part.p, step, l, q);
+    FSA_CHECK_LAUNCH();
+  };
   lowrank_mixed(H, C, g.R32.p, g.S32.p);
-  kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p, g.Z32.p,
-                                                      g.part.p, kStepInit, 0, q);
-  FSA_CHECK_LAUNCH();
+  z_update(kStepInit, 0);
   FSA_CUDA(cudaMemcpyAsync(g.W032.p, g.Z32.p, nc * sizeof(float), cudaMemcpyDeviceToDevice, s));
   const StagedLaunch sl = staged_launch(H, ldc);
   launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha, q);
@@ -1039,9 +1049,7 @@ void pcg_mixed_run(Handle& H, MixedCtx& C, const CGLayout& lay, const fsa_opts& 
     lowrank_mixed_tail(H, C, g.S32.p);
     {
       ProfScope ps("pcg_z", 3.0 * blk_bytes + 4.0 * n, s);   // R, S read, Z written; D^-1
-      kv4_z_update<<<v4z.blocks, v4z.threads, v4z.smem, s>>>(n, lay.c, ldc, v4z.rpb, g.R32.p, g.S32.p, op.Dinv32.p,
-                                                          g.Z32.p, g.part.p, kStepBeta, it, q);
-      FSA_CHECK_LAUNCH();
+      z_update(kStepBeta, it);
     }
     launch_spmm_f32(H, lay, sl, s, op.vals32.p, g.Z32.p, g.S32.p, g.V32.p, g.H32.p, g.beta.p, g.part.p, kStepAlpha,
                     q);

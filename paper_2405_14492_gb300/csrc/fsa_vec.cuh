@@ -870,6 +870,135 @@ static __global__ void __launch_bounds__(256, 5) kv4_z_update(int64_t n, int c, 
   finish_scalars(step, part, ldc, c, l, q, red4);
 }
 
+// Z = (R - S) Dinv ; part = r^T z, streamed through shared memory by bulk
+// copies.  A block takes the chunks blockIdx.x, + gridDim.x, ... of kZPer rpb
+// rows (R and S rows are contiguous, so a chunk of each is one bulk copy);
+// thread 0 keeps kZStages chunks in flight, their completion counted in bytes
+// on the slot's mbarrier, and every thread computes its kZPer rows of a landed
+// chunk from shared memory (the rows' D^-1 are plain loads issued before the
+// wait) and stores Z.  Waits are bounded: a wait that runs out records
+// kErrTimeout, the block stops computing, waits (bounded) for its copies in
+// flight and still takes part in the scalar step.
+constexpr int kZPer = 2, kZStages = 6;
+static __global__ void __launch_bounds__(256) kz_bulk(int64_t n, int c, int ldc, int rpb, const float* __restrict__ R,
+                                                      const float* __restrict__ S, const float* __restrict__ Dinv,
+                                                      float* __restrict__ Z, double* __restrict__ part, int step, int l,
+                                                      CGScalars q) {
+  extern __shared__ __align__(16) unsigned char zsm[];
+  const int c4 = ldc >> 2, crow = kZPer * rpb;   // rows per chunk
+  const size_t slot_f = (size_t)crow * ldc;      // floats per array and slot
+  float* buf = reinterpret_cast<float*>(zsm);    // [kZStages][R, S][crow * ldc]
+  uint64_t* full = reinterpret_cast<uint64_t*>(buf + (size_t)kZStages * 2 * slot_f);
+  const int cq = threadIdx.x % c4, rr0 = threadIdx.x / c4;
+  const int64_t nchunks = (n + crow - 1) / crow;
+  const int64_t mine = nchunks > (int64_t)blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kZStages; ++s) sp_mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto chunk_rows = [&](int64_t k, int64_t& r0) {
+    r0 = ((int64_t)blockIdx.x + k * gridDim.x) * crow;
+    return (int)min((int64_t)crow, n - r0);
+  };
+  auto issue = [&](int64_t k) {   // thread 0: chunk k of this block into slot k % kZStages
+    int64_t r0;
+    const int rows = chunk_rows(k, r0);
+    const int s = (int)(k % kZStages);
+    const uint32_t bytes = (uint32_t)rows * (uint32_t)ldc * 4u;
+    sp_mbar_expect_tx(&full[s], 2u * bytes);
+    sp_bulk_load(buf + (size_t)s * 2 * slot_f, R + r0 * ldc, bytes, &full[s]);
+    sp_bulk_load(buf + (size_t)s * 2 * slot_f + slot_f, S + r0 * ldc, bytes, &full[s]);
+  };
+  int64_t issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < min((int64_t)kZStages, mine); ++issued) issue(issued);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float sub[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+  int64_t k = 0;
+  for (; k < mine; ++k) {
+    int64_t r0;
+    const int rows = chunk_rows(k, r0);
+    const int s = (int)(k % kZStages);
+    float d[kZPer];
+#pragma unroll
+    for (int j = 0; j < kZPer; ++j) {
+      const int rr = rr0 + j * rpb;
+      d[j] = rr < rows ? Dinv[r0 + rr] : 0.f;
+    }
+    const bool ok = sp_mbar_wait(&full[s], (uint32_t)(k / kZStages) & 1u, q.err);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) sp_flag(q.err);
+      break;
+    }
+    const float* bR = buf + (size_t)s * 2 * slot_f;
+    const float* bS = bR + slot_f;
+#pragma unroll
+    for (int j = 0; j < kZPer; ++j) {
+      const int rr = rr0 + j * rpb;
+      if (rr < rows) {
+        const float4 r = *reinterpret_cast<const float4*>(bR + (size_t)rr * ldc + 4 * cq);
+        const float4 sv = *reinterpret_cast<const float4*>(bS + (size_t)rr * ldc + 4 * cq);
+        // columns >= c hold zeros in R and S, so Z is zero there
+        const float4 z = make_float4((r.x - sv.x) * d[j], (r.y - sv.y) * d[j], (r.z - sv.z) * d[j],
+                                     (r.w - sv.w) * d[j]);
+        *reinterpret_cast<float4*>(Z + (r0 + rr) * ldc + 4 * cq) = z;
+        sub[0] += r.x * z.x; sub[1] += r.y * z.y; sub[2] += r.z * z.z; sub[3] += r.w * z.w;
+      }
+    }
+    if (++cnt == 16) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) { acc[kk] += (double)sub[kk]; sub[kk] = 0.f; }
+      cnt = 0;
+    }
+    __syncthreads();   // slot s is free
+    if (threadIdx.x == 0 && issued < mine) issue(issued++);
+  }
+  if (threadIdx.x == 0) {
+    // after a timed-out wait no copy may still be in flight when the block
+    // moves on: wait (bounded) for every chunk issued and not yet consumed
+    for (int64_t j = k; j < issued; ++j)
+      if (!sp_mbar_wait(&full[j % kZStages], (uint32_t)(j / kZStages) & 1u, nullptr)) sp_flag(q.err);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) acc[kk] += (double)sub[kk];
+  double* red4 = reinterpret_cast<double*>(zsm);   // the stages are idle now
+  vec4_block_partials(acc, ldc, c4, rpb, red4, part);
+  finish_scalars(step, part, ldc, c, l, q, red4);
+}
+
+// launch shape of kz_bulk: rpb x c4 threads, the stages' shared memory, one
+// full wave of resident blocks (at most the layout's partial rows); blocks = 0
+// where the device refuses the shared memory
+struct ZBulkLaunch {
+  int blocks = 0, threads = 32, rpb = 1;
+  size_t smem = 0;
+};
+static inline ZBulkLaunch zbulk_launch(const CGLayout& lay) {
+  ZBulkLaunch z;
+  const int c4 = lay.ldc / 4;
+  z.rpb = std::max(1, 256 / c4);
+  z.threads = z.rpb * c4;
+  const size_t stages = (size_t)kZStages * 2 * kZPer * z.rpb * lay.ldc * sizeof(float) + kZStages * sizeof(uint64_t);
+  z.smem = std::max(stages, (size_t)z.threads * 4 * sizeof(double));
+  if (cudaFuncSetAttribute(kz_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return z;
+  }
+  int dev = 0, sms = 152, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kz_bulk, z.threads, z.smem) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  z.blocks = per > 0 ? std::min(lay.nblk, sms * per) : 0;
+  return z;
+}
+
 // CUDA-event timing of one launch under the profiling hooks (fsa_profile.h):
 // records the tag's algorithmic bytes with the launch's device time
 struct ProfScope {
