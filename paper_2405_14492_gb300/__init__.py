@@ -17,7 +17,7 @@ from ._native import (FSA_EXPONENTIAL, FSA_FP64, FSA_MATERN_1_5, FSA_MIXED_BF16,
 
 __all__ = ["FSAHandle", "FSAServer", "FSALogLik", "FsaError", "FSA_EXPONENTIAL", "FSA_MATERN_1_5", "FSA_FP64",
            "FSA_MIXED_BF16", "FSA_MIXED_BF16X2", "FSA_PROBE_RADEMACHER", "FSA_PROBE_GAUSSIAN", "make_opts",
-           "cov_code"]
+           "cov_code", "fit_mle"]
 
 
 def cov_code(nu: float) -> int:
@@ -316,3 +316,42 @@ class _Lazy:
 
 
 FSALogLik = _Lazy()
+
+
+def fit_mle(handle, y, theta0, opts=None, max_iter: int = 100, tol_grad: float = 1e-9, history_size: int = 10):
+    """Maximum-likelihood estimate of theta = (sigma1^2, rho, nugget) by L-BFGS
+    on top of ``FSALogLik`` (the paper estimates its parameters this way, §4).
+
+    The optimiser works on phi = log theta, so every iterate stays positive,
+    and minimises -l(exp(phi)) / n with torch's L-BFGS and a strong-Wolfe line
+    search.  Every objective evaluation is one ``handle.loglik_grad`` call
+    (one ``fsa_loglik_grad`` on a GPU handle).  ``opts`` fixes the probes
+    (its seed) for every call, so the objective is one deterministic function
+    of theta, as the line search needs.  Stops when the gradient in phi falls
+    below ``tol_grad`` (scaled by 1/n) or after ``max_iter`` iterations.
+
+    Returns a dict: theta (np.ndarray), loglik at theta, iterations,
+    evaluations (handle calls) and converged (gradient criterion met)."""
+    import torch
+
+    y_np = np.asarray(y, dtype=np.float64)
+    n = y_np.shape[0]
+    phi = torch.tensor(np.log(np.asarray(theta0, dtype=np.float64)), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.LBFGS([phi], lr=1.0, max_iter=max_iter, tolerance_grad=tol_grad, tolerance_change=0.0,
+                            history_size=history_size, line_search_fn="strong_wolfe")
+    evals = [0]
+
+    def closure():
+        opt.zero_grad()
+        loss = -FSALogLik.apply(torch.exp(phi), handle, y_np, opts) / n
+        loss.backward()
+        evals[0] += 1
+        return loss
+
+    opt.step(closure)
+    state = opt.state[opt._params[0]]
+    th = np.exp(phi.detach().numpy())
+    ll, g, _ = handle.loglik_grad(y_np, th, opts)
+    gphi = np.max(np.abs(-np.asarray(g) * th / n))
+    return {"theta": th, "loglik": float(ll), "iterations": int(state.get("n_iter", 0)),
+            "evaluations": evals[0], "converged": bool(gphi <= tol_grad)}
