@@ -47,7 +47,9 @@ typedef enum {
   FSA_ERR_TIMEOUT = 6,         /* a bounded device or host wait ran out */
   FSA_ERR_BUSY = 7,            /* serving: result not ready yet */
   FSA_ERR_CUDA = 8,            /* a CUDA runtime error, or another system error (a thread that could not start) */
-  FSA_ERR_UNSUPPORTED = 9      /* option not available on this device / build */
+  FSA_ERR_UNSUPPORTED = 9,     /* option not available on this device / build */
+  FSA_ERR_BOUNDS = 10          /* checked build (FSA_CHECKED) only: a device index check failed, the
+                                  access it guarded was skipped; a defect of this library, outputs invalid */
 } fsa_status;
 
 typedef enum {

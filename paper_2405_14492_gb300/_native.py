@@ -12,11 +12,15 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfsa.so")
+# FSA_CHECKED=1 in the environment loads the checked build (device index
+# checks that report FSA_ERR_BOUNDS; build.py --checked) in place of the default
+CHECKED = os.environ.get("FSA_CHECKED", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "libfsa_checked.so" if CHECKED else "libfsa.so")
 
 FSA_OK = 0
 STATUS = {0: "FSA_OK", 1: "FSA_ERR_ARG", 2: "FSA_ERR_OOM", 3: "FSA_ERR_NOT_PD", 4: "FSA_ERR_NO_CONVERGENCE",
-          5: "FSA_ERR_NAN", 6: "FSA_ERR_TIMEOUT", 7: "FSA_ERR_BUSY", 8: "FSA_ERR_CUDA", 9: "FSA_ERR_UNSUPPORTED"}
+          5: "FSA_ERR_NAN", 6: "FSA_ERR_TIMEOUT", 7: "FSA_ERR_BUSY", 8: "FSA_ERR_CUDA", 9: "FSA_ERR_UNSUPPORTED",
+          10: "FSA_ERR_BOUNDS"}
 FSA_EXPONENTIAL, FSA_MATERN_1_5 = 0, 1
 FSA_FP64, FSA_MIXED_BF16, FSA_MIXED_BF16X2 = 0, 1, 2
 FSA_PROBE_RADEMACHER, FSA_PROBE_GAUSSIAN = 0, 1
@@ -131,7 +135,7 @@ def _declare(lib):
 
 
 def lib():
-    """The loaded libfsa.so (raises if it was not built)."""
+    """The loaded libfsa.so, or libfsa_checked.so under FSA_CHECKED=1 (raises if it was not built)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):

@@ -3,6 +3,11 @@
 Every CUDA translation unit under csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a) and linked into
 paper_2405_14492_gb300/libfsa.so.  Rebuilds only what changed.
+
+``--checked`` (build(checked=True)) builds the checked variant instead:
+-DFSA_CHECKED, its own objects, paper_2405_14492_gb300/libfsa_checked.so.  Its
+device index checks report FSA_ERR_BOUNDS in place of a memory fault; the
+binding loads it when FSA_CHECKED=1 is set in the environment.
 """
 from __future__ import annotations
 
@@ -40,8 +45,8 @@ def _headers():
     return hs
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra: list[str], bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
@@ -52,22 +57,25 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+def build(verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    bdir = BUILD + "_checked" if checked else BUILD
+    lib = os.path.join(HERE, "libfsa_checked.so") if checked else LIB
+    os.makedirs(bdir, exist_ok=True)
+    extra = list(extra or []) + (["-DFSA_CHECKED"] if checked else [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-ldl"]
+    if not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = sys.argv[1:]
+    build(verbose=True, extra=[a for a in args if a != "--checked"], checked="--checked" in args)

@@ -183,6 +183,7 @@ const char* fsa_status_string(fsa_status s) {
     case FSA_ERR_BUSY: return "FSA_ERR_BUSY";
     case FSA_ERR_CUDA: return "FSA_ERR_CUDA";
     case FSA_ERR_UNSUPPORTED: return "FSA_ERR_UNSUPPORTED";
+    case FSA_ERR_BOUNDS: return "FSA_ERR_BOUNDS";
   }
   return "FSA_ERR_UNKNOWN";
 }

@@ -178,6 +178,21 @@ enum : unsigned {
   kErrBounds = 8u,
 };
 
+// Checked build (-DFSA_CHECKED; compute-sanitizer is not available here):
+// FSA_INDEX_OK(cond, err) tests a data-dependent index before the access it
+// guards.  A failed test records kErrBounds in the error word (when the launch
+// has one), and the caller skips the access.  In the default build it is the
+// constant true, so the guarded code is unchanged.
+#ifdef FSA_CHECKED
+__device__ __forceinline__ bool fsa_index_ok(bool ok, unsigned* err) {
+  if (!ok && err) atomicOr(err, kErrBounds);
+  return ok;
+}
+#define FSA_INDEX_OK(cond, err) ::fsa::fsa_index_ok((cond), (err))
+#else
+#define FSA_INDEX_OK(cond, err) true
+#endif
+
 // in-place ascending heap sort of a[0..len) by one thread: O(len log len)
 // steps whatever the input order, so a crowded cell or a long neighbour row
 // (a taper range close to the extent of the points) costs seconds at worst,

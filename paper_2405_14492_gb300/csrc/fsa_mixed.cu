@@ -620,14 +620,18 @@ __global__ void k_probe_finish_mixed(int64_t n, int l, int ldc, int ldz, int kin
 // word 0 the staged column, word 1 + g the FP32 value of the group's row g in
 // that column (bits), or 0 where the column is not one of its neighbours
 __global__ void k_grp_values(const int32_t* __restrict__ ptile, const int4* __restrict__ src,
-                             const float* __restrict__ vals32, int4* __restrict__ ent) {
+                             const float* __restrict__ vals32, int4* __restrict__ ent, unsigned* __restrict__ err) {
   const int t = blockIdx.x;
   const int32_t* rec = ptile + (int64_t)t * kTileWords;
   if (rec[15]) return;   // bad tile: no union entries
   const int64_t e0 = (int64_t)(uint32_t)rec[8] | ((int64_t)rec[9] << 32);
   const int64_t eb = (int64_t)(uint32_t)rec[12] | ((int64_t)rec[13] << 32);
-  const int ne = rec[14];
-  auto val = [&](int r) { return r >= 0 ? __float_as_int(vals32[e0 + r]) : 0; };
+  const int ne = rec[14], tnnz = rec[10];
+  auto val = [&](int r) {
+    if (r < 0) return 0;
+    if (!FSA_INDEX_OK(r < tnnz, err)) return 0;   // a source inside the tile's nonzeros (checked build)
+    return __float_as_int(vals32[e0 + r]);
+  };
   for (int i = threadIdx.x; i < ne; i += blockDim.x) {
     const int64_t x = kEntVec * (eb + i);
     const int4 a = src[x];
@@ -773,7 +777,7 @@ void build_operator_mixed(Handle& H, const fsa_theta& th, int precision) {
   // the values of the SpMM row groups' union entries, read by one bulk copy per tile
   op.grp_ent.ensure((size_t)std::max<int64_t>(H.grp_entries, 1) * kEntVec);
   if (H.sp_ntiles > 0 && H.grp_entries > 0) {
-    k_grp_values<<<H.sp_ntiles, 128, 0, s>>>(H.sp_ptile.p, H.grp_src.p, op.vals32.p, op.grp_ent.p);
+    k_grp_values<<<H.sp_ntiles, 128, 0, s>>>(H.sp_ptile.p, H.grp_src.p, op.vals32.p, op.grp_ent.p, H.err);
     FSA_CHECK_LAUNCH();
   }
   // Woodbury core M = I + A^T D^-1 A on the tensor cores (split-K, FP64 reduction)

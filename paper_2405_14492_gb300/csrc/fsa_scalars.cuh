@@ -19,6 +19,7 @@ struct CGScalars {
   unsigned* ticket;
   double tol;
   int fixed, L;
+  int64_t nrows;   // rows of the CG block (the index checks of the checked build)
 };
 
 enum ScalarStep : int { kStepNone = 0, kStepInit = 1, kStepAlpha = 2, kStepResid = 3, kStepBeta = 4 };

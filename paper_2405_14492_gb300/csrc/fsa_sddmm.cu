@@ -54,11 +54,13 @@ __device__ __forceinline__ void stage_rows(__nv_bfloat16* dst, int drow, int dst
   }
 }
 
-// the row of each of the tile's nonzeros (srow) and its staged column (ssc)
+// the row of each of the tile's nonzeros (srow) and its staged column (ssc);
+// err: the error word of the checked build's index checks
 __device__ __forceinline__ void tile_rows(const TileRec& T, const int64_t* __restrict__ rowptr,
-                                          const int32_t* __restrict__ scol, int* srow, int* ssc) {
+                                          const int32_t* __restrict__ scol, int* srow, int* ssc, unsigned* err) {
   for (int r = threadIdx.x; r < T.nr; r += kSdThreads) {
     const int tb = (int)(rowptr[T.p0 + r] - T.e0), te = (int)(rowptr[T.p0 + r + 1] - T.e0);
+    if (!FSA_INDEX_OK(tb >= 0 && tb <= te && te <= T.ne, err)) continue;
     for (int t = tb; t < te; ++t) srow[t] = r;
   }
   if (ssc)
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_csr_values_tiles(
     const int32_t* __restrict__ scol, const double* __restrict__ xs, const double* __restrict__ ys,
     const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Alo, int cov, double s1, double rho,
     double nug, double gamma, double* __restrict__ vals, float* __restrict__ vals32, double* __restrict__ D,
-    float* __restrict__ D32, float* __restrict__ Dinv32) {
+    float* __restrict__ D32, float* __restrict__ Dinv32, unsigned* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int planes = Alo ? 2 : 1;
   const size_t plane = (size_t)cap_rows * kSdRowV;   // elements
@@ -171,7 +173,9 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_csr_values_tiles(
       }
       continue;
     }
-    tile_rows(T, rowptr, scol, srow, ssc);
+    tile_rows(T, rowptr, scol, srow, ssc, err);
+    const int nst = T.n0 + T.n1 + T.n2;   // staged rows
+    (void)nst;                            // read by the checked build only
     auto issue = [&](int kb) {
       __nv_bfloat16* sb = st + (size_t)(kb & 1) * planes * plane;
       for (int p = 0; p < planes; ++p) {
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_csr_values_tiles(
         const int t = threadIdx.x + u * kSdThreads;
         if (t < T.ne) {
           const int ri = T.n0 + (T.p0 + srow[t] - T.r1b), rj = ssc[t];
+          if (!FSA_INDEX_OK(ri >= 0 && ri < nst && rj >= 0 && rj < nst, err)) continue;
           const uint4* hi_i = reinterpret_cast<const uint4*>(sb + (size_t)ri * kSdRowV);
           const uint4* hi_j = reinterpret_cast<const uint4*>(sb + (size_t)rj * kSdRowV);
           const uint4* lo_i = planes == 2 ? reinterpret_cast<const uint4*>(sb + plane + (size_t)ri * kSdRowV) : nullptr;
@@ -258,7 +263,7 @@ bool csr_values_tiles(Handle& H, const fsa_theta& th, const __nv_bfloat16* A, co
   k_csr_values_tiles<<<L.blocks, kSdThreads, L.smem, H.stream>>>(
       H.ntiles, H.ptile.p, H.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, H.n, m_pad, H.rowptr.p, H.col.p,
       H.scol.p, H.xs.p, H.ys.p, A, Alo, H.cov, th.sigma1_sq, th.rho, th.nugget, H.gamma, op.vals.p, op.vals32.p,
-      op.D.p, op.D32.p, op.Dinv32.p);
+      op.D.p, op.D32.p, op.Dinv32.p, H.err);
   FSA_CHECK_LAUNCH();
   return true;
 }
@@ -307,7 +312,8 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_dvals_tiles(
     const int32_t* __restrict__ scol, const double* __restrict__ xs, const double* __restrict__ ys,
     const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ Alo, const __nv_bfloat16* __restrict__ B,
     const __nv_bfloat16* __restrict__ Blo, const __nv_bfloat16* __restrict__ Q, const __nv_bfloat16* __restrict__ Qlo,
-    int cov, double s1, double rho, double gamma, float* __restrict__ dvals, float* __restrict__ dD) {
+    int cov, double s1, double rho, double gamma, float* __restrict__ dvals, float* __restrict__ dD,
+    unsigned* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smraw[];
   // per stage: A hi, A lo, q hi, q lo of the ranges (cap_rows rows each), then b hi, b lo of the tile rows
   const size_t plane = (size_t)cap_rows * kSdRowV, tplane = (size_t)cap_trows * kSdRowV;
@@ -329,7 +335,9 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_dvals_tiles(
       }
       continue;
     }
-    tile_rows(T, rowptr, scol, srow, ssc);
+    tile_rows(T, rowptr, scol, srow, ssc, err);
+    const int nst = T.n0 + T.n1 + T.n2;   // staged rows
+    (void)nst;                            // read by the checked build only
     auto issue = [&](int kb) {
       __nv_bfloat16* sb = st + (size_t)(kb & 1) * sstage;
       const __nv_bfloat16* srcs[4] = {A, Alo, Q, Qlo};
@@ -358,6 +366,7 @@ __global__ void __launch_bounds__(kSdThreads, 1) k_dvals_tiles(
         if (t < T.ne) {
           const int r = srow[t];
           const int ri = T.n0 + (T.p0 + r - T.r1b), rj = ssc[t];
+          if (!FSA_INDEX_OK(r >= 0 && r < T.nr && ri >= 0 && ri < nst && rj >= 0 && rj < nst, err)) continue;
           auto row = [&](int pl, int k) { return reinterpret_cast<const uint4*>(sb + pl * plane + (size_t)k * kSdRowV); };
           const uint4* bh = reinterpret_cast<const uint4*>(sb + 4 * plane + (size_t)r * kSdRowV);
           const uint4* bl = reinterpret_cast<const uint4*>(sb + 4 * plane + tplane + (size_t)r * kSdRowV);
@@ -402,7 +411,7 @@ bool dvals_tiles(Handle& H, const fsa_theta& th, int m_pad, const __nv_bfloat16*
   if (L.blocks <= 0) return false;
   k_dvals_tiles<<<L.blocks, kSdThreads, L.smem, H.stream>>>(
       H.ntiles, H.ptile.p, H.tile_bad.p, L.cap_rows, L.cap_nnz, L.cap_trows, H.n, m_pad, H.rowptr.p, H.col.p,
-      H.scol.p, H.xs.p, H.ys.p, A, Alo, B, Blo, Q, Qlo, H.cov, th.sigma1_sq, th.rho, H.gamma, dvals, dD);
+      H.scol.p, H.xs.p, H.ys.p, A, Alo, B, Blo, Q, Qlo, H.cov, th.sigma1_sq, th.rho, H.gamma, dvals, dD, H.err);
   FSA_CHECK_LAUNCH();
   return true;
 }

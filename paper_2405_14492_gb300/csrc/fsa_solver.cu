@@ -316,6 +316,7 @@ CGScalars make_scalars(Handle& H, const fsa_opts& o, int L) {
   q.tol = o.cg_tol;
   q.fixed = o.fixed_iters > 0 ? 1 : 0;
   q.L = L;
+  q.nrows = H.n;
   return q;
 }
 
@@ -339,6 +340,7 @@ void check_err(Handle& H) {
     FSA_CUDA(cudaMemsetAsync(H.err, 0, sizeof(unsigned), H.stream));
     if (e & kErrNotPD) throw Error{FSA_ERR_NOT_PD, "a Cholesky pivot or D_s entry was not positive"};
     if (e & kErrTimeout) throw Error{FSA_ERR_TIMEOUT, "a bounded device wait ran out"};
+    if (e & kErrBounds) throw Error{FSA_ERR_BOUNDS, "a device index check of the checked build failed"};
     if (e & kErrNaN) throw Error{FSA_ERR_NAN, "non-finite value in the computation"};
     throw Error{FSA_ERR_CUDA, "device error flag " + std::to_string(e)};
   }

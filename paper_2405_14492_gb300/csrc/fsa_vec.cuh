@@ -151,8 +151,9 @@ __global__ void __launch_bounds__(256) kv_spmm_fused(int64_t n, int c, int ldc, 
     for (int s = 0; s < NS; ++s) acc[s] = 0;
     for (int64_t base = rb; base < re; base += 32) {
       const int m = (int)((re - base) < 32 ? (re - base) : 32);
-      const int myc = lane < m ? colidx[base + lane] : 0;
-      const T myv = lane < m ? (T)vals[base + lane] : (T)0;
+      int myc = lane < m ? colidx[base + lane] : 0;
+      T myv = lane < m ? (T)vals[base + lane] : (T)0;
+      if (!FSA_INDEX_OK(myc >= 0 && myc < n, q.err)) { myc = 0; myv = (T)0; }   // checked build
 #pragma unroll 4
       for (int t = 0; t < m; ++t) {
         const int j = __shfl_sync(0xffffffffu, myc, t);
@@ -235,8 +236,9 @@ static __global__ void __launch_bounds__(256) kv_spmm_fused_f4(int64_t n, int c,
     }
     for (int64_t base = rb; base < re; base += 32) {
       const int m = (int)((re - base) < 32 ? (re - base) : 32);
-      const int myc = lane < m ? colidx[base + lane] : 0;
-      const float myv = lane < m ? vals[base + lane] : 0.f;
+      int myc = lane < m ? colidx[base + lane] : 0;
+      float myv = lane < m ? vals[base + lane] : 0.f;
+      if (!FSA_INDEX_OK(myc >= 0 && myc < n, q.err)) { myc = 0; myv = 0.f; }   // checked build
 #pragma unroll 8
       for (int t = 0; t < m; ++t) {
         const int j = __shfl_sync(0xffffffffu, myc, t);
@@ -505,11 +507,18 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         const int p0 = rec[0], nr = rec[1], r0b = rec[2], n0 = rec[3], r1b = rec[4], n1 = rec[5], r2b = rec[6],
                   n2 = rec[7], gb = rec[11], ne = rec[14];
         const int64_t eb = (int64_t)(uint32_t)rec[12] | ((int64_t)rec[13] << 32);
-        const int ng = (nr + kGrpRows - 1) / kGrpRows;
+        // the tile's rows and neighbour ranges inside the points (checked build);
+        // a record that fails is skipped whole
+        const bool rec_ok = FSA_INDEX_OK(p0 >= 0 && nr >= 0 && (int64_t)p0 + nr <= q.nrows && r0b >= 0 && n0 >= 0 &&
+                                             (int64_t)r0b + n0 <= q.nrows && r1b >= 0 && n1 >= 0 &&
+                                             (int64_t)r1b + n1 <= q.nrows && r2b >= 0 && n2 >= 0 &&
+                                             (int64_t)r2b + n2 <= q.nrows && ne >= 0 && eb >= 0,
+                                         q.err);
+        const int ng = rec_ok ? (nr + kGrpRows - 1) / kGrpRows : 0;
         int ga, gz;
         sp_gofs_range(gb, ng, ga, gz);
         const SpTileLayout lay = sp_tile_layout(n0 + n1 + n2, nr, ne, gz - ga, ldc, use_b);
-        const bool staged = !rec[15] && lay.bytes <= ring.bytes;
+        const bool staged = rec_ok && !rec[15] && lay.bytes <= ring.bytes;
         int base = 0;
         ra[s] = rz[s] = 0;
         if (staged) {
@@ -529,7 +538,8 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
           rz[s] = head;
         }
         int* mt = smeta[s];
-        mt[0] = p0; mt[1] = nr; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0; mt[5] = ng;
+        mt[0] = p0; mt[1] = rec_ok ? nr : 0; mt[2] = n0; mt[3] = r1b; mt[4] = staged ? 1 : 0; mt[5] = ng;
+        mt[12] = n0 + n1 + n2;   // staged Z rows
         mt[6] = base + lay.go + (gb - ga) * 4;
         mt[7] = base; mt[8] = base + lay.s; mt[9] = base + lay.v; mt[10] = base + lay.h; mt[11] = base + lay.en;
         if (staged) {
@@ -606,7 +616,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
         break;
       }
       const int* mt = smeta[s];
-      const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3], ng = mt[5];
+      const int p0 = mt[0], nr = mt[1], n0 = mt[2], r1b = mt[3], ng = mt[5], zrows = mt[12];
       const bool staged = mt[4] != 0;
       const int* gos = reinterpret_cast<const int*>(smraw + mt[6]);
       const float4* zs = reinterpret_cast<const float4*>(smraw + mt[7]);
@@ -641,6 +651,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
             for (int e = eb; e < ee; ++e) {
               const int4 m0 = en[kEntVec * e];
               const int4 m1 = kEntVec == 2 ? en[kEntVec * e + 1] : make_int4(0, 0, 0, 0);
+              if (!FSA_INDEX_OK(m0.x >= 0 && m0.x < zrows, q.err)) continue;
               const float4 z = zs[m0.x * c4 + lane];
               const float w[7] = {__int_as_float(m0.y), __int_as_float(m0.z), __int_as_float(m0.w),
                                   __int_as_float(m1.x), __int_as_float(m1.y), __int_as_float(m1.z),
@@ -656,7 +667,9 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
               if (g < gr) {
                 const int r = r0 + g;
                 const int64_t i = (int64_t)p0 + r;
-                const float4 zi = zs[(n0 + (int)(i - r1b)) * c4 + lane];
+                const int zo = n0 + (int)(i - r1b);   // the own row among the staged ones
+                if (!FSA_INDEX_OK(zo >= 0 && zo < zrows, q.err)) continue;
+                const float4 zi = zs[zo * c4 + lane];
                 float4 sv, vv = make_float4(0.f, 0.f, 0.f, 0.f), hh = vv;
                 if (kSpStageOwn) {
                   sv = ss[r * c4 + lane];
@@ -676,6 +689,7 @@ static __global__ void __launch_bounds__(kSpThreads, 1) kv_spmm_tma(
                 const int64_t rb = rowptr[i], re = rowptr[i + 1];
                 for (int64_t t = rb; t < re; ++t) {
                   const float v = vals[t];
+                  if (!FSA_INDEX_OK(colidx[t] >= 0 && colidx[t] < q.nrows, q.err)) continue;
                   const float4 z = Z4[(int64_t)colidx[t] * c4 + lane];
                   acc[g].x = fmaf(v, z.x, acc[g].x); acc[g].y = fmaf(v, z.y, acc[g].y);
                   acc[g].z = fmaf(v, z.z, acc[g].z); acc[g].w = fmaf(v, z.w, acc[g].w);
@@ -1099,9 +1113,11 @@ static inline void launch_spmm_f32(const Handle& Hd, const CGLayout& lay, const 
       e1 = profile_event();
       FSA_CUDA(cudaEventRecord(e0, s));
     }
+    CGScalars qn = q;
+    qn.nrows = Hd.n;   // the bound of the checked build's row checks
     kv_spmm_tma<<<std::min(L.blocks, lay.nblk), kSpThreads, L.smem, s>>>(
         Hd.sp_ntiles, Hd.sp_ptile.p, L.ring, lay.c, lay.ldc, Hd.rowptr.p, Hd.col.p, Hd.op.grp_ent.p, Hd.gofs.p, vals, Z,
-        S, V, Hv, beta, part, step, q);
+        S, V, Hv, beta, part, step, qn);
     FSA_CHECK_LAUNCH();
     if (prof) {
       FSA_CUDA(cudaEventRecord(e1, s));

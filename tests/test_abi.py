@@ -39,6 +39,20 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, f"not exported: {missing}"
 
 
+def test_checked_build_compiles_and_exports_every_declared_symbol():
+    """The checked variant (-DFSA_CHECKED: device index checks that report
+    FSA_ERR_BOUNDS instead of a memory fault) builds from the same sources
+    into its own library, with the same boundary, and names the new status."""
+    from paper_2405_14492_gb300 import build as B
+    path = B.build(checked=True)
+    assert os.path.basename(path) == "libfsa_checked.so"
+    lib = ctypes.CDLL(path)
+    missing = [s for s in sorted(_declared_symbols()) if not hasattr(lib, s)]
+    assert not missing, f"not exported: {missing}"
+    lib.fsa_status_string.restype = ctypes.c_char_p
+    assert lib.fsa_status_string(10) == b"FSA_ERR_BOUNDS"
+
+
 def test_host_only_entry_points(libpath):
     from paper_2405_14492_gb300 import _native as N
     o = N.default_opts()
