@@ -19,7 +19,7 @@ from parity_helpers import bilinear_scales, mixed_traceP_scales, precond_scales
 
 pytestmark = pytest.mark.gpu
 
-# FP64 form: the benchmark spec's 1e-6 for gradients under the same probes, on
+# FP64 form: a relative 1e-6 for gradients under the same probes, on
 # |x| |M y| + |M x| |y| of each bilinear term (parity_helpers).  Mixed BF16X2
 # form: delta = 4 x 2^-17, the bound of the headline-path test; its exact
 # traces Tr(P_hat^-1 dP_hat) move with the pair-rounded D_s (parity_helpers).
