@@ -109,3 +109,16 @@ def test_lbfgs_driver_reaches_the_dense_maximum_likelihood_estimate():
     assert abs(out["loglik"] + r.fun) < 1e-8 * abs(r.fun)
     # one handle call per evaluation, plus the final one for the returned loglik
     assert h.calls == out["evaluations"] + 1
+
+
+def test_lbfgs_driver_reports_an_unfinished_run(problem):
+    """With too few iterations for its gradient tolerance, ``fit_mle`` returns
+    its last iterate with ``converged`` false (and a log-likelihood no lower
+    than at the start)."""
+    h, y, th = problem
+    start = np.array(th) * np.array([1.5, 0.6, 1.4])
+    out = F.fit_mle(h, y, start, max_iter=2, tol_grad=1e-12)
+    assert not out["converged"]
+    assert out["iterations"] <= 2
+    ll0 = O.DenseFSA(*h.args, tuple(start)).loglik(y)[0]
+    assert out["loglik"] >= ll0
